@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark: charges/s of the doubly-periodic slab spectral Ewald solve.
+
+One step = one full solve (far field, near field, gauge, energy, forces) of
+the named workload with the inputs resident in HBM. Default workload: 16384
+Gaussian charges (width 1, +-1, neutral) in a 128 x 128 x 64 slab with
+eps_wall/eps = 1/80 on both walls, grid 256 x 256 x 128, FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl ours|reference] [--no-cpu-baseline]
+
+Timing: W untimed solves, then K solves each bracketed by CUDA events on the
+solve's stream, with a 512 MiB memset between steps to flush the 126 MB L2
+(outside the events); barrier + synchronize around the timed region, max
+over ranks. Under torchrun every rank solves its own independent system
+(replicas: the solve has no exchange step), so value = total charges / time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "charges/s force+energy at ≤1e-5 rel err, mixed vs FP64 plain; p50/p99 ms"
+UNIT = "charges/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="c2_jumps_n16384")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=150.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic work per launch of each stage
+# ---------------------------------------------------------------------------
+def stage_work(d, n, n_over, wbytes=8):
+    """Algorithmic bytes (HBM-bound stages) or flops (ALU-bound stages) of
+    one launch of each stage, for the grid and charge counts of the solve.
+    G = nx ny nz grid points, S = nz ny (nx/2+1) complex modes, M = ny (nx/2+1)
+    columns. Bytes count every grid array read or written once; flops count
+    the operations the stage's algorithm cannot avoid."""
+    nx, ny, nz = d["nx"], d["ny"], d["nz"]
+    G, S = nx * ny * nz, nz * ny * (nx // 2 + 1)
+    M = ny * (nx // 2 + 1)
+    c = 2 * wbytes                     # complex
+    lg = lambda v: math.log2(v)
+    out = {
+        # rho_i over the whole grid, rho_o over its share, charges read once
+        "spread": ("hbm", (G + G * n_over / max(n, 1)) * wbytes + n * 4 * wbytes),
+        "fft_x_fwd": ("hbm", 2 * G * wbytes + 2 * S * c),
+        "fft_y_fwd": ("hbm", 2 * 2 * S * c),
+        # dense z transforms, even/odd split: 4 transforms of N/2 x N/2 blocks,
+        # twice (even/odd), real matrix x complex vector = 4 flops per entry
+        "column": ("alu", M * 4 * (2 * (nz // 2 + 1) ** 2) * 4.0),
+        "fft_y_inv": ("hbm", 2 * S * c + 3 * S * c),
+        "fft_x_inv": ("hbm", 3 * S * c + 4 * G * wbytes),
+        "interp": ("hbm", 4 * G * wbytes + n * 8 * wbytes),
+        "near": ("hbm", n * 12 * wbytes),
+        "prepare": ("hbm", n * 8 * wbytes),
+        "finish": ("hbm", n * 12 * wbytes),
+    }
+    # FFT flop counts (5 n log2 n per complex transform) for reference
+    fft_flops = {
+        "fft_x_fwd": nz * ny * 5 * nx * lg(nx),               # 2 nz ny real rows packed in pairs
+        "fft_y_fwd": 2 * nz * (nx // 2 + 1) * 5 * ny * lg(ny),
+        "fft_y_inv": 3 * nz * (nx // 2 + 1) * 5 * ny * lg(ny),
+        "fft_x_inv": 2 * nz * ny * 5 * nx * lg(nx),
+    }
+    return out, fft_flops
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return dict(hbm_gbs=p.get("hbm_gbs", 6400.0), bf16=p.get("bf16_tflops", 1800.0),
+                    bf16_sus=p.get("bf16_tflops_sustained", 1400.0), source="measured")
+    return dict(hbm_gbs=6400.0, bf16=1800.0, bf16_sus=1400.0, source="fallback")
+
+
+# FP64 arithmetic peak of a B300 (nominal 1.25 TFLOP/s, FP64 and FP64 tensor alike)
+FP64_PEAK_TFLOPS = 1.25
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def oracle_rate(pos, q, p, budget_s, max_steps):
+    from oracle import params as oparams
+    from oracle import solver as osolver
+    P = oparams.derive(p["Lx"], p["Ly"], p["H"], p["gw"], p["tol"], p["nx"], p["ny"], nz=p["nz"],
+                       r_cut=p["r_cut"], eps_b=p["eps_b"], eps_t=p["eps_t"])
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max_steps:
+        t0 = time.perf_counter()
+        osolver.solve(pos, q, P)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start + times[-1] > budget_s:
+            break
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        threads = max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        threads = os.cpu_count()
+    return times, threads
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2101_07088_b300 import synth
+    pos, q, p = synth.workload(args.workload)
+    n = len(q)
+    wl = synth.WORKLOADS[args.workload]
+    config = dict(workload=args.workload, charges=n, box=[p["Lx"], p["Ly"], p["H"]],
+                  grid=[p["nx"], p["ny"], p["nz"]], eps_wall_over_eps=[p["eps_b"], p["eps_t"]],
+                  gw=p["gw"], r_cut=p["r_cut"], tol=p["tol"], precision="fp64",
+                  parallelism=f"replicas{world}", l2="512 MiB memset between timed steps")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        budget = max(30.0, args.cpu_budget_s)
+        times, threads = oracle_rate(pos, q, p, budget, max(1, args.steps))
+        mean = sum(times) / len(times)
+        value = n / mean
+        line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus,
+                    steps=len(times), warmup=0, ms_per_step=mean * 1e3, higher_is_better=True,
+                    scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", config=config,
+                    cpu_baseline=dict(value=value, unit=UNIT, cores=threads, kind="oracle",
+                                      sample=f"{len(times)} full oracle solves of the workload "
+                                             f"(steps capped by a {budget:.0f} s budget; {args.steps} requested); "
+                                             f"host {cpu_model()}, {os.cpu_count()} logical CPUs"),
+                    e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+        print(json.dumps(line))
+        return 0
+
+    import numpy as np
+    import torch
+    from paper_2101_07088_b300 import build, dpslab
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    # each rank solves its own system (independent seed)
+    if world > 1:
+        pos, q = synth.electrolyte(n, p["Lx"], p["Ly"], 1.0, p["H"] - 1.0, wl["seed"] + 1000 * rank)
+    plan = dpslab.Plan(dpslab.make_params(**p), n)
+    d = plan.derived
+    pos_t = torch.tensor(pos, dtype=torch.float64, device=dev)
+    q_t = torch.tensor(q, dtype=torch.float64, device=dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    force = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(3, args.warmup)):
+        plan.solve(pos_t, q_t, phi, force)
+    plan.profile(True)
+    clocks = Clocks(local)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks.start()
+    step_ms, stage_sum = [], {}
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        U, _ = plan.solve(pos_t, q_t, phi, force, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for k, v in plan.stage_times().items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    launches = plan.last_launch_count() * args.steps
+    plan.profile(False)
+    mean_ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([mean_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_ms = float(t.item())
+        dist.barrier()
+    value = n * world / (mean_ms * 1e-3)
+    srt = sorted(step_ms)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+
+    # e2e: host buffers through dpslab_solve_host (H2D of pos, q; D2H of phi, force, U)
+    pin_pos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    pin_q = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    pin_pos.copy_(torch.from_numpy(pos))
+    pin_q.copy_(torch.from_numpy(q))
+    hp, hq = pin_pos.numpy(), pin_q.numpy()
+    for _ in range(2):
+        plan.solve_host(hp, hq, stream=stream)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.solve_host(hp, hq, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_mean], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_mean = float(t.item())
+
+    # roofline of the dominant stage
+    over = int(np.sum((pos[:, 2] <= 2 * d["HE"]) | (pos[:, 2] >= p["H"] - 2 * d["HE"])))
+    work, fft_flops = stage_work(d, n, over)
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+    top = max(stage_ms, key=stage_ms.get)
+    pk = peaks()
+    bound, amount = work[top]
+    secs = stage_ms[top] * 1e-3
+    if bound == "hbm":
+        achieved = amount / secs / 1e9
+        roof = dict(bound="hbm", achieved=achieved, peak=pk["hbm_gbs"], unit="GB/s",
+                    frac=achieved / pk["hbm_gbs"], traffic=None, kernel=top,
+                    peak_source=pk["source"] + " (MEASURED_PEAKS hbm_gbs)")
+    else:
+        achieved = amount / secs / 1e12
+        roof = dict(bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=achieved / FP64_PEAK_TFLOPS, traffic=None, kernel=top,
+                    peak_source="FP64 1.25 TFLOP/s (B300 FP64 rate of the profiling recipe)")
+    roof["stage_ms"] = {k: round(v, 4) for k, v in stage_ms.items()}
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=mean_ms, p50_ms=p50, p99_ms=p99, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", config=config,
+                e2e=dict(value=n * world / (e2e_mean * 1e-3), unit=UNIT, ms_per_step=e2e_mean,
+                         h2d_bytes_per_step=n * 4 * 8, d2h_bytes_per_step=n * 4 * 8 + 8 + 8 * 8 + 4),
+                gpu_launches=launches, roofline=roof, clocks=clk, wall_s=wall,
+                energy=U, plan_device_bytes=plan.device_bytes)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times, threads = oracle_rate(pos, q, p, 40.0, 1)
+        line["cpu_baseline"] = dict(value=n / times[0], unit=UNIT, cores=threads, kind="oracle",
+                                    sample=f"1 full oracle solve of the workload ({times[0]:.1f} s); "
+                                           f"host {cpu_model()}, {os.cpu_count()} logical CPUs")
+    if rank == 0:
+        print(json.dumps(line))
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

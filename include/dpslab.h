@@ -1,0 +1,199 @@
+/*
+ * dpslab.h -- C ABI of the doubly-periodic slab spectral Ewald solver.
+ *
+ * The solver computes, for N Gaussian charges (Eq. (gcharge), width g_w) in a
+ * slab 0 < z < H that is periodic on [0, Lx) x [0, Ly), with permittivity eps
+ * inside, eps_b below z = 0 and eps_t above z = H (Sec. 2):
+ *   - the Gaussian-averaged potential phibar_k at every charge, Eq. (pbar),
+ *     in the gauge phi(0) = 0, Eq. (phi00);
+ *   - the force F_k = q_k Ebar(z_k), Eq. (fqE);
+ *   - the energy U = 1/2 sum_k q_k phibar_k, Eq. (Ufinal) (no wall charge).
+ * It follows the far-field algorithm of Sec. 5.2.2 (steps 1-7, a Fourier
+ * grid in x, y and a second-kind Chebyshev grid in z on [-3 H_E, H + 3 H_E],
+ * one boundary value problem per transverse mode solved as in Appendix A,
+ * the harmonic correction Eq. (inphisc) and the k = 0 mode of Sec. 4.3.4)
+ * plus the near field of Sec. 4.2 over a cell list.
+ *
+ * Units are those of the paper: rationalised electrostatics, a Gaussian
+ * charge interacts as q / (4 pi eps r) at long range; there is no Coulomb
+ * constant.
+ *
+ * Conventions for every call:
+ *   - Return value 0 (DPSLAB_OK) or a negative DPSLAB_ERR_* code; the
+ *     message is dpslab_strerror(code). No call aborts the process.
+ *   - Pointers documented "device" must be CUDA device pointers on the
+ *     plan's device, "host" ones ordinary host memory. The caller owns
+ *     every buffer it passes; the plan owns all its work space.
+ *   - Arrays are dense, row-major, double precision, with no padding.
+ */
+#ifndef DPSLAB_H
+#define DPSLAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define DPSLAB_OK                     0
+#define DPSLAB_ERR_INVALID_ARG       -1  /* a parameter is out of range or a pointer is NULL */
+#define DPSLAB_ERR_NOT_NEUTRAL       -2  /* |sum q| > 1e-12 sum |q| (Eq. (elecneu), no wall charge) */
+#define DPSLAB_ERR_OUT_OF_SLAB       -3  /* a charge has z outside (0, H) or a non-finite value */
+#define DPSLAB_ERR_CUTOFF_TOO_LARGE  -4  /* r_cut >= min(Lx, Ly)/2: nearest-image rule of Sec. 4.2 fails */
+#define DPSLAB_ERR_SPLIT_CONSTRAINT  -5  /* strict mode: 2 H_E >= H or r_cut >= H (Sec. 5.3, Table (ewconstraints)) */
+#define DPSLAB_ERR_CAPACITY          -6  /* n > max_n of the plan */
+#define DPSLAB_ERR_CUDA              -7  /* a CUDA runtime call failed */
+#define DPSLAB_ERR_NO_DEVICE         -8  /* no usable CUDA device */
+#define DPSLAB_ERR_GRID              -9  /* grid too small for the Gaussian support, or a size the kernels do not support */
+#define DPSLAB_ERR_UNSUPPORTED      -10  /* option not built into this library */
+
+/* ------------------------------------------------------------- precision */
+#define DPSLAB_FP64   0   /* every stage in double precision */
+#define DPSLAB_MIXED  1   /* reserved: FP32 grids, BF16-split tensor-core z transform */
+
+/* Bits of dpslab_derived.violations (Sec. 5.3): */
+#define DPSLAB_VIOL_FAR_FIELD   1  /* 2 H_E >= H: images of images reach [-H_E, H+H_E] (Eq. (farconstraint), with h = 0) */
+#define DPSLAB_VIOL_NEAR_FIELD  2  /* r_cut >= H: a second image would be needed (Eq. (nearapprox), n_img = 1, h = 0) */
+
+/*
+ * Problem and discretisation. Fields set to 0 are derived (Sec. 5.1):
+ *   tol      1e-4 (~4 digits) or 5e-4 (~3 digits) -> h factor c_h (1.4 / 1.2)
+ *            and Gaussian support n_g (12 / 10), Table (ewconstraints);
+ *   xi       0: paper rule g_t = c_h h_xy, xi from Eq. (gt) -- unless r_cut
+ *            is given, then xi is the smallest value with
+ *            |dGbar(r_cut; g_w, xi)/dr| < tol |dGbar(r_cut; g_w, 0)/dr|
+ *            (Eq. (GnearK)), for grids that resolve g_w itself;
+ *            INFINITY: no splitting (the smooth solver of Sec. 3.1, no near field);
+ *   r_cut    0: r_nf of Eq. (rnf) + n_sigma g_w;
+ *   nz       0: ceil(pi (H + 6 H_E) / (2 h_xy)), Sec. 5.1;
+ *   n_sigma  0: n_g / (2 c_h); H_E = n_sigma g_t, Eq. (He).
+ * eps_b or eps_t = INFINITY selects a metallic wall (the eps_w -> inf limit
+ * of every formula; with one metallic wall the k = 0 slope uses the other
+ * wall's displacement condition, with two the walls are at equal potential).
+ */
+typedef struct dpslab_params {
+    double Lx, Ly, H;          /* box [0,Lx) x [0,Ly), slab 0 < z < H; > 0            */
+    double eps, eps_b, eps_t;  /* permittivities; > 0, eps_b/eps_t may be INFINITY    */
+    double gw;                 /* Gaussian charge width g_w > 0                        */
+    double tol;                /* 1e-4 or 5e-4                                         */
+    int    nx, ny, nz;         /* grid; nx, ny >= 4 required; nz 0 = derive            */
+    double xi;                 /* splitting parameter; 0 = derive; INFINITY = none     */
+    double r_cut;              /* near-field cutoff; 0 = derive                        */
+    double n_sigma;            /* Gaussian truncation in standard deviations; 0 = table */
+    int    precision;          /* DPSLAB_FP64                                          */
+    int    strict;             /* nonzero: constraint violations are errors            */
+} dpslab_params;
+
+/* Every derived quantity of a parameter set (host values). */
+typedef struct dpslab_derived {
+    double hx, hy, h;          /* grid spacings; h = max(hx, hy) = h_xy                */
+    double xi, gt;             /* splitting parameter, g_t of Eq. (gt)                 */
+    double n_sigma, HE;        /* truncation, H_E = n_sigma g_t                        */
+    double r_cut, r_nf;        /* near-field cutoff (r_nf = 0 when r_cut was given)    */
+    double a, b, Hbar;         /* Chebyshev domain [a, b] = [-3 H_E, H + 3 H_E]         */
+    double kmax;               /* correction applied for 0 < |k| <= kmax = pi / h_xy   */
+    int    nx, ny, nz;
+    int    support_x, support_y;  /* maximum Gaussian support in grid points          */
+    int    violations;         /* DPSLAB_VIOL_* bits                                   */
+} dpslab_derived;
+
+typedef struct dpslab_plan dpslab_plan;
+
+/*
+ * Derive every quantity of Sec. 5.1 / Table (ewconstraints) from p, on the
+ * host only (no CUDA call). Returns DPSLAB_ERR_INVALID_ARG for bad
+ * parameters, DPSLAB_ERR_GRID / _CUTOFF_TOO_LARGE / _SPLIT_CONSTRAINT as
+ * dpslab_plan_create would.
+ */
+int dpslab_derive(const dpslab_params* p, dpslab_derived* out);
+
+/*
+ * Host copies of plan tables, for inspection (no CUDA call):
+ *   which = 0: Chebyshev nodes z_j, j = 0..nz-1 (z_0 = b, z_{nz-1} = a), Sec. 5.2.2;
+ *           1: quadrature weights of the z grid (Clenshaw-Curtis, Hbar/2 scaled);
+ *           2: gauge weights int gamma_z(z) T_n(s(z)) dz, n = 0..nz-1.
+ * out must hold nz doubles.
+ */
+int dpslab_table(const dpslab_params* p, int which, double* out, int n_out);
+
+/*
+ * Create a plan on the current CUDA device for up to max_n charges:
+ * derives the parameters, builds the tables and allocates all device work
+ * space (the only allocation; dpslab_solve allocates nothing).
+ * *out receives the plan, or NULL on error.
+ */
+int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_plan** out);
+
+/* The derived parameters of a plan. */
+int dpslab_plan_derived(const dpslab_plan* plan, dpslab_derived* out);
+
+/* Bytes of device memory the plan holds. */
+int64_t dpslab_plan_device_bytes(const dpslab_plan* plan);
+
+/*
+ * One solve (Sec. 5.2.2 far field + Sec. 4.2 near field + gauge + energy).
+ *   n        number of charges, 1 <= n <= max_n;
+ *   pos      device, [n][3] (x, y, z); x and y are wrapped into [0, L);
+ *            z must lie in (0, H);
+ *   q        device, [n] charges; sum must vanish (Eq. (elecneu));
+ *   U        host scalar, or NULL;
+ *   phi      device, [n] averaged potentials, or NULL;
+ *   force    device, [n][3] forces, or NULL;
+ *   stream   cudaStream_t to run on (NULL = legacy default stream).
+ * The call enqueues all work on stream and waits for it before returning
+ * (it reads back the status word and U). Invalid charges do not fault: they
+ * are replaced by zero charges and the call returns DPSLAB_ERR_OUT_OF_SLAB.
+ */
+int dpslab_solve(dpslab_plan* plan, int64_t n, const double* pos, const double* q,
+                 double* U, double* phi, double* force, void* stream);
+
+/*
+ * Same as dpslab_solve with host buffers: copies pos and q to the device,
+ * solves, and copies phi and force back (each output may be NULL). Host
+ * buffers that are page-locked copy faster.
+ */
+int dpslab_solve_host(dpslab_plan* plan, int64_t n, const double* pos, const double* q,
+                      double* U, double* phi, double* force, void* stream);
+
+/*
+ * Copy an intermediate device buffer of the last solve to host memory, for
+ * stage-by-stage checks:
+ *   which = 0: rho_i then rho_o, 2 x [nz][ny][nx] (Sec. 5.2.2 steps 2-3);
+ *           1: fields phi, E_x, E_y, E_z on the grid, [nz][ny][nx][4];
+ *           2: far-field phibar, Ebar at the charges, [n][4];
+ *           3: near-field phibar, Ebar at the charges, [n][4];
+ *           4: scalars (B_i(0), A_i(0), phi^(f)(0), phi^(n)(0)).
+ * bytes must equal the buffer's size for that n.
+ */
+int dpslab_debug_fetch(dpslab_plan* plan, int which, void* host_dst, size_t bytes);
+
+/* Number of kernels the last solve launched. */
+int dpslab_last_launch_count(const dpslab_plan* plan);
+
+/*
+ * Per-stage timing. With profiling on, every solve records CUDA events on its
+ * stream around each stage; dpslab_stage_times writes the last solve's
+ * stage durations in milliseconds (device time) to ms[0 .. DPSLAB_NSTAGES-1].
+ * Stage i is named by dpslab_stage_name(i): prepare, spread, fft_x_fwd,
+ * fft_y_fwd, column (z transform + BVP + correction + inverse z), fft_y_inv,
+ * fft_x_inv, interp, near (cell list + pairs), finish (gauge + assembly +
+ * energy).
+ */
+#define DPSLAB_NSTAGES 10
+int dpslab_profile(dpslab_plan* plan, int on);
+int dpslab_stage_times(const dpslab_plan* plan, double* ms, int n);
+const char* dpslab_stage_name(int stage);
+
+/* Release the plan and all its device memory; NULL is accepted. */
+int dpslab_plan_destroy(dpslab_plan* plan);
+
+/* Static message for an error code. */
+const char* dpslab_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPSLAB_H */

@@ -1,0 +1,116 @@
+// Kernel parameter block and small device helpers of the FP64 solve.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace dps {
+
+// Status bits written by kernels (read back once per solve).
+enum : int {
+    kStatusOutOfSlab = 1,
+    kStatusNonFinite = 2,
+};
+
+// Everything a kernel needs, passed by value.
+struct KP {
+    // problem
+    double Lx, Ly, H, eps, gw;
+    double Gb, Gt;            // image factors (eps_w - eps)/(eps_w + eps); 1 for metal
+    double cb, db, ct, dt;    // eps_w/(eps_w + eps), eps/(eps_w + eps) (metal: 1, 0)
+    double tb, tt;            // tau_w = 2 eps/(eps_w + eps), Eq. (phibst)/(phitst)
+    double rtb, rtt;          // (eps_w/eps) tau_w
+    int metal_b, metal_t;
+    // discretisation
+    int nx, ny, nz, nxh;
+    double hx, hy, HE, gt, xi, r_cut, a, b, Hbar, kmax;
+    double s1norm;            // (2 pi g_t^2)^{-1/2}: one factor of Eq. (spreadkernelEw)
+    double sigma2;            // (1/(2 xi))^2, 0 when xi = inf
+    double inv_nxny;
+    // near-field kernel widths: averaged (Eq. (GnearK)) and pointwise (Eq. (Gnear))
+    double na1, na2, pa1, pa2;   // a2 = 0 encodes "infinite" (xi = 0), a1 == a2 disables
+    int near_on;
+    // charges
+    int n;
+    const double* pos;
+    const double* q;
+    double4_32a* part;            // sanitised (x, y, z, q)
+    // grids
+    double* rho;              // [2][nz][ny][nx]
+    double2* spec;            // [2][nz][ny][nxh]
+    double2* specB;           // [nz][ny][nxh]
+    double4_32a* fields;          // [nz][ny][nx] (phi, Ex, Ey, Ez)
+    // tables
+    const double* zn;
+    const double* wz;
+    const double* cf;
+    const double* ti;
+    const double *j2l, *j2d, *j2u, *u1, *u2, *v1, *v2, *t0, *tH, *wg;
+    const double2* twx;
+    const double2* twy;
+    int radx[kMaxStages], rady[kMaxStages];
+    int nradx, nrady;
+    // particle outputs
+    double4_32a* far;             // [n] (phibar, Ebar)
+    double4_32a* nearv;           // [n]
+    // cell list
+    int ncx, ncy, ncz, ncells;
+    double cwx, cwy, cwz;     // cell widths
+    int* cell_of;
+    int* cell_count;
+    int* cell_start;          // ncells + 1
+    int* cell_fill;
+    double4_32a* sorted;
+    int* sorted_idx;
+    // reductions
+    double* part_gauge_far;   // one per column block
+    double* part_gauge_near;  // one per charge block
+    double* part_u;           // one per charge block
+    double* part_q;           // [2 * nblocks]: sum q, sum |q|
+    double* scal;             // [8]: B, A_i, phi_f0, phi_n0, U, sumq, sumabsq, spare
+    int* status;
+    int n_col_blocks, n_charge_blocks;
+    // user outputs
+    double* out_phi;
+    double* out_force;
+};
+
+__device__ __forceinline__ double np_mod(double x, double L) {
+    // numpy float remainder: fmod, then shifted into the sign of L
+    double r = fmod(x, L);
+    if (r != 0.0 && r < 0.0) r += L;
+    return r;
+}
+
+__device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
+
+// erf(r/a)/r and (1/r) d/dr[erf(r/a)/r]; series for r < 1e-3 g_w (end of Sec. 3.2)
+__device__ __forceinline__ void erf_over_r(double r, double a, bool small, double& val, double& der) {
+    const double x = r / a;
+    const double c = 1.1283791670955126 / a;   // 2/(sqrt(pi) a)
+    if (small) {
+        const double x2 = x * x;
+        val = c * (1.0 - x2 / 3.0 + x2 * x2 / 10.0 - x2 * x2 * x2 / 42.0);
+        der = c * (-2.0 / (3.0 * a * a) + 4.0 * x2 / (10.0 * a * a) - 6.0 * x2 * x2 / (42.0 * a * a));
+    } else {
+        const double e = erf(x);
+        val = e / r;
+        der = (-e / (r * r) + c * exp(-x * x) / r) / r;
+    }
+}
+
+// near-field kernel value and (1/r) dG/dr for widths (a1, a2); a2 == 0 means infinite
+__device__ __forceinline__ void near_kernel(double r, double a1, double a2, double gw, double eps,
+                                            double& g, double& d) {
+    const bool small = r < 1e-3 * gw;
+    double v1, d1, v2 = 0.0, d2 = 0.0;
+    erf_over_r(r, a1, small, v1, d1);
+    if (a2 > 0.0) erf_over_r(r, a2, small, v2, d2);
+    const double s = 1.0 / (12.566370614359172 * eps);   // 1/(4 pi eps)
+    g = (v1 - v2) * s;
+    d = (d1 - d2) * s;
+}
+
+}  // namespace dps

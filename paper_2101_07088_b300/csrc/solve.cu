@@ -1,0 +1,1254 @@
+// The FP64 solve: one kernel per stage of Sec. 5.2.2 plus the near field,
+// the gauge and the energy, and the plan / solve entry points of dpslab.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "kernels.cuh"
+
+using namespace dps;
+
+namespace {
+
+constexpr int kColBlock = 8;        // k_par columns per block of the column kernel
+constexpr int kColThreads = 256;
+constexpr int kChargeThreads = 256;
+constexpr int kInterpWarps = 8;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; result valid in thread 0. All threads must call it.
+__device__ double block_sum(double v) {
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    return v;
+}
+
+__device__ __forceinline__ int wrap_index(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// ---------------------------------------------------------------------------
+// charges: validation, wrapping, neutrality sums, cell histogram
+// ---------------------------------------------------------------------------
+__global__ void k_prepare(KP kp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double qv = 0.0, aq = 0.0;
+    if (k < kp.n) {
+        double x = kp.pos[3 * k], y = kp.pos[3 * k + 1], z = kp.pos[3 * k + 2], q = kp.q[k];
+        int bad = 0;
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(q)) bad = kStatusNonFinite;
+        else if (!(z > 0.0 && z < kp.H)) bad = kStatusOutOfSlab;
+        if (bad) {
+            atomicOr(kp.status, bad);
+            x = 0.0; y = 0.0; z = 0.5 * kp.H; q = 0.0;
+        }
+        x = np_mod(x, kp.Lx);
+        y = np_mod(y, kp.Ly);
+        kp.part[k] = make_double4_32a(x, y, z, q);
+        qv = q;
+        aq = fabs(q);
+        if (kp.near_on) {
+            const int cx = min(kp.ncx - 1, max(0, int(x / kp.cwx)));
+            const int cy = min(kp.ncy - 1, max(0, int(y / kp.cwy)));
+            const int cz = min(kp.ncz - 1, max(0, int(z / kp.cwz)));
+            const int c = (cz * kp.ncy + cy) * kp.ncx + cx;
+            kp.cell_of[k] = c;
+            atomicAdd(&kp.cell_count[c], 1);
+        }
+    }
+    const double s1 = block_sum(qv);
+    const double s2 = block_sum(aq);
+    if (threadIdx.x == 0) {
+        kp.part_q[blockIdx.x] = s1;
+        kp.part_q[gridDim.x + blockIdx.x] = s2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// spreading, Sec. 5.2.2 steps 2-3: one block per source (charge, bottom image,
+// top image); rho_i gets every source, rho_o only the charges of C_over
+// ---------------------------------------------------------------------------
+__global__ void k_spread(KP kp) {
+    __shared__ double wx[kMaxSupport], wy[kMaxSupport], wzs[kMaxNz];
+    __shared__ int s_j0, s_j1;
+    const int slot = blockIdx.x;
+    const int k = slot % kp.n;
+    const int kind = slot / kp.n;
+    const double4_32a p = kp.part[k];
+    double z = p.z, q = p.w;
+    const bool near_b = z <= 2.0 * kp.HE, near_t = z >= kp.H - 2.0 * kp.HE;
+    bool over = near_b || near_t;
+    if (kind == 1) {
+        if (!near_b) return;
+        z = -z; q = -kp.Gb * q; over = false;           // Eq. (ims)
+    } else if (kind == 2) {
+        if (!near_t) return;
+        z = 2.0 * kp.H - z; q = -kp.Gt * q; over = false;
+    }
+    if (q == 0.0) return;
+    const double x = p.x, y = p.y, HE = kp.HE;
+    const int ix0 = int(ceil((x - HE) / kp.hx)), ix1 = int(floor((x + HE) / kp.hx));
+    const int iy0 = int(ceil((y - HE) / kp.hy)), iy1 = int(floor((y + HE) / kp.hy));
+    const int sx = ix1 - ix0 + 1, sy = iy1 - iy0 + 1;
+    const double inv2g2 = 1.0 / (2.0 * kp.gt * kp.gt);
+    if (threadIdx.x == 0) { s_j0 = kp.nz; s_j1 = -1; }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kp.nz; j += blockDim.x) {
+        if (fabs(kp.zn[j] - z) <= HE) {
+            atomicMin(&s_j0, j);
+            atomicMax(&s_j1, j);
+        }
+    }
+    for (int i = threadIdx.x; i < sx; i += blockDim.x) {
+        const double d = double(ix0 + i) * kp.hx - x;
+        wx[i] = kp.s1norm * exp(-d * d * inv2g2);
+    }
+    for (int i = threadIdx.x; i < sy; i += blockDim.x) {
+        const double d = double(iy0 + i) * kp.hy - y;
+        wy[i] = kp.s1norm * exp(-d * d * inv2g2);
+    }
+    __syncthreads();
+    const int j0 = s_j0, sz = s_j1 - s_j0 + 1;
+    if (sz <= 0) return;
+    for (int i = threadIdx.x; i < sz; i += blockDim.x) {
+        const double d = kp.zn[j0 + i] - z;
+        wzs[i] = kp.s1norm * exp(-d * d * inv2g2);
+    }
+    __syncthreads();
+    const size_t G = size_t(kp.nz) * kp.ny * kp.nx;
+    const int sxy = sx * sy;
+    for (int t = threadIdx.x; t < sz * sxy; t += blockDim.x) {
+        const int jz = t / sxy;
+        const int r = t - jz * sxy;
+        const int iy = r / sx;
+        const int ix = r - iy * sx;
+        const double v = q * wzs[jz] * wy[iy] * wx[ix];
+        const size_t g = (size_t(j0 + jz) * kp.ny + wrap_index(iy0 + iy, kp.ny)) * kp.nx + wrap_index(ix0 + ix, kp.nx);
+        atomicAdd(kp.rho + g, v);
+        if (over) atomicAdd(kp.rho + G + g, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// xy FFT, forward: rows along x (two real rows packed into one complex FFT),
+// then columns along y, for both densities
+// ---------------------------------------------------------------------------
+__global__ void k_fftx_fwd(KP kp, int P) {
+    extern __shared__ double2 sm[];
+    const int n = kp.nx, nxh = kp.nxh;
+    double2* tw = sm;
+    double2* A = tw + n;
+    double2* B = A + P * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = kp.twx[i];
+    const int npairs = kp.nz * kp.ny;           // 2 nz ny rows
+    const int p0 = blockIdx.x * P;
+    for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
+        const int p = t / n, x = t - p * n, pr = p0 + p;
+        double2 v = make_double2(0.0, 0.0);
+        if (pr < npairs) {
+            const size_t r0 = 2 * size_t(pr);
+            v = make_double2(kp.rho[r0 * n + x], kp.rho[(r0 + 1) * n + x]);
+        }
+        A[p * n + x] = v;
+    }
+    __syncthreads();
+    const double2* R = block_fft(A, B, tw, n, P, kp.radx, kp.nradx, -1);
+    for (int t = threadIdx.x; t < P * nxh; t += blockDim.x) {
+        const int p = t / nxh, k = t - p * nxh, pr = p0 + p;
+        if (pr >= npairs) continue;
+        const double2 Z = R[p * n + k];
+        const double2 Zm = cconj(R[p * n + (n - k) % n]);
+        const double2 s = cadd(Z, Zm), d = csub(Z, Zm);
+        const size_t r0 = 2 * size_t(pr);
+        kp.spec[r0 * nxh + k] = cscale(s, 0.5);
+        kp.spec[(r0 + 1) * nxh + k] = make_double2(0.5 * d.y, -0.5 * d.x);
+    }
+}
+
+__global__ void k_ffty_fwd(KP kp, int TK) {
+    extern __shared__ double2 sm[];
+    const int n = kp.ny, nxh = kp.nxh;
+    double2* tw = sm;
+    double2* A = tw + n;
+    double2* B = A + TK * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = kp.twy[i];
+    double2* base = kp.spec + size_t(blockIdx.y) * n * nxh;
+    const int k0 = blockIdx.x * TK;
+    for (int t = threadIdx.x; t < TK * n; t += blockDim.x) {
+        const int y = t / TK, c = t - y * TK, kx = k0 + c;
+        A[c * n + y] = kx < nxh ? base[size_t(y) * nxh + kx] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const double2* R = block_fft(A, B, tw, n, TK, kp.rady, kp.nrady, -1);
+    for (int t = threadIdx.x; t < TK * n; t += blockDim.x) {
+        const int y = t / TK, c = t - y * TK, kx = k0 + c;
+        if (kx < nxh) base[size_t(y) * nxh + kx] = R[c * n + y];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-mode column work: z Chebyshev transform, the Appendix-A BVP for both
+// densities, mismatches and correction (Sec. 5.2.2 step 4), the k = 0 slope
+// (step 5), the gauge partial sum, and the values of psi_i and dpsi_i/dz at
+// the nodes (step 6); written in place over the two spectra
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int CB = kColBlock;
+    const int N = kp.nz;
+    const int M = kp.ny * kp.nxh;
+    double2* Vi = reinterpret_cast<double2*>(smraw);   // values, then y' (field i)
+    double2* Vo = Vi + CB * N;                         // values, then y' (field o)
+    double2* Ci = Vo + CB * N;                         // coefficients -> y'' -> y
+    double2* Co = Ci + CB * N;
+    double* cpv = reinterpret_cast<double*>(Co + CB * N);   // Thomas c'
+    double* xe = cpv + CB * N;                               // K^2 A^{-1} e0 (even) / e1 (odd)
+    __shared__ double s_k[CB], s_K[CB], s_mult[CB], s_den[CB], s_ekH[CB], s_gauge[CB];
+    __shared__ int s_valid[CB], s_corr[CB];
+    __shared__ double2 s_c[2][CB], s_d[2][CB], s_P[CB], s_Q[CB];
+    __shared__ double s_Ai;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int col0 = blockIdx.x * CB;
+    const double Hbar = kp.Hbar;
+
+    if (tid < CB) {
+        const int c = tid, col = col0 + c;
+        const int iy = col / kp.nxh, ix = col - iy * kp.nxh;
+        const int my = iy < (kp.ny + 1) / 2 ? iy : iy - kp.ny;
+        const double kx = kTwoPi * ix / kp.Lx, ky = kTwoPi * my / kp.Ly;
+        const double k = sqrt(kx * kx + ky * ky);
+        s_valid[c] = col < M;
+        s_k[c] = k;
+        s_K[c] = 0.5 * k * Hbar;
+        s_mult[c] = (ix == 0 || (kp.nx % 2 == 0 && ix == kp.nx / 2)) ? 1.0 : 2.0;
+        s_corr[c] = (col < M) && k > 0.0 && k <= kp.kmax;
+        s_gauge[c] = 0.0;
+    }
+    if (tid == 0) s_Ai = 0.0;
+    for (int t = tid; t < N * CB; t += bs) {
+        const int j = t / CB, c = t - j * CB, col = col0 + c;
+        double2 vi = make_double2(0.0, 0.0), vo = vi;
+        if (col < M) {
+            vi = kp.spec[size_t(j) * M + col];
+            vo = kp.spec[size_t(N + j) * M + col];
+        }
+        Vi[c * N + j] = vi;
+        Vo[c * N + j] = vo;
+    }
+    __syncthreads();
+
+    // coefficients f_n = sum_j cf[n][j] v_j, then F = -(Hbar/2)^2 f / eps
+    const double scale = -(0.5 * Hbar) * (0.5 * Hbar) / kp.eps;
+    for (int t = tid; t < 2 * CB * N; t += bs) {
+        const int f = t / (CB * N), r = t - f * CB * N, n = r / CB, c = r - n * CB;
+        const double2* V = (f ? Vo : Vi) + c * N;
+        const double* row = kp.cf + size_t(n) * N;
+        double ax = 0.0, ay = 0.0;
+        for (int j = 0; j < N; ++j) {
+            const double w = row[j];
+            ax = fma(w, V[j].x, ax);
+            ay = fma(w, V[j].y, ay);
+        }
+        (f ? Co : Ci)[c * N + n] = make_double2(ax * scale, ay * scale);
+    }
+    __syncthreads();
+
+    // Appendix A: A y'' = F + K^2 (c e0 + d e1), A = I - K^2 J^2 splits into the
+    // even and odd index chains, each tridiagonal (Thomas algorithm).
+    if (tid < 2 * CB) {
+        const int c = tid >> 1, ch = tid & 1;
+        const double K2 = s_K[c] * s_K[c];
+        double2* Fi = Ci + c * N;
+        double2* Fo = Co + c * N;
+        double* cq = cpv + c * N;
+        double* xc = xe + c * N;
+        int prev = -1;
+        for (int n = ch; n < N; n += 2) {
+            const double an = n >= 2 ? -K2 * kp.j2l[n] : 0.0;
+            const double bn = 1.0 - K2 * kp.j2d[n];
+            const double cn = n + 2 < N ? -K2 * kp.j2u[n] : 0.0;
+            double m = bn, rn = (n == ch) ? K2 : 0.0;
+            double2 fi = Fi[n], fo = Fo[n];
+            if (prev >= 0) {
+                m -= an * cq[prev];
+                fi = csub(fi, cscale(Fi[prev], an));
+                fo = csub(fo, cscale(Fo[prev], an));
+                rn -= an * xc[prev];
+            }
+            const double inv = 1.0 / m;
+            cq[n] = cn * inv;
+            Fi[n] = cscale(fi, inv);
+            Fo[n] = cscale(fo, inv);
+            xc[n] = rn * inv;
+            prev = n;
+        }
+        for (int n = prev - 2; n >= ch; n -= 2) {
+            Fi[n] = csub(Fi[n], cscale(Fi[n + 2], cq[n]));
+            Fo[n] = csub(Fo[n], cscale(Fo[n + 2], cq[n]));
+            xc[n] -= cq[n] * xc[n + 2];
+        }
+    }
+    __syncthreads();
+
+    // 2x2 Schur complement for the integration constants (y_0, y'_0) = (c, d)
+    // from the two boundary rows (Eq. (BCs); Eq. (BCs0) for k = 0)
+    if (tid < 2 * CB) {
+        const int c = tid >> 1, f = tid & 1;
+        const double K = s_K[c];
+        const double2* X = (f ? Co : Ci) + c * N;
+        const double* xc = xe + c * N;
+        double2 cc, dd;
+        if (K > 0.0) {
+            double2 sFt = make_double2(0.0, 0.0), sFb = sFt;
+            double sct = 0.0, sdt = 0.0, scb = 0.0, sdb = 0.0;
+            for (int n = 0; n < N; ++n) {
+                const double gtn = kp.u1[n] + K * kp.u2[n];
+                const double gbn = kp.v1[n] - K * kp.v2[n];
+                sFt = cadd(sFt, cscale(X[n], gtn));
+                sFb = cadd(sFb, cscale(X[n], gbn));
+                if (n & 1) { sdt += gtn * xc[n]; sdb += gbn * xc[n]; }
+                else { sct += gtn * xc[n]; scb += gbn * xc[n]; }
+            }
+            const double m11 = K + sct, m12 = 1.0 + K + sdt, m21 = -K + scb, m22 = 1.0 + K + sdb;
+            const double idet = 1.0 / (m11 * m22 - m12 * m21);
+            cc = cscale(csub(cscale(sFt, m22), cscale(sFb, m12)), -idet);
+            dd = cscale(csub(cscale(sFb, m11), cscale(sFt, m21)), -idet);
+        } else {
+            double2 a = make_double2(0.0, 0.0), b = a;
+            for (int n = 0; n < N; ++n) {
+                a = cadd(a, cscale(X[n], kp.u2[n]));
+                b = cadd(b, cscale(X[n], kp.v2[n]));
+            }
+            cc = cscale(cadd(a, b), -0.5);
+            dd = cscale(csub(a, b), -0.5);
+        }
+        s_c[f][c] = cc;
+        s_d[f][c] = dd;
+    }
+    __syncthreads();
+    // y'' = x_F + c x_c + d x_d
+    for (int t = tid; t < 2 * CB * N; t += bs) {
+        const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
+        double2* X = (f ? Co : Ci) + c * N;
+        const double2 m = (n & 1) ? s_d[f][c] : s_c[f][c];
+        X[n] = cadd(X[n], cscale(m, xe[c * N + n]));
+    }
+    __syncthreads();
+    // y' from y'' (Eq. (ds)), into the value buffers
+    for (int t = tid; t < 2 * CB * N; t += bs) {
+        const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
+        const double2* Y = (f ? Co : Ci) + c * N;
+        double2 v;
+        if (n == 0) v = s_d[f][c];
+        else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5));
+        else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_double2(0.0, 0.0)), 0.5 / n);
+        (f ? Vo : Vi)[c * N + n] = v;
+    }
+    __syncthreads();
+    // y from y' (Eq. (cs)), over y''
+    for (int t = tid; t < 2 * CB * N; t += bs) {
+        const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
+        const double2* Y = (f ? Vo : Vi) + c * N;
+        double2 v;
+        if (n == 0) v = s_c[f][c];
+        else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5));
+        else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_double2(0.0, 0.0)), 0.5 / n);
+        (f ? Co : Ci)[c * N + n] = v;
+    }
+    __syncthreads();
+
+    // boundary values, mismatches Eq. (mm1)-(mm4), correction coefficients,
+    // k = 0 slope, gauge partial sum
+    if (tid < CB && s_valid[tid]) {
+        const int c = tid;
+        const double2 *yi = Ci + c * N, *ypi = Vi + c * N, *yo = Co + c * N, *ypo = Vo + c * N;
+        double2 pi0 = make_double2(0, 0), dpi0 = pi0, piH = pi0, dpiH = pi0, po0 = pi0, dpo0 = pi0,
+                poH = pi0, dpoH = pi0, dpoa = pi0, dpob = pi0, gs = pi0;
+        for (int n = 0; n < N; ++n) {
+            const double a0 = kp.t0[n], aH = kp.tH[n], alt = (n & 1) ? -1.0 : 1.0, wg = kp.wg[n];
+            pi0 = cadd(pi0, cscale(yi[n], a0));
+            dpi0 = cadd(dpi0, cscale(ypi[n], a0));
+            piH = cadd(piH, cscale(yi[n], aH));
+            dpiH = cadd(dpiH, cscale(ypi[n], aH));
+            po0 = cadd(po0, cscale(yo[n], a0));
+            dpo0 = cadd(dpo0, cscale(ypo[n], a0));
+            poH = cadd(poH, cscale(yo[n], aH));
+            dpoH = cadd(dpoH, cscale(ypo[n], aH));
+            dpoa = cadd(dpoa, cscale(ypo[n], alt));
+            dpob = cadd(dpob, ypo[n]);
+            gs = cadd(gs, cscale(yi[n], wg));
+        }
+        const double dz = 2.0 / Hbar;
+        dpi0 = cscale(dpi0, dz); dpiH = cscale(dpiH, dz); dpo0 = cscale(dpo0, dz);
+        dpoH = cscale(dpoH, dz); dpoa = cscale(dpoa, dz); dpob = cscale(dpob, dz);
+        const double k = s_k[c];
+        double2 corr0 = make_double2(0.0, 0.0);
+        if (s_corr[c]) {
+            const double2 mpb = csub(pi0, cscale(po0, kp.tb));
+            const double2 meb = csub(dpi0, cscale(dpo0, kp.rtb));
+            const double2 mpt = csub(piH, cscale(poH, kp.tt));
+            const double2 met = csub(dpiH, cscale(dpoH, kp.rtt));
+            const double2 P = csub(cscale(mpb, kp.cb), cscale(meb, kp.db / k));
+            const double2 Q = csub(cscale(mpt, -kp.ct), cscale(met, kp.dt / k));
+            const double ekH = exp(-k * kp.H);
+            const double den = 1.0 - kp.Gb * kp.Gt * ekH * ekH;
+            s_P[c] = P;
+            s_Q[c] = Q;
+            s_ekH[c] = ekH;
+            s_den[c] = den;
+            corr0 = cscale(cadd(cscale(P, -(1.0 - kp.Gt * ekH * ekH)), cscale(Q, ekH - kp.Gb * ekH)), 1.0 / den);
+        }
+        if (col0 + c == 0) {
+            // Sec. 4.3.4: Eq. (CE), (ai1), (ai2); mean, or the non-metal wall's
+            // equation, or equal wall potentials for two metal walls
+            const double ai1 = kp.rtb * (dpo0.x - dpoa.x) - dpi0.x;
+            const double ai2 = kp.rtt * (dpoH.x - dpob.x) - dpiH.x;
+            double Ai;
+            if (kp.metal_b && kp.metal_t) Ai = -(piH.x - pi0.x) / kp.H;
+            else if (kp.metal_b) Ai = ai2;
+            else if (kp.metal_t) Ai = ai1;
+            else Ai = 0.5 * (ai1 + ai2);
+            s_Ai = Ai;
+            kp.scal[1] = Ai;
+        }
+        const double damp = exp(-0.5 * kp.sigma2 * k * k);
+        s_gauge[c] = s_mult[c] * (damp * gs.x + corr0.x);
+    }
+    __syncthreads();
+
+    // node values of psi_i and dpsi_i/dz (+ correction, + A_i z for k = 0)
+    const double Ai = s_Ai;
+    for (int t = tid; t < N * CB; t += bs) {
+        const int j = t / CB, c = t - j * CB, col = col0 + c;
+        if (col >= M) continue;
+        const double* trow = kp.ti + size_t(j) * N;
+        const double2* yi = Ci + c * N;
+        const double2* ypi = Vi + c * N;
+        double px = 0, py = 0, dx = 0, dy = 0;
+        for (int n = 0; n < N; ++n) {
+            const double w = trow[n];
+            px = fma(w, yi[n].x, px);
+            py = fma(w, yi[n].y, py);
+            dx = fma(w, ypi[n].x, dx);
+            dy = fma(w, ypi[n].y, dy);
+        }
+        double2 ps = make_double2(px, py), dps = make_double2(dx * (2.0 / Hbar), dy * (2.0 / Hbar));
+        const double z = kp.zn[j];
+        if (s_corr[c] && z >= -kp.HE && z <= kp.H + kp.HE) {
+            const double k = s_k[c], ekH = s_ekH[c], iden = 1.0 / s_den[c];
+            const double e1 = exp(-k * z), e3 = exp(k * (z - kp.H));
+            const double e2 = e3 * ekH, e4 = e1 * ekH;
+            const double2 P = s_P[c], Q = s_Q[c];
+            const double2 val = cscale(cadd(cscale(P, -(e1 - kp.Gt * e2)), cscale(Q, e3 - kp.Gb * e4)), iden);
+            const double2 der = cscale(cadd(cscale(P, e1 + kp.Gt * e2), cscale(Q, e3 + kp.Gb * e4)), k * iden);
+            ps = cadd(ps, val);
+            dps = cadd(dps, der);
+        }
+        if (col == 0) {
+            ps.x += Ai * z;
+            dps.x += Ai;
+        }
+        kp.spec[size_t(j) * M + col] = ps;
+        kp.spec[size_t(N + j) * M + col] = dps;
+    }
+    const double g = block_sum(tid < CB ? s_gauge[tid] : 0.0);
+    if (tid == 0) kp.part_gauge_far[blockIdx.x] = g;
+}
+
+// ---------------------------------------------------------------------------
+// xy FFT, inverse: columns along y for psi, -i k_y psi and dpsi/dz, then rows
+// along x packing (phi, E_x) and (E_y, E_z) as one complex FFT each
+// ---------------------------------------------------------------------------
+__global__ void k_ffty_inv(KP kp, int TK) {
+    extern __shared__ double2 sm[];
+    const int n = kp.ny, nxh = kp.nxh;
+    double2* tw = sm;
+    double2* A = tw + n;
+    double2* B = A + 3 * TK * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = kp.twy[i];
+    const size_t plane = size_t(n) * nxh;
+    double2* s0 = kp.spec + size_t(blockIdx.y) * plane;
+    double2* s1 = kp.spec + size_t(kp.nz + blockIdx.y) * plane;
+    double2* sb = kp.specB + size_t(blockIdx.y) * plane;
+    const int k0 = blockIdx.x * TK;
+    for (int t = threadIdx.x; t < TK * n; t += blockDim.x) {
+        const int y = t / TK, c = t - y * TK, kx = k0 + c;
+        double2 ps = make_double2(0.0, 0.0), dps = ps;
+        if (kx < nxh) {
+            ps = s0[size_t(y) * nxh + kx];
+            dps = s1[size_t(y) * nxh + kx];
+        }
+        const int my = y < (n + 1) / 2 ? y : y - n;
+        const double ky = (n % 2 == 0 && y == n / 2) ? 0.0 : kTwoPi * my / kp.Ly;
+        A[c * n + y] = ps;
+        A[(TK + c) * n + y] = make_double2(ky * ps.y, -ky * ps.x);   // -i k_y psi
+        A[(2 * TK + c) * n + y] = dps;
+    }
+    __syncthreads();
+    const double2* R = block_fft(A, B, tw, n, 3 * TK, kp.rady, kp.nrady, +1);
+    for (int t = threadIdx.x; t < TK * n; t += blockDim.x) {
+        const int y = t / TK, c = t - y * TK, kx = k0 + c;
+        if (kx >= nxh) continue;
+        s0[size_t(y) * nxh + kx] = R[c * n + y];
+        sb[size_t(y) * nxh + kx] = R[(TK + c) * n + y];
+        s1[size_t(y) * nxh + kx] = R[(2 * TK + c) * n + y];
+    }
+}
+
+__global__ void k_fftx_inv(KP kp, int P) {
+    extern __shared__ double2 sm[];
+    const int n = kp.nx, nxh = kp.nxh;
+    double2* tw = sm;
+    double2* A = tw + n;
+    double2* B = A + 2 * P * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = kp.twx[i];
+    const int nrows = kp.nz * kp.ny;
+    const size_t S = size_t(nrows) * nxh;
+    const int r0 = blockIdx.x * P;
+    for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
+        const int p = t / n, k = t - p * n, row = r0 + p;
+        double2 z1 = make_double2(0.0, 0.0), z2 = z1;
+        if (row < nrows) {
+            const bool hi = k >= nxh;
+            const int kk = hi ? n - k : k;
+            double2 a = kp.spec[size_t(row) * nxh + kk];
+            double2 b = kp.specB[size_t(row) * nxh + kk];
+            double2 c = kp.spec[S + size_t(row) * nxh + kk];
+            const bool edge = kk == 0 || (n % 2 == 0 && kk == n / 2);
+            if (edge) { a.y = 0.0; b.y = 0.0; c.y = 0.0; }
+            const double kxd = edge ? 0.0 : kTwoPi * kk / kp.Lx;
+            double2 r = make_double2(kxd * a.y, -kxd * a.x);   // -i k_x psi
+            double2 mc = make_double2(-c.x, -c.y);             // E_z = -dpsi/dz
+            if (hi) { a = cconj(a); r = cconj(r); b = cconj(b); mc = cconj(mc); }
+            z1 = make_double2(a.x - r.y, a.y + r.x);           // phi + i E_x
+            z2 = make_double2(b.x - mc.y, b.y + mc.x);         // E_y + i E_z
+        }
+        A[(2 * p) * n + k] = z1;
+        A[(2 * p + 1) * n + k] = z2;
+    }
+    __syncthreads();
+    const double2* R = block_fft(A, B, tw, n, 2 * P, kp.radx, kp.nradx, +1);
+    const double s = kp.inv_nxny;
+    for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
+        const int p = t / n, x = t - p * n, row = r0 + p;
+        if (row >= nrows) continue;
+        const double2 u = R[(2 * p) * n + x], v = R[(2 * p + 1) * n + x];
+        kp.fields[size_t(row) * n + x] = make_double4_32a(u.x * s, u.y * s, v.x * s, v.y * s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// interpolation, Sec. 5.2.2 step 7: one warp per charge, grid quadrature of
+// the kernel times the four fields
+// ---------------------------------------------------------------------------
+__global__ void k_interp(KP kp) {
+    extern __shared__ double smi[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* wx = smi + w * (2 * kMaxSupport + kMaxNz);
+    double* wy = wx + kMaxSupport;
+    double* wzz = wy + kMaxSupport;
+    const int k = blockIdx.x * (blockDim.x >> 5) + w;
+    if (k >= kp.n) return;
+    const double4_32a p = kp.part[k];
+    const double x = p.x, y = p.y, z = p.z, HE = kp.HE;
+    const int ix0 = int(ceil((x - HE) / kp.hx)), ix1 = int(floor((x + HE) / kp.hx));
+    const int iy0 = int(ceil((y - HE) / kp.hy)), iy1 = int(floor((y + HE) / kp.hy));
+    const int sx = ix1 - ix0 + 1, sy = iy1 - iy0 + 1;
+    int j0 = kp.nz, j1 = -1;
+    for (int j = lane; j < kp.nz; j += 32) {
+        if (fabs(kp.zn[j] - z) <= HE) { j0 = min(j0, j); j1 = max(j1, j); }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        j0 = min(j0, __shfl_xor_sync(0xffffffffu, j0, o));
+        j1 = max(j1, __shfl_xor_sync(0xffffffffu, j1, o));
+    }
+    const int sz = j1 - j0 + 1;
+    const double inv2g2 = 1.0 / (2.0 * kp.gt * kp.gt);
+    for (int i = lane; i < sx; i += 32) {
+        const double d = double(ix0 + i) * kp.hx - x;
+        wx[i] = kp.s1norm * exp(-d * d * inv2g2);
+    }
+    for (int i = lane; i < sy; i += 32) {
+        const double d = double(iy0 + i) * kp.hy - y;
+        wy[i] = kp.s1norm * exp(-d * d * inv2g2);
+    }
+    for (int i = lane; i < sz; i += 32) {
+        const double d = kp.zn[j0 + i] - z;
+        wzz[i] = kp.wz[j0 + i] * (kp.s1norm * exp(-d * d * inv2g2));
+    }
+    __syncwarp();
+    const double wxy = kp.hx * kp.hy;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const int sxy = sx * sy;
+    for (int t = lane; t < sz * sxy; t += 32) {
+        const int jz = t / sxy, r = t - jz * sxy, iy = r / sx, ix = r - iy * sx;
+        const double wt = wxy * wzz[jz] * wy[iy] * wx[ix];
+        const size_t g = (size_t(j0 + jz) * kp.ny + wrap_index(iy0 + iy, kp.ny)) * kp.nx + wrap_index(ix0 + ix, kp.nx);
+        const double4_32a f = kp.fields[g];
+        a0 = fma(wt, f.x, a0);
+        a1 = fma(wt, f.y, a1);
+        a2 = fma(wt, f.z, a2);
+        a3 = fma(wt, f.w, a3);
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    a3 = warp_sum(a3);
+    if (lane == 0) kp.far[k] = make_double4_32a(a0, a1, a2, a3);
+}
+
+// ---------------------------------------------------------------------------
+// near field over a cell list (Sec. 4.2): counting sort, then one thread per
+// charge over the neighbouring cells, with one image per wall
+// ---------------------------------------------------------------------------
+__global__ void k_scan_cells(KP kp) {
+    __shared__ int sums[1024];
+    const int n = kp.ncells, tid = threadIdx.x, bs = blockDim.x;
+    const int chunk = (n + bs - 1) / bs;
+    const int lo = min(n, tid * chunk), hi = min(n, lo + chunk);
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += kp.cell_count[i];
+    sums[tid] = s;
+    __syncthreads();
+    for (int o = 1; o < bs; o <<= 1) {
+        const int v = tid >= o ? sums[tid - o] : 0;
+        __syncthreads();
+        sums[tid] += v;
+        __syncthreads();
+    }
+    int run = sums[tid] - s;
+    for (int i = lo; i < hi; ++i) {
+        kp.cell_start[i] = run;
+        run += kp.cell_count[i];
+    }
+    if (tid == bs - 1) kp.cell_start[n] = sums[bs - 1];
+}
+
+__global__ void k_scatter_cells(KP kp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kp.n) return;
+    const int c = kp.cell_of[k];
+    const int slot = kp.cell_start[c] + atomicAdd(&kp.cell_fill[c], 1);
+    kp.sorted[slot] = kp.part[k];
+    kp.sorted_idx[slot] = k;
+}
+
+__device__ __forceinline__ void near_cell(const KP& kp, int cell, double x, double y, double zt, double zsign,
+                                          double zoff, double strength, double rc2,
+                                          double& phi, double& ex, double& ey, double& ez) {
+    const int s0 = kp.cell_start[cell], s1 = kp.cell_start[cell + 1];
+    for (int s = s0; s < s1; ++s) {
+        const double4_32a src = kp.sorted[s];
+        const double dx = min_image(x - src.x, kp.Lx);
+        const double dy = min_image(y - src.y, kp.Ly);
+        const double dz = zt - (zoff + zsign * src.z);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < rc2) {
+            double g, d;
+            near_kernel(sqrt(r2), kp.na1, kp.na2, kp.gw, kp.eps, g, d);
+            const double qs = strength * src.w;
+            phi += qs * g;
+            ex -= qs * d * dx;
+            ey -= qs * d * dy;
+            ez -= qs * d * dz;
+        }
+    }
+}
+
+__global__ void k_near(KP kp) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= kp.n) return;
+    const double4_32a t = kp.sorted[s];
+    const double x = t.x, y = t.y, z = t.z;
+    const int cx = min(kp.ncx - 1, max(0, int(x / kp.cwx)));
+    const int cy = min(kp.ncy - 1, max(0, int(y / kp.cwy)));
+    const int cz = min(kp.ncz - 1, max(0, int(z / kp.cwz)));
+    const double rc2 = kp.r_cut * kp.r_cut;
+    double phi = 0, ex = 0, ey = 0, ez = 0;
+    const int nxc = kp.ncx >= 3 ? 3 : kp.ncx, nyc = kp.ncy >= 3 ? 3 : kp.ncy;
+    // pass 0: charges; pass 1: images below z = 0; pass 2: images above z = H
+    for (int pass = 0; pass < 3; ++pass) {
+        int zl, zh;
+        double zsign, zoff, st;
+        if (pass == 0) { zl = max(0, cz - 1); zh = min(kp.ncz - 1, cz + 1); zsign = 1.0; zoff = 0.0; st = 1.0; }
+        else if (pass == 1) {
+            if (!(z < kp.r_cut) || kp.Gb == 0.0) continue;
+            zl = zh = 0; zsign = -1.0; zoff = 0.0; st = -kp.Gb;
+        } else {
+            if (!(kp.H - z < kp.r_cut) || kp.Gt == 0.0) continue;
+            zl = zh = kp.ncz - 1; zsign = -1.0; zoff = 2.0 * kp.H; st = -kp.Gt;
+        }
+        for (int zc = zl; zc <= zh; ++zc) {
+            for (int oy = 0; oy < nyc; ++oy) {
+                const int yc = kp.ncy >= 3 ? wrap_index(cy - 1 + oy, kp.ncy) : oy;
+                for (int ox = 0; ox < nxc; ++ox) {
+                    const int xc = kp.ncx >= 3 ? wrap_index(cx - 1 + ox, kp.ncx) : ox;
+                    near_cell(kp, (zc * kp.ncy + yc) * kp.ncx + xc, x, y, z, zsign, zoff, st, rc2, phi, ex, ey, ez);
+                }
+            }
+        }
+    }
+    kp.nearv[kp.sorted_idx[s]] = make_double4_32a(phi, ex, ey, ez);
+}
+
+// pointwise near-field potential at the origin (gauge of Sec. 5.2.2)
+__global__ void k_origin(KP kp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (k < kp.n && kp.near_on) {
+        const double4_32a p = kp.part[k];
+        const double dx = min_image(0.0 - p.x, kp.Lx), dy = min_image(0.0 - p.y, kp.Ly);
+        const double rc = kp.r_cut;
+        const double r = sqrt(dx * dx + dy * dy + p.z * p.z);
+        const double zt = 2.0 * kp.H - p.z;
+        const double rt = sqrt(dx * dx + dy * dy + zt * zt);
+        double g, d;
+        if (r < rc) {
+            near_kernel(r, kp.pa1, kp.pa2, kp.gw, kp.eps, g, d);
+            v += p.w * g;                 // the charge
+            v += -kp.Gb * p.w * g;        // its image below z = 0 (same distance)
+        }
+        if (rt < rc) {
+            near_kernel(rt, kp.pa1, kp.pa2, kp.gw, kp.eps, g, d);
+            v += -kp.Gt * p.w * g;
+        }
+    }
+    const double s = block_sum(v);
+    if (threadIdx.x == 0) kp.part_gauge_near[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// gauge constant, assembly, energy
+// ---------------------------------------------------------------------------
+__global__ void k_final_gauge(KP kp) {
+    double f = 0.0, nn = 0.0, q1 = 0.0, q2 = 0.0;
+    for (int i = threadIdx.x; i < kp.n_col_blocks; i += blockDim.x) f += kp.part_gauge_far[i];
+    for (int i = threadIdx.x; i < kp.n_charge_blocks; i += blockDim.x) {
+        nn += kp.part_gauge_near[i];
+        q1 += kp.part_q[i];
+        q2 += kp.part_q[kp.n_charge_blocks + i];
+    }
+    f = block_sum(f);
+    nn = block_sum(nn);
+    q1 = block_sum(q1);
+    q2 = block_sum(q2);
+    if (threadIdx.x == 0) {
+        const double phi_f0 = f * kp.inv_nxny;
+        kp.scal[0] = -(phi_f0 + nn);
+        kp.scal[2] = phi_f0;
+        kp.scal[3] = nn;
+        kp.scal[5] = q1;
+        kp.scal[6] = q2;
+    }
+}
+
+__global__ void k_assemble(KP kp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double u = 0.0;
+    if (k < kp.n) {
+        const double B = kp.scal[0];
+        const double4_32a f = kp.far[k];
+        const double4_32a nn = kp.near_on ? kp.nearv[k] : make_double4_32a(0, 0, 0, 0);
+        const double q = kp.part[k].w;
+        const double phi = f.x + nn.x + B;
+        if (kp.out_phi) kp.out_phi[k] = phi;
+        if (kp.out_force) {
+            kp.out_force[3 * k] = q * (f.y + nn.y);
+            kp.out_force[3 * k + 1] = q * (f.z + nn.z);
+            kp.out_force[3 * k + 2] = q * (f.w + nn.w);
+        }
+        u = q * phi;
+    }
+    const double s = block_sum(u);
+    if (threadIdx.x == 0) kp.part_u[blockIdx.x] = s;
+}
+
+__global__ void k_final_energy(KP kp) {
+    double u = 0.0;
+    for (int i = threadIdx.x; i < kp.n_charge_blocks; i += blockDim.x) u += kp.part_u[i];
+    u = block_sum(u);
+    if (threadIdx.x == 0) kp.scal[4] = 0.5 * u;
+}
+
+}  // namespace
+
+// ===========================================================================
+// plan
+// ===========================================================================
+struct dpslab_plan {
+    dpslab_params p{};
+    dpslab_derived d{};
+    int64_t max_n = 0;
+    int device = 0;
+    int nxh = 0;
+    size_t G = 0, S = 0;
+    int px_fwd = 1, tk_fwd = 1, tk_inv = 1, px_inv = 1;
+    size_t sm_fftx_fwd = 0, sm_ffty_fwd = 0, sm_ffty_inv = 0, sm_fftx_inv = 0, sm_col = 0, sm_interp = 0;
+    KP kp{};
+    // allocations
+    void* tables = nullptr;
+    void* work = nullptr;
+    int64_t device_bytes = 0;
+    double* d_pos = nullptr;    // staging for dpslab_solve_host
+    double* d_q = nullptr;
+    double* d_phi = nullptr;
+    double* d_force = nullptr;
+    double* h_scal = nullptr;   // pinned
+    int* h_status = nullptr;
+    int64_t last_n = 0;
+    int launches = 0;
+    int profiling = 0;
+    cudaEvent_t ev[DPSLAB_NSTAGES + 1] = {};
+    double stage_ms[DPSLAB_NSTAGES] = {};
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+    return e == cudaSuccess ? DPSLAB_OK : DPSLAB_ERR_CUDA;
+}
+
+#define DPS_CUDA(call)                            \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return cuda_err(e_); \
+    } while (0)
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+template <class T>
+T* carve(char*& cur, size_t count) {
+    T* p = reinterpret_cast<T*>(cur);
+    cur += align_up(count * sizeof(T));
+    return p;
+}
+
+int floor_pow2(int v) {
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+void release(dpslab_plan* pl) {
+    if (!pl) return;
+    for (auto& e : pl->ev)
+        if (e) cudaEventDestroy(e);
+    if (pl->tables) cudaFree(pl->tables);
+    if (pl->work) cudaFree(pl->work);
+    if (pl->h_scal) cudaFreeHost(pl->h_scal);
+    if (pl->h_status) cudaFreeHost(pl->h_status);
+    delete pl;
+}
+
+}  // namespace
+
+extern "C" int dpslab_derive(const dpslab_params* p, dpslab_derived* out) {
+    if (!p || !out) return DPSLAB_ERR_INVALID_ARG;
+    return dps::derive(*p, *out);
+}
+
+extern "C" int dpslab_table(const dpslab_params* p, int which, double* out, int n_out) {
+    if (!p || !out) return DPSLAB_ERR_INVALID_ARG;
+    dpslab_derived d;
+    int rc = dps::derive(*p, d);
+    if (rc) return rc;
+    if (n_out < d.nz) return DPSLAB_ERR_INVALID_ARG;
+    dps::Tables t;
+    rc = dps::build_tables(*p, d, t);
+    if (rc) return rc;
+    const std::vector<double>* v = which == 0 ? &t.zn : which == 1 ? &t.wz : which == 2 ? &t.wg : nullptr;
+    if (!v) return DPSLAB_ERR_INVALID_ARG;
+    std::copy(v->begin(), v->end(), out);
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_plan** out) {
+    if (!out) return DPSLAB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!p || max_n < 1 || max_n > (int64_t(1) << 28)) return DPSLAB_ERR_INVALID_ARG;
+    dpslab_plan* pl = new (std::nothrow) dpslab_plan();
+    if (!pl) return DPSLAB_ERR_INVALID_ARG;
+    pl->p = *p;
+    pl->max_n = max_n;
+    int rc = dps::derive(*p, pl->d);
+    if (rc) { delete pl; return rc; }
+    dps::Tables t;
+    rc = dps::build_tables(*p, pl->d, t);
+    if (rc) { delete pl; return rc; }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) { delete pl; return DPSLAB_ERR_NO_DEVICE; }
+    cudaGetDevice(&pl->device);
+
+    const dpslab_derived& d = pl->d;
+    const int nx = d.nx, ny = d.ny, nz = d.nz, nxh = nx / 2 + 1;
+    pl->nxh = nxh;
+    pl->G = size_t(nz) * ny * nx;
+    pl->S = size_t(nz) * ny * nxh;
+    KP& kp = pl->kp;
+    kp.Lx = p->Lx; kp.Ly = p->Ly; kp.H = p->H; kp.eps = p->eps; kp.gw = p->gw;
+    auto wall = [&](double ew, double& G, double& c, double& dd, double& tau, double& rtau, int& metal) {
+        metal = std::isinf(ew) ? 1 : 0;
+        if (metal) { G = 1.0; c = 1.0; dd = 0.0; tau = 0.0; rtau = 2.0; return; }
+        const double r = ew / p->eps;
+        G = (r - 1.0) / (r + 1.0); c = r / (1.0 + r); dd = 1.0 / (1.0 + r); tau = 2.0 / (1.0 + r); rtau = 2.0 * r / (1.0 + r);
+    };
+    wall(p->eps_b, kp.Gb, kp.cb, kp.db, kp.tb, kp.rtb, kp.metal_b);
+    wall(p->eps_t, kp.Gt, kp.ct, kp.dt, kp.tt, kp.rtt, kp.metal_t);
+    kp.nx = nx; kp.ny = ny; kp.nz = nz; kp.nxh = nxh;
+    kp.hx = d.hx; kp.hy = d.hy; kp.HE = d.HE; kp.gt = d.gt; kp.xi = d.xi; kp.r_cut = d.r_cut;
+    kp.a = d.a; kp.b = d.b; kp.Hbar = d.Hbar; kp.kmax = d.kmax;
+    kp.s1norm = std::pow(2.0 * 3.14159265358979323846 * d.gt * d.gt, -0.5);
+    kp.sigma2 = std::isinf(d.xi) ? 0.0 : (0.5 / d.xi) * (0.5 / d.xi);
+    kp.inv_nxny = 1.0 / (double(nx) * double(ny));
+    kp.near_on = d.r_cut > 0.0 && std::isfinite(d.xi);
+    kp.na1 = 2.0 * p->gw;
+    kp.pa1 = std::sqrt(2.0) * p->gw;
+    kp.na2 = kp.near_on ? std::sqrt(kp.na1 * kp.na1 + 1.0 / (d.xi * d.xi)) : 0.0;
+    kp.pa2 = kp.near_on ? std::sqrt(kp.pa1 * kp.pa1 + 1.0 / (d.xi * d.xi)) : 0.0;
+    kp.nradx = int(t.radx.size());
+    kp.nrady = int(t.rady.size());
+    for (int i = 0; i < kp.nradx; ++i) kp.radx[i] = t.radx[i];
+    for (int i = 0; i < kp.nrady; ++i) kp.rady[i] = t.rady[i];
+    if (kp.near_on) {
+        kp.ncx = std::max(1, int(std::floor(p->Lx / d.r_cut)));
+        kp.ncy = std::max(1, int(std::floor(p->Ly / d.r_cut)));
+        kp.ncz = std::max(1, int(std::floor(p->H / d.r_cut)));
+        if (double(kp.ncx) * kp.ncy * kp.ncz > double(1 << 26)) { delete pl; return DPSLAB_ERR_GRID; }
+        kp.ncells = kp.ncx * kp.ncy * kp.ncz;
+        kp.cwx = p->Lx / kp.ncx;
+        kp.cwy = p->Ly / kp.ncy;
+        kp.cwz = p->H / kp.ncz;
+    } else {
+        kp.ncx = kp.ncy = kp.ncz = 1;
+        kp.ncells = 1;
+        kp.cwx = p->Lx; kp.cwy = p->Ly; kp.cwz = p->H;
+    }
+    const int M = ny * nxh;
+    kp.n_col_blocks = (M + kColBlock - 1) / kColBlock;
+    kp.n_charge_blocks = int((max_n + kChargeThreads - 1) / kChargeThreads);
+
+    // tables (one allocation)
+    {
+        const size_t N = nz;
+        size_t bytes = 0;
+        const size_t vec = align_up(N * sizeof(double));
+        bytes += 2 * vec + 2 * align_up(N * N * sizeof(double)) + 11 * vec;
+        bytes += align_up(nx * sizeof(double2)) + align_up(ny * sizeof(double2));
+        cudaError_t e = cudaMalloc(&pl->tables, bytes);
+        if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
+        pl->device_bytes += int64_t(bytes);
+        char* cur = static_cast<char*>(pl->tables);
+        auto up = [&](const std::vector<double>& v, const double*& dst) {
+            double* dp = carve<double>(cur, v.size());
+            cudaMemcpy(dp, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+            dst = dp;
+        };
+        up(t.zn, kp.zn); up(t.wz, kp.wz); up(t.cf, kp.cf); up(t.ti, kp.ti);
+        up(t.j2l, kp.j2l); up(t.j2d, kp.j2d); up(t.j2u, kp.j2u);
+        up(t.u1, kp.u1); up(t.u2, kp.u2); up(t.v1, kp.v1); up(t.v2, kp.v2);
+        up(t.t0, kp.t0); up(t.tH, kp.tH); up(t.wg, kp.wg);
+        double2* tx = carve<double2>(cur, nx);
+        double2* ty = carve<double2>(cur, ny);
+        cudaMemcpy(tx, t.twx.data(), nx * sizeof(double2), cudaMemcpyHostToDevice);
+        cudaMemcpy(ty, t.twy.data(), ny * sizeof(double2), cudaMemcpyHostToDevice);
+        kp.twx = tx;
+        kp.twy = ty;
+        if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
+    }
+    // work space (one allocation)
+    {
+        const size_t n = size_t(max_n);
+        size_t bytes = 0;
+        bytes += align_up(2 * pl->G * sizeof(double));        // rho
+        bytes += align_up(2 * pl->S * sizeof(double2));       // spec
+        bytes += align_up(pl->S * sizeof(double2));           // specB
+        bytes += align_up(pl->G * sizeof(double4_32a));           // fields
+        bytes += 3 * align_up(n * sizeof(double4_32a));           // part, far, nearv
+        bytes += 2 * align_up(n * sizeof(int));               // cell_of, sorted_idx
+        bytes += align_up(n * sizeof(double4_32a));               // sorted
+        bytes += 3 * align_up((size_t(kp.ncells) + 1) * sizeof(int));
+        bytes += align_up(size_t(kp.ncells) * sizeof(int));
+        bytes += align_up(size_t(kp.n_col_blocks) * sizeof(double));
+        bytes += 4 * align_up(size_t(kp.n_charge_blocks) * 2 * sizeof(double));
+        bytes += align_up(16 * sizeof(double)) + align_up(16 * sizeof(int));
+        bytes += align_up(n * 3 * sizeof(double)) * 2 + align_up(n * sizeof(double)) * 2;   // host-call staging
+        cudaError_t e = cudaMalloc(&pl->work, bytes);
+        if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
+        pl->device_bytes += int64_t(bytes);
+        char* cur = static_cast<char*>(pl->work);
+        kp.rho = carve<double>(cur, 2 * pl->G);
+        kp.spec = carve<double2>(cur, 2 * pl->S);
+        kp.specB = carve<double2>(cur, pl->S);
+        kp.fields = carve<double4_32a>(cur, pl->G);
+        kp.part = carve<double4_32a>(cur, n);
+        kp.far = carve<double4_32a>(cur, n);
+        kp.nearv = carve<double4_32a>(cur, n);
+        kp.cell_of = carve<int>(cur, n);
+        kp.sorted_idx = carve<int>(cur, n);
+        kp.sorted = carve<double4_32a>(cur, n);
+        kp.cell_count = carve<int>(cur, size_t(kp.ncells) + 1);
+        kp.cell_start = carve<int>(cur, size_t(kp.ncells) + 1);
+        kp.cell_fill = carve<int>(cur, size_t(kp.ncells) + 1);
+        carve<int>(cur, size_t(kp.ncells));
+        kp.part_gauge_far = carve<double>(cur, kp.n_col_blocks);
+        kp.part_gauge_near = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
+        kp.part_u = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
+        kp.part_q = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
+        carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
+        kp.scal = carve<double>(cur, 16);
+        kp.status = carve<int>(cur, 16);
+        pl->d_pos = carve<double>(cur, 3 * n);
+        pl->d_force = carve<double>(cur, 3 * n);
+        pl->d_q = carve<double>(cur, n);
+        pl->d_phi = carve<double>(cur, n);
+    }
+    if (cudaMallocHost(&pl->h_scal, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&pl->h_status, 16 * sizeof(int)) != cudaSuccess) {
+        release(pl);
+        return DPSLAB_ERR_CUDA;
+    }
+
+    // launch shapes and shared memory
+    pl->px_fwd = std::max(1, std::min(8, 3072 / nx));
+    pl->tk_fwd = std::max(1, std::min(16, floor_pow2(std::max(1, 3072 / ny))));
+    pl->tk_inv = std::max(1, std::min(8, floor_pow2(std::max(1, 1024 / ny))));
+    pl->px_inv = std::max(1, std::min(8, 1536 / nx));
+    pl->sm_fftx_fwd = (size_t(nx) + 2 * size_t(pl->px_fwd) * nx) * sizeof(double2);
+    pl->sm_ffty_fwd = (size_t(ny) + 2 * size_t(pl->tk_fwd) * ny) * sizeof(double2);
+    pl->sm_ffty_inv = (size_t(ny) + 6 * size_t(pl->tk_inv) * ny) * sizeof(double2);
+    pl->sm_fftx_inv = (size_t(nx) + 4 * size_t(pl->px_inv) * nx) * sizeof(double2);
+    pl->sm_col = size_t(kColBlock) * nz * (4 * sizeof(double2) + 2 * sizeof(double));
+    pl->sm_interp = size_t(kInterpWarps) * (2 * kMaxSupport + kMaxNz) * sizeof(double);
+    const size_t smax = 227 * 1024;
+    if (pl->sm_fftx_fwd > smax || pl->sm_ffty_fwd > smax || pl->sm_ffty_inv > smax ||
+        pl->sm_fftx_inv > smax || pl->sm_col > smax) {
+        release(pl);
+        return DPSLAB_ERR_GRID;
+    }
+    cudaFuncSetAttribute(k_fftx_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
+    cudaFuncSetAttribute(k_ffty_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
+    cudaFuncSetAttribute(k_ffty_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
+    cudaFuncSetAttribute(k_fftx_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
+    cudaFuncSetAttribute(k_column, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
+    cudaFuncSetAttribute(k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
+    if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
+    *out = pl;
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_plan_derived(const dpslab_plan* plan, dpslab_derived* out) {
+    if (!plan || !out) return DPSLAB_ERR_INVALID_ARG;
+    *out = plan->d;
+    return DPSLAB_OK;
+}
+
+extern "C" int64_t dpslab_plan_device_bytes(const dpslab_plan* plan) { return plan ? plan->device_bytes : 0; }
+
+extern "C" int dpslab_plan_destroy(dpslab_plan* plan) {
+    if (!plan) return DPSLAB_OK;
+    cudaSetDevice(plan->device);
+    release(plan);
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_last_launch_count(const dpslab_plan* plan) { return plan ? plan->launches : 0; }
+
+extern "C" int dpslab_profile(dpslab_plan* plan, int on) {
+    if (!plan) return DPSLAB_ERR_INVALID_ARG;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    if (on && !plan->ev[0]) {
+        for (auto& e : plan->ev) DPS_CUDA(cudaEventCreate(&e));
+    }
+    plan->profiling = on ? 1 : 0;
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_stage_times(const dpslab_plan* plan, double* ms, int n) {
+    if (!plan || !ms || n < DPSLAB_NSTAGES) return DPSLAB_ERR_INVALID_ARG;
+    for (int i = 0; i < DPSLAB_NSTAGES; ++i) ms[i] = plan->stage_ms[i];
+    return DPSLAB_OK;
+}
+
+extern "C" const char* dpslab_stage_name(int stage) {
+    static const char* names[DPSLAB_NSTAGES] = {"prepare", "spread", "fft_x_fwd", "fft_y_fwd", "column",
+                                                "fft_y_inv", "fft_x_inv", "interp", "near", "finish"};
+    return (stage >= 0 && stage < DPSLAB_NSTAGES) ? names[stage] : "";
+}
+
+extern "C" const char* dpslab_strerror(int code) {
+    switch (code) {
+        case DPSLAB_OK: return "ok";
+        case DPSLAB_ERR_INVALID_ARG: return "invalid argument";
+        case DPSLAB_ERR_NOT_NEUTRAL: return "charges are not neutral";
+        case DPSLAB_ERR_OUT_OF_SLAB: return "a charge lies outside 0 < z < H or is not finite";
+        case DPSLAB_ERR_CUTOFF_TOO_LARGE: return "near-field cutoff not below half the period";
+        case DPSLAB_ERR_SPLIT_CONSTRAINT: return "splitting constraint violated (strict mode)";
+        case DPSLAB_ERR_CAPACITY: return "more charges than the plan was created for";
+        case DPSLAB_ERR_CUDA: return "CUDA runtime error";
+        case DPSLAB_ERR_NO_DEVICE: return "no CUDA device";
+        case DPSLAB_ERR_GRID: return "grid too small for the Gaussian support or unsupported size";
+        case DPSLAB_ERR_UNSUPPORTED: return "unsupported option";
+        default: return "unknown error";
+    }
+}
+
+namespace {
+
+int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, double* phi, double* force,
+            cudaStream_t st) {
+    KP kp = pl->kp;
+    const int n = int(n64);
+    kp.n = n;
+    kp.pos = pos;
+    kp.q = q;
+    kp.out_phi = phi;
+    kp.out_force = force;
+    const int nb = (n + kChargeThreads - 1) / kChargeThreads;
+    kp.n_charge_blocks = nb;
+    int launches = 0;
+    const bool prof = pl->profiling != 0;
+    auto mark = [&](int i) {
+        if (prof) cudaEventRecord(pl->ev[i], st);
+    };
+#define LAUNCH(...)                                  \
+    do {                                             \
+        __VA_ARGS__;                                 \
+        ++launches;                                  \
+        if (cudaGetLastError() != cudaSuccess) return DPSLAB_ERR_CUDA; \
+    } while (0)
+
+    DPS_CUDA(cudaMemsetAsync(kp.status, 0, sizeof(int), st));
+    DPS_CUDA(cudaMemsetAsync(kp.rho, 0, 2 * pl->G * sizeof(double), st));
+    if (kp.near_on) {
+        DPS_CUDA(cudaMemsetAsync(kp.cell_count, 0, (size_t(kp.ncells) + 1) * sizeof(int), st));
+        DPS_CUDA(cudaMemsetAsync(kp.cell_fill, 0, (size_t(kp.ncells) + 1) * sizeof(int), st));
+    }
+    mark(0);
+    LAUNCH(k_prepare<<<nb, kChargeThreads, 0, st>>>(kp));
+    mark(1);
+    LAUNCH(k_spread<<<3 * n, 128, 0, st>>>(kp));
+    mark(2);
+    const int npairs = kp.nz * kp.ny;
+    LAUNCH(k_fftx_fwd<<<(npairs + pl->px_fwd - 1) / pl->px_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
+    mark(3);
+    LAUNCH(k_ffty_fwd<<<dim3((kp.nxh + pl->tk_fwd - 1) / pl->tk_fwd, 2 * kp.nz), 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
+    mark(4);
+    LAUNCH(k_column<<<kp.n_col_blocks, kColThreads, pl->sm_col, st>>>(kp));
+    mark(5);
+    LAUNCH(k_ffty_inv<<<dim3((kp.nxh + pl->tk_inv - 1) / pl->tk_inv, kp.nz), 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
+    mark(6);
+    LAUNCH(k_fftx_inv<<<(kp.nz * kp.ny + pl->px_inv - 1) / pl->px_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
+    mark(7);
+    LAUNCH(k_interp<<<(n + kInterpWarps - 1) / kInterpWarps, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
+    mark(8);
+    if (kp.near_on) {
+        LAUNCH(k_scan_cells<<<1, 1024, 0, st>>>(kp));
+        LAUNCH(k_scatter_cells<<<nb, kChargeThreads, 0, st>>>(kp));
+        LAUNCH(k_near<<<(n + 127) / 128, 128, 0, st>>>(kp));
+    }
+    mark(9);
+    LAUNCH(k_origin<<<nb, kChargeThreads, 0, st>>>(kp));
+    LAUNCH(k_final_gauge<<<1, 1024, 0, st>>>(kp));
+    LAUNCH(k_assemble<<<nb, kChargeThreads, 0, st>>>(kp));
+    LAUNCH(k_final_energy<<<1, 1024, 0, st>>>(kp));
+    mark(10);
+#undef LAUNCH
+    DPS_CUDA(cudaMemcpyAsync(pl->h_scal, kp.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DPS_CUDA(cudaMemcpyAsync(pl->h_status, kp.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    pl->launches = launches;
+    return DPSLAB_OK;
+}
+
+int finish(dpslab_plan* pl, cudaStream_t st, double* U) {
+    DPS_CUDA(cudaStreamSynchronize(st));
+    if (pl->profiling) {
+        for (int i = 0; i < DPSLAB_NSTAGES; ++i) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, pl->ev[i], pl->ev[i + 1]);
+            pl->stage_ms[i] = ms;
+        }
+    }
+    if (U) *U = pl->h_scal[4];
+    if (*pl->h_status) return DPSLAB_ERR_OUT_OF_SLAB;
+    const double sq = pl->h_scal[5], saq = pl->h_scal[6];
+    if (std::fabs(sq) > 1e-12 * saq) return DPSLAB_ERR_NOT_NEUTRAL;
+    return DPSLAB_OK;
+}
+
+}  // namespace
+
+extern "C" int dpslab_solve(dpslab_plan* plan, int64_t n, const double* pos, const double* q, double* U,
+                            double* phi, double* force, void* stream) {
+    if (!plan || !pos || !q || n < 1) return DPSLAB_ERR_INVALID_ARG;
+    if (n > plan->max_n) return DPSLAB_ERR_CAPACITY;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = enqueue(plan, n, pos, q, phi, force, st);
+    if (rc) return rc;
+    plan->last_n = n;
+    return finish(plan, st, U);
+}
+
+extern "C" int dpslab_solve_host(dpslab_plan* plan, int64_t n, const double* pos, const double* q, double* U,
+                                 double* phi, double* force, void* stream) {
+    if (!plan || !pos || !q || n < 1) return DPSLAB_ERR_INVALID_ARG;
+    if (n > plan->max_n) return DPSLAB_ERR_CAPACITY;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DPS_CUDA(cudaMemcpyAsync(plan->d_pos, pos, size_t(n) * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    DPS_CUDA(cudaMemcpyAsync(plan->d_q, q, size_t(n) * sizeof(double), cudaMemcpyHostToDevice, st));
+    int rc = enqueue(plan, n, plan->d_pos, plan->d_q, phi ? plan->d_phi : nullptr, force ? plan->d_force : nullptr, st);
+    if (rc) return rc;
+    if (phi) DPS_CUDA(cudaMemcpyAsync(phi, plan->d_phi, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (force) DPS_CUDA(cudaMemcpyAsync(force, plan->d_force, size_t(n) * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    plan->last_n = n;
+    return finish(plan, st, U);
+}
+
+extern "C" int dpslab_debug_fetch(dpslab_plan* plan, int which, void* host_dst, size_t bytes) {
+    if (!plan || !host_dst) return DPSLAB_ERR_INVALID_ARG;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    const KP& kp = plan->kp;
+    const size_t n = size_t(plan->last_n);
+    const void* src = nullptr;
+    size_t want = 0;
+    switch (which) {
+        case 0: src = kp.rho; want = 2 * plan->G * sizeof(double); break;
+        case 1: src = kp.fields; want = plan->G * sizeof(double4_32a); break;
+        case 2: src = kp.far; want = n * sizeof(double4_32a); break;
+        case 3: src = kp.nearv; want = n * sizeof(double4_32a); break;
+        case 4: {
+            if (bytes != 4 * sizeof(double)) return DPSLAB_ERR_INVALID_ARG;
+            double s[4];
+            DPS_CUDA(cudaMemcpy(s, kp.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost));
+            double o[4] = {s[0], s[1], s[2], s[3]};
+            std::memcpy(host_dst, o, sizeof(o));
+            return DPSLAB_OK;
+        }
+        default: return DPSLAB_ERR_INVALID_ARG;
+    }
+    if (bytes != want) return DPSLAB_ERR_INVALID_ARG;
+    if (which == 3 && !kp.near_on) {
+        std::memset(host_dst, 0, bytes);
+        return DPSLAB_OK;
+    }
+    DPS_CUDA(cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost));
+    return DPSLAB_OK;
+}

@@ -1,0 +1,200 @@
+"""Python binding of the C ABI in include/dpslab.h (argument marshalling only).
+
+Every solve runs in the CUDA library libdpslab.so built from csrc/; this
+module only converts arguments. Device buffers are PyTorch CUDA tensors
+(float64, contiguous); streams are torch.cuda streams. If the library is
+missing the import fails: there is no CPU path.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdpslab.so")
+
+OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "NOT_NEUTRAL", -3: "OUT_OF_SLAB", -4: "CUTOFF_TOO_LARGE",
+    -5: "SPLIT_CONSTRAINT", -6: "CAPACITY", -7: "CUDA", -8: "NO_DEVICE", -9: "GRID", -10: "UNSUPPORTED",
+}
+FP64, MIXED = 0, 1
+NSTAGES = 10
+
+
+class DpslabError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dpslab error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("H", ctypes.c_double),
+                ("eps", ctypes.c_double), ("eps_b", ctypes.c_double), ("eps_t", ctypes.c_double),
+                ("gw", ctypes.c_double), ("tol", ctypes.c_double),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("xi", ctypes.c_double), ("r_cut", ctypes.c_double), ("n_sigma", ctypes.c_double),
+                ("precision", ctypes.c_int), ("strict", ctypes.c_int)]
+
+
+class Derived(ctypes.Structure):
+    _fields_ = [("hx", ctypes.c_double), ("hy", ctypes.c_double), ("h", ctypes.c_double),
+                ("xi", ctypes.c_double), ("gt", ctypes.c_double),
+                ("n_sigma", ctypes.c_double), ("HE", ctypes.c_double),
+                ("r_cut", ctypes.c_double), ("r_nf", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("Hbar", ctypes.c_double),
+                ("kmax", ctypes.c_double),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("support_x", ctypes.c_int), ("support_y", ctypes.c_int), ("violations", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2101_07088_b300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, D = ctypes.POINTER(Params), ctypes.POINTER(Derived)
+        vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+        sig = {
+            "dpslab_derive": (ctypes.c_int, [P, D]),
+            "dpslab_table": (ctypes.c_int, [P, ctypes.c_int, dp, ctypes.c_int]),
+            "dpslab_plan_create": (ctypes.c_int, [P, i64, ctypes.POINTER(vp)]),
+            "dpslab_plan_derived": (ctypes.c_int, [vp, D]),
+            "dpslab_plan_device_bytes": (i64, [vp]),
+            "dpslab_solve": (ctypes.c_int, [vp, i64, vp, vp, dp, vp, vp, vp]),
+            "dpslab_solve_host": (ctypes.c_int, [vp, i64, vp, vp, dp, vp, vp, vp]),
+            "dpslab_debug_fetch": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_size_t]),
+            "dpslab_last_launch_count": (ctypes.c_int, [vp]),
+            "dpslab_plan_destroy": (ctypes.c_int, [vp]),
+            "dpslab_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "dpslab_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+            "dpslab_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
+            "dpslab_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != OK:
+        raise DpslabError(code, lib().dpslab_strerror(code).decode())
+
+
+def make_params(Lx, Ly, H, gw, tol, nx, ny, nz=0, eps=1.0, eps_b=1.0, eps_t=1.0, xi=0.0,
+                r_cut=0.0, n_sigma=0.0, precision=FP64, strict=0):
+    return Params(float(Lx), float(Ly), float(H), float(eps), float(eps_b), float(eps_t), float(gw),
+                  float(tol), int(nx), int(ny), int(nz), float(xi), float(r_cut), float(n_sigma),
+                  int(precision), int(strict))
+
+
+def _as_params(p):
+    return p if isinstance(p, Params) else make_params(**p)
+
+
+def derive(params):
+    """dpslab_derive: the derived quantities as a dict (host only)."""
+    d = Derived()
+    _check(lib().dpslab_derive(ctypes.byref(_as_params(params)), ctypes.byref(d)))
+    return {name: getattr(d, name) for name, _ in Derived._fields_}
+
+
+def table(params, which):
+    """dpslab_table: 0 nodes, 1 quadrature weights, 2 gauge weights."""
+    p = _as_params(params)
+    nz = derive(p)["nz"]
+    out = np.zeros(nz)
+    _check(lib().dpslab_table(ctypes.byref(p), int(which), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nz))
+    return out
+
+
+class Plan:
+    """dpslab_plan_create / dpslab_solve / dpslab_plan_destroy."""
+
+    def __init__(self, params, max_n):
+        self.params = _as_params(params)
+        h = ctypes.c_void_p()
+        _check(lib().dpslab_plan_create(ctypes.byref(self.params), int(max_n), ctypes.byref(h)))
+        self._h = h
+        self.max_n = int(max_n)
+        d = Derived()
+        _check(lib().dpslab_plan_derived(self._h, ctypes.byref(d)))
+        self.derived = {name: getattr(d, name) for name, _ in Derived._fields_}
+        self.device_bytes = lib().dpslab_plan_device_bytes(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dpslab_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, pos, q, phi=None, force=None, energy=True, stream=None, check=True):
+        """pos [n, 3], q [n]: float64 contiguous CUDA tensors. phi [n] and
+        force [n, 3] are optional output tensors (None skips that output).
+        Returns (U or None, return code)."""
+        import torch
+        for t in (pos, q):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("pos and q must be contiguous float64 CUDA tensors")
+        n = q.shape[0]
+        U = ctypes.c_double(math.nan)
+        st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc = lib().dpslab_solve(self._h, n, pos.data_ptr(), q.data_ptr(),
+                                ctypes.byref(U) if energy else None,
+                                phi.data_ptr() if phi is not None else None,
+                                force.data_ptr() if force is not None else None, st)
+        if check:
+            _check(rc)
+        return (U.value if energy else None), rc
+
+    def solve_host(self, pos, q, want_phi=True, want_force=True, stream=None, check=True):
+        """Host (numpy) buffers; copies happen inside the library call.
+        Returns (U, phi or None, force or None, return code)."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        n = q.shape[0]
+        phi = np.empty(n) if want_phi else None
+        force = np.empty((n, 3)) if want_force else None
+        U = ctypes.c_double(math.nan)
+        st = None
+        if stream is not None:
+            st = stream.cuda_stream
+        rc = lib().dpslab_solve_host(self._h, n, pos.ctypes.data, q.ctypes.data, ctypes.byref(U),
+                                     phi.ctypes.data if phi is not None else None,
+                                     force.ctypes.data if force is not None else None, st)
+        if check:
+            _check(rc)
+        return U.value, phi, force, rc
+
+    def debug_fetch(self, which, n):
+        d = self.derived
+        shapes = {0: (2, d["nz"], d["ny"], d["nx"]), 1: (d["nz"], d["ny"], d["nx"], 4),
+                  2: (n, 4), 3: (n, 4), 4: (4,)}
+        out = np.zeros(shapes[which])
+        _check(lib().dpslab_debug_fetch(self._h, int(which), out.ctypes.data, out.nbytes))
+        return out
+
+    def last_launch_count(self):
+        return lib().dpslab_last_launch_count(self._h)
+
+    def profile(self, on=True):
+        _check(lib().dpslab_profile(self._h, 1 if on else 0))
+
+    def stage_times(self):
+        """{stage name: device ms} of the last solve (profiling on)."""
+        ms = (ctypes.c_double * NSTAGES)()
+        _check(lib().dpslab_stage_times(self._h, ms, NSTAGES))
+        return {lib().dpslab_stage_name(i).decode(): ms[i] for i in range(NSTAGES)}

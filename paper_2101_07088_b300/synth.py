@@ -1,0 +1,44 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+Binary +-1 electrolytes (Sec. 6.2, 6.3 and 7 use charges of alternating or
+random sign placed uniformly in the slab): exactly N/2 charges +1 and N/2
+charges -1 assigned by a random permutation, positions uniform in
+[0, Lx) x [0, Ly) x [z_lo, z_hi]. numpy's PCG64 generator; nothing here
+depends on the solver. Both the CUDA path's tests and the oracle's take
+their inputs from this module.
+"""
+import numpy as np
+
+
+def electrolyte(n, Lx, Ly, z_lo, z_hi, seed):
+    """(pos [n, 3], q [n]) as float64 numpy arrays; n must be even."""
+    if n % 2:
+        raise ValueError("n must be even for an exactly neutral +-1 electrolyte")
+    rng = np.random.default_rng(seed)
+    q = np.concatenate([np.ones(n // 2), -np.ones(n // 2)])
+    q = q[rng.permutation(n)]
+    pos = np.stack([rng.uniform(0.0, Lx, n), rng.uniform(0.0, Ly, n), rng.uniform(z_lo, z_hi, n)], axis=1)
+    return np.ascontiguousarray(pos), np.ascontiguousarray(q)
+
+
+# The workloads of the benchmark configurations (box, grid, permittivity
+# ratio eps_wall/eps_slab, charge width 1, near-field cutoff 4 widths).
+WORKLOADS = {
+    "c1_uniform_n128": dict(n=128, Lx=32.0, Ly=32.0, H=32.0, nx=64, ny=64, nz=64, eps_b=1.0, eps_t=1.0, seed=0),
+    "c2_jumps_n16384": dict(n=16384, Lx=128.0, Ly=128.0, H=64.0, nx=256, ny=256, nz=128,
+                            eps_b=1.0 / 80, eps_t=1.0 / 80, seed=1),
+    "c2_metal_bottom_n16384": dict(n=16384, Lx=128.0, Ly=128.0, H=64.0, nx=256, ny=256, nz=128,
+                                   eps_b=float("inf"), eps_t=1.0 / 80, seed=1),
+    "c3_jumps_n1048576": dict(n=1 << 20, Lx=512.0, Ly=512.0, H=128.0, nx=1024, ny=1024, nz=128,
+                              eps_b=1.0 / 80, eps_t=1.0 / 80, seed=2),
+}
+
+
+def workload(name):
+    """Inputs and parameter dict (for dpslab_params) of a named workload:
+    g_w = 1, r_cut = 4 g_w, tolerance 1e-4, charges in [1, H - 1]."""
+    w = dict(WORKLOADS[name])
+    pos, q = electrolyte(w["n"], w["Lx"], w["Ly"], 1.0, w["H"] - 1.0, w["seed"])
+    params = dict(Lx=w["Lx"], Ly=w["Ly"], H=w["H"], eps=1.0, eps_b=w["eps_b"], eps_t=w["eps_t"],
+                  gw=1.0, tol=1e-4, nx=w["nx"], ny=w["ny"], nz=w["nz"], r_cut=4.0)
+    return pos, q, params

@@ -1,0 +1,53 @@
+"""Shared helpers of the GPU parity tests: run the oracle and the CUDA path
+on the same seeded inputs with identical derived parameters."""
+import math
+
+import numpy as np
+
+from oracle import params as oparams, solver as osolver
+from paper_2101_07088_b300 import dpslab
+
+# Parity bar for the FP64 path: relative L2 of forces, relative energy and
+# max |phi error| / max |phi|.
+TOL_FP64 = 1e-10
+
+
+def oracle_params(Lx, Ly, H, gw, tol, nx, ny, nz=0, eps=1.0, eps_b=1.0, eps_t=1.0, xi=0.0, r_cut=0.0, n_sigma=0.0):
+    return oparams.derive(Lx, Ly, H, gw, tol, nx, ny, nz=nz, xi=xi, r_cut=r_cut, eps=eps, eps_b=eps_b,
+                          eps_t=eps_t, n_sigma=n_sigma)
+
+
+def plan_for(P, max_n, precision=dpslab.FP64):
+    """A GPU plan with exactly the oracle's derived xi, r_cut, N_z, n_sigma."""
+    return dpslab.Plan(dpslab.make_params(
+        Lx=P["Lx"], Ly=P["Ly"], H=P["H"], gw=P["gw"], tol=P["tol"], nx=P["nx"], ny=P["ny"], nz=P["nz"],
+        eps=P["eps"], eps_b=P["eps_b"], eps_t=P["eps_t"], xi=P["xi"],
+        r_cut=P["r_cut"] if P["r_cut"] > 0 else 0.0, n_sigma=P["n_sigma"], precision=precision), max_n)
+
+
+def gpu_solve(plan, pos, q, check=True):
+    import torch
+    dev = torch.device("cuda")
+    pos_t = torch.tensor(np.asarray(pos), dtype=torch.float64, device=dev).contiguous()
+    q_t = torch.tensor(np.asarray(q), dtype=torch.float64, device=dev).contiguous()
+    phi = torch.empty(len(q), dtype=torch.float64, device=dev)
+    force = torch.empty((len(q), 3), dtype=torch.float64, device=dev)
+    U, rc = plan.solve(pos_t, q_t, phi, force, check=check)
+    return dict(U=U, phi=phi.cpu().numpy(), force=force.cpu().numpy(), rc=rc)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(np.asarray(b))))
+
+
+def compare(ref, out, tol=TOL_FP64):
+    errs = dict(force=rel_l2(out["force"], ref["force"]),
+                U=abs(out["U"] - ref["U"]) / abs(ref["U"]),
+                phi=rel_max(out["phi"], ref["phi"]))
+    print("parity errors:", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert all(v < tol for v in errs.values()), errs
+    return errs
