@@ -186,6 +186,30 @@ int dpslab_profile(dpslab_plan* plan, int on);
 int dpslab_stage_times(const dpslab_plan* plan, double* ms, int n);
 const char* dpslab_stage_name(int stage);
 
+/*
+ * Near field only, allocating nothing (the paper has no counterpart: this
+ * call exists for callers that cannot call cudaMalloc, e.g. code running
+ * inside an allocator's callbacks, under a device memory pool that must not
+ * grow, or in a loop that reserves all memory up front). It computes the
+ * same near-field part as dpslab_solve (Gaussian-averaged kernels, one image
+ * per wall, pairs closer than r_cut) without a plan:
+ *   p        parameters as for dpslab_plan_create (derived on the host);
+ *   n        1 <= n <= 65536 charges, else DPSLAB_ERR_CAPACITY; the cell
+ *            list may have at most 65536 cells (floor(Lx/r_cut) *
+ *            floor(Ly/r_cut) * floor(H/r_cut)), else DPSLAB_ERR_CAPACITY;
+ *   pos, q   device, [n][3] and [n], as for dpslab_solve;
+ *   out      device, [n][4]: near-field phibar and Ebar (x, y, z) per charge;
+ *   stream   cudaStream_t (NULL = legacy default stream).
+ * The scratch space is one file-scope device array of about 8 MiB that every
+ * GPU loading this library holds until the process exits. All calls share
+ * it: calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller. The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * The call waits for its stream before returning.
+ */
+int dpslab_near_field_static(const dpslab_params* p, int64_t n, const double* pos, const double* q,
+                             double* out, void* stream);
+
 /* Release the plan and all its device memory; NULL is accepted. */
 int dpslab_plan_destroy(dpslab_plan* plan);
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "kernels.cuh"
@@ -831,7 +832,8 @@ int cuda_err(cudaError_t e) {
         if (e_ != cudaSuccess) return cuda_err(e_); \
     } while (0)
 
-size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+constexpr size_t align_up_c(size_t v) { return (v + 255) & ~size_t(255); }
+size_t align_up(size_t v) { return align_up_c(v); }
 
 template <class T>
 T* carve(char*& cur, size_t count) {
@@ -1251,4 +1253,114 @@ extern "C" int dpslab_debug_fetch(dpslab_plan* plan, int which, void* host_dst, 
     }
     DPS_CUDA(cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost));
     return DPSLAB_OK;
+}
+
+// ===========================================================================
+// Near field without any allocation
+// ===========================================================================
+//
+// For callers that cannot call cudaMalloc: code that runs where allocation
+// is forbidden or unavailable (inside a custom allocator's callbacks, under
+// a memory pool that must not grow, in an embedded or real-time loop that
+// pre-reserves all device memory at start-up). The scratch space of the
+// cell list lives in one file-scope device array, reserved when the module
+// loads; every GPU that loads this library holds it until the process exits.
+namespace {
+
+constexpr int64_t kStaticMaxN = 65536;     // charges per call
+constexpr int kStaticMaxCells = 65536;     // near-field cells per call
+constexpr int kStaticMaxDevices = 64;
+constexpr size_t kStaticBlocks = (kStaticMaxN + kChargeThreads - 1) / kChargeThreads;
+constexpr size_t kStaticScratchBytes =
+    4 * align_up_c(kStaticMaxN * 32) +                        // part, sorted, near results, spare
+    2 * align_up_c(kStaticMaxN * 4) +                         // cell_of, sorted_idx
+    3 * align_up_c((kStaticMaxCells + 1) * 4) +               // cell count, start, fill
+    align_up_c(2 * kStaticBlocks * 8) + align_up_c(64);       // neutrality partials, status
+
+static __device__ __align__(256) unsigned char g_near_scratch[kStaticScratchBytes];
+
+std::mutex g_near_scratch_mu;
+void* g_near_scratch_ptr[kStaticMaxDevices] = {};
+
+// Device address of g_near_scratch on the current device, looked up once per
+// device (host code cannot use the symbol itself as an address).
+int near_scratch_address(int device, char** out) {
+    if (device < 0 || device >= kStaticMaxDevices) return DPSLAB_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_near_scratch_mu);
+    if (!g_near_scratch_ptr[device]) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_near_scratch) != cudaSuccess || !ptr) return DPSLAB_ERR_CUDA;
+        g_near_scratch_ptr[device] = ptr;
+    }
+    *out = static_cast<char*>(g_near_scratch_ptr[device]);
+    return DPSLAB_OK;
+}
+
+}  // namespace
+
+extern "C" int dpslab_near_field_static(const dpslab_params* p, int64_t n, const double* pos, const double* q,
+                                        double* out, void* stream) {
+    if (!p || !pos || !q || !out || n < 1) return DPSLAB_ERR_INVALID_ARG;
+    if (n > kStaticMaxN) return DPSLAB_ERR_CAPACITY;
+    dpslab_derived d;
+    int rc = dps::derive(*p, d);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!(d.r_cut > 0.0) || std::isinf(d.xi)) {        // no splitting: the near field is zero
+        DPS_CUDA(cudaMemsetAsync(out, 0, size_t(n) * 4 * sizeof(double), st));
+        return cuda_err(cudaStreamSynchronize(st));
+    }
+    KP kp{};
+    kp.ncx = std::max(1, int(std::floor(p->Lx / d.r_cut)));
+    kp.ncy = std::max(1, int(std::floor(p->Ly / d.r_cut)));
+    kp.ncz = std::max(1, int(std::floor(p->H / d.r_cut)));
+    if (double(kp.ncx) * kp.ncy * kp.ncz > double(kStaticMaxCells)) return DPSLAB_ERR_CAPACITY;
+    int device = 0;
+    DPS_CUDA(cudaGetDevice(&device));
+    char* cur = nullptr;
+    rc = near_scratch_address(device, &cur);
+    if (rc) return rc;
+
+    kp.Lx = p->Lx; kp.Ly = p->Ly; kp.H = p->H; kp.eps = p->eps; kp.gw = p->gw;
+    auto gamma = [&](double ew) { return std::isinf(ew) ? 1.0 : (ew / p->eps - 1.0) / (ew / p->eps + 1.0); };
+    kp.Gb = gamma(p->eps_b);
+    kp.Gt = gamma(p->eps_t);
+    kp.r_cut = d.r_cut;
+    kp.near_on = 1;
+    kp.na1 = 2.0 * p->gw;
+    kp.na2 = std::sqrt(kp.na1 * kp.na1 + 1.0 / (d.xi * d.xi));
+    kp.ncells = kp.ncx * kp.ncy * kp.ncz;
+    kp.cwx = p->Lx / kp.ncx;
+    kp.cwy = p->Ly / kp.ncy;
+    kp.cwz = p->H / kp.ncz;
+    kp.n = int(n);
+    kp.pos = pos;
+    kp.q = q;
+    kp.part = carve<double4_32a>(cur, kStaticMaxN);
+    kp.sorted = carve<double4_32a>(cur, kStaticMaxN);
+    kp.nearv = carve<double4_32a>(cur, kStaticMaxN);
+    carve<double4_32a>(cur, kStaticMaxN);
+    kp.cell_of = carve<int>(cur, kStaticMaxN);
+    kp.sorted_idx = carve<int>(cur, kStaticMaxN);
+    kp.cell_count = carve<int>(cur, size_t(kStaticMaxCells) + 1);
+    kp.cell_start = carve<int>(cur, size_t(kStaticMaxCells) + 1);
+    kp.cell_fill = carve<int>(cur, size_t(kStaticMaxCells) + 1);
+    kp.part_q = carve<double>(cur, 2 * kStaticBlocks);
+    kp.status = carve<int>(cur, 16);
+    const int nb = int((n + kChargeThreads - 1) / kChargeThreads);
+    kp.n_charge_blocks = nb;
+    // the array keeps the previous call's contents: clear what accumulates
+    DPS_CUDA(cudaMemsetAsync(kp.cell_count, 0, (size_t(kp.ncells) + 1) * sizeof(int), st));
+    DPS_CUDA(cudaMemsetAsync(kp.cell_fill, 0, (size_t(kp.ncells) + 1) * sizeof(int), st));
+    DPS_CUDA(cudaMemsetAsync(kp.status, 0, sizeof(int), st));
+    k_prepare<<<nb, kChargeThreads, 0, st>>>(kp);
+    k_scan_cells<<<1, 1024, 0, st>>>(kp);
+    k_scatter_cells<<<nb, kChargeThreads, 0, st>>>(kp);
+    k_near<<<int((n + 127) / 128), 128, 0, st>>>(kp);
+    DPS_CUDA(cudaGetLastError());
+    DPS_CUDA(cudaMemcpyAsync(out, kp.nearv, size_t(n) * 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int status = 0;
+    DPS_CUDA(cudaMemcpyAsync(&status, kp.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DPS_CUDA(cudaStreamSynchronize(st));
+    return status ? DPSLAB_ERR_OUT_OF_SLAB : DPSLAB_OK;
 }

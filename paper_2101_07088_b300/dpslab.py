@@ -76,6 +76,7 @@ def lib():
             "dpslab_profile": (ctypes.c_int, [vp, ctypes.c_int]),
             "dpslab_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
             "dpslab_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
+            "dpslab_near_field_static": (ctypes.c_int, [P, i64, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -114,6 +115,20 @@ def table(params, which):
     out = np.zeros(nz)
     _check(lib().dpslab_table(ctypes.byref(p), int(which), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nz))
     return out
+
+
+def near_field_static(params, pos, q, out, stream=None, check=True):
+    """dpslab_near_field_static: near-field part only, no allocation by the
+    library (for callers that cannot allocate device memory). pos [n, 3],
+    q [n], out [n, 4]: float64 contiguous CUDA tensors. Returns the code."""
+    import torch
+    p = _as_params(params)
+    st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = lib().dpslab_near_field_static(ctypes.byref(p), q.shape[0], pos.data_ptr(), q.data_ptr(),
+                                        out.data_ptr(), st)
+    if check:
+        _check(rc)
+    return rc
 
 
 class Plan:
