@@ -22,8 +22,18 @@ struct Complex {
 struct Tables {
     std::vector<double> zn;          // Chebyshev nodes z_j, descending, Sec. 5.2.2
     std::vector<double> wz;          // Clenshaw-Curtis weights times Hbar/2
-    std::vector<double> cf;          // [n][j]: node values -> Chebyshev coefficients
-    std::vector<double> ti;          // [j][n]: T_n(s_j) = cos(pi n j/(N-1))
+    // Chebyshev transforms on the extrema grid split by the symmetry
+    // cos(pi n (m-j)/m) = (-1)^n cos(pi n j/m), m = N-1: with
+    // S_a = v_a + v_{m-a}, D_a = v_a - v_{m-a} (a < m-a; S = v at a middle
+    // node), even coefficients use S and odd ones D:
+    // cft[a][q], q < N: row q < (N+1)/2 is even n = 2q (input S_a), row
+    // q >= (N+1)/2 is odd n = 2(q - (N+1)/2) + 1 (input D_a), a < (N+1)/2
+    // (entries with no input are 0); stored input-major so that consecutive
+    // output rows are consecutive in memory.
+    std::vector<double> cft;
+    // values at nodes a and m-a are E +/- O, E (O) the sum over even (odd) n:
+    std::vector<double> tie;         // [n/2][a] = cos(pi n a/m), even n, a < (N+1)/2
+    std::vector<double> tio;         // [(n-1)/2][a], odd n
     std::vector<double> j2l, j2d, j2u;   // diagonals (n-2, n, n+2) of J^2, Appendix A
     std::vector<double> u1, u2, v1, v2;  // 1^T J, 1^T J^2, (-1)^T J, (-1)^T J^2
     std::vector<double> t0, tH;      // T_n(s(0)), T_n(s(H))

@@ -45,8 +45,8 @@ struct KP {
     // tables
     const double* zn;
     const double* wz;
-    const double* cf;
-    const double* ti;
+    const double* cft;        // split forward transform, input-major (see Tables)
+    const double *tie, *tio;  // split inverse transform, [n/2][a]
     const double *j2l, *j2d, *j2u, *u1, *u2, *v1, *v2, *t0, *tH, *wg;
     const double2* twx;
     const double2* twy;

@@ -169,17 +169,23 @@ int build_tables(const dpslab_params& p, const dpslab_derived& d, Tables& t) {
         t.wz[j] = double(cj / m * s * 0.5L * d.Hbar);
     }
 
-    // Chebyshev transforms on the extrema grid (DCT-I form)
-    t.cf.assign(size_t(N) * N, 0.0);
-    t.ti.assign(size_t(N) * N, 0.0);
-    for (int n = 0; n < N; ++n) {
-        for (int j = 0; j < N; ++j) {
-            const double c = cs[(size_t(n) * j) % (2 * m)];
-            const double wj = (j == 0 || j == m) ? 0.5 : 1.0;
-            const double wn = (n == 0 || n == m) ? 0.5 : 1.0;
-            t.cf[size_t(n) * N + j] = 2.0 / m * wj * wn * c;
-            t.ti[size_t(j) * N + n] = c;
-        }
+    // Chebyshev transforms on the extrema grid (DCT-I form):
+    // fhat_n = (2/m) w_n sum_j w_j v_j cos(pi n j/m), w = 1/2 at the ends
+    const int JE = (N + 1) / 2, JO = N / 2;
+    auto fwd = [&](int n, int j) {
+        const double wj = (j == 0 || j == m) ? 0.5 : 1.0;
+        const double wn = (n == 0 || n == m) ? 0.5 : 1.0;
+        return 2.0 / m * wj * wn * cs[(size_t(n) * j) % (2 * m)];
+    };
+    t.cft.assign(size_t(JE) * N, 0.0);
+    t.tie.assign(size_t(JE) * JE, 0.0);
+    t.tio.assign(size_t(JO) * JE, 0.0);
+    for (int a = 0; a < JE; ++a) {
+        for (int q = 0; q < JE; ++q) t.cft[size_t(a) * N + q] = fwd(2 * q, a);
+        if (a < JO)
+            for (int q = 0; q < JO; ++q) t.cft[size_t(a) * N + JE + q] = fwd(2 * q + 1, a);
+        for (int r = 0; r < JE; ++r) t.tie[size_t(r) * JE + a] = cs[(size_t(2 * r) * a) % (2 * m)];
+        for (int r = 0; r < JO; ++r) t.tio[size_t(r) * JE + a] = cs[(size_t(2 * r + 1) * a) % (2 * m)];
     }
 
     // Appendix A: J maps coefficients of a function to those of its integral

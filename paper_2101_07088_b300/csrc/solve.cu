@@ -15,8 +15,8 @@ using namespace dps;
 
 namespace {
 
-constexpr int kColBlock = 8;        // k_par columns per block of the column kernel
-constexpr int kColThreads = 256;
+constexpr int kColBlock = 4;        // k_par columns per block of the column kernel (one warp each)
+constexpr int kColThreads = 32 * kColBlock;
 constexpr int kChargeThreads = 256;
 constexpr int kInterpWarps = 8;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
@@ -255,19 +255,42 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
     }
     __syncthreads();
 
-    // coefficients f_n = sum_j cf[n][j] v_j, then F = -(Hbar/2)^2 f / eps
-    const double scale = -(0.5 * Hbar) * (0.5 * Hbar) / kp.eps;
-    for (int t = tid; t < 2 * CB * N; t += bs) {
-        const int f = t / (CB * N), r = t - f * CB * N, n = r / CB, c = r - n * CB;
-        const double2* V = (f ? Vo : Vi) + c * N;
-        const double* row = kp.cf + size_t(n) * N;
-        double ax = 0.0, ay = 0.0;
-        for (int j = 0; j < N; ++j) {
-            const double w = row[j];
-            ax = fma(w, V[j].x, ax);
-            ay = fma(w, V[j].y, ay);
+    // coefficients f_n = sum_j cf[n][j] v_j, then F = -(Hbar/2)^2 f / eps,
+    // split by the node symmetry: V[a] <- v_a + v_{m-a}, V[m-a] <- v_a - v_{m-a}
+    const int m = N - 1, JE = (N + 1) / 2, JO = N / 2;
+    for (int t = tid; t < 2 * CB * JE; t += bs) {
+        const int f = t / (CB * JE), r = t - f * CB * JE, c = r / JE, a = r - c * JE;
+        if (a < m - a) {
+            double2* V = (f ? Vo : Vi) + c * N;
+            const double2 va = V[a], vb = V[m - a];
+            V[a] = cadd(va, vb);
+            V[m - a] = csub(va, vb);
         }
-        (f ? Co : Ci)[c * N + n] = make_double2(ax * scale, ay * scale);
+    }
+    __syncthreads();
+    const double scale = -(0.5 * Hbar) * (0.5 * Hbar) / kp.eps;
+    // thread (c, q): output row q of both densities; q < JE even n = 2q from
+    // S_a = V[a], q >= JE odd n from D_a = V[m - a]; lanes run over q so the
+    // table loads are contiguous and the V loads are broadcasts
+    for (int t = tid; t < CB * N; t += bs) {
+        const int c = t / N, q = t - c * N;
+        const bool odd = q >= JE;
+        const int na = odd ? JO : JE;
+        const double2* vi = Vi + c * N;
+        const double2* vo = Vo + c * N;
+        double ix = 0.0, iy = 0.0, ox = 0.0, oy = 0.0;
+        for (int a = 0; a < na; ++a) {
+            const double w = kp.cft[size_t(a) * N + q];
+            const int ia = odd ? m - a : a;
+            const double2 u = vi[ia], v = vo[ia];
+            ix = fma(w, u.x, ix);
+            iy = fma(w, u.y, iy);
+            ox = fma(w, v.x, ox);
+            oy = fma(w, v.y, oy);
+        }
+        const int n = odd ? 2 * (q - JE) + 1 : 2 * q;
+        Ci[c * N + n] = make_double2(ix * scale, iy * scale);
+        Co[c * N + n] = make_double2(ox * scale, oy * scale);
     }
     __syncthreads();
 
@@ -309,39 +332,44 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
     __syncthreads();
 
     // 2x2 Schur complement for the integration constants (y_0, y'_0) = (c, d)
-    // from the two boundary rows (Eq. (BCs); Eq. (BCs0) for k = 0)
-    if (tid < 2 * CB) {
-        const int c = tid >> 1, f = tid & 1;
+    // from the two boundary rows (Eq. (BCs); Eq. (BCs0) for k = 0); warp w
+    // handles column w, lanes split the sums over n
+    {
+        const int c = tid >> 5, lane = tid & 31;
         const double K = s_K[c];
-        const double2* X = (f ? Co : Ci) + c * N;
+        const double2* Xi = Ci + c * N;
+        const double2* Xo = Co + c * N;
         const double* xc = xe + c * N;
-        double2 cc, dd;
-        if (K > 0.0) {
-            double2 sFt = make_double2(0.0, 0.0), sFb = sFt;
-            double sct = 0.0, sdt = 0.0, scb = 0.0, sdb = 0.0;
-            for (int n = 0; n < N; ++n) {
-                const double gtn = kp.u1[n] + K * kp.u2[n];
-                const double gbn = kp.v1[n] - K * kp.v2[n];
-                sFt = cadd(sFt, cscale(X[n], gtn));
-                sFb = cadd(sFb, cscale(X[n], gbn));
-                if (n & 1) { sdt += gtn * xc[n]; sdb += gbn * xc[n]; }
-                else { sct += gtn * xc[n]; scb += gbn * xc[n]; }
-            }
-            const double m11 = K + sct, m12 = 1.0 + K + sdt, m21 = -K + scb, m22 = 1.0 + K + sdb;
-            const double idet = 1.0 / (m11 * m22 - m12 * m21);
-            cc = cscale(csub(cscale(sFt, m22), cscale(sFb, m12)), -idet);
-            dd = cscale(csub(cscale(sFb, m11), cscale(sFt, m21)), -idet);
-        } else {
-            double2 a = make_double2(0.0, 0.0), b = a;
-            for (int n = 0; n < N; ++n) {
-                a = cadd(a, cscale(X[n], kp.u2[n]));
-                b = cadd(b, cscale(X[n], kp.v2[n]));
-            }
-            cc = cscale(cadd(a, b), -0.5);
-            dd = cscale(csub(a, b), -0.5);
+        double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int n = lane; n < N; n += 32) {
+            const double gtn = K > 0.0 ? kp.u1[n] + K * kp.u2[n] : kp.u2[n];
+            const double gbn = K > 0.0 ? kp.v1[n] - K * kp.v2[n] : kp.v2[n];
+            acc[0] = fma(gtn, Xi[n].x, acc[0]); acc[1] = fma(gtn, Xi[n].y, acc[1]);
+            acc[2] = fma(gbn, Xi[n].x, acc[2]); acc[3] = fma(gbn, Xi[n].y, acc[3]);
+            acc[4] = fma(gtn, Xo[n].x, acc[4]); acc[5] = fma(gtn, Xo[n].y, acc[5]);
+            acc[6] = fma(gbn, Xo[n].x, acc[6]); acc[7] = fma(gbn, Xo[n].y, acc[7]);
+            if (n & 1) { acc[9] = fma(gtn, xc[n], acc[9]); acc[11] = fma(gbn, xc[n], acc[11]); }
+            else { acc[8] = fma(gtn, xc[n], acc[8]); acc[10] = fma(gbn, xc[n], acc[10]); }
         }
-        s_c[f][c] = cc;
-        s_d[f][c] = dd;
+        for (int i = 0; i < 12; ++i) acc[i] = warp_sum(acc[i]);
+        if (lane < 2) {
+            const int f = lane;
+            const double2 sFt = f ? make_double2(acc[4], acc[5]) : make_double2(acc[0], acc[1]);
+            const double2 sFb = f ? make_double2(acc[6], acc[7]) : make_double2(acc[2], acc[3]);
+            double2 cc, dd;
+            if (K > 0.0) {
+                const double m11 = K + acc[8], m12 = 1.0 + K + acc[9], m21 = -K + acc[10], m22 = 1.0 + K + acc[11];
+                const double idet = 1.0 / (m11 * m22 - m12 * m21);
+                cc = cscale(csub(cscale(sFt, m22), cscale(sFb, m12)), -idet);
+                dd = cscale(csub(cscale(sFb, m11), cscale(sFt, m21)), -idet);
+            } else {
+                // sum y_n = c + d + u2.y'' = 0, sum (-1)^n y_n = c - d + v2.y'' = 0
+                cc = cscale(cadd(sFt, sFb), -0.5);
+                dd = cscale(csub(sFt, sFb), -0.5);
+            }
+            s_c[f][c] = cc;
+            s_d[f][c] = dd;
+        }
     }
     __syncthreads();
     // y'' = x_F + c x_c + d x_d
@@ -376,98 +404,117 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
     __syncthreads();
 
     // boundary values, mismatches Eq. (mm1)-(mm4), correction coefficients,
-    // k = 0 slope, gauge partial sum
-    if (tid < CB && s_valid[tid]) {
-        const int c = tid;
+    // k = 0 slope, gauge partial sum (warp per column, lanes over n)
+    {
+        const int c = tid >> 5, lane = tid & 31;
         const double2 *yi = Ci + c * N, *ypi = Vi + c * N, *yo = Co + c * N, *ypo = Vo + c * N;
-        double2 pi0 = make_double2(0, 0), dpi0 = pi0, piH = pi0, dpiH = pi0, po0 = pi0, dpo0 = pi0,
-                poH = pi0, dpoH = pi0, dpoa = pi0, dpob = pi0, gs = pi0;
-        for (int n = 0; n < N; ++n) {
+        double acc[22];
+        for (int i = 0; i < 22; ++i) acc[i] = 0.0;
+        for (int n = lane; n < N; n += 32) {
             const double a0 = kp.t0[n], aH = kp.tH[n], alt = (n & 1) ? -1.0 : 1.0, wg = kp.wg[n];
-            pi0 = cadd(pi0, cscale(yi[n], a0));
-            dpi0 = cadd(dpi0, cscale(ypi[n], a0));
-            piH = cadd(piH, cscale(yi[n], aH));
-            dpiH = cadd(dpiH, cscale(ypi[n], aH));
-            po0 = cadd(po0, cscale(yo[n], a0));
-            dpo0 = cadd(dpo0, cscale(ypo[n], a0));
-            poH = cadd(poH, cscale(yo[n], aH));
-            dpoH = cadd(dpoH, cscale(ypo[n], aH));
-            dpoa = cadd(dpoa, cscale(ypo[n], alt));
-            dpob = cadd(dpob, ypo[n]);
-            gs = cadd(gs, cscale(yi[n], wg));
+            acc[0] = fma(a0, yi[n].x, acc[0]);   acc[1] = fma(a0, yi[n].y, acc[1]);     // psi_i*(0)
+            acc[2] = fma(a0, ypi[n].x, acc[2]);  acc[3] = fma(a0, ypi[n].y, acc[3]);    // psi_i*'(0)
+            acc[4] = fma(aH, yi[n].x, acc[4]);   acc[5] = fma(aH, yi[n].y, acc[5]);     // psi_i*(H)
+            acc[6] = fma(aH, ypi[n].x, acc[6]);  acc[7] = fma(aH, ypi[n].y, acc[7]);    // psi_i*'(H)
+            acc[8] = fma(a0, yo[n].x, acc[8]);   acc[9] = fma(a0, yo[n].y, acc[9]);     // psi_o*(0)
+            acc[10] = fma(a0, ypo[n].x, acc[10]); acc[11] = fma(a0, ypo[n].y, acc[11]); // psi_o*'(0)
+            acc[12] = fma(aH, yo[n].x, acc[12]); acc[13] = fma(aH, yo[n].y, acc[13]);   // psi_o*(H)
+            acc[14] = fma(aH, ypo[n].x, acc[14]); acc[15] = fma(aH, ypo[n].y, acc[15]); // psi_o*'(H)
+            acc[16] = fma(alt, ypo[n].x, acc[16]); acc[17] += ypo[n].x;                // psi_o*'(a), (b)
+            acc[18] = fma(wg, yi[n].x, acc[18]); acc[19] = fma(wg, yi[n].y, acc[19]);   // gauge sum
         }
-        const double dz = 2.0 / Hbar;
-        dpi0 = cscale(dpi0, dz); dpiH = cscale(dpiH, dz); dpo0 = cscale(dpo0, dz);
-        dpoH = cscale(dpoH, dz); dpoa = cscale(dpoa, dz); dpob = cscale(dpob, dz);
-        const double k = s_k[c];
-        double2 corr0 = make_double2(0.0, 0.0);
-        if (s_corr[c]) {
-            const double2 mpb = csub(pi0, cscale(po0, kp.tb));
-            const double2 meb = csub(dpi0, cscale(dpo0, kp.rtb));
-            const double2 mpt = csub(piH, cscale(poH, kp.tt));
-            const double2 met = csub(dpiH, cscale(dpoH, kp.rtt));
-            const double2 P = csub(cscale(mpb, kp.cb), cscale(meb, kp.db / k));
-            const double2 Q = csub(cscale(mpt, -kp.ct), cscale(met, kp.dt / k));
-            const double ekH = exp(-k * kp.H);
-            const double den = 1.0 - kp.Gb * kp.Gt * ekH * ekH;
-            s_P[c] = P;
-            s_Q[c] = Q;
-            s_ekH[c] = ekH;
-            s_den[c] = den;
-            corr0 = cscale(cadd(cscale(P, -(1.0 - kp.Gt * ekH * ekH)), cscale(Q, ekH - kp.Gb * ekH)), 1.0 / den);
+        for (int i = 0; i < 20; ++i) acc[i] = warp_sum(acc[i]);
+        if (lane == 0 && s_valid[c]) {
+            const double dz = 2.0 / Hbar;
+            const double2 pi0 = make_double2(acc[0], acc[1]), dpi0 = make_double2(acc[2] * dz, acc[3] * dz);
+            const double2 piH = make_double2(acc[4], acc[5]), dpiH = make_double2(acc[6] * dz, acc[7] * dz);
+            const double2 po0 = make_double2(acc[8], acc[9]), dpo0 = make_double2(acc[10] * dz, acc[11] * dz);
+            const double2 poH = make_double2(acc[12], acc[13]), dpoH = make_double2(acc[14] * dz, acc[15] * dz);
+            const double dpoa = acc[16] * dz, dpob = acc[17] * dz;
+            const double k = s_k[c];
+            double2 corr0 = make_double2(0.0, 0.0);
+            if (s_corr[c]) {
+                const double2 mpb = csub(pi0, cscale(po0, kp.tb));
+                const double2 meb = csub(dpi0, cscale(dpo0, kp.rtb));
+                const double2 mpt = csub(piH, cscale(poH, kp.tt));
+                const double2 met = csub(dpiH, cscale(dpoH, kp.rtt));
+                const double2 P = csub(cscale(mpb, kp.cb), cscale(meb, kp.db / k));
+                const double2 Q = csub(cscale(mpt, -kp.ct), cscale(met, kp.dt / k));
+                const double ekH = exp(-k * kp.H);
+                const double den = 1.0 - kp.Gb * kp.Gt * ekH * ekH;
+                s_P[c] = P;
+                s_Q[c] = Q;
+                s_ekH[c] = ekH;
+                s_den[c] = den;
+                corr0 = cscale(cadd(cscale(P, -(1.0 - kp.Gt * ekH * ekH)), cscale(Q, ekH - kp.Gb * ekH)), 1.0 / den);
+            }
+            if (col0 + c == 0) {
+                // Sec. 4.3.4: Eq. (CE), (ai1), (ai2); mean, or the non-metal wall's
+                // equation, or equal wall potentials for two metal walls
+                const double ai1 = kp.rtb * (dpo0.x - dpoa) - dpi0.x;
+                const double ai2 = kp.rtt * (dpoH.x - dpob) - dpiH.x;
+                double Ai;
+                if (kp.metal_b && kp.metal_t) Ai = -(piH.x - pi0.x) / kp.H;
+                else if (kp.metal_b) Ai = ai2;
+                else if (kp.metal_t) Ai = ai1;
+                else Ai = 0.5 * (ai1 + ai2);
+                s_Ai = Ai;
+                kp.scal[1] = Ai;
+            }
+            const double damp = exp(-0.5 * kp.sigma2 * k * k);
+            s_gauge[c] = s_mult[c] * (damp * acc[18] + corr0.x);
         }
-        if (col0 + c == 0) {
-            // Sec. 4.3.4: Eq. (CE), (ai1), (ai2); mean, or the non-metal wall's
-            // equation, or equal wall potentials for two metal walls
-            const double ai1 = kp.rtb * (dpo0.x - dpoa.x) - dpi0.x;
-            const double ai2 = kp.rtt * (dpoH.x - dpob.x) - dpiH.x;
-            double Ai;
-            if (kp.metal_b && kp.metal_t) Ai = -(piH.x - pi0.x) / kp.H;
-            else if (kp.metal_b) Ai = ai2;
-            else if (kp.metal_t) Ai = ai1;
-            else Ai = 0.5 * (ai1 + ai2);
-            s_Ai = Ai;
-            kp.scal[1] = Ai;
-        }
-        const double damp = exp(-0.5 * kp.sigma2 * k * k);
-        s_gauge[c] = s_mult[c] * (damp * gs.x + corr0.x);
     }
     __syncthreads();
 
-    // node values of psi_i and dpsi_i/dz (+ correction, + A_i z for k = 0)
+    // node values of psi_i and dpsi_i/dz (+ correction, + A_i z for k = 0):
+    // nodes a and m-a from the even (E) and odd (O) coefficient sums, E +/- O
     const double Ai = s_Ai;
-    for (int t = tid; t < N * CB; t += bs) {
-        const int j = t / CB, c = t - j * CB, col = col0 + c;
+    for (int t = tid; t < JE * CB; t += bs) {
+        const int c = t / JE, a = t - c * JE, col = col0 + c;
         if (col >= M) continue;
-        const double* trow = kp.ti + size_t(j) * N;
         const double2* yi = Ci + c * N;
         const double2* ypi = Vi + c * N;
-        double px = 0, py = 0, dx = 0, dy = 0;
-        for (int n = 0; n < N; ++n) {
-            const double w = trow[n];
-            px = fma(w, yi[n].x, px);
-            py = fma(w, yi[n].y, py);
-            dx = fma(w, ypi[n].x, dx);
-            dy = fma(w, ypi[n].y, dy);
+        double ex = 0, ey = 0, dex = 0, dey = 0, ox = 0, oy = 0, dox = 0, doy = 0;
+        for (int r = 0; r < JE; ++r) {
+            const double w = kp.tie[size_t(r) * JE + a];
+            ex = fma(w, yi[2 * r].x, ex);
+            ey = fma(w, yi[2 * r].y, ey);
+            dex = fma(w, ypi[2 * r].x, dex);
+            dey = fma(w, ypi[2 * r].y, dey);
         }
-        double2 ps = make_double2(px, py), dps = make_double2(dx * (2.0 / Hbar), dy * (2.0 / Hbar));
-        const double z = kp.zn[j];
-        if (s_corr[c] && z >= -kp.HE && z <= kp.H + kp.HE) {
-            const double k = s_k[c], ekH = s_ekH[c], iden = 1.0 / s_den[c];
-            const double e1 = exp(-k * z), e3 = exp(k * (z - kp.H));
-            const double e2 = e3 * ekH, e4 = e1 * ekH;
-            const double2 P = s_P[c], Q = s_Q[c];
-            const double2 val = cscale(cadd(cscale(P, -(e1 - kp.Gt * e2)), cscale(Q, e3 - kp.Gb * e4)), iden);
-            const double2 der = cscale(cadd(cscale(P, e1 + kp.Gt * e2), cscale(Q, e3 + kp.Gb * e4)), k * iden);
-            ps = cadd(ps, val);
-            dps = cadd(dps, der);
+        for (int r = 0; r < JO; ++r) {
+            const double w = kp.tio[size_t(r) * JE + a];
+            ox = fma(w, yi[2 * r + 1].x, ox);
+            oy = fma(w, yi[2 * r + 1].y, oy);
+            dox = fma(w, ypi[2 * r + 1].x, dox);
+            doy = fma(w, ypi[2 * r + 1].y, doy);
         }
-        if (col == 0) {
-            ps.x += Ai * z;
-            dps.x += Ai;
+        const double sz = 2.0 / Hbar;
+        for (int side = 0; side < 2; ++side) {
+            const int j = side ? m - a : a;
+            if (side && j == a) break;
+            const double sg = side ? -1.0 : 1.0;
+            double2 ps = make_double2(ex + sg * ox, ey + sg * oy);
+            double2 dps = make_double2((dex + sg * dox) * sz, (dey + sg * doy) * sz);
+            const double z = kp.zn[j];
+            if (s_corr[c] && z >= -kp.HE && z <= kp.H + kp.HE) {
+                const double k = s_k[c], ekH = s_ekH[c], iden = 1.0 / s_den[c];
+                const double e1 = exp(-k * z), e3 = exp(k * (z - kp.H));
+                const double e2 = e3 * ekH, e4 = e1 * ekH;
+                const double2 P = s_P[c], Q = s_Q[c];
+                const double2 val = cscale(cadd(cscale(P, -(e1 - kp.Gt * e2)), cscale(Q, e3 - kp.Gb * e4)), iden);
+                const double2 der = cscale(cadd(cscale(P, e1 + kp.Gt * e2), cscale(Q, e3 + kp.Gb * e4)), k * iden);
+                ps = cadd(ps, val);
+                dps = cadd(dps, der);
+            }
+            if (col == 0) {
+                ps.x += Ai * z;
+                dps.x += Ai;
+            }
+            kp.spec[size_t(j) * M + col] = ps;
+            kp.spec[size_t(N + j) * M + col] = dps;
         }
-        kp.spec[size_t(j) * M + col] = ps;
-        kp.spec[size_t(N + j) * M + col] = dps;
     }
     const double g = block_sum(tid < CB ? s_gauge[tid] : 0.0);
     if (tid == 0) kp.part_gauge_far[blockIdx.x] = g;
@@ -951,7 +998,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         const size_t N = nz;
         size_t bytes = 0;
         const size_t vec = align_up(N * sizeof(double));
-        bytes += 2 * vec + 2 * align_up(N * N * sizeof(double)) + 11 * vec;
+        bytes += 2 * vec + 4 * align_up(N * N * sizeof(double)) + 11 * vec;
         bytes += align_up(nx * sizeof(double2)) + align_up(ny * sizeof(double2));
         cudaError_t e = cudaMalloc(&pl->tables, bytes);
         if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
@@ -962,7 +1009,8 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
             cudaMemcpy(dp, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
             dst = dp;
         };
-        up(t.zn, kp.zn); up(t.wz, kp.wz); up(t.cf, kp.cf); up(t.ti, kp.ti);
+        up(t.zn, kp.zn); up(t.wz, kp.wz);
+        up(t.cft, kp.cft); up(t.tie, kp.tie); up(t.tio, kp.tio);
         up(t.j2l, kp.j2l); up(t.j2d, kp.j2d); up(t.j2u, kp.j2u);
         up(t.u1, kp.u1); up(t.u2, kp.u2); up(t.v1, kp.v1); up(t.v2, kp.v2);
         up(t.t0, kp.t0); up(t.tH, kp.tH); up(t.wg, kp.wg);
