@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="c2_jumps_n16384")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=150.0)
@@ -198,7 +199,7 @@ def main():
     wl = synth.WORKLOADS[args.workload]
     config = dict(workload=args.workload, charges=n, box=[p["Lx"], p["Ly"], p["H"]],
                   grid=[p["nx"], p["ny"], p["nz"]], eps_wall_over_eps=[p["eps_b"], p["eps_t"]],
-                  gw=p["gw"], r_cut=p["r_cut"], tol=p["tol"], precision="fp64",
+                  gw=p["gw"], r_cut=p["r_cut"], tol=p["tol"], precision=args.precision,
                   parallelism=f"replicas{world}", l2="512 MiB memset between timed steps")
 
     if args.impl == "reference":
@@ -235,7 +236,8 @@ def main():
     # each rank solves its own system (independent seed)
     if world > 1:
         pos, q = synth.electrolyte(n, p["Lx"], p["Ly"], 1.0, p["H"] - 1.0, wl["seed"] + 1000 * rank)
-    plan = dpslab.Plan(dpslab.make_params(**p), n)
+    prec = dpslab.MIXED if args.precision == "mixed" else dpslab.FP64
+    plan = dpslab.Plan(dpslab.make_params(precision=prec, **p), n)
     d = plan.derived
     pos_t = torch.tensor(pos, dtype=torch.float64, device=dev)
     q_t = torch.tensor(q, dtype=torch.float64, device=dev)
@@ -307,7 +309,7 @@ def main():
 
     # roofline of the dominant stage
     over = int(np.sum((pos[:, 2] <= 2 * d["HE"]) | (pos[:, 2] >= p["H"] - 2 * d["HE"])))
-    work, fft_flops = stage_work(d, n, over)
+    work, fft_flops = stage_work(d, n, over, wbytes=4 if args.precision == "mixed" else 8)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
     top = max(stage_ms, key=stage_ms.get)
     pk = peaks()
@@ -327,7 +329,8 @@ def main():
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=mean_ms, p50_ms=p50, p99_ms=p99, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic", config=config,
+                vs_baseline=None, dtype="f64" if args.precision == "fp64" else "f32+f64", data="synthetic",
+                config=config,
                 e2e=dict(value=n * world / (e2e_mean * 1e-3), unit=UNIT, ms_per_step=e2e_mean,
                          h2d_bytes_per_step=n * 4 * 8, d2h_bytes_per_step=n * 4 * 8 + 8 + 8 * 8 + 4),
                 gpu_launches=launches, roofline=roof, clocks=clk, wall_s=wall,

@@ -28,14 +28,26 @@ __device__ __forceinline__ double2 cmul_i(double2 a, int dir) {
     return dir < 0 ? make_double2(a.y, -a.x) : make_double2(-a.y, a.x);
 }
 
-__device__ __forceinline__ double2 twiddle(const double2* tw, int k, int dir) {
-    const double2 w = tw[k];
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul_i(float2 a, int dir) {
+    return dir < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+template <class C>
+__device__ __forceinline__ C twiddle(const C* tw, int k, int dir) {
+    const C w = tw[k];
     return dir < 0 ? w : cconj(w);
 }
 
 // Returns the buffer holding the result (a or b). Ends with __syncthreads().
-__device__ inline double2* block_fft(double2* a, double2* b, const double2* tw, int n, int nseq,
-                                     const int* radices, int nstages, int dir) {
+template <class C>
+__device__ inline C* block_fft(C* a, C* b, const C* tw, int n, int nseq, const int* radices, int nstages, int dir) {
     int Ns = 1;
     for (int s = 0; s < nstages; ++s) {
         const int R = radices[s];
@@ -45,29 +57,29 @@ __device__ inline double2* block_fft(double2* a, double2* b, const double2* tw, 
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
             const int q = t / nR;
             const int j = t - q * nR;
-            const double2* x = a + q * n;
-            double2* y = b + q * n;
+            const C* x = a + q * n;
+            C* y = b + q * n;
             const int jm = j % Ns;
             const int out0 = (j / Ns) * Ns * R + jm;
             if (R == 4) {
-                double2 v0 = x[j];
-                double2 v1 = x[j + nR];
-                double2 v2 = x[j + 2 * nR];
-                double2 v3 = x[j + 3 * nR];
+                C v0 = x[j];
+                C v1 = x[j + nR];
+                C v2 = x[j + 2 * nR];
+                C v3 = x[j + 3 * nR];
                 if (jm) {
                     v1 = cmul(v1, twiddle(tw, jm * step, dir));
                     v2 = cmul(v2, twiddle(tw, 2 * jm * step, dir));
                     v3 = cmul(v3, twiddle(tw, 3 * jm * step, dir));
                 }
-                const double2 s02 = cadd(v0, v2), d02 = csub(v0, v2);
-                const double2 s13 = cadd(v1, v3), d13 = cmul_i(csub(v1, v3), dir);
+                const C s02 = cadd(v0, v2), d02 = csub(v0, v2);
+                const C s13 = cadd(v1, v3), d13 = cmul_i(csub(v1, v3), dir);
                 y[out0] = cadd(s02, s13);
                 y[out0 + Ns] = cadd(d02, d13);
                 y[out0 + 2 * Ns] = csub(s02, s13);
                 y[out0 + 3 * Ns] = csub(d02, d13);
             } else if (R == 2) {
-                double2 v0 = x[j];
-                double2 v1 = x[j + nR];
+                C v0 = x[j];
+                C v1 = x[j + nR];
                 if (jm) v1 = cmul(v1, twiddle(tw, jm * step, dir));
                 y[out0] = cadd(v0, v1);
                 y[out0 + Ns] = csub(v0, v1);
@@ -75,7 +87,7 @@ __device__ inline double2* block_fft(double2* a, double2* b, const double2* tw, 
                 // y[out0 + r' Ns] = sum_r x[j + r nR] w^(r (jm step + r' nR))
                 for (int rp = 0; rp < R; ++rp) {
                     const int e = (jm * step + rp * nR) % n;
-                    double2 acc = x[j];
+                    C acc = x[j];
                     int idx = 0;
                     for (int r = 1; r < R; ++r) {
                         idx += e;
@@ -87,7 +99,7 @@ __device__ inline double2* block_fft(double2* a, double2* b, const double2* tw, 
             }
         }
         __syncthreads();
-        double2* tmp = a;
+        C* tmp = a;
         a = b;
         b = tmp;
         Ns *= R;

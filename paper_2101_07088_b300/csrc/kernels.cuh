@@ -37,11 +37,13 @@ struct KP {
     const double* pos;
     const double* q;
     double4_32a* part;            // sanitised (x, y, z, q)
-    // grids
-    double* rho;              // [2][nz][ny][nx]
-    double2* spec;            // [2][nz][ny][nxh]
-    double2* specB;           // [nz][ny][nxh]
-    double4_32a* fields;          // [nz][ny][nx] (phi, Ex, Ey, Ez)
+    // grids, in the plan's grid precision R (double for DPSLAB_FP64, float
+    // for DPSLAB_MIXED)
+    void* rho;                // R [2][nz][ny][nx]
+    void* spec;               // complex R [2][nz][ny][nxh]
+    void* specB;              // complex R [nz][ny][nxh]
+    void* fields;             // R4 [nz][ny][nx] (phi, Ex, Ey, Ez)
+    int mixed;
     // tables
     const double* zn;
     const double* wz;
@@ -50,6 +52,10 @@ struct KP {
     const double *j2l, *j2d, *j2u, *u1, *u2, *v1, *v2, *t0, *tH, *wg;
     const double2* twx;
     const double2* twy;
+    const float2* twx32;      // the same twiddles rounded to float
+    const float2* twy32;
+    // float copies of the column tables (mixed precision)
+    const float *cft32, *tie32, *tio32, *j2l32, *j2d32, *j2u32, *u132, *u232, *v132, *v232, *t032, *tH32, *wg32;
     int radx[kMaxStages], rady[kMaxStages];
     int nradx, nrady;
     // particle outputs
@@ -77,6 +83,23 @@ struct KP {
     double* out_force;
 };
 
+template <class R> struct Prec;
+template <> struct Prec<double> {
+    using C = double2;
+    using V4 = double4_32a;
+    static __device__ __forceinline__ V4 v4(double a, double b, double c, double d) { return make_double4_32a(a, b, c, d); }
+};
+template <> struct Prec<float> {
+    using C = float2;
+    using V4 = float4;
+    static __device__ __forceinline__ V4 v4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double derf(double x) { return erf(x); }
+__device__ __forceinline__ float derf(float x) { return erff(x); }
+__device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+
 __device__ __forceinline__ double np_mod(double x, double L) {
     // numpy float remainder: fmod, then shifted into the sign of L
     double r = fmod(x, L);
@@ -87,28 +110,29 @@ __device__ __forceinline__ double np_mod(double x, double L) {
 __device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
 
 // erf(r/a)/r and (1/r) d/dr[erf(r/a)/r]; series for r < 1e-3 g_w (end of Sec. 3.2)
-__device__ __forceinline__ void erf_over_r(double r, double a, bool small, double& val, double& der) {
-    const double x = r / a;
-    const double c = 1.1283791670955126 / a;   // 2/(sqrt(pi) a)
+template <class R>
+__device__ __forceinline__ void erf_over_r(R r, R a, bool small, R& val, R& der) {
+    const R x = r / a;
+    const R c = R(1.1283791670955126) / a;   // 2/(sqrt(pi) a)
     if (small) {
-        const double x2 = x * x;
-        val = c * (1.0 - x2 / 3.0 + x2 * x2 / 10.0 - x2 * x2 * x2 / 42.0);
-        der = c * (-2.0 / (3.0 * a * a) + 4.0 * x2 / (10.0 * a * a) - 6.0 * x2 * x2 / (42.0 * a * a));
+        const R x2 = x * x;
+        val = c * (R(1) - x2 / R(3) + x2 * x2 / R(10) - x2 * x2 * x2 / R(42));
+        der = c * (R(-2) / (R(3) * a * a) + R(4) * x2 / (R(10) * a * a) - R(6) * x2 * x2 / (R(42) * a * a));
     } else {
-        const double e = erf(x);
+        const R e = derf(x);
         val = e / r;
-        der = (-e / (r * r) + c * exp(-x * x) / r) / r;
+        der = (-e / (r * r) + c * dexp(-x * x) / r) / r;
     }
 }
 
 // near-field kernel value and (1/r) dG/dr for widths (a1, a2); a2 == 0 means infinite
-__device__ __forceinline__ void near_kernel(double r, double a1, double a2, double gw, double eps,
-                                            double& g, double& d) {
-    const bool small = r < 1e-3 * gw;
-    double v1, d1, v2 = 0.0, d2 = 0.0;
-    erf_over_r(r, a1, small, v1, d1);
-    if (a2 > 0.0) erf_over_r(r, a2, small, v2, d2);
-    const double s = 1.0 / (12.566370614359172 * eps);   // 1/(4 pi eps)
+template <class R>
+__device__ __forceinline__ void near_kernel(R r, R a1, R a2, R gw, R eps, R& g, R& d) {
+    const bool small = r < R(1e-3) * gw;
+    R v1, d1, v2 = 0, d2 = 0;
+    erf_over_r<R>(r, a1, small, v1, d1);
+    if (a2 > R(0)) erf_over_r<R>(r, a2, small, v2, d2);
+    const R s = R(1) / (R(12.566370614359172) * eps);   // 1/(4 pi eps)
     g = (v1 - v2) * s;
     d = (d1 - d2) * s;
 }

@@ -76,7 +76,7 @@ int derive(const dpslab_params& p, dpslab_derived& d) {
     if (!(p.eps_b > 0.0) || !(p.eps_t > 0.0)) return DPSLAB_ERR_INVALID_ARG;   // may be +inf
     if (p.nx < 4 || p.ny < 4 || p.nx > kMaxFft || p.ny > kMaxFft) return DPSLAB_ERR_GRID;
     if (p.nz != 0 && (p.nz < 4 || p.nz > kMaxNz)) return DPSLAB_ERR_GRID;
-    if (p.precision != DPSLAB_FP64) return DPSLAB_ERR_UNSUPPORTED;
+    if (p.precision != DPSLAB_FP64 && p.precision != DPSLAB_MIXED) return DPSLAB_ERR_UNSUPPORTED;
     if (!(p.xi >= 0.0) || !(p.r_cut >= 0.0) || !(p.n_sigma >= 0.0)) return DPSLAB_ERR_INVALID_ARG;
 
     // Table (ewconstraints)

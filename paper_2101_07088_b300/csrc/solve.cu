@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -84,10 +85,12 @@ __global__ void k_prepare(KP kp) {
 
 // ---------------------------------------------------------------------------
 // spreading, Sec. 5.2.2 steps 2-3: one block per source (charge, bottom image,
-// top image); rho_i gets every source, rho_o only the charges of C_over
+// top image); rho_i gets every source, rho_o only the charges of C_over.
+// Offsets from the grid points are taken in double; weights and grid in R.
 // ---------------------------------------------------------------------------
+template <class R>
 __global__ void k_spread(KP kp) {
-    __shared__ double wx[kMaxSupport], wy[kMaxSupport], wzs[kMaxNz];
+    __shared__ R wx[kMaxSupport], wy[kMaxSupport], wzs[kMaxNz];
     __shared__ int s_j0, s_j1;
     const int slot = blockIdx.x;
     const int k = slot % kp.n;
@@ -119,88 +122,117 @@ __global__ void k_spread(KP kp) {
     }
     for (int i = threadIdx.x; i < sx; i += blockDim.x) {
         const double d = double(ix0 + i) * kp.hx - x;
-        wx[i] = kp.s1norm * exp(-d * d * inv2g2);
+        wx[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
     }
     for (int i = threadIdx.x; i < sy; i += blockDim.x) {
         const double d = double(iy0 + i) * kp.hy - y;
-        wy[i] = kp.s1norm * exp(-d * d * inv2g2);
+        wy[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
     }
     __syncthreads();
     const int j0 = s_j0, sz = s_j1 - s_j0 + 1;
     if (sz <= 0) return;
     for (int i = threadIdx.x; i < sz; i += blockDim.x) {
         const double d = kp.zn[j0 + i] - z;
-        wzs[i] = kp.s1norm * exp(-d * d * inv2g2);
+        wzs[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
     }
     __syncthreads();
+    R* rho = static_cast<R*>(kp.rho);
     const size_t G = size_t(kp.nz) * kp.ny * kp.nx;
     const int sxy = sx * sy;
+    const R qr = R(q);
     for (int t = threadIdx.x; t < sz * sxy; t += blockDim.x) {
         const int jz = t / sxy;
         const int r = t - jz * sxy;
         const int iy = r / sx;
         const int ix = r - iy * sx;
-        const double v = q * wzs[jz] * wy[iy] * wx[ix];
+        const R v = qr * wzs[jz] * wy[iy] * wx[ix];
         const size_t g = (size_t(j0 + jz) * kp.ny + wrap_index(iy0 + iy, kp.ny)) * kp.nx + wrap_index(ix0 + ix, kp.nx);
-        atomicAdd(kp.rho + g, v);
-        if (over) atomicAdd(kp.rho + G + g, v);
+        atomicAdd(rho + g, v);
+        if (over) atomicAdd(rho + G + g, v);
     }
 }
+
+template <class R> __device__ __forceinline__ const typename Prec<R>::C* twx_of(const KP& kp);
+template <> __device__ __forceinline__ const double2* twx_of<double>(const KP& kp) { return kp.twx; }
+template <> __device__ __forceinline__ const float2* twx_of<float>(const KP& kp) { return kp.twx32; }
+template <class R> __device__ __forceinline__ const typename Prec<R>::C* twy_of(const KP& kp);
+template <> __device__ __forceinline__ const double2* twy_of<double>(const KP& kp) { return kp.twy; }
+template <> __device__ __forceinline__ const float2* twy_of<float>(const KP& kp) { return kp.twy32; }
 
 // ---------------------------------------------------------------------------
 // xy FFT, forward: rows along x (two real rows packed into one complex FFT),
 // then columns along y, for both densities
 // ---------------------------------------------------------------------------
+template <class R>
 __global__ void k_fftx_fwd(KP kp, int P) {
-    extern __shared__ double2 sm[];
+    using C = typename Prec<R>::C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
     const int n = kp.nx, nxh = kp.nxh;
-    double2* tw = sm;
-    double2* A = tw + n;
-    double2* B = A + P * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = kp.twx[i];
+    C* tw = sm;
+    C* A = tw + n;
+    C* B = A + P * n;
+    const C* twg = twx_of<R>(kp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    const R* rho = static_cast<const R*>(kp.rho);
+    C* spec = static_cast<C*>(kp.spec);
     const int npairs = kp.nz * kp.ny;           // 2 nz ny rows
     const int p0 = blockIdx.x * P;
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t / n, x = t - p * n, pr = p0 + p;
-        double2 v = make_double2(0.0, 0.0);
+        C v;
+        v.x = R(0);
+        v.y = R(0);
         if (pr < npairs) {
             const size_t r0 = 2 * size_t(pr);
-            v = make_double2(kp.rho[r0 * n + x], kp.rho[(r0 + 1) * n + x]);
+            v.x = rho[r0 * n + x];
+            v.y = rho[(r0 + 1) * n + x];
         }
         A[p * n + x] = v;
     }
     __syncthreads();
-    const double2* R = block_fft(A, B, tw, n, P, kp.radx, kp.nradx, -1);
+    const C* Rr = block_fft(A, B, tw, n, P, kp.radx, kp.nradx, -1);
     for (int t = threadIdx.x; t < P * nxh; t += blockDim.x) {
         const int p = t / nxh, k = t - p * nxh, pr = p0 + p;
         if (pr >= npairs) continue;
-        const double2 Z = R[p * n + k];
-        const double2 Zm = cconj(R[p * n + (n - k) % n]);
-        const double2 s = cadd(Z, Zm), d = csub(Z, Zm);
+        const C Z = Rr[p * n + k];
+        const C Zm = cconj(Rr[p * n + (n - k) % n]);
+        const C sum = cadd(Z, Zm), d = csub(Z, Zm);
         const size_t r0 = 2 * size_t(pr);
-        kp.spec[r0 * nxh + k] = cscale(s, 0.5);
-        kp.spec[(r0 + 1) * nxh + k] = make_double2(0.5 * d.y, -0.5 * d.x);
+        spec[r0 * nxh + k] = cscale(sum, R(0.5));
+        C b;
+        b.x = R(0.5) * d.y;
+        b.y = R(-0.5) * d.x;
+        spec[(r0 + 1) * nxh + k] = b;
     }
 }
 
+template <class R>
 __global__ void k_ffty_fwd(KP kp, int TK) {
-    extern __shared__ double2 sm[];
+    using C = typename Prec<R>::C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
     const int n = kp.ny, nxh = kp.nxh;
-    double2* tw = sm;
-    double2* A = tw + n;
-    double2* B = A + TK * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = kp.twy[i];
-    double2* base = kp.spec + size_t(blockIdx.y) * n * nxh;
+    C* tw = sm;
+    C* A = tw + n;
+    C* B = A + TK * n;
+    const C* twg = twy_of<R>(kp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    C* base = static_cast<C*>(kp.spec) + size_t(blockIdx.y) * n * nxh;
     const int k0 = blockIdx.x * TK;
     for (int t = threadIdx.x; t < TK * n; t += blockDim.x) {
         const int y = t / TK, c = t - y * TK, kx = k0 + c;
-        A[c * n + y] = kx < nxh ? base[size_t(y) * nxh + kx] : make_double2(0.0, 0.0);
+        C v;
+        v.x = R(0);
+        v.y = R(0);
+        if (kx < nxh) v = base[size_t(y) * nxh + kx];
+        A[c * n + y] = v;
     }
     __syncthreads();
-    const double2* R = block_fft(A, B, tw, n, TK, kp.rady, kp.nrady, -1);
+    const C* Rr = block_fft(A, B, tw, n, TK, kp.rady, kp.nrady, -1);
     for (int t = threadIdx.x; t < TK * n; t += blockDim.x) {
         const int y = t / TK, c = t - y * TK, kx = k0 + c;
-        if (kx < nxh) base[size_t(y) * nxh + kx] = R[c * n + y];
+        if (kx < nxh) base[size_t(y) * nxh + kx] = Rr[c * n + y];
     }
 }
 
@@ -228,6 +260,7 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
     const int tid = threadIdx.x, bs = blockDim.x;
     const int col0 = blockIdx.x * CB;
     const double Hbar = kp.Hbar;
+    double2* const spd = static_cast<double2*>(kp.spec);
 
     if (tid < CB) {
         const int c = tid, col = col0 + c;
@@ -247,8 +280,8 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
         const int j = t / CB, c = t - j * CB, col = col0 + c;
         double2 vi = make_double2(0.0, 0.0), vo = vi;
         if (col < M) {
-            vi = kp.spec[size_t(j) * M + col];
-            vo = kp.spec[size_t(N + j) * M + col];
+            vi = spd[size_t(j) * M + col];
+            vo = spd[size_t(N + j) * M + col];
         }
         Vi[c * N + j] = vi;
         Vo[c * N + j] = vo;
@@ -512,8 +545,321 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
                 ps.x += Ai * z;
                 dps.x += Ai;
             }
-            kp.spec[size_t(j) * M + col] = ps;
-            kp.spec[size_t(N + j) * M + col] = dps;
+            spd[size_t(j) * M + col] = ps;
+            spd[size_t(N + j) * M + col] = dps;
+        }
+    }
+    const double g = block_sum(tid < CB ? s_gauge[tid] : 0.0);
+    if (tid == 0) kp.part_gauge_far[blockIdx.x] = g;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision column kernel (DPSLAB_MIXED): the same steps as k_column
+// with the transforms, the banded solve and the node values in float; the
+// Schur 2x2 systems, the boundary values, the mismatches, the correction
+// coefficients, the k = 0 slope and the gauge sum in double. The correction
+// is evaluated at the nodes in float: its normalised form only multiplies
+// decaying factors bounded by e^{k_max H_E}, far inside float range.
+// ---------------------------------------------------------------------------
+constexpr int kColBlockM = 8;
+constexpr int kColThreadsM = 32 * kColBlockM;
+
+__global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int CB = kColBlockM;
+    const int N = kp.nz;
+    const int M = kp.ny * kp.nxh;
+    float2* Vi = reinterpret_cast<float2*>(smraw);
+    float2* Vo = Vi + CB * N;
+    float2* Ci = Vo + CB * N;
+    float2* Co = Ci + CB * N;
+    float* cpv = reinterpret_cast<float*>(Co + CB * N);
+    float* xe = cpv + CB * N;
+    __shared__ double s_k[CB], s_K[CB], s_mult[CB], s_gauge[CB];
+    __shared__ float s_den[CB], s_ekH[CB];
+    __shared__ int s_valid[CB], s_corr[CB];
+    __shared__ float2 s_c[2][CB], s_d[2][CB], s_P[CB], s_Q[CB];
+    __shared__ double s_Ai;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int col0 = blockIdx.x * CB;
+    const double Hbar = kp.Hbar;
+    float2* const sp = static_cast<float2*>(kp.spec);
+
+    if (tid < CB) {
+        const int c = tid, col = col0 + c;
+        const int iy = col / kp.nxh, ix = col - iy * kp.nxh;
+        const int my = iy < (kp.ny + 1) / 2 ? iy : iy - kp.ny;
+        const double kx = kTwoPi * ix / kp.Lx, ky = kTwoPi * my / kp.Ly;
+        const double k = sqrt(kx * kx + ky * ky);
+        s_valid[c] = col < M;
+        s_k[c] = k;
+        s_K[c] = 0.5 * k * Hbar;
+        s_mult[c] = (ix == 0 || (kp.nx % 2 == 0 && ix == kp.nx / 2)) ? 1.0 : 2.0;
+        s_corr[c] = (col < M) && k > 0.0 && k <= kp.kmax;
+        s_gauge[c] = 0.0;
+    }
+    if (tid == 0) s_Ai = 0.0;
+    for (int t = tid; t < N * CB; t += bs) {
+        const int j = t / CB, c = t - j * CB, col = col0 + c;
+        float2 vi = make_float2(0.f, 0.f), vo = vi;
+        if (col < M) {
+            vi = sp[size_t(j) * M + col];
+            vo = sp[size_t(N + j) * M + col];
+        }
+        Vi[c * N + j] = vi;
+        Vo[c * N + j] = vo;
+    }
+    __syncthreads();
+
+    const int m = N - 1, JE = (N + 1) / 2, JO = N / 2;
+    for (int t = tid; t < 2 * CB * JE; t += bs) {
+        const int f = t / (CB * JE), r = t - f * CB * JE, c = r / JE, a = r - c * JE;
+        if (a < m - a) {
+            float2* V = (f ? Vo : Vi) + c * N;
+            const float2 va = V[a], vb = V[m - a];
+            V[a] = cadd(va, vb);
+            V[m - a] = csub(va, vb);
+        }
+    }
+    __syncthreads();
+    const float scale = float(-(0.5 * Hbar) * (0.5 * Hbar) / kp.eps);
+    for (int t = tid; t < CB * N; t += bs) {
+        const int c = t / N, q = t - c * N;
+        const bool odd = q >= JE;
+        const int na = odd ? JO : JE;
+        const float2* vi = Vi + c * N;
+        const float2* vo = Vo + c * N;
+        float ix = 0.f, iy = 0.f, ox = 0.f, oy = 0.f;
+        for (int a = 0; a < na; ++a) {
+            const float w = kp.cft32[size_t(a) * N + q];
+            const int ia = odd ? m - a : a;
+            const float2 u = vi[ia], v = vo[ia];
+            ix = fmaf(w, u.x, ix);
+            iy = fmaf(w, u.y, iy);
+            ox = fmaf(w, v.x, ox);
+            oy = fmaf(w, v.y, oy);
+        }
+        const int n = odd ? 2 * (q - JE) + 1 : 2 * q;
+        Ci[c * N + n] = make_float2(ix * scale, iy * scale);
+        Co[c * N + n] = make_float2(ox * scale, oy * scale);
+    }
+    __syncthreads();
+
+    // Appendix A banded solve (even and odd chains), float
+    if (tid < 2 * CB) {
+        const int c = tid >> 1, ch = tid & 1;
+        const float K2 = float(s_K[c] * s_K[c]);
+        float2* Fi = Ci + c * N;
+        float2* Fo = Co + c * N;
+        float* cq = cpv + c * N;
+        float* xc = xe + c * N;
+        int prev = -1;
+        for (int n = ch; n < N; n += 2) {
+            const float an = n >= 2 ? -K2 * kp.j2l32[n] : 0.f;
+            const float bn = 1.f - K2 * kp.j2d32[n];
+            const float cn = n + 2 < N ? -K2 * kp.j2u32[n] : 0.f;
+            float mm = bn, rn = (n == ch) ? K2 : 0.f;
+            float2 fi = Fi[n], fo = Fo[n];
+            if (prev >= 0) {
+                mm -= an * cq[prev];
+                fi = csub(fi, cscale(Fi[prev], an));
+                fo = csub(fo, cscale(Fo[prev], an));
+                rn -= an * xc[prev];
+            }
+            const float inv = 1.f / mm;
+            cq[n] = cn * inv;
+            Fi[n] = cscale(fi, inv);
+            Fo[n] = cscale(fo, inv);
+            xc[n] = rn * inv;
+            prev = n;
+        }
+        for (int n = prev - 2; n >= ch; n -= 2) {
+            Fi[n] = csub(Fi[n], cscale(Fi[n + 2], cq[n]));
+            Fo[n] = csub(Fo[n], cscale(Fo[n + 2], cq[n]));
+            xc[n] -= cq[n] * xc[n + 2];
+        }
+    }
+    __syncthreads();
+
+    // Schur 2x2 (warp per column; lane partial sums in float, reduced and
+    // solved in double)
+    {
+        const int c = tid >> 5, lane = tid & 31;
+        const float K = float(s_K[c]);
+        const float2* Xi = Ci + c * N;
+        const float2* Xo = Co + c * N;
+        const float* xc = xe + c * N;
+        float acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int n = lane; n < N; n += 32) {
+            const float gtn = K > 0.f ? kp.u132[n] + K * kp.u232[n] : kp.u232[n];
+            const float gbn = K > 0.f ? kp.v132[n] - K * kp.v232[n] : kp.v232[n];
+            acc[0] = fmaf(gtn, Xi[n].x, acc[0]); acc[1] = fmaf(gtn, Xi[n].y, acc[1]);
+            acc[2] = fmaf(gbn, Xi[n].x, acc[2]); acc[3] = fmaf(gbn, Xi[n].y, acc[3]);
+            acc[4] = fmaf(gtn, Xo[n].x, acc[4]); acc[5] = fmaf(gtn, Xo[n].y, acc[5]);
+            acc[6] = fmaf(gbn, Xo[n].x, acc[6]); acc[7] = fmaf(gbn, Xo[n].y, acc[7]);
+            if (n & 1) { acc[9] = fmaf(gtn, xc[n], acc[9]); acc[11] = fmaf(gbn, xc[n], acc[11]); }
+            else { acc[8] = fmaf(gtn, xc[n], acc[8]); acc[10] = fmaf(gbn, xc[n], acc[10]); }
+        }
+        double da[12];
+        for (int i = 0; i < 12; ++i) da[i] = warp_sum(double(acc[i]));
+        if (lane < 2) {
+            const int f = lane;
+            const double2 sFt = f ? make_double2(da[4], da[5]) : make_double2(da[0], da[1]);
+            const double2 sFb = f ? make_double2(da[6], da[7]) : make_double2(da[2], da[3]);
+            const double Kd = s_K[c];
+            double2 cc, dd;
+            if (Kd > 0.0) {
+                const double m11 = Kd + da[8], m12 = 1.0 + Kd + da[9], m21 = -Kd + da[10], m22 = 1.0 + Kd + da[11];
+                const double idet = 1.0 / (m11 * m22 - m12 * m21);
+                cc = cscale(csub(cscale(sFt, m22), cscale(sFb, m12)), -idet);
+                dd = cscale(csub(cscale(sFb, m11), cscale(sFt, m21)), -idet);
+            } else {
+                cc = cscale(cadd(sFt, sFb), -0.5);
+                dd = cscale(csub(sFt, sFb), -0.5);
+            }
+            s_c[f][c] = make_float2(float(cc.x), float(cc.y));
+            s_d[f][c] = make_float2(float(dd.x), float(dd.y));
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < 2 * CB * N; t += bs) {
+        const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
+        float2* X = (f ? Co : Ci) + c * N;
+        const float2 mm = (n & 1) ? s_d[f][c] : s_c[f][c];
+        X[n] = cadd(X[n], cscale(mm, xe[c * N + n]));
+    }
+    __syncthreads();
+    for (int t = tid; t < 2 * CB * N; t += bs) {
+        const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
+        const float2* Y = (f ? Co : Ci) + c * N;
+        float2 v;
+        if (n == 0) v = s_d[f][c];
+        else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
+        else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
+        (f ? Vo : Vi)[c * N + n] = v;
+    }
+    __syncthreads();
+    for (int t = tid; t < 2 * CB * N; t += bs) {
+        const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
+        const float2* Y = (f ? Vo : Vi) + c * N;
+        float2 v;
+        if (n == 0) v = s_c[f][c];
+        else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
+        else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
+        (f ? Co : Ci)[c * N + n] = v;
+    }
+    __syncthreads();
+
+    // boundary values (lane sums in float, reduction in double), mismatches,
+    // correction coefficients, k = 0 slope, gauge partial sum (double)
+    {
+        const int c = tid >> 5, lane = tid & 31;
+        const float2 *yi = Ci + c * N, *ypi = Vi + c * N, *yo = Co + c * N, *ypo = Vo + c * N;
+        float acc[20];
+        for (int i = 0; i < 20; ++i) acc[i] = 0.f;
+        for (int n = lane; n < N; n += 32) {
+            const float a0 = kp.t032[n], aH = kp.tH32[n], alt = (n & 1) ? -1.f : 1.f, wg = kp.wg32[n];
+            acc[0] = fmaf(a0, yi[n].x, acc[0]);   acc[1] = fmaf(a0, yi[n].y, acc[1]);
+            acc[2] = fmaf(a0, ypi[n].x, acc[2]);  acc[3] = fmaf(a0, ypi[n].y, acc[3]);
+            acc[4] = fmaf(aH, yi[n].x, acc[4]);   acc[5] = fmaf(aH, yi[n].y, acc[5]);
+            acc[6] = fmaf(aH, ypi[n].x, acc[6]);  acc[7] = fmaf(aH, ypi[n].y, acc[7]);
+            acc[8] = fmaf(a0, yo[n].x, acc[8]);   acc[9] = fmaf(a0, yo[n].y, acc[9]);
+            acc[10] = fmaf(a0, ypo[n].x, acc[10]); acc[11] = fmaf(a0, ypo[n].y, acc[11]);
+            acc[12] = fmaf(aH, yo[n].x, acc[12]); acc[13] = fmaf(aH, yo[n].y, acc[13]);
+            acc[14] = fmaf(aH, ypo[n].x, acc[14]); acc[15] = fmaf(aH, ypo[n].y, acc[15]);
+            acc[16] = fmaf(alt, ypo[n].x, acc[16]); acc[17] += ypo[n].x;
+            acc[18] = fmaf(wg, yi[n].x, acc[18]); acc[19] = fmaf(wg, yi[n].y, acc[19]);
+        }
+        double da[20];
+        for (int i = 0; i < 20; ++i) da[i] = warp_sum(double(acc[i]));
+        if (lane == 0 && s_valid[c]) {
+            const double dz = 2.0 / Hbar;
+            const double2 pi0 = make_double2(da[0], da[1]), dpi0 = make_double2(da[2] * dz, da[3] * dz);
+            const double2 piH = make_double2(da[4], da[5]), dpiH = make_double2(da[6] * dz, da[7] * dz);
+            const double2 po0 = make_double2(da[8], da[9]), dpo0 = make_double2(da[10] * dz, da[11] * dz);
+            const double2 poH = make_double2(da[12], da[13]), dpoH = make_double2(da[14] * dz, da[15] * dz);
+            const double dpoa = da[16] * dz, dpob = da[17] * dz;
+            const double k = s_k[c];
+            double2 corr0 = make_double2(0.0, 0.0);
+            if (s_corr[c]) {
+                const double2 mpb = csub(pi0, cscale(po0, kp.tb));
+                const double2 meb = csub(dpi0, cscale(dpo0, kp.rtb));
+                const double2 mpt = csub(piH, cscale(poH, kp.tt));
+                const double2 met = csub(dpiH, cscale(dpoH, kp.rtt));
+                const double2 P = csub(cscale(mpb, kp.cb), cscale(meb, kp.db / k));
+                const double2 Q = csub(cscale(mpt, -kp.ct), cscale(met, kp.dt / k));
+                const double ekH = exp(-k * kp.H);
+                const double den = 1.0 - kp.Gb * kp.Gt * ekH * ekH;
+                s_P[c] = make_float2(float(P.x), float(P.y));
+                s_Q[c] = make_float2(float(Q.x), float(Q.y));
+                s_ekH[c] = float(ekH);
+                s_den[c] = float(den);
+                corr0 = cscale(cadd(cscale(P, -(1.0 - kp.Gt * ekH * ekH)), cscale(Q, ekH - kp.Gb * ekH)), 1.0 / den);
+            }
+            if (col0 + c == 0) {
+                const double ai1 = kp.rtb * (dpo0.x - dpoa) - dpi0.x;
+                const double ai2 = kp.rtt * (dpoH.x - dpob) - dpiH.x;
+                double Ai;
+                if (kp.metal_b && kp.metal_t) Ai = -(piH.x - pi0.x) / kp.H;
+                else if (kp.metal_b) Ai = ai2;
+                else if (kp.metal_t) Ai = ai1;
+                else Ai = 0.5 * (ai1 + ai2);
+                s_Ai = Ai;
+                kp.scal[1] = Ai;
+            }
+            const double damp = exp(-0.5 * kp.sigma2 * k * k);
+            s_gauge[c] = s_mult[c] * (damp * da[18] + corr0.x);
+        }
+    }
+    __syncthreads();
+
+    // node values (float), correction at the nodes (float)
+    const float Ai = float(s_Ai);
+    const float Gb = float(kp.Gb), Gt = float(kp.Gt), Hf = float(kp.H), HEf = float(kp.HE);
+    for (int t = tid; t < JE * CB; t += bs) {
+        const int c = t / JE, a = t - c * JE, col = col0 + c;
+        if (col >= M) continue;
+        const float2* yi = Ci + c * N;
+        const float2* ypi = Vi + c * N;
+        float ex = 0, ey = 0, dex = 0, dey = 0, ox = 0, oy = 0, dox = 0, doy = 0;
+        for (int r = 0; r < JE; ++r) {
+            const float w = kp.tie32[size_t(r) * JE + a];
+            ex = fmaf(w, yi[2 * r].x, ex);
+            ey = fmaf(w, yi[2 * r].y, ey);
+            dex = fmaf(w, ypi[2 * r].x, dex);
+            dey = fmaf(w, ypi[2 * r].y, dey);
+        }
+        for (int r = 0; r < JO; ++r) {
+            const float w = kp.tio32[size_t(r) * JE + a];
+            ox = fmaf(w, yi[2 * r + 1].x, ox);
+            oy = fmaf(w, yi[2 * r + 1].y, oy);
+            dox = fmaf(w, ypi[2 * r + 1].x, dox);
+            doy = fmaf(w, ypi[2 * r + 1].y, doy);
+        }
+        const float sz = float(2.0 / Hbar);
+        for (int side = 0; side < 2; ++side) {
+            const int j = side ? m - a : a;
+            if (side && j == a) break;
+            const float sg = side ? -1.f : 1.f;
+            float2 ps = make_float2(ex + sg * ox, ey + sg * oy);
+            float2 dps = make_float2((dex + sg * dox) * sz, (dey + sg * doy) * sz);
+            const float z = float(kp.zn[j]);
+            if (s_corr[c] && z >= -HEf && z <= Hf + HEf) {
+                const float k = float(s_k[c]), ekH = s_ekH[c], iden = 1.f / s_den[c];
+                const float e1 = expf(-k * z), e3 = expf(k * (z - Hf));
+                const float e2 = e3 * ekH, e4 = e1 * ekH;
+                const float2 P = s_P[c], Q = s_Q[c];
+                const float2 val = cscale(cadd(cscale(P, -(e1 - Gt * e2)), cscale(Q, e3 - Gb * e4)), iden);
+                const float2 der = cscale(cadd(cscale(P, e1 + Gt * e2), cscale(Q, e3 + Gb * e4)), k * iden);
+                ps = cadd(ps, val);
+                dps = cadd(dps, der);
+            }
+            if (col == 0) {
+                ps.x += Ai * z;
+                dps.x += Ai;
+            }
+            sp[size_t(j) * M + col] = ps;
+            sp[size_t(N + j) * M + col] = dps;
         }
     }
     const double g = block_sum(tid < CB ? s_gauge[tid] : 0.0);
@@ -524,96 +870,122 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
 // xy FFT, inverse: columns along y for psi, -i k_y psi and dpsi/dz, then rows
 // along x packing (phi, E_x) and (E_y, E_z) as one complex FFT each
 // ---------------------------------------------------------------------------
+template <class R>
 __global__ void k_ffty_inv(KP kp, int TK) {
-    extern __shared__ double2 sm[];
+    using C = typename Prec<R>::C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
     const int n = kp.ny, nxh = kp.nxh;
-    double2* tw = sm;
-    double2* A = tw + n;
-    double2* B = A + 3 * TK * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = kp.twy[i];
+    C* tw = sm;
+    C* A = tw + n;
+    C* B = A + 3 * TK * n;
+    const C* twg = twy_of<R>(kp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
     const size_t plane = size_t(n) * nxh;
-    double2* s0 = kp.spec + size_t(blockIdx.y) * plane;
-    double2* s1 = kp.spec + size_t(kp.nz + blockIdx.y) * plane;
-    double2* sb = kp.specB + size_t(blockIdx.y) * plane;
+    C* s0 = static_cast<C*>(kp.spec) + size_t(blockIdx.y) * plane;
+    C* s1 = static_cast<C*>(kp.spec) + size_t(kp.nz + blockIdx.y) * plane;
+    C* sb = static_cast<C*>(kp.specB) + size_t(blockIdx.y) * plane;
     const int k0 = blockIdx.x * TK;
     for (int t = threadIdx.x; t < TK * n; t += blockDim.x) {
         const int y = t / TK, c = t - y * TK, kx = k0 + c;
-        double2 ps = make_double2(0.0, 0.0), dps = ps;
+        C ps, dps;
+        ps.x = ps.y = dps.x = dps.y = R(0);
         if (kx < nxh) {
             ps = s0[size_t(y) * nxh + kx];
             dps = s1[size_t(y) * nxh + kx];
         }
         const int my = y < (n + 1) / 2 ? y : y - n;
-        const double ky = (n % 2 == 0 && y == n / 2) ? 0.0 : kTwoPi * my / kp.Ly;
+        const R ky = (n % 2 == 0 && y == n / 2) ? R(0) : R(kTwoPi * my / kp.Ly);
+        C dy;
+        dy.x = ky * ps.y;                          // -i k_y psi
+        dy.y = -ky * ps.x;
         A[c * n + y] = ps;
-        A[(TK + c) * n + y] = make_double2(ky * ps.y, -ky * ps.x);   // -i k_y psi
+        A[(TK + c) * n + y] = dy;
         A[(2 * TK + c) * n + y] = dps;
     }
     __syncthreads();
-    const double2* R = block_fft(A, B, tw, n, 3 * TK, kp.rady, kp.nrady, +1);
+    const C* Rr = block_fft(A, B, tw, n, 3 * TK, kp.rady, kp.nrady, +1);
     for (int t = threadIdx.x; t < TK * n; t += blockDim.x) {
         const int y = t / TK, c = t - y * TK, kx = k0 + c;
         if (kx >= nxh) continue;
-        s0[size_t(y) * nxh + kx] = R[c * n + y];
-        sb[size_t(y) * nxh + kx] = R[(TK + c) * n + y];
-        s1[size_t(y) * nxh + kx] = R[(2 * TK + c) * n + y];
+        s0[size_t(y) * nxh + kx] = Rr[c * n + y];
+        sb[size_t(y) * nxh + kx] = Rr[(TK + c) * n + y];
+        s1[size_t(y) * nxh + kx] = Rr[(2 * TK + c) * n + y];
     }
 }
 
+template <class R>
 __global__ void k_fftx_inv(KP kp, int P) {
-    extern __shared__ double2 sm[];
+    using C = typename Prec<R>::C;
+    using V4 = typename Prec<R>::V4;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
     const int n = kp.nx, nxh = kp.nxh;
-    double2* tw = sm;
-    double2* A = tw + n;
-    double2* B = A + 2 * P * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = kp.twx[i];
+    C* tw = sm;
+    C* A = tw + n;
+    C* B = A + 2 * P * n;
+    const C* twg = twx_of<R>(kp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    const C* spec = static_cast<const C*>(kp.spec);
+    const C* specB = static_cast<const C*>(kp.specB);
+    V4* fields = static_cast<V4*>(kp.fields);
     const int nrows = kp.nz * kp.ny;
     const size_t S = size_t(nrows) * nxh;
     const int r0 = blockIdx.x * P;
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t / n, k = t - p * n, row = r0 + p;
-        double2 z1 = make_double2(0.0, 0.0), z2 = z1;
+        C z1, z2;
+        z1.x = z1.y = z2.x = z2.y = R(0);
         if (row < nrows) {
             const bool hi = k >= nxh;
             const int kk = hi ? n - k : k;
-            double2 a = kp.spec[size_t(row) * nxh + kk];
-            double2 b = kp.specB[size_t(row) * nxh + kk];
-            double2 c = kp.spec[S + size_t(row) * nxh + kk];
+            C a = spec[size_t(row) * nxh + kk];
+            C b = specB[size_t(row) * nxh + kk];
+            C c = spec[S + size_t(row) * nxh + kk];
             const bool edge = kk == 0 || (n % 2 == 0 && kk == n / 2);
-            if (edge) { a.y = 0.0; b.y = 0.0; c.y = 0.0; }
-            const double kxd = edge ? 0.0 : kTwoPi * kk / kp.Lx;
-            double2 r = make_double2(kxd * a.y, -kxd * a.x);   // -i k_x psi
-            double2 mc = make_double2(-c.x, -c.y);             // E_z = -dpsi/dz
+            if (edge) { a.y = R(0); b.y = R(0); c.y = R(0); }
+            const R kxd = edge ? R(0) : R(kTwoPi * kk / kp.Lx);
+            C r, mc;
+            r.x = kxd * a.y;                     // -i k_x psi
+            r.y = -kxd * a.x;
+            mc.x = -c.x;                         // E_z = -dpsi/dz
+            mc.y = -c.y;
             if (hi) { a = cconj(a); r = cconj(r); b = cconj(b); mc = cconj(mc); }
-            z1 = make_double2(a.x - r.y, a.y + r.x);           // phi + i E_x
-            z2 = make_double2(b.x - mc.y, b.y + mc.x);         // E_y + i E_z
+            z1.x = a.x - r.y;                    // phi + i E_x
+            z1.y = a.y + r.x;
+            z2.x = b.x - mc.y;                   // E_y + i E_z
+            z2.y = b.y + mc.x;
         }
         A[(2 * p) * n + k] = z1;
         A[(2 * p + 1) * n + k] = z2;
     }
     __syncthreads();
-    const double2* R = block_fft(A, B, tw, n, 2 * P, kp.radx, kp.nradx, +1);
-    const double s = kp.inv_nxny;
+    const C* Rr = block_fft(A, B, tw, n, 2 * P, kp.radx, kp.nradx, +1);
+    const R s = R(kp.inv_nxny);
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t / n, x = t - p * n, row = r0 + p;
         if (row >= nrows) continue;
-        const double2 u = R[(2 * p) * n + x], v = R[(2 * p + 1) * n + x];
-        kp.fields[size_t(row) * n + x] = make_double4_32a(u.x * s, u.y * s, v.x * s, v.y * s);
+        const C u = Rr[(2 * p) * n + x], v = Rr[(2 * p + 1) * n + x];
+        fields[size_t(row) * n + x] = Prec<R>::v4(u.x * s, u.y * s, v.x * s, v.y * s);
     }
 }
 
 // ---------------------------------------------------------------------------
 // interpolation, Sec. 5.2.2 step 7: one warp per charge, grid quadrature of
-// the kernel times the four fields
+// the kernel times the four fields (lane sums in R, warp sum in double)
 // ---------------------------------------------------------------------------
+template <class R>
 __global__ void k_interp(KP kp) {
-    extern __shared__ double smi[];
+    using V4 = typename Prec<R>::V4;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R* smi = reinterpret_cast<R*>(smraw);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* wx = smi + w * (2 * kMaxSupport + kMaxNz);
-    double* wy = wx + kMaxSupport;
-    double* wzz = wy + kMaxSupport;
+    R* wx = smi + w * (2 * kMaxSupport + kMaxNz);
+    R* wy = wx + kMaxSupport;
+    R* wzz = wy + kMaxSupport;
     const int k = blockIdx.x * (blockDim.x >> 5) + w;
     if (k >= kp.n) return;
+    const V4* fields = static_cast<const V4*>(kp.fields);
     const double4_32a p = kp.part[k];
     const double x = p.x, y = p.y, z = p.z, HE = kp.HE;
     const int ix0 = int(ceil((x - HE) / kp.hx)), ix1 = int(floor((x + HE) / kp.hx));
@@ -631,35 +1003,33 @@ __global__ void k_interp(KP kp) {
     const double inv2g2 = 1.0 / (2.0 * kp.gt * kp.gt);
     for (int i = lane; i < sx; i += 32) {
         const double d = double(ix0 + i) * kp.hx - x;
-        wx[i] = kp.s1norm * exp(-d * d * inv2g2);
+        wx[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
     }
     for (int i = lane; i < sy; i += 32) {
         const double d = double(iy0 + i) * kp.hy - y;
-        wy[i] = kp.s1norm * exp(-d * d * inv2g2);
+        wy[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
     }
     for (int i = lane; i < sz; i += 32) {
         const double d = kp.zn[j0 + i] - z;
-        wzz[i] = kp.wz[j0 + i] * (kp.s1norm * exp(-d * d * inv2g2));
+        wzz[i] = R(kp.wz[j0 + i]) * (R(kp.s1norm) * dexp(R(-d * d * inv2g2)));
     }
     __syncwarp();
-    const double wxy = kp.hx * kp.hy;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const R wxy = R(kp.hx * kp.hy);
+    R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     const int sxy = sx * sy;
     for (int t = lane; t < sz * sxy; t += 32) {
         const int jz = t / sxy, r = t - jz * sxy, iy = r / sx, ix = r - iy * sx;
-        const double wt = wxy * wzz[jz] * wy[iy] * wx[ix];
+        const R wt = wxy * wzz[jz] * wy[iy] * wx[ix];
         const size_t g = (size_t(j0 + jz) * kp.ny + wrap_index(iy0 + iy, kp.ny)) * kp.nx + wrap_index(ix0 + ix, kp.nx);
-        const double4_32a f = kp.fields[g];
+        const V4 f = fields[g];
         a0 = fma(wt, f.x, a0);
         a1 = fma(wt, f.y, a1);
         a2 = fma(wt, f.z, a2);
         a3 = fma(wt, f.w, a3);
     }
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    a2 = warp_sum(a2);
-    a3 = warp_sum(a3);
-    if (lane == 0) kp.far[k] = make_double4_32a(a0, a1, a2, a3);
+    const double b0 = warp_sum(double(a0)), b1 = warp_sum(double(a1));
+    const double b2 = warp_sum(double(a2)), b3 = warp_sum(double(a3));
+    if (lane == 0) kp.far[k] = make_double4_32a(b0, b1, b2, b3);
 }
 
 // ---------------------------------------------------------------------------
@@ -698,9 +1068,10 @@ __global__ void k_scatter_cells(KP kp) {
     kp.sorted_idx[slot] = k;
 }
 
+template <class R>
 __device__ __forceinline__ void near_cell(const KP& kp, int cell, double x, double y, double zt, double zsign,
                                           double zoff, double strength, double rc2,
-                                          double& phi, double& ex, double& ey, double& ez) {
+                                          R& phi, R& ex, R& ey, R& ez) {
     const int s0 = kp.cell_start[cell], s1 = kp.cell_start[cell + 1];
     for (int s = s0; s < s1; ++s) {
         const double4_32a src = kp.sorted[s];
@@ -709,17 +1080,18 @@ __device__ __forceinline__ void near_cell(const KP& kp, int cell, double x, doub
         const double dz = zt - (zoff + zsign * src.z);
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < rc2) {
-            double g, d;
-            near_kernel(sqrt(r2), kp.na1, kp.na2, kp.gw, kp.eps, g, d);
-            const double qs = strength * src.w;
+            R g, d;
+            near_kernel<R>(R(sqrt(r2)), R(kp.na1), R(kp.na2), R(kp.gw), R(kp.eps), g, d);
+            const R qs = R(strength * src.w);
             phi += qs * g;
-            ex -= qs * d * dx;
-            ey -= qs * d * dy;
-            ez -= qs * d * dz;
+            ex -= qs * d * R(dx);
+            ey -= qs * d * R(dy);
+            ez -= qs * d * R(dz);
         }
     }
 }
 
+template <class R>
 __global__ void k_near(KP kp) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= kp.n) return;
@@ -729,7 +1101,7 @@ __global__ void k_near(KP kp) {
     const int cy = min(kp.ncy - 1, max(0, int(y / kp.cwy)));
     const int cz = min(kp.ncz - 1, max(0, int(z / kp.cwz)));
     const double rc2 = kp.r_cut * kp.r_cut;
-    double phi = 0, ex = 0, ey = 0, ez = 0;
+    R phi = 0, ex = 0, ey = 0, ez = 0;
     const int nxc = kp.ncx >= 3 ? 3 : kp.ncx, nyc = kp.ncy >= 3 ? 3 : kp.ncy;
     // pass 0: charges; pass 1: images below z = 0; pass 2: images above z = H
     for (int pass = 0; pass < 3; ++pass) {
@@ -748,7 +1120,7 @@ __global__ void k_near(KP kp) {
                 const int yc = kp.ncy >= 3 ? wrap_index(cy - 1 + oy, kp.ncy) : oy;
                 for (int ox = 0; ox < nxc; ++ox) {
                     const int xc = kp.ncx >= 3 ? wrap_index(cx - 1 + ox, kp.ncx) : ox;
-                    near_cell(kp, (zc * kp.ncy + yc) * kp.ncx + xc, x, y, z, zsign, zoff, st, rc2, phi, ex, ey, ez);
+                    near_cell<R>(kp, (zc * kp.ncy + yc) * kp.ncx + xc, x, y, z, zsign, zoff, st, rc2, phi, ex, ey, ez);
                 }
             }
         }
@@ -769,12 +1141,12 @@ __global__ void k_origin(KP kp) {
         const double rt = sqrt(dx * dx + dy * dy + zt * zt);
         double g, d;
         if (r < rc) {
-            near_kernel(r, kp.pa1, kp.pa2, kp.gw, kp.eps, g, d);
+            near_kernel<double>(r, kp.pa1, kp.pa2, kp.gw, kp.eps, g, d);
             v += p.w * g;                 // the charge
             v += -kp.Gb * p.w * g;        // its image below z = 0 (same distance)
         }
         if (rt < rc) {
-            near_kernel(rt, kp.pa1, kp.pa2, kp.gw, kp.eps, g, d);
+            near_kernel<double>(rt, kp.pa1, kp.pa2, kp.gw, kp.eps, g, d);
             v += -kp.Gt * p.w * g;
         }
     }
@@ -990,7 +1362,11 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         kp.cwx = p->Lx; kp.cwy = p->Ly; kp.cwz = p->H;
     }
     const int M = ny * nxh;
-    kp.n_col_blocks = (M + kColBlock - 1) / kColBlock;
+    const bool mixed = p->precision == DPSLAB_MIXED;
+    kp.mixed = mixed ? 1 : 0;
+    const int col_block = mixed ? kColBlockM : kColBlock;
+    kp.n_col_blocks = (M + col_block - 1) / col_block;
+    const size_t rsz = mixed ? sizeof(float) : sizeof(double);   // grid element size
     kp.n_charge_blocks = int((max_n + kChargeThreads - 1) / kChargeThreads);
 
     // tables (one allocation)
@@ -1000,6 +1376,8 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         const size_t vec = align_up(N * sizeof(double));
         bytes += 2 * vec + 4 * align_up(N * N * sizeof(double)) + 11 * vec;
         bytes += align_up(nx * sizeof(double2)) + align_up(ny * sizeof(double2));
+        bytes += 2 * align_up(N * N * sizeof(float)) + 12 * align_up(N * sizeof(float));   // float copies
+        bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
         cudaError_t e = cudaMalloc(&pl->tables, bytes);
         if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
         pl->device_bytes += int64_t(bytes);
@@ -1020,16 +1398,35 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         cudaMemcpy(ty, t.twy.data(), ny * sizeof(double2), cudaMemcpyHostToDevice);
         kp.twx = tx;
         kp.twy = ty;
+        auto upf = [&](const std::vector<double>& v, const float*& dst) {
+            std::vector<float> f(v.begin(), v.end());
+            float* dp = carve<float>(cur, f.size());
+            cudaMemcpy(dp, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+            dst = dp;
+        };
+        upf(t.cft, kp.cft32); upf(t.tie, kp.tie32); upf(t.tio, kp.tio32);
+        upf(t.j2l, kp.j2l32); upf(t.j2d, kp.j2d32); upf(t.j2u, kp.j2u32);
+        upf(t.u1, kp.u132); upf(t.u2, kp.u232); upf(t.v1, kp.v132); upf(t.v2, kp.v232);
+        upf(t.t0, kp.t032); upf(t.tH, kp.tH32); upf(t.wg, kp.wg32);
+        auto upc = [&](const std::vector<dps::Complex>& v, const float2*& dst) {
+            std::vector<float2> f(v.size());
+            for (size_t i = 0; i < v.size(); ++i) f[i] = make_float2(float(v[i].re), float(v[i].im));
+            float2* dp = carve<float2>(cur, f.size());
+            cudaMemcpy(dp, f.data(), f.size() * sizeof(float2), cudaMemcpyHostToDevice);
+            dst = dp;
+        };
+        upc(t.twx, kp.twx32);
+        upc(t.twy, kp.twy32);
         if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
     }
     // work space (one allocation)
     {
         const size_t n = size_t(max_n);
         size_t bytes = 0;
-        bytes += align_up(2 * pl->G * sizeof(double));        // rho
-        bytes += align_up(2 * pl->S * sizeof(double2));       // spec
-        bytes += align_up(pl->S * sizeof(double2));           // specB
-        bytes += align_up(pl->G * sizeof(double4_32a));           // fields
+        bytes += align_up(2 * pl->G * rsz);                   // rho
+        bytes += align_up(2 * pl->S * 2 * rsz);               // spec
+        bytes += align_up(pl->S * 2 * rsz);                   // specB
+        bytes += align_up(pl->G * 4 * rsz);                   // fields
         bytes += 3 * align_up(n * sizeof(double4_32a));           // part, far, nearv
         bytes += 2 * align_up(n * sizeof(int));               // cell_of, sorted_idx
         bytes += align_up(n * sizeof(double4_32a));               // sorted
@@ -1043,10 +1440,10 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
         pl->device_bytes += int64_t(bytes);
         char* cur = static_cast<char*>(pl->work);
-        kp.rho = carve<double>(cur, 2 * pl->G);
-        kp.spec = carve<double2>(cur, 2 * pl->S);
-        kp.specB = carve<double2>(cur, pl->S);
-        kp.fields = carve<double4_32a>(cur, pl->G);
+        kp.rho = carve<char>(cur, 2 * pl->G * rsz);
+        kp.spec = carve<char>(cur, 2 * pl->S * 2 * rsz);
+        kp.specB = carve<char>(cur, pl->S * 2 * rsz);
+        kp.fields = carve<char>(cur, pl->G * 4 * rsz);
         kp.part = carve<double4_32a>(cur, n);
         kp.far = carve<double4_32a>(cur, n);
         kp.nearv = carve<double4_32a>(cur, n);
@@ -1080,24 +1477,34 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
     pl->tk_fwd = std::max(1, std::min(16, floor_pow2(std::max(1, 3072 / ny))));
     pl->tk_inv = std::max(1, std::min(8, floor_pow2(std::max(1, 1024 / ny))));
     pl->px_inv = std::max(1, std::min(8, 1536 / nx));
-    pl->sm_fftx_fwd = (size_t(nx) + 2 * size_t(pl->px_fwd) * nx) * sizeof(double2);
-    pl->sm_ffty_fwd = (size_t(ny) + 2 * size_t(pl->tk_fwd) * ny) * sizeof(double2);
-    pl->sm_ffty_inv = (size_t(ny) + 6 * size_t(pl->tk_inv) * ny) * sizeof(double2);
-    pl->sm_fftx_inv = (size_t(nx) + 4 * size_t(pl->px_inv) * nx) * sizeof(double2);
-    pl->sm_col = size_t(kColBlock) * nz * (4 * sizeof(double2) + 2 * sizeof(double));
-    pl->sm_interp = size_t(kInterpWarps) * (2 * kMaxSupport + kMaxNz) * sizeof(double);
+    const size_t csz = 2 * rsz;                               // complex element size
+    pl->sm_fftx_fwd = (size_t(nx) + 2 * size_t(pl->px_fwd) * nx) * csz;
+    pl->sm_ffty_fwd = (size_t(ny) + 2 * size_t(pl->tk_fwd) * ny) * csz;
+    pl->sm_ffty_inv = (size_t(ny) + 6 * size_t(pl->tk_inv) * ny) * csz;
+    pl->sm_fftx_inv = (size_t(nx) + 4 * size_t(pl->px_inv) * nx) * csz;
+    pl->sm_col = size_t(col_block) * nz * (4 * csz + 2 * rsz);
+    pl->sm_interp = size_t(kInterpWarps) * (2 * kMaxSupport + kMaxNz) * rsz;
     const size_t smax = 227 * 1024;
     if (pl->sm_fftx_fwd > smax || pl->sm_ffty_fwd > smax || pl->sm_ffty_inv > smax ||
         pl->sm_fftx_inv > smax || pl->sm_col > smax) {
         release(pl);
         return DPSLAB_ERR_GRID;
     }
-    cudaFuncSetAttribute(k_fftx_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
-    cudaFuncSetAttribute(k_ffty_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
-    cudaFuncSetAttribute(k_ffty_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
-    cudaFuncSetAttribute(k_fftx_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
-    cudaFuncSetAttribute(k_column, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
-    cudaFuncSetAttribute(k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
+    if (mixed) {
+        cudaFuncSetAttribute(k_fftx_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
+        cudaFuncSetAttribute(k_ffty_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
+        cudaFuncSetAttribute(k_ffty_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
+        cudaFuncSetAttribute(k_fftx_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
+        cudaFuncSetAttribute(k_column_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
+        cudaFuncSetAttribute(k_interp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
+    } else {
+        cudaFuncSetAttribute(k_fftx_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
+        cudaFuncSetAttribute(k_ffty_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
+        cudaFuncSetAttribute(k_ffty_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
+        cudaFuncSetAttribute(k_fftx_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
+        cudaFuncSetAttribute(k_column, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
+        cudaFuncSetAttribute(k_interp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
+    }
     if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
     *out = pl;
     return DPSLAB_OK;
@@ -1185,7 +1592,8 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     } while (0)
 
     DPS_CUDA(cudaMemsetAsync(kp.status, 0, sizeof(int), st));
-    DPS_CUDA(cudaMemsetAsync(kp.rho, 0, 2 * pl->G * sizeof(double), st));
+    const size_t rsz = kp.mixed ? sizeof(float) : sizeof(double);
+    DPS_CUDA(cudaMemsetAsync(kp.rho, 0, 2 * pl->G * rsz, st));
     if (kp.near_on) {
         DPS_CUDA(cudaMemsetAsync(kp.cell_count, 0, (size_t(kp.ncells) + 1) * sizeof(int), st));
         DPS_CUDA(cudaMemsetAsync(kp.cell_fill, 0, (size_t(kp.ncells) + 1) * sizeof(int), st));
@@ -1193,25 +1601,46 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     mark(0);
     LAUNCH(k_prepare<<<nb, kChargeThreads, 0, st>>>(kp));
     mark(1);
-    LAUNCH(k_spread<<<3 * n, 128, 0, st>>>(kp));
+    if (kp.mixed) LAUNCH(k_spread<float><<<3 * n, 128, 0, st>>>(kp));
+    else LAUNCH(k_spread<double><<<3 * n, 128, 0, st>>>(kp));
     mark(2);
     const int npairs = kp.nz * kp.ny;
-    LAUNCH(k_fftx_fwd<<<(npairs + pl->px_fwd - 1) / pl->px_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
-    mark(3);
-    LAUNCH(k_ffty_fwd<<<dim3((kp.nxh + pl->tk_fwd - 1) / pl->tk_fwd, 2 * kp.nz), 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
-    mark(4);
-    LAUNCH(k_column<<<kp.n_col_blocks, kColThreads, pl->sm_col, st>>>(kp));
-    mark(5);
-    LAUNCH(k_ffty_inv<<<dim3((kp.nxh + pl->tk_inv - 1) / pl->tk_inv, kp.nz), 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
-    mark(6);
-    LAUNCH(k_fftx_inv<<<(kp.nz * kp.ny + pl->px_inv - 1) / pl->px_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
-    mark(7);
-    LAUNCH(k_interp<<<(n + kInterpWarps - 1) / kInterpWarps, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
+    const dim3 gy_fwd((kp.nxh + pl->tk_fwd - 1) / pl->tk_fwd, 2 * kp.nz);
+    const dim3 gy_inv((kp.nxh + pl->tk_inv - 1) / pl->tk_inv, kp.nz);
+    const int gx_fwd = (npairs + pl->px_fwd - 1) / pl->px_fwd;
+    const int gx_inv = (kp.nz * kp.ny + pl->px_inv - 1) / pl->px_inv;
+    const int gi = (n + kInterpWarps - 1) / kInterpWarps;
+    if (kp.mixed) {
+        LAUNCH(k_fftx_fwd<float><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
+        mark(3);
+        LAUNCH(k_ffty_fwd<float><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
+        mark(4);
+        LAUNCH(k_column_mixed<<<kp.n_col_blocks, kColThreadsM, pl->sm_col, st>>>(kp));
+        mark(5);
+        LAUNCH(k_ffty_inv<float><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
+        mark(6);
+        LAUNCH(k_fftx_inv<float><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
+        mark(7);
+        LAUNCH(k_interp<float><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
+    } else {
+        LAUNCH(k_fftx_fwd<double><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
+        mark(3);
+        LAUNCH(k_ffty_fwd<double><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
+        mark(4);
+        LAUNCH(k_column<<<kp.n_col_blocks, kColThreads, pl->sm_col, st>>>(kp));
+        mark(5);
+        LAUNCH(k_ffty_inv<double><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
+        mark(6);
+        LAUNCH(k_fftx_inv<double><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
+        mark(7);
+        LAUNCH(k_interp<double><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
+    }
     mark(8);
     if (kp.near_on) {
         LAUNCH(k_scan_cells<<<1, 1024, 0, st>>>(kp));
         LAUNCH(k_scatter_cells<<<nb, kChargeThreads, 0, st>>>(kp));
-        LAUNCH(k_near<<<(n + 127) / 128, 128, 0, st>>>(kp));
+        if (kp.mixed) LAUNCH(k_near<float><<<(n + 127) / 128, 128, 0, st>>>(kp));
+        else LAUNCH(k_near<double><<<(n + 127) / 128, 128, 0, st>>>(kp));
     }
     mark(9);
     LAUNCH(k_origin<<<nb, kChargeThreads, 0, st>>>(kp));
@@ -1279,9 +1708,11 @@ extern "C" int dpslab_debug_fetch(dpslab_plan* plan, int which, void* host_dst, 
     const size_t n = size_t(plan->last_n);
     const void* src = nullptr;
     size_t want = 0;
+    const size_t rsz = kp.mixed ? sizeof(float) : sizeof(double);
+    size_t count = 0;   // grid elements to widen from float (mixed)
     switch (which) {
-        case 0: src = kp.rho; want = 2 * plan->G * sizeof(double); break;
-        case 1: src = kp.fields; want = plan->G * sizeof(double4_32a); break;
+        case 0: src = kp.rho; want = 2 * plan->G * sizeof(double); count = 2 * plan->G; break;
+        case 1: src = kp.fields; want = plan->G * 4 * sizeof(double); count = 4 * plan->G; break;
         case 2: src = kp.far; want = n * sizeof(double4_32a); break;
         case 3: src = kp.nearv; want = n * sizeof(double4_32a); break;
         case 4: {
@@ -1297,6 +1728,13 @@ extern "C" int dpslab_debug_fetch(dpslab_plan* plan, int which, void* host_dst, 
     if (bytes != want) return DPSLAB_ERR_INVALID_ARG;
     if (which == 3 && !kp.near_on) {
         std::memset(host_dst, 0, bytes);
+        return DPSLAB_OK;
+    }
+    if (count && rsz == sizeof(float)) {
+        std::vector<float> tmp(count);
+        DPS_CUDA(cudaMemcpy(tmp.data(), src, count * sizeof(float), cudaMemcpyDeviceToHost));
+        double* d = static_cast<double*>(host_dst);
+        for (size_t i = 0; i < count; ++i) d[i] = tmp[i];
         return DPSLAB_OK;
     }
     DPS_CUDA(cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost));
@@ -1404,7 +1842,7 @@ extern "C" int dpslab_near_field_static(const dpslab_params* p, int64_t n, const
     k_prepare<<<nb, kChargeThreads, 0, st>>>(kp);
     k_scan_cells<<<1, 1024, 0, st>>>(kp);
     k_scatter_cells<<<nb, kChargeThreads, 0, st>>>(kp);
-    k_near<<<int((n + 127) / 128), 128, 0, st>>>(kp);
+    k_near<double><<<int((n + 127) / 128), 128, 0, st>>>(kp);
     DPS_CUDA(cudaGetLastError());
     DPS_CUDA(cudaMemcpyAsync(out, kp.nearv, size_t(n) * 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     int status = 0;

@@ -10,6 +10,11 @@ from paper_2101_07088_b300 import dpslab
 # Parity bar for the FP64 path: relative L2 of forces, relative energy and
 # max |phi error| / max |phi|.
 TOL_FP64 = 1e-10
+# Mixed precision (FP32 grids, FFTs, spreading, interpolation, near field,
+# FP64 correction coefficients, k = 0 mode and energy): force and energy
+# targets of the method's mixed-precision form, relative to FP64.
+TOL_MIXED_FORCE = 1e-5
+TOL_MIXED_ENERGY = 1e-7
 
 
 def oracle_params(Lx, Ly, H, gw, tol, nx, ny, nz=0, eps=1.0, eps_b=1.0, eps_t=1.0, xi=0.0, r_cut=0.0, n_sigma=0.0):

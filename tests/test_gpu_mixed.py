@@ -1,0 +1,77 @@
+"""Mixed-precision path (DPSLAB_MIXED) vs the FP64 oracle and the FP64 GPU
+path (needs a B300).
+
+Targets: relative L2 force error <= 1e-5 and relative energy error <= 1e-7
+against FP64 at the same discretisation; potentials are reported."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import (TOL_MIXED_ENERGY, TOL_MIXED_FORCE, gpu_solve, oracle_params, plan_for, rel_l2,
+                         rel_max)
+from oracle import solver as osolver
+from paper_2101_07088_b300 import build, dpslab, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def _check(ref, out, label):
+    errs = dict(force=rel_l2(out["force"], ref["force"]), U=abs(out["U"] - ref["U"]) / abs(ref["U"]),
+                phi=rel_max(out["phi"], ref["phi"]))
+    print(label, "mixed errors:", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert errs["force"] < TOL_MIXED_FORCE, errs
+    assert errs["U"] < TOL_MIXED_ENERGY, errs
+    return errs
+
+
+CASES = [
+    ("c1_uniform_n128", None),
+    ("c2_jumps_n16384", None),
+    ("c2_metal_bottom_n16384", None),
+]
+
+
+@pytest.mark.parametrize("name,_", CASES, ids=[c[0] for c in CASES])
+def test_mixed_against_oracle(name, _):
+    pos, q, p = synth.workload(name)
+    P = oracle_params(p["Lx"], p["Ly"], p["H"], p["gw"], p["tol"], p["nx"], p["ny"], nz=p["nz"],
+                      eps_b=p["eps_b"], eps_t=p["eps_t"], r_cut=p["r_cut"])
+    ref = osolver.solve(pos, q, P)
+    out = gpu_solve(plan_for(P, len(q), precision=dpslab.MIXED), pos, q)
+    _check(ref, out, name)
+
+
+def test_mixed_small_ragged_and_paper_rule():
+    P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, 40, nz=37, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
+    pos, q = synth.electrolyte(102, 24.0, 20.0, 1.0, 19.0, seed=3)
+    _check(osolver.solve(pos, q, P), gpu_solve(plan_for(P, 102, precision=dpslab.MIXED), pos, q), "ragged")
+    P = oracle_params(2.0, 2.0, 1.0, 0.01, 1e-4, 38, 38, eps_b=0.05, eps_t=0.02)
+    pos, q = synth.electrolyte(40, 2.0, 2.0, 0.045, 0.955, seed=5)
+    _check(osolver.solve(pos, q, P), gpu_solve(plan_for(P, 40, precision=dpslab.MIXED), pos, q), "paper-rule")
+
+
+def test_mixed_against_fp64_gpu_at_one_million_charges():
+    """2^20 charges, 1024 x 1024 x 128: the oracle would take hours, so the
+    mixed path is compared with the FP64 GPU path (itself held to 1e-10
+    against the oracle on every smaller case)."""
+    pos, q, p = synth.workload("c3_jumps_n1048576")
+    P = oracle_params(p["Lx"], p["Ly"], p["H"], p["gw"], p["tol"], p["nx"], p["ny"], nz=p["nz"],
+                      eps_b=p["eps_b"], eps_t=p["eps_t"], r_cut=p["r_cut"])
+    plan64 = plan_for(P, len(q))
+    ref = gpu_solve(plan64, pos, q)
+    plan64.close()
+    plan32 = plan_for(P, len(q), precision=dpslab.MIXED)
+    out = gpu_solve(plan32, pos, q)
+    _check(ref, out, "c3")
+    # zero net lateral force (walls push only along z) holds at any size
+    s = np.sum(np.abs(out["force"][:, :2]))
+    assert abs(np.sum(out["force"][:, 0])) < 1e-6 * s and abs(np.sum(out["force"][:, 1])) < 1e-6 * s
