@@ -14,6 +14,16 @@ enum : int {
     kStatusNonFinite = 2,
 };
 
+// One spreading source with its support precomputed: grid indices
+// xlo..xlo+sx-1, ylo..ylo+sy-1 (unwrapped) and nodes j0..j1, offsets of the
+// first x and y index from the source, strength, and whether it also feeds
+// rho_o (a charge of C_over).
+struct SrcRec {
+    double z, q, d0x, d0y;
+    int xlo, ylo, j0, j1;
+    int sx, sy, over, pad;
+};
+
 // Everything a kernel needs, passed by value.
 struct KP {
     // problem
@@ -32,6 +42,11 @@ struct KP {
     // near-field kernel widths: averaged (Eq. (GnearK)) and pointwise (Eq. (Gnear))
     double na1, na2, pa1, pa2;   // a2 = 0 encodes "infinite" (xi = 0), a1 == a2 disables
     int near_on;
+    // Narrow widths (1/a2 close to 1/a1): the averaged kernel as
+    // (2/sqrt(pi)) int_{1/a2}^{1/a1} e^{-r^2 s^2} ds by 4-point Gauss-Legendre,
+    // nodes gq_s and weights gq_w on that interval (used in float)
+    int near_quad;
+    float gq_s[4], gq_w[4];
     // charges
     int n;
     const double* pos;
@@ -61,6 +76,13 @@ struct KP {
     // particle outputs
     double4_32a* far;             // [n] (phibar, Ebar)
     double4_32a* nearv;           // [n]
+    // spreading tiles: 16 x 16 xy grid points by `slab` z nodes; the sources
+    // (charges and their images) are counting-sorted into (slab, tile) buckets
+    int ntx, nty, ntiles, tile_r, slab, nslabs, nbuckets, supx, supy;
+    int* tile_count;          // per bucket
+    int* tile_start;          // nbuckets + 1
+    int* tile_fill;
+    struct SrcRec* srcs;      // bucketed source records
     // cell list
     int ncx, ncy, ncz, ncells;
     double cwx, cwy, cwz;     // cell widths
@@ -69,6 +91,7 @@ struct KP {
     int* cell_start;          // ncells + 1
     int* cell_fill;
     double4_32a* sorted;
+    float4* sorted_rel;       // float offsets from the cell corner, and q (mixed near field)
     int* sorted_idx;
     // reductions
     double* part_gauge_far;   // one per column block
@@ -135,6 +158,25 @@ __device__ __forceinline__ void near_kernel(R r, R a1, R a2, R gw, R eps, R& g, 
     const R s = R(1) / (R(12.566370614359172) * eps);   // 1/(4 pi eps)
     g = (v1 - v2) * s;
     d = (d1 - d2) * s;
+}
+
+// Averaged near-field kernel in float without cancellation (narrow widths):
+// Gbar = (1/(4 pi eps)) (2/sqrt(pi)) int e^{-r^2 s^2} ds and
+// (1/r) dGbar/dr = -(1/(4 pi eps)) (4/sqrt(pi)) int s^2 e^{-r^2 s^2} ds over
+// s in [1/a2, 1/a1]; the erf difference of Eq. (GnearK) written as an integral.
+__device__ __forceinline__ void near_kernel_quad(const KP& kp, float r, float& g, float& d) {
+    const float r2 = r * r;
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float s = kp.gq_s[i];
+        const float e = kp.gq_w[i] * expf(-r2 * s * s);
+        a += e;
+        b += s * s * e;
+    }
+    const float c = float(1.0 / (12.566370614359172 * kp.eps));
+    g = 1.1283791670955126f * a * c;
+    d = -2.2567583341910252f * b * c;
 }
 
 }  // namespace dps

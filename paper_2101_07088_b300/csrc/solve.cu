@@ -20,7 +20,14 @@ constexpr int kColBlock = 4;        // k_par columns per block of the column ker
 constexpr int kColThreads = 32 * kColBlock;
 constexpr int kChargeThreads = 256;
 constexpr int kInterpWarps = 8;
+constexpr int kTile = 16;           // spreading tile: kTile x kTile xy grid points, one thread each
+constexpr int kSpreadBatch = 32;    // sources per batch in the tiled spreading
 constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -83,72 +90,256 @@ __global__ void k_prepare(KP kp) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// spreading, Sec. 5.2.2 steps 2-3: one block per source (charge, bottom image,
-// top image); rho_i gets every source, rho_o only the charges of C_over.
-// Offsets from the grid points are taken in double; weights and grid in R.
-// ---------------------------------------------------------------------------
-template <class R>
-__global__ void k_spread(KP kp) {
-    __shared__ R wx[kMaxSupport], wy[kMaxSupport], wzs[kMaxNz];
-    __shared__ int s_j0, s_j1;
-    const int slot = blockIdx.x;
-    const int k = slot % kp.n;
-    const int kind = slot / kp.n;
-    const double4_32a p = kp.part[k];
-    double z = p.z, q = p.w;
-    const bool near_b = z <= 2.0 * kp.HE, near_t = z >= kp.H - 2.0 * kp.HE;
-    bool over = near_b || near_t;
-    if (kind == 1) {
-        if (!near_b) return;
-        z = -z; q = -kp.Gb * q; over = false;           // Eq. (ims)
-    } else if (kind == 2) {
-        if (!near_t) return;
-        z = 2.0 * kp.H - z; q = -kp.Gt * q; over = false;
-    }
-    if (q == 0.0) return;
-    const double x = p.x, y = p.y, HE = kp.HE;
-    const int ix0 = int(ceil((x - HE) / kp.hx)), ix1 = int(floor((x + HE) / kp.hx));
-    const int iy0 = int(ceil((y - HE) / kp.hy)), iy1 = int(floor((y + HE) / kp.hy));
-    const int sx = ix1 - ix0 + 1, sy = iy1 - iy0 + 1;
-    const double inv2g2 = 1.0 / (2.0 * kp.gt * kp.gt);
-    if (threadIdx.x == 0) { s_j0 = kp.nz; s_j1 = -1; }
+// exclusive scan of count[0..n) into start[0..n], one block of 1024 threads
+__global__ void k_scan(const int* count, int* start, int n) {
+    __shared__ int sums[1024];
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int chunk = (n + bs - 1) / bs;
+    const int lo = min(n, tid * chunk), hi = min(n, lo + chunk);
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += count[i];
+    sums[tid] = s;
     __syncthreads();
-    for (int j = threadIdx.x; j < kp.nz; j += blockDim.x) {
-        if (fabs(kp.zn[j] - z) <= HE) {
-            atomicMin(&s_j0, j);
-            atomicMax(&s_j1, j);
+    for (int o = 1; o < bs; o <<= 1) {
+        const int v = tid >= o ? sums[tid - o] : 0;
+        __syncthreads();
+        sums[tid] += v;
+        __syncthreads();
+    }
+    int run = sums[tid] - s;
+    for (int i = lo; i < hi; ++i) {
+        start[i] = run;
+        run += count[i];
+    }
+    if (tid == bs - 1) start[n] = sums[bs - 1];
+}
+
+// Nodes j with |z_j - z| <= H_E (the nodes descend in j): first an estimate
+// from arccos, then the exact test on the node values.
+__device__ __forceinline__ void node_range(const KP& kp, double z, int& j0, int& j1) {
+    const int N = kp.nz;
+    const double sc = double(N - 1) / 3.14159265358979323846;
+    auto jof = [&](double zz) {
+        const double sv = fmin(1.0, fmax(-1.0, 2.0 * (zz - kp.a) / kp.Hbar - 1.0));
+        return acos(sv) * sc;
+    };
+    j0 = max(0, int(floor(jof(z + kp.HE))) - 1);
+    j1 = min(N - 1, int(ceil(jof(z - kp.HE))) + 1);
+    while (j0 <= j1 && kp.zn[j0] - z > kp.HE) ++j0;
+    while (j1 >= j0 && z - kp.zn[j1] > kp.HE) --j1;
+    // the estimate brackets the range; widen if rounding cut it
+    while (j0 > 0 && fabs(kp.zn[j0 - 1] - z) <= kp.HE) --j0;
+    while (j1 < N - 1 && fabs(kp.zn[j1 + 1] - z) <= kp.HE) ++j1;
+}
+
+// Source s (0: the charge, 1: its image below z = 0, 2: above z = H) of
+// charge p, Sec. 5.2.2 step 1 and Eq. (ims); false if it does not exist.
+__device__ __forceinline__ bool make_source(const KP& kp, const double4_32a& p, int s, SrcRec& r, int& tile) {
+    double z = p.z, q = p.w;
+    const bool nb = p.z <= 2.0 * kp.HE, nt = p.z >= kp.H - 2.0 * kp.HE;
+    if (s == 1) {
+        if (!nb || kp.Gb == 0.0) return false;
+        z = -p.z; q = -kp.Gb * p.w;
+    } else if (s == 2) {
+        if (!nt || kp.Gt == 0.0) return false;
+        z = 2.0 * kp.H - p.z; q = -kp.Gt * p.w;
+    }
+    const double HE = kp.HE;
+    r.z = z;
+    r.q = q;
+    r.xlo = int(ceil((p.x - HE) / kp.hx));
+    r.ylo = int(ceil((p.y - HE) / kp.hy));
+    r.sx = int(floor((p.x + HE) / kp.hx)) - r.xlo + 1;
+    r.sy = int(floor((p.y + HE) / kp.hy)) - r.ylo + 1;
+    r.d0x = double(r.xlo) * kp.hx - p.x;
+    r.d0y = double(r.ylo) * kp.hy - p.y;
+    node_range(kp, z, r.j0, r.j1);
+    r.over = (s == 0) && (nb || nt);
+    r.pad = 0;
+    const int tx = min(kp.ntx - 1, int(floor(p.x / kp.hx)) / kTile);
+    const int ty = min(kp.nty - 1, int(floor(p.y / kp.hy)) / kTile);
+    tile = ty * kp.ntx + tx;
+    return r.j0 <= r.j1 && q != 0.0;
+}
+
+__global__ void k_count_sources(KP kp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kp.n) return;
+    const double4_32a p = kp.part[k];
+    for (int s = 0; s < 3; ++s) {
+        SrcRec r;
+        int tile;
+        if (!make_source(kp, p, s, r, tile)) continue;
+        for (int sl = r.j0 / kp.slab; sl <= r.j1 / kp.slab; ++sl) atomicAdd(&kp.tile_count[sl * kp.ntiles + tile], 1);
+    }
+}
+
+__global__ void k_scatter_sources(KP kp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kp.n) return;
+    const double4_32a p = kp.part[k];
+    for (int s = 0; s < 3; ++s) {
+        SrcRec r;
+        int tile;
+        if (!make_source(kp, p, s, r, tile)) continue;
+        for (int sl = r.j0 / kp.slab; sl <= r.j1 / kp.slab; ++sl) {
+            const int b = sl * kp.ntiles + tile;
+            kp.srcs[kp.tile_start[b] + atomicAdd(&kp.tile_fill[b], 1)] = r;
         }
     }
-    for (int i = threadIdx.x; i < sx; i += blockDim.x) {
-        const double d = double(ix0 + i) * kp.hx - x;
-        wx[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
-    }
-    for (int i = threadIdx.x; i < sy; i += blockDim.x) {
-        const double d = double(iy0 + i) * kp.hy - y;
-        wy[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
+}
+
+// ---------------------------------------------------------------------------
+// spreading, Sec. 5.2.2 steps 2-3, output-stationary: block (tile, z slab)
+// owns kTile x kTile grid columns (one thread each) and kp.slab z nodes, and
+// sums every source of the neighbouring tiles into shared memory; each grid
+// point is written once. rho_i gets every source, rho_o only charges of
+// C_over (z within 2 H_E of a wall; images lie outside 0 < z < H). The
+// support is the closed box |dx|, |dy|, |dz| <= H_E with the same index rule
+// ceil((x - H_E)/h) .. floor((x + H_E)/h) as a direct scatter.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(kTile * kTile) k_spread_tiled(KP kp) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int B = kSpreadBatch;
+    const int SZ = kp.slab;
+    const int TX = (kp.supx + 31) & ~31, TY = (kp.supy + 31) & ~31;   // table strides
+    R* acc_i = reinterpret_cast<R*>(smraw);                 // [SZ][256]
+    R* acc_o = acc_i + SZ * kTile * kTile;                   // [SZ][256]
+    R* wxt = acc_o + SZ * kTile * kTile;                     // [B][TX]
+    R* wyt = wxt + B * TX;                                   // [B][TY]
+    R* wzt = wyt + B * TY;                                   // [B][SZ]
+    __shared__ int s_dx0[B], s_dy0[B], s_sx[B], s_sy[B], s_z0[B], s_z1[B], s_over[B], s_ok[B];
+    __shared__ R s_q[B];
+    __shared__ double s_d0x[B], s_d0y[B], s_zs[B];
+    __shared__ int s_tiles[64], s_pre[65];
+    __shared__ unsigned s_mx[kTile], s_my[kTile];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x, txi = tile % kp.ntx, tyi = tile / kp.ntx;
+    const int slab = blockIdx.y;
+    const int js = slab * SZ, je = min(kp.nz, js + SZ);
+    const int gx0 = txi * kTile, gy0 = tyi * kTile;
+    const int tw = min(kp.nx, gx0 + kTile) - gx0, th = min(kp.ny, gy0 + kTile) - gy0;
+    const int lx = tid % kTile, ly = tid / kTile;
+    const int gx = gx0 + lx, gy = gy0 + ly;
+    const bool mine = lx < tw && ly < th;
+    for (int i = tid; i < 2 * SZ * kTile * kTile; i += blockDim.x) acc_i[i] = R(0);
+    if (tid == 0) {
+        const int r = kp.tile_r;
+        const int nxs = min(2 * r + 1, kp.ntx), nys = min(2 * r + 1, kp.nty);
+        int cnt = 0, run = 0;
+        for (int oy = 0; oy < nys; ++oy) {
+            const int ty = nys == kp.nty ? oy : wrap_index(tyi - r + oy, kp.nty);
+            for (int ox = 0; ox < nxs; ++ox) {
+                const int tx = nxs == kp.ntx ? ox : wrap_index(txi - r + ox, kp.ntx);
+                const int bk = slab * kp.ntiles + ty * kp.ntx + tx;
+                s_tiles[cnt] = bk;
+                s_pre[cnt] = run;
+                run += kp.tile_start[bk + 1] - kp.tile_start[bk];
+                ++cnt;
+            }
+        }
+        s_pre[cnt] = run;
+        s_tiles[63] = cnt;
     }
     __syncthreads();
-    const int j0 = s_j0, sz = s_j1 - s_j0 + 1;
-    if (sz <= 0) return;
-    for (int i = threadIdx.x; i < sz; i += blockDim.x) {
-        const double d = kp.zn[j0 + i] - z;
-        wzs[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
+    const int ntl = s_tiles[63], total = s_pre[ntl];
+    const R ig2 = R(1.0 / (2.0 * kp.gt * kp.gt));
+    const R s1 = R(kp.s1norm);
+    for (int base = 0; base < total; base += B) {
+        // phase 1: warp 0, one lane per source of the batch; then the
+        // coverage masks, transposed with ballots: bit b of s_mx[lx] says
+        // source b covers tile column lx (likewise s_my[ly] for rows)
+        if (tid < B) {
+            const int c = base + tid;
+            int ok = 0;
+            unsigned xm = 0u, ym = 0u;
+            if (c < total) {
+                int t = 0;
+                while (s_pre[t + 1] <= c) ++t;
+                const SrcRec r = kp.srcs[kp.tile_start[s_tiles[t]] + (c - s_pre[t])];
+                // offset of the tile's first column/row within the support (mod n)
+                const int dx0 = wrap_index(gx0 - r.xlo, kp.nx), dy0 = wrap_index(gy0 - r.ylo, kp.ny);
+                for (int l = 0; l < tw; ++l) {
+                    int i = dx0 + l;
+                    if (i >= kp.nx) i -= kp.nx;
+                    if (i < r.sx) xm |= 1u << l;
+                }
+                for (int l = 0; l < th; ++l) {
+                    int i = dy0 + l;
+                    if (i >= kp.ny) i -= kp.ny;
+                    if (i < r.sy) ym |= 1u << l;
+                }
+                const int z0 = max(r.j0, js), z1 = min(r.j1, je - 1);
+                ok = xm && ym && z0 <= z1;
+                s_dx0[tid] = dx0; s_dy0[tid] = dy0; s_sx[tid] = r.sx; s_sy[tid] = r.sy;
+                s_z0[tid] = z0; s_z1[tid] = z1; s_over[tid] = r.over; s_q[tid] = R(r.q);
+                s_d0x[tid] = r.d0x; s_d0y[tid] = r.d0y; s_zs[tid] = r.z;
+            }
+            s_ok[tid] = ok;
+            if (!ok) { xm = 0u; ym = 0u; }
+            for (int l = 0; l < kTile; ++l) {
+                const unsigned bx = __ballot_sync(0xffffffffu, (xm >> l) & 1u);
+                const unsigned by = __ballot_sync(0xffffffffu, (ym >> l) & 1u);
+                if (tid == 0) { s_mx[l] = bx; s_my[l] = by; }
+            }
+        }
+        __syncthreads();
+        // phase 2: warp w fills the weight tables of sources w, w + 8, ...
+        // (offset d = d0 + i h, d0 taken in double per source)
+        for (int b = warp; b < B; b += (kTile * kTile) / 32) {
+            if (!s_ok[b]) continue;
+            const R d0x = R(s_d0x[b]), d0y = R(s_d0y[b]);
+            for (int i = lane; i < s_sx[b]; i += 32) {
+                const R d = d0x + R(i) * R(kp.hx);
+                wxt[b * TX + i] = s1 * dexp(-d * d * ig2);
+            }
+            for (int i = lane; i < s_sy[b]; i += 32) {
+                const R d = d0y + R(i) * R(kp.hy);
+                wyt[b * TY + i] = s1 * dexp(-d * d * ig2);
+            }
+            for (int i = lane; i <= s_z1[b] - s_z0[b]; i += 32) {
+                const R d = R(kp.zn[s_z0[b] + i] - s_zs[b]);
+                wzt[b * SZ + i] = s1 * dexp(-d * d * ig2);
+            }
+        }
+        __syncthreads();
+        // phase 3: each thread adds the sources covering its grid column
+        if (mine) {
+            unsigned hits = s_mx[lx] & s_my[ly];
+            while (hits) {
+                const int b = __ffs(hits) - 1;
+                hits &= hits - 1u;
+                int ix = s_dx0[b] + lx;
+                if (ix >= kp.nx) ix -= kp.nx;
+                int iy = s_dy0[b] + ly;
+                if (iy >= kp.ny) iy -= kp.ny;
+                const R w = s_q[b] * wxt[b * TX + ix] * wyt[b * TY + iy];
+                const int z0 = s_z0[b], z1 = s_z1[b];
+                const R* wz = wzt + b * SZ - z0;
+                R* ai = acc_i + (z0 - js) * kTile * kTile + tid;
+                if (s_over[b]) {
+                    R* ao = acc_o + (z0 - js) * kTile * kTile + tid;
+                    for (int j = z0; j <= z1; ++j, ai += kTile * kTile, ao += kTile * kTile) {
+                        const R v = w * wz[j];
+                        *ai += v;
+                        *ao += v;
+                    }
+                } else {
+                    for (int j = z0; j <= z1; ++j, ai += kTile * kTile) *ai += w * wz[j];
+                }
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    R* rho = static_cast<R*>(kp.rho);
-    const size_t G = size_t(kp.nz) * kp.ny * kp.nx;
-    const int sxy = sx * sy;
-    const R qr = R(q);
-    for (int t = threadIdx.x; t < sz * sxy; t += blockDim.x) {
-        const int jz = t / sxy;
-        const int r = t - jz * sxy;
-        const int iy = r / sx;
-        const int ix = r - iy * sx;
-        const R v = qr * wzs[jz] * wy[iy] * wx[ix];
-        const size_t g = (size_t(j0 + jz) * kp.ny + wrap_index(iy0 + iy, kp.ny)) * kp.nx + wrap_index(ix0 + ix, kp.nx);
-        atomicAdd(rho + g, v);
-        if (over) atomicAdd(rho + G + g, v);
+    if (mine) {
+        R* rho = static_cast<R*>(kp.rho);
+        const size_t G = size_t(kp.nz) * kp.ny * kp.nx;
+        for (int j = js; j < je; ++j) {
+            const size_t g = (size_t(j) * kp.ny + gy) * kp.nx + gx;
+            rho[g] = acc_i[(j - js) * kTile * kTile + tid];
+            rho[G + g] = acc_o[(j - js) * kTile * kTile + tid];
+        }
     }
 }
 
@@ -568,13 +759,14 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int CB = kColBlockM;
     const int N = kp.nz;
+    const int NP = N + 1;              // padded column stride (shared-memory banks)
     const int M = kp.ny * kp.nxh;
     float2* Vi = reinterpret_cast<float2*>(smraw);
-    float2* Vo = Vi + CB * N;
-    float2* Ci = Vo + CB * N;
-    float2* Co = Ci + CB * N;
-    float* cpv = reinterpret_cast<float*>(Co + CB * N);
-    float* xe = cpv + CB * N;
+    float2* Vo = Vi + CB * NP;
+    float2* Ci = Vo + CB * NP;
+    float2* Co = Ci + CB * NP;
+    float* cpv = reinterpret_cast<float*>(Co + CB * NP);
+    float* xe = cpv + CB * NP;
     __shared__ double s_k[CB], s_K[CB], s_mult[CB], s_gauge[CB];
     __shared__ float s_den[CB], s_ekH[CB];
     __shared__ int s_valid[CB], s_corr[CB];
@@ -606,8 +798,8 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
             vi = sp[size_t(j) * M + col];
             vo = sp[size_t(N + j) * M + col];
         }
-        Vi[c * N + j] = vi;
-        Vo[c * N + j] = vo;
+        Vi[c * NP + j] = vi;
+        Vo[c * NP + j] = vo;
     }
     __syncthreads();
 
@@ -615,7 +807,7 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     for (int t = tid; t < 2 * CB * JE; t += bs) {
         const int f = t / (CB * JE), r = t - f * CB * JE, c = r / JE, a = r - c * JE;
         if (a < m - a) {
-            float2* V = (f ? Vo : Vi) + c * N;
+            float2* V = (f ? Vo : Vi) + c * NP;
             const float2 va = V[a], vb = V[m - a];
             V[a] = cadd(va, vb);
             V[m - a] = csub(va, vb);
@@ -627,8 +819,8 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         const int c = t / N, q = t - c * N;
         const bool odd = q >= JE;
         const int na = odd ? JO : JE;
-        const float2* vi = Vi + c * N;
-        const float2* vo = Vo + c * N;
+        const float2* vi = Vi + c * NP;
+        const float2* vo = Vo + c * NP;
         float ix = 0.f, iy = 0.f, ox = 0.f, oy = 0.f;
         for (int a = 0; a < na; ++a) {
             const float w = kp.cft32[size_t(a) * N + q];
@@ -640,8 +832,8 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
             oy = fmaf(w, v.y, oy);
         }
         const int n = odd ? 2 * (q - JE) + 1 : 2 * q;
-        Ci[c * N + n] = make_float2(ix * scale, iy * scale);
-        Co[c * N + n] = make_float2(ox * scale, oy * scale);
+        Ci[c * NP + n] = make_float2(ix * scale, iy * scale);
+        Co[c * NP + n] = make_float2(ox * scale, oy * scale);
     }
     __syncthreads();
 
@@ -649,10 +841,10 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     if (tid < 2 * CB) {
         const int c = tid >> 1, ch = tid & 1;
         const float K2 = float(s_K[c] * s_K[c]);
-        float2* Fi = Ci + c * N;
-        float2* Fo = Co + c * N;
-        float* cq = cpv + c * N;
-        float* xc = xe + c * N;
+        float2* Fi = Ci + c * NP;
+        float2* Fo = Co + c * NP;
+        float* cq = cpv + c * NP;
+        float* xc = xe + c * NP;
         int prev = -1;
         for (int n = ch; n < N; n += 2) {
             const float an = n >= 2 ? -K2 * kp.j2l32[n] : 0.f;
@@ -686,9 +878,9 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     {
         const int c = tid >> 5, lane = tid & 31;
         const float K = float(s_K[c]);
-        const float2* Xi = Ci + c * N;
-        const float2* Xo = Co + c * N;
-        const float* xc = xe + c * N;
+        const float2* Xi = Ci + c * NP;
+        const float2* Xo = Co + c * NP;
+        const float* xc = xe + c * NP;
         float acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int n = lane; n < N; n += 32) {
             const float gtn = K > 0.f ? kp.u132[n] + K * kp.u232[n] : kp.u232[n];
@@ -701,7 +893,7 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
             else { acc[8] = fmaf(gtn, xc[n], acc[8]); acc[10] = fmaf(gbn, xc[n], acc[10]); }
         }
         double da[12];
-        for (int i = 0; i < 12; ++i) da[i] = warp_sum(double(acc[i]));
+        for (int i = 0; i < 12; ++i) da[i] = double(warp_sum_f(acc[i]));
         if (lane < 2) {
             const int f = lane;
             const double2 sFt = f ? make_double2(da[4], da[5]) : make_double2(da[0], da[1]);
@@ -724,29 +916,29 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     __syncthreads();
     for (int t = tid; t < 2 * CB * N; t += bs) {
         const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
-        float2* X = (f ? Co : Ci) + c * N;
+        float2* X = (f ? Co : Ci) + c * NP;
         const float2 mm = (n & 1) ? s_d[f][c] : s_c[f][c];
-        X[n] = cadd(X[n], cscale(mm, xe[c * N + n]));
+        X[n] = cadd(X[n], cscale(mm, xe[c * NP + n]));
     }
     __syncthreads();
     for (int t = tid; t < 2 * CB * N; t += bs) {
         const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
-        const float2* Y = (f ? Co : Ci) + c * N;
+        const float2* Y = (f ? Co : Ci) + c * NP;
         float2 v;
         if (n == 0) v = s_d[f][c];
         else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
         else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
-        (f ? Vo : Vi)[c * N + n] = v;
+        (f ? Vo : Vi)[c * NP + n] = v;
     }
     __syncthreads();
     for (int t = tid; t < 2 * CB * N; t += bs) {
         const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
-        const float2* Y = (f ? Vo : Vi) + c * N;
+        const float2* Y = (f ? Vo : Vi) + c * NP;
         float2 v;
         if (n == 0) v = s_c[f][c];
         else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
         else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
-        (f ? Co : Ci)[c * N + n] = v;
+        (f ? Co : Ci)[c * NP + n] = v;
     }
     __syncthreads();
 
@@ -754,7 +946,7 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     // correction coefficients, k = 0 slope, gauge partial sum (double)
     {
         const int c = tid >> 5, lane = tid & 31;
-        const float2 *yi = Ci + c * N, *ypi = Vi + c * N, *yo = Co + c * N, *ypo = Vo + c * N;
+        const float2 *yi = Ci + c * NP, *ypi = Vi + c * NP, *yo = Co + c * NP, *ypo = Vo + c * NP;
         float acc[20];
         for (int i = 0; i < 20; ++i) acc[i] = 0.f;
         for (int n = lane; n < N; n += 32) {
@@ -771,7 +963,7 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
             acc[18] = fmaf(wg, yi[n].x, acc[18]); acc[19] = fmaf(wg, yi[n].y, acc[19]);
         }
         double da[20];
-        for (int i = 0; i < 20; ++i) da[i] = warp_sum(double(acc[i]));
+        for (int i = 0; i < 20; ++i) da[i] = double(warp_sum_f(acc[i]));
         if (lane == 0 && s_valid[c]) {
             const double dz = 2.0 / Hbar;
             const double2 pi0 = make_double2(da[0], da[1]), dpi0 = make_double2(da[2] * dz, da[3] * dz);
@@ -819,8 +1011,8 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     for (int t = tid; t < JE * CB; t += bs) {
         const int c = t / JE, a = t - c * JE, col = col0 + c;
         if (col >= M) continue;
-        const float2* yi = Ci + c * N;
-        const float2* ypi = Vi + c * N;
+        const float2* yi = Ci + c * NP;
+        const float2* ypi = Vi + c * NP;
         float ex = 0, ey = 0, dex = 0, dey = 0, ox = 0, oy = 0, dox = 0, doy = 0;
         for (int r = 0; r < JE; ++r) {
             const float w = kp.tie32[size_t(r) * JE + a];
@@ -983,10 +1175,13 @@ __global__ void k_interp(KP kp) {
     R* wx = smi + w * (2 * kMaxSupport + kMaxNz);
     R* wy = wx + kMaxSupport;
     R* wzz = wy + kMaxSupport;
-    const int k = blockIdx.x * (blockDim.x >> 5) + w;
-    if (k >= kp.n) return;
+    const int slot = blockIdx.x * (blockDim.x >> 5) + w;
+    if (slot >= kp.n) return;
+    // charges in cell-list order when there is one: neighbouring warps then
+    // gather overlapping parts of the grid, which stay in L2
+    const int k = kp.near_on ? kp.sorted_idx[slot] : slot;
     const V4* fields = static_cast<const V4*>(kp.fields);
-    const double4_32a p = kp.part[k];
+    const double4_32a p = kp.near_on ? kp.sorted[slot] : kp.part[k];
     const double x = p.x, y = p.y, z = p.z, HE = kp.HE;
     const int ix0 = int(ceil((x - HE) / kp.hx)), ix1 = int(floor((x + HE) / kp.hx));
     const int iy0 = int(ceil((y - HE) / kp.hy)), iy1 = int(floor((y + HE) / kp.hy));
@@ -1000,18 +1195,21 @@ __global__ void k_interp(KP kp) {
         j1 = max(j1, __shfl_xor_sync(0xffffffffu, j1, o));
     }
     const int sz = j1 - j0 + 1;
-    const double inv2g2 = 1.0 / (2.0 * kp.gt * kp.gt);
+    const R ig2 = R(1.0 / (2.0 * kp.gt * kp.gt));
+    const R s1 = R(kp.s1norm);
+    // offsets: base in double, then d0 + i h in R
+    const R d0x = R(double(ix0) * kp.hx - x), d0y = R(double(iy0) * kp.hy - y);
     for (int i = lane; i < sx; i += 32) {
-        const double d = double(ix0 + i) * kp.hx - x;
-        wx[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
+        const R d = d0x + R(i) * R(kp.hx);
+        wx[i] = s1 * dexp(-d * d * ig2);
     }
     for (int i = lane; i < sy; i += 32) {
-        const double d = double(iy0 + i) * kp.hy - y;
-        wy[i] = R(kp.s1norm) * dexp(R(-d * d * inv2g2));
+        const R d = d0y + R(i) * R(kp.hy);
+        wy[i] = s1 * dexp(-d * d * ig2);
     }
     for (int i = lane; i < sz; i += 32) {
-        const double d = kp.zn[j0 + i] - z;
-        wzz[i] = R(kp.wz[j0 + i]) * (R(kp.s1norm) * dexp(R(-d * d * inv2g2)));
+        const R d = R(kp.zn[j0 + i] - z);
+        wzz[i] = R(kp.wz[j0 + i]) * (s1 * dexp(-d * d * ig2));
     }
     __syncwarp();
     const R wxy = R(kp.hx * kp.hy);
@@ -1027,8 +1225,12 @@ __global__ void k_interp(KP kp) {
         a2 = fma(wt, f.z, a2);
         a3 = fma(wt, f.w, a3);
     }
-    const double b0 = warp_sum(double(a0)), b1 = warp_sum(double(a1));
-    const double b2 = warp_sum(double(a2)), b3 = warp_sum(double(a3));
+    double b0, b1, b2, b3;
+    if (sizeof(R) == sizeof(float)) {
+        b0 = warp_sum_f(float(a0)); b1 = warp_sum_f(float(a1)); b2 = warp_sum_f(float(a2)); b3 = warp_sum_f(float(a3));
+    } else {
+        b0 = warp_sum(double(a0)); b1 = warp_sum(double(a1)); b2 = warp_sum(double(a2)); b3 = warp_sum(double(a3));
+    }
     if (lane == 0) kp.far[k] = make_double4_32a(b0, b1, b2, b3);
 }
 
@@ -1064,8 +1266,12 @@ __global__ void k_scatter_cells(KP kp) {
     if (k >= kp.n) return;
     const int c = kp.cell_of[k];
     const int slot = kp.cell_start[c] + atomicAdd(&kp.cell_fill[c], 1);
-    kp.sorted[slot] = kp.part[k];
+    const double4_32a p = kp.part[k];
+    kp.sorted[slot] = p;
     kp.sorted_idx[slot] = k;
+    const int cx = c % kp.ncx, cy = (c / kp.ncx) % kp.ncy, cz = c / (kp.ncx * kp.ncy);
+    kp.sorted_rel[slot] = make_float4(float(p.x - cx * kp.cwx), float(p.y - cy * kp.cwy), float(p.z - cz * kp.cwz),
+                                      float(p.w));
 }
 
 template <class R>
@@ -1081,7 +1287,14 @@ __device__ __forceinline__ void near_cell(const KP& kp, int cell, double x, doub
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < rc2) {
             R g, d;
-            near_kernel<R>(R(sqrt(r2)), R(kp.na1), R(kp.na2), R(kp.gw), R(kp.eps), g, d);
+            if (sizeof(R) == sizeof(float) && kp.near_quad) {
+                float gf, df;
+                near_kernel_quad(kp, float(sqrt(r2)), gf, df);
+                g = R(gf);
+                d = R(df);
+            } else {
+                near_kernel<R>(R(sqrt(r2)), R(kp.na1), R(kp.na2), R(kp.gw), R(kp.eps), g, d);
+            }
             const R qs = R(strength * src.w);
             phi += qs * g;
             ex -= qs * d * R(dx);
@@ -1121,6 +1334,76 @@ __global__ void k_near(KP kp) {
                 for (int ox = 0; ox < nxc; ++ox) {
                     const int xc = kp.ncx >= 3 ? wrap_index(cx - 1 + ox, kp.ncx) : ox;
                     near_cell<R>(kp, (zc * kp.ncy + yc) * kp.ncx + xc, x, y, z, zsign, zoff, st, rc2, phi, ex, ey, ez);
+                }
+            }
+        }
+    }
+    kp.nearv[kp.sorted_idx[s]] = make_double4_32a(phi, ex, ey, ez);
+}
+
+// Near field in float (mixed precision): positions are kept as float offsets
+// from their cell's corner, so a pair's separation is the offset difference
+// plus a whole number of cell widths; no double arithmetic per pair. Images:
+// the bottom image of a source in cell layer 0 sits at -z, so the z
+// separation from a target in layer 0 is z_t + z_s; for the top image use the
+// distances to z = H, which are (cell height - offset) in the top layer.
+__global__ void k_near_f32(KP kp) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= kp.n) return;
+    const float4 t = kp.sorted_rel[s];
+    const double4_32a ta = kp.sorted[s];
+    const int cx = min(kp.ncx - 1, max(0, int(ta.x / kp.cwx)));
+    const int cy = min(kp.ncy - 1, max(0, int(ta.y / kp.cwy)));
+    const int cz = min(kp.ncz - 1, max(0, int(ta.z / kp.cwz)));
+    const float cwx = float(kp.cwx), cwy = float(kp.cwy), cwz = float(kp.cwz);
+    const float Lx = float(kp.Lx), Ly = float(kp.Ly);
+    const float rc2 = float(kp.r_cut * kp.r_cut);
+    const bool wrap3x = kp.ncx >= 3, wrap3y = kp.ncy >= 3;
+    const int nxc = wrap3x ? 3 : kp.ncx, nyc = wrap3y ? 3 : kp.ncy;
+    float phi = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+    auto pair = [&](float dx, float dy, float dz, float qs) {
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < rc2) {
+            float g, d;
+            if (kp.near_quad) near_kernel_quad(kp, sqrtf(r2), g, d);
+            else near_kernel<float>(sqrtf(r2), float(kp.na1), float(kp.na2), float(kp.gw), float(kp.eps), g, d);
+            phi += qs * g;
+            ex -= qs * d * dx;
+            ey -= qs * d * dy;
+            ez -= qs * d * dz;
+        }
+    };
+    for (int pass = 0; pass < 3; ++pass) {
+        int zl, zh;
+        float st;
+        if (pass == 0) { zl = max(0, cz - 1); zh = min(kp.ncz - 1, cz + 1); st = 1.f; }
+        else if (pass == 1) {
+            if (!(ta.z < kp.r_cut) || kp.Gb == 0.0) continue;
+            zl = zh = 0; st = float(-kp.Gb);
+        } else {
+            if (!(kp.H - ta.z < kp.r_cut) || kp.Gt == 0.0) continue;
+            zl = zh = kp.ncz - 1; st = float(-kp.Gt);
+        }
+        for (int zc = zl; zc <= zh; ++zc) {
+            for (int oy = 0; oy < nyc; ++oy) {
+                const int yu = wrap3y ? cy - 1 + oy : oy;            // unwrapped neighbour row
+                const int yc = wrap3y ? wrap_index(yu, kp.ncy) : oy;
+                for (int ox = 0; ox < nxc; ++ox) {
+                    const int xu = wrap3x ? cx - 1 + ox : ox;
+                    const int xc = wrap3x ? wrap_index(xu, kp.ncx) : ox;
+                    const int cell = (zc * kp.ncy + yc) * kp.ncx + xc;
+                    const float sxh = float(cx - xu) * cwx, syh = float(cy - yu) * cwy;
+                    for (int q = kp.cell_start[cell]; q < kp.cell_start[cell + 1]; ++q) {
+                        const float4 src = kp.sorted_rel[q];
+                        float dx = t.x - src.x + sxh, dy = t.y - src.y + syh;
+                        if (!wrap3x) { if (dx > 0.5f * Lx) dx -= Lx; else if (dx < -0.5f * Lx) dx += Lx; }
+                        if (!wrap3y) { if (dy > 0.5f * Ly) dy -= Ly; else if (dy < -0.5f * Ly) dy += Ly; }
+                        float dz;
+                        if (pass == 0) dz = t.z - src.z + float(cz - zc) * cwz;
+                        else if (pass == 1) dz = t.z + src.z;
+                        else dz = -((cwz - t.z) + (cwz - src.z));
+                        pair(dx, dy, dz, st * src.w);
+                    }
                 }
             }
         }
@@ -1220,7 +1503,7 @@ struct dpslab_plan {
     int nxh = 0;
     size_t G = 0, S = 0;
     int px_fwd = 1, tk_fwd = 1, tk_inv = 1, px_inv = 1;
-    size_t sm_fftx_fwd = 0, sm_ffty_fwd = 0, sm_ffty_inv = 0, sm_fftx_inv = 0, sm_col = 0, sm_interp = 0;
+    size_t sm_fftx_fwd = 0, sm_ffty_fwd = 0, sm_ffty_inv = 0, sm_fftx_inv = 0, sm_col = 0, sm_interp = 0, sm_spread = 0;
     KP kp{};
     // allocations
     void* tables = nullptr;
@@ -1343,6 +1626,20 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
     kp.pa1 = std::sqrt(2.0) * p->gw;
     kp.na2 = kp.near_on ? std::sqrt(kp.na1 * kp.na1 + 1.0 / (d.xi * d.xi)) : 0.0;
     kp.pa2 = kp.near_on ? std::sqrt(kp.pa1 * kp.pa1 + 1.0 / (d.xi * d.xi)) : 0.0;
+    kp.near_quad = 0;
+    if (kp.near_on) {
+        // 4-point Gauss-Legendre on [1/a2, 1/a1] when r_cut (1/a1 - 1/a2) is small
+        const double s1 = 1.0 / kp.na1, s2 = 1.0 / kp.na2, hw = 0.5 * (s1 - s2), mid = 0.5 * (s1 + s2);
+        if ((s1 - s2) * d.r_cut < 0.05) {
+            const double x[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
+            const double w[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461, 0.3478548451374538};
+            for (int i = 0; i < 4; ++i) {
+                kp.gq_s[i] = float(mid + hw * x[i]);
+                kp.gq_w[i] = float(hw * w[i]);
+            }
+            kp.near_quad = 1;
+        }
+    }
     kp.nradx = int(t.radx.size());
     kp.nrady = int(t.rady.size());
     for (int i = 0; i < kp.nradx; ++i) kp.radx[i] = t.radx[i];
@@ -1361,8 +1658,25 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         kp.ncells = 1;
         kp.cwx = p->Lx; kp.cwy = p->Ly; kp.cwz = p->H;
     }
+    // spreading tiles
+    kp.ntx = (nx + kTile - 1) / kTile;
+    kp.nty = (ny + kTile - 1) / kTile;
+    kp.ntiles = kp.ntx * kp.nty;
+    {
+        // a source can reach the block's tile from r tiles away; one tile more
+        // when the last tile is narrower than kTile points
+        const int rx = int(std::ceil(d.HE / (kTile * d.hx))) + (nx % kTile ? 1 : 0);
+        const int ry = int(std::ceil(d.HE / (kTile * d.hy))) + (ny % kTile ? 1 : 0);
+        kp.tile_r = std::max(rx, ry);
+        if (kp.tile_r > 3) { delete pl; return DPSLAB_ERR_GRID; }
+    }
     const int M = ny * nxh;
     const bool mixed = p->precision == DPSLAB_MIXED;
+    kp.slab = mixed ? 32 : 16;
+    kp.nslabs = (nz + kp.slab - 1) / kp.slab;
+    kp.nbuckets = kp.ntiles * kp.nslabs;
+    kp.supx = d.support_x;
+    kp.supy = d.support_y;
     kp.mixed = mixed ? 1 : 0;
     const int col_block = mixed ? kColBlockM : kColBlock;
     kp.n_col_blocks = (M + col_block - 1) / col_block;
@@ -1430,6 +1744,9 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         bytes += 3 * align_up(n * sizeof(double4_32a));           // part, far, nearv
         bytes += 2 * align_up(n * sizeof(int));               // cell_of, sorted_idx
         bytes += align_up(n * sizeof(double4_32a));               // sorted
+        bytes += align_up(n * sizeof(float4));                    // sorted_rel
+        bytes += 3 * align_up((size_t(kp.nbuckets) + 1) * sizeof(int));   // bucket count/start/fill
+        bytes += align_up(size_t(3 * n) * size_t(kp.nslabs) * sizeof(SrcRec));   // worst case: every source in every slab
         bytes += 3 * align_up((size_t(kp.ncells) + 1) * sizeof(int));
         bytes += align_up(size_t(kp.ncells) * sizeof(int));
         bytes += align_up(size_t(kp.n_col_blocks) * sizeof(double));
@@ -1450,6 +1767,11 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         kp.cell_of = carve<int>(cur, n);
         kp.sorted_idx = carve<int>(cur, n);
         kp.sorted = carve<double4_32a>(cur, n);
+        kp.sorted_rel = carve<float4>(cur, n);
+        kp.tile_count = carve<int>(cur, size_t(kp.nbuckets) + 1);
+        kp.tile_start = carve<int>(cur, size_t(kp.nbuckets) + 1);
+        kp.tile_fill = carve<int>(cur, size_t(kp.nbuckets) + 1);
+        kp.srcs = carve<SrcRec>(cur, size_t(3 * n) * size_t(kp.nslabs));
         kp.cell_count = carve<int>(cur, size_t(kp.ncells) + 1);
         kp.cell_start = carve<int>(cur, size_t(kp.ncells) + 1);
         kp.cell_fill = carve<int>(cur, size_t(kp.ncells) + 1);
@@ -1482,11 +1804,13 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
     pl->sm_ffty_fwd = (size_t(ny) + 2 * size_t(pl->tk_fwd) * ny) * csz;
     pl->sm_ffty_inv = (size_t(ny) + 6 * size_t(pl->tk_inv) * ny) * csz;
     pl->sm_fftx_inv = (size_t(nx) + 4 * size_t(pl->px_inv) * nx) * csz;
-    pl->sm_col = size_t(col_block) * nz * (4 * csz + 2 * rsz);
+    pl->sm_col = size_t(col_block) * (nz + (mixed ? 1 : 0)) * (4 * csz + 2 * rsz);
     pl->sm_interp = size_t(kInterpWarps) * (2 * kMaxSupport + kMaxNz) * rsz;
+    pl->sm_spread = (2 * size_t(kp.slab) * kTile * kTile +
+                     size_t(kSpreadBatch) * (((kp.supx + 31) & ~31) + ((kp.supy + 31) & ~31) + kp.slab)) * rsz;
     const size_t smax = 227 * 1024;
     if (pl->sm_fftx_fwd > smax || pl->sm_ffty_fwd > smax || pl->sm_ffty_inv > smax ||
-        pl->sm_fftx_inv > smax || pl->sm_col > smax) {
+        pl->sm_fftx_inv > smax || pl->sm_col > smax || pl->sm_spread > smax) {
         release(pl);
         return DPSLAB_ERR_GRID;
     }
@@ -1497,6 +1821,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         cudaFuncSetAttribute(k_fftx_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
         cudaFuncSetAttribute(k_column_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
         cudaFuncSetAttribute(k_interp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
+        cudaFuncSetAttribute(k_spread_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_spread));
     } else {
         cudaFuncSetAttribute(k_fftx_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
         cudaFuncSetAttribute(k_ffty_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
@@ -1504,6 +1829,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         cudaFuncSetAttribute(k_fftx_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
         cudaFuncSetAttribute(k_column, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
         cudaFuncSetAttribute(k_interp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
+        cudaFuncSetAttribute(k_spread_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_spread));
     }
     if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
     *out = pl;
@@ -1592,17 +1918,25 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     } while (0)
 
     DPS_CUDA(cudaMemsetAsync(kp.status, 0, sizeof(int), st));
-    const size_t rsz = kp.mixed ? sizeof(float) : sizeof(double);
-    DPS_CUDA(cudaMemsetAsync(kp.rho, 0, 2 * pl->G * rsz, st));
+    DPS_CUDA(cudaMemsetAsync(kp.tile_count, 0, (size_t(kp.nbuckets) + 1) * sizeof(int), st));
+    DPS_CUDA(cudaMemsetAsync(kp.tile_fill, 0, (size_t(kp.nbuckets) + 1) * sizeof(int), st));
     if (kp.near_on) {
         DPS_CUDA(cudaMemsetAsync(kp.cell_count, 0, (size_t(kp.ncells) + 1) * sizeof(int), st));
         DPS_CUDA(cudaMemsetAsync(kp.cell_fill, 0, (size_t(kp.ncells) + 1) * sizeof(int), st));
     }
     mark(0);
     LAUNCH(k_prepare<<<nb, kChargeThreads, 0, st>>>(kp));
+    if (kp.near_on) {   // cell list: the near field's pairs and the interpolation's order
+        LAUNCH(k_scan_cells<<<1, 1024, 0, st>>>(kp));
+        LAUNCH(k_scatter_cells<<<nb, kChargeThreads, 0, st>>>(kp));
+    }
     mark(1);
-    if (kp.mixed) LAUNCH(k_spread<float><<<3 * n, 128, 0, st>>>(kp));
-    else LAUNCH(k_spread<double><<<3 * n, 128, 0, st>>>(kp));
+    LAUNCH(k_count_sources<<<nb, kChargeThreads, 0, st>>>(kp));
+    LAUNCH(k_scan<<<1, 1024, 0, st>>>(kp.tile_count, kp.tile_start, kp.nbuckets));
+    LAUNCH(k_scatter_sources<<<nb, kChargeThreads, 0, st>>>(kp));
+    const dim3 gs(kp.ntiles, kp.nslabs);
+    if (kp.mixed) LAUNCH(k_spread_tiled<float><<<gs, kTile * kTile, pl->sm_spread, st>>>(kp));
+    else LAUNCH(k_spread_tiled<double><<<gs, kTile * kTile, pl->sm_spread, st>>>(kp));
     mark(2);
     const int npairs = kp.nz * kp.ny;
     const dim3 gy_fwd((kp.nxh + pl->tk_fwd - 1) / pl->tk_fwd, 2 * kp.nz);
@@ -1637,9 +1971,7 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     }
     mark(8);
     if (kp.near_on) {
-        LAUNCH(k_scan_cells<<<1, 1024, 0, st>>>(kp));
-        LAUNCH(k_scatter_cells<<<nb, kChargeThreads, 0, st>>>(kp));
-        if (kp.mixed) LAUNCH(k_near<float><<<(n + 127) / 128, 128, 0, st>>>(kp));
+        if (kp.mixed) LAUNCH(k_near_f32<<<(n + 127) / 128, 128, 0, st>>>(kp));
         else LAUNCH(k_near<double><<<(n + 127) / 128, 128, 0, st>>>(kp));
     }
     mark(9);
@@ -1825,7 +2157,7 @@ extern "C" int dpslab_near_field_static(const dpslab_params* p, int64_t n, const
     kp.part = carve<double4_32a>(cur, kStaticMaxN);
     kp.sorted = carve<double4_32a>(cur, kStaticMaxN);
     kp.nearv = carve<double4_32a>(cur, kStaticMaxN);
-    carve<double4_32a>(cur, kStaticMaxN);
+    kp.sorted_rel = reinterpret_cast<float4*>(carve<double4_32a>(cur, kStaticMaxN));   // 16 of the 32 bytes
     kp.cell_of = carve<int>(cur, kStaticMaxN);
     kp.sorted_idx = carve<int>(cur, kStaticMaxN);
     kp.cell_count = carve<int>(cur, size_t(kStaticMaxCells) + 1);

@@ -31,6 +31,14 @@ WORKLOADS = {
                                    eps_b=float("inf"), eps_t=1.0 / 80, seed=1),
     "c3_jumps_n1048576": dict(n=1 << 20, Lx=512.0, Ly=512.0, H=128.0, nx=1024, ny=1024, nz=128,
                               eps_b=1.0 / 80, eps_t=1.0 / 80, seed=2),
+    # 1/64 of the 2^20-charge box at the same slab, density and grid spacing
+    # (a bounded sample of that workload for the CPU oracle)
+    "c3s_jumps_n16384": dict(n=16384, Lx=64.0, Ly=64.0, H=128.0, nx=128, ny=128, nz=128,
+                             eps_b=1.0 / 80, eps_t=1.0 / 80, seed=7),
+    # a quarter of the 2^20-charge box at the same density and grid spacing
+    # (for profiler captures that must stay a few GB)
+    "c3q_jumps_n262144": dict(n=1 << 18, Lx=256.0, Ly=256.0, H=128.0, nx=512, ny=512, nz=128,
+                              eps_b=1.0 / 80, eps_t=1.0 / 80, seed=6),
 }
 
 
