@@ -304,12 +304,15 @@ __global__ void __launch_bounds__(kTile * kTile) k_spread_tiled(KP kp) {
             }
         }
         __syncthreads();
-        // phase 3: each thread adds the sources covering its grid column
-        if (mine) {
-            unsigned hits = s_mx[lx] & s_my[ly];
+        // phase 3: the warp walks the union of its lanes' covering sources
+        // (uniform loop, broadcast loads); each covered lane adds its column
+        {
+            const unsigned mine_hits = mine ? (s_mx[lx] & s_my[ly]) : 0u;
+            unsigned hits = __reduce_or_sync(0xffffffffu, mine_hits);
             while (hits) {
                 const int b = __ffs(hits) - 1;
                 hits &= hits - 1u;
+                if (!((mine_hits >> b) & 1u)) continue;
                 int ix = s_dx0[b] + lx;
                 if (ix >= kp.nx) ix -= kp.nx;
                 int iy = s_dy0[b] + ly;
@@ -1074,6 +1077,7 @@ __global__ void k_ffty_inv(KP kp, int TK) {
     const C* twg = twy_of<R>(kp);
     for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
     const size_t plane = size_t(n) * nxh;
+    const R kys = R(kTwoPi / kp.Ly);
     C* s0 = static_cast<C*>(kp.spec) + size_t(blockIdx.y) * plane;
     C* s1 = static_cast<C*>(kp.spec) + size_t(kp.nz + blockIdx.y) * plane;
     C* sb = static_cast<C*>(kp.specB) + size_t(blockIdx.y) * plane;
@@ -1087,7 +1091,7 @@ __global__ void k_ffty_inv(KP kp, int TK) {
             dps = s1[size_t(y) * nxh + kx];
         }
         const int my = y < (n + 1) / 2 ? y : y - n;
-        const R ky = (n % 2 == 0 && y == n / 2) ? R(0) : R(kTwoPi * my / kp.Ly);
+        const R ky = (n % 2 == 0 && y == n / 2) ? R(0) : (sizeof(R) == sizeof(double) ? R(kTwoPi * my / kp.Ly) : kys * R(my));
         C dy;
         dy.x = ky * ps.y;                          // -i k_y psi
         dy.y = -ky * ps.x;
@@ -1123,6 +1127,7 @@ __global__ void k_fftx_inv(KP kp, int P) {
     V4* fields = static_cast<V4*>(kp.fields);
     const int nrows = kp.nz * kp.ny;
     const size_t S = size_t(nrows) * nxh;
+    const R kxs = R(kTwoPi / kp.Lx);
     const int r0 = blockIdx.x * P;
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t / n, k = t - p * n, row = r0 + p;
@@ -1136,7 +1141,7 @@ __global__ void k_fftx_inv(KP kp, int P) {
             C c = spec[S + size_t(row) * nxh + kk];
             const bool edge = kk == 0 || (n % 2 == 0 && kk == n / 2);
             if (edge) { a.y = R(0); b.y = R(0); c.y = R(0); }
-            const R kxd = edge ? R(0) : R(kTwoPi * kk / kp.Lx);
+            const R kxd = edge ? R(0) : (sizeof(R) == sizeof(double) ? R(kTwoPi * kk / kp.Lx) : kxs * R(kk));
             C r, mc;
             r.x = kxd * a.y;                     // -i k_x psi
             r.y = -kxd * a.x;
