@@ -18,6 +18,16 @@ enum : int {
 // xlo..xlo+sx-1, ylo..ylo+sy-1 (unwrapped) and nodes j0..j1, offsets of the
 // first x and y index from the source, strength, and whether it also feeds
 // rho_o (a charge of C_over).
+// Interpolation window of one charge (mixed precision), Sec. 5.2.2 step 7:
+// the same index rule as the spreading, evaluated once per charge in double;
+// offsets of the first x and y points and z as a float pair.
+struct IRec {
+    float d0x, d0y;           // x_lo h_x - x, y_lo h_y - y
+    float zhi, zlo;           // z = zhi + zlo
+    int xlo, ylo;
+    short sx, sy, j0, j1;     // support sizes, first and last z node
+};
+
 struct SrcRec {
     double z, q, d0x, d0y;
     int xlo, ylo, j0, j1;
@@ -47,6 +57,15 @@ struct KP {
     // nodes gq_s and weights gq_w on that interval (used in float)
     int near_quad;
     float gq_s[4], gq_w[4];
+    // float copies of the scalars the mixed-precision kernels use per element
+    struct {
+        float kxs, kys;                   // 2 pi/Lx, 2 pi/Ly
+        float H, HE, Hbar, sz;            // sz = 2/Hbar (d/dz of the scaled coordinate)
+        float scale;                      // -(Hbar/2)^2/eps (right-hand side of Eq. (blocksys))
+        float Gb, Gt, cb, db, ct, dt, tb, tt, rtb, rtt;
+        float sigma2;
+        float hx, hy, ig2, s1norm;        // grid steps, 1/(2 g_t^2), (2 pi g_t^2)^{-1/2}
+    } f;
     // charges
     int n;
     const double* pos;
@@ -70,6 +89,9 @@ struct KP {
     const float2* twx32;      // the same twiddles rounded to float
     const float2* twy32;
     // float copies of the column tables (mixed precision)
+    const float* zn32;        // z_j rounded to float
+    const float* znlo32;      // z_j - zn32[j] (z_j as a float pair)
+    const float* wzh32;       // Clenshaw-Curtis weight times h_x h_y
     const float *cft32, *tie32, *tio32, *j2l32, *j2d32, *j2u32, *u132, *u232, *v132, *v232, *t032, *tH32, *wg32;
     int radx[kMaxStages], rady[kMaxStages];
     int nradx, nrady;
@@ -92,6 +114,7 @@ struct KP {
     int* cell_fill;
     double4_32a* sorted;
     float4* sorted_rel;       // float offsets from the cell corner, and q (mixed near field)
+    IRec* irec;               // [n] interpolation windows, in interpolation order (mixed)
     int* sorted_idx;
     // reductions
     double* part_gauge_far;   // one per column block

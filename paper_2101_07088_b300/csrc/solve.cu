@@ -770,14 +770,13 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     float2* Co = Ci + CB * NP;
     float* cpv = reinterpret_cast<float*>(Co + CB * NP);
     float* xe = cpv + CB * NP;
-    __shared__ double s_k[CB], s_K[CB], s_mult[CB], s_gauge[CB];
-    __shared__ float s_den[CB], s_ekH[CB];
+    __shared__ float s_k[CB], s_K[CB], s_mult[CB], s_den[CB], s_ekH[CB];
+    __shared__ double s_gauge[CB];
     __shared__ int s_valid[CB], s_corr[CB];
     __shared__ float2 s_c[2][CB], s_d[2][CB], s_P[CB], s_Q[CB];
     __shared__ double s_Ai;
     const int tid = threadIdx.x, bs = blockDim.x;
     const int col0 = blockIdx.x * CB;
-    const double Hbar = kp.Hbar;
     float2* const sp = static_cast<float2*>(kp.spec);
 
     if (tid < CB) {
@@ -787,9 +786,9 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         const double kx = kTwoPi * ix / kp.Lx, ky = kTwoPi * my / kp.Ly;
         const double k = sqrt(kx * kx + ky * ky);
         s_valid[c] = col < M;
-        s_k[c] = k;
-        s_K[c] = 0.5 * k * Hbar;
-        s_mult[c] = (ix == 0 || (kp.nx % 2 == 0 && ix == kp.nx / 2)) ? 1.0 : 2.0;
+        s_k[c] = float(k);
+        s_K[c] = float(0.5 * k * kp.Hbar);
+        s_mult[c] = (ix == 0 || (kp.nx % 2 == 0 && ix == kp.nx / 2)) ? 1.f : 2.f;
         s_corr[c] = (col < M) && k > 0.0 && k <= kp.kmax;
         s_gauge[c] = 0.0;
     }
@@ -817,7 +816,7 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         }
     }
     __syncthreads();
-    const float scale = float(-(0.5 * Hbar) * (0.5 * Hbar) / kp.eps);
+    const float scale = kp.f.scale;
     for (int t = tid; t < CB * N; t += bs) {
         const int c = t / N, q = t - c * N;
         const bool odd = q >= JE;
@@ -843,7 +842,7 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     // Appendix A banded solve (even and odd chains), float
     if (tid < 2 * CB) {
         const int c = tid >> 1, ch = tid & 1;
-        const float K2 = float(s_K[c] * s_K[c]);
+        const float K2 = s_K[c] * s_K[c];
         float2* Fi = Ci + c * NP;
         float2* Fo = Co + c * NP;
         float* cq = cpv + c * NP;
@@ -876,11 +875,10 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     }
     __syncthreads();
 
-    // Schur 2x2 (warp per column; lane partial sums in float, reduced and
-    // solved in double)
+    // Schur 2x2 (warp per column, float)
     {
         const int c = tid >> 5, lane = tid & 31;
-        const float K = float(s_K[c]);
+        const float K = s_K[c];
         const float2* Xi = Ci + c * NP;
         const float2* Xo = Co + c * NP;
         const float* xc = xe + c * NP;
@@ -895,25 +893,24 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
             if (n & 1) { acc[9] = fmaf(gtn, xc[n], acc[9]); acc[11] = fmaf(gbn, xc[n], acc[11]); }
             else { acc[8] = fmaf(gtn, xc[n], acc[8]); acc[10] = fmaf(gbn, xc[n], acc[10]); }
         }
-        double da[12];
-        for (int i = 0; i < 12; ++i) da[i] = double(warp_sum_f(acc[i]));
+        float da[12];
+        for (int i = 0; i < 12; ++i) da[i] = warp_sum_f(acc[i]);
         if (lane < 2) {
             const int f = lane;
-            const double2 sFt = f ? make_double2(da[4], da[5]) : make_double2(da[0], da[1]);
-            const double2 sFb = f ? make_double2(da[6], da[7]) : make_double2(da[2], da[3]);
-            const double Kd = s_K[c];
-            double2 cc, dd;
-            if (Kd > 0.0) {
-                const double m11 = Kd + da[8], m12 = 1.0 + Kd + da[9], m21 = -Kd + da[10], m22 = 1.0 + Kd + da[11];
-                const double idet = 1.0 / (m11 * m22 - m12 * m21);
+            const float2 sFt = f ? make_float2(da[4], da[5]) : make_float2(da[0], da[1]);
+            const float2 sFb = f ? make_float2(da[6], da[7]) : make_float2(da[2], da[3]);
+            float2 cc, dd;
+            if (K > 0.f) {
+                const float m11 = K + da[8], m12 = 1.f + K + da[9], m21 = -K + da[10], m22 = 1.f + K + da[11];
+                const float idet = 1.f / (m11 * m22 - m12 * m21);
                 cc = cscale(csub(cscale(sFt, m22), cscale(sFb, m12)), -idet);
                 dd = cscale(csub(cscale(sFb, m11), cscale(sFt, m21)), -idet);
             } else {
-                cc = cscale(cadd(sFt, sFb), -0.5);
-                dd = cscale(csub(sFt, sFb), -0.5);
+                cc = cscale(cadd(sFt, sFb), -0.5f);
+                dd = cscale(csub(sFt, sFb), -0.5f);
             }
-            s_c[f][c] = make_float2(float(cc.x), float(cc.y));
-            s_d[f][c] = make_float2(float(dd.x), float(dd.y));
+            s_c[f][c] = cc;
+            s_d[f][c] = dd;
         }
     }
     __syncthreads();
@@ -945,8 +942,8 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     }
     __syncthreads();
 
-    // boundary values (lane sums in float, reduction in double), mismatches,
-    // correction coefficients, k = 0 slope, gauge partial sum (double)
+    // boundary values, mismatches, correction coefficients and the gauge
+    // term in float; the k = 0 slope in double
     {
         const int c = tid >> 5, lane = tid & 31;
         const float2 *yi = Ci + c * NP, *ypi = Vi + c * NP, *yo = Co + c * NP, *ypo = Vo + c * NP;
@@ -965,52 +962,56 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
             acc[16] = fmaf(alt, ypo[n].x, acc[16]); acc[17] += ypo[n].x;
             acc[18] = fmaf(wg, yi[n].x, acc[18]); acc[19] = fmaf(wg, yi[n].y, acc[19]);
         }
-        double da[20];
-        for (int i = 0; i < 20; ++i) da[i] = double(warp_sum_f(acc[i]));
+        float da[20];
+        for (int i = 0; i < 20; ++i) da[i] = warp_sum_f(acc[i]);
         if (lane == 0 && s_valid[c]) {
-            const double dz = 2.0 / Hbar;
-            const double2 pi0 = make_double2(da[0], da[1]), dpi0 = make_double2(da[2] * dz, da[3] * dz);
-            const double2 piH = make_double2(da[4], da[5]), dpiH = make_double2(da[6] * dz, da[7] * dz);
-            const double2 po0 = make_double2(da[8], da[9]), dpo0 = make_double2(da[10] * dz, da[11] * dz);
-            const double2 poH = make_double2(da[12], da[13]), dpoH = make_double2(da[14] * dz, da[15] * dz);
-            const double dpoa = da[16] * dz, dpob = da[17] * dz;
-            const double k = s_k[c];
-            double2 corr0 = make_double2(0.0, 0.0);
+            const float dz = kp.f.sz;
+            const float2 pi0 = make_float2(da[0], da[1]), dpi0 = make_float2(da[2] * dz, da[3] * dz);
+            const float2 piH = make_float2(da[4], da[5]), dpiH = make_float2(da[6] * dz, da[7] * dz);
+            const float2 po0 = make_float2(da[8], da[9]), dpo0 = make_float2(da[10] * dz, da[11] * dz);
+            const float2 poH = make_float2(da[12], da[13]), dpoH = make_float2(da[14] * dz, da[15] * dz);
+            const float k = s_k[c];
+            float corr0 = 0.f;
             if (s_corr[c]) {
-                const double2 mpb = csub(pi0, cscale(po0, kp.tb));
-                const double2 meb = csub(dpi0, cscale(dpo0, kp.rtb));
-                const double2 mpt = csub(piH, cscale(poH, kp.tt));
-                const double2 met = csub(dpiH, cscale(dpoH, kp.rtt));
-                const double2 P = csub(cscale(mpb, kp.cb), cscale(meb, kp.db / k));
-                const double2 Q = csub(cscale(mpt, -kp.ct), cscale(met, kp.dt / k));
-                const double ekH = exp(-k * kp.H);
-                const double den = 1.0 - kp.Gb * kp.Gt * ekH * ekH;
-                s_P[c] = make_float2(float(P.x), float(P.y));
-                s_Q[c] = make_float2(float(Q.x), float(Q.y));
-                s_ekH[c] = float(ekH);
-                s_den[c] = float(den);
-                corr0 = cscale(cadd(cscale(P, -(1.0 - kp.Gt * ekH * ekH)), cscale(Q, ekH - kp.Gb * ekH)), 1.0 / den);
+                const float2 mpb = csub(pi0, cscale(po0, kp.f.tb));
+                const float2 meb = csub(dpi0, cscale(dpo0, kp.f.rtb));
+                const float2 mpt = csub(piH, cscale(poH, kp.f.tt));
+                const float2 met = csub(dpiH, cscale(dpoH, kp.f.rtt));
+                const float ik = 1.f / k;
+                const float2 P = csub(cscale(mpb, kp.f.cb), cscale(meb, kp.f.db * ik));
+                const float2 Q = csub(cscale(mpt, -kp.f.ct), cscale(met, kp.f.dt * ik));
+                const float ekH = expf(-k * kp.f.H);
+                const float den = 1.f - kp.f.Gb * kp.f.Gt * ekH * ekH;
+                s_P[c] = P;
+                s_Q[c] = Q;
+                s_ekH[c] = ekH;
+                s_den[c] = den;
+                corr0 = (-P.x * (1.f - kp.f.Gt * ekH * ekH) + Q.x * (ekH - kp.f.Gb * ekH)) / den;
             }
             if (col0 + c == 0) {
-                const double ai1 = kp.rtb * (dpo0.x - dpoa) - dpi0.x;
-                const double ai2 = kp.rtt * (dpoH.x - dpob) - dpiH.x;
+                const double ddz = 2.0 / kp.Hbar;
+                const double dpi0x = double(da[2]) * ddz, dpiHx = double(da[6]) * ddz;
+                const double dpo0x = double(da[10]) * ddz, dpoHx = double(da[14]) * ddz;
+                const double dpoa = double(da[16]) * ddz, dpob = double(da[17]) * ddz;
+                const double ai1 = kp.rtb * (dpo0x - dpoa) - dpi0x;
+                const double ai2 = kp.rtt * (dpoHx - dpob) - dpiHx;
                 double Ai;
-                if (kp.metal_b && kp.metal_t) Ai = -(piH.x - pi0.x) / kp.H;
+                if (kp.metal_b && kp.metal_t) Ai = -(double(da[4]) - double(da[0])) / kp.H;
                 else if (kp.metal_b) Ai = ai2;
                 else if (kp.metal_t) Ai = ai1;
                 else Ai = 0.5 * (ai1 + ai2);
                 s_Ai = Ai;
                 kp.scal[1] = Ai;
             }
-            const double damp = exp(-0.5 * kp.sigma2 * k * k);
-            s_gauge[c] = s_mult[c] * (damp * da[18] + corr0.x);
+            const float damp = expf(-0.5f * kp.f.sigma2 * k * k);
+            s_gauge[c] = double(s_mult[c] * (damp * da[18] + corr0));
         }
     }
     __syncthreads();
 
     // node values (float), correction at the nodes (float)
     const float Ai = float(s_Ai);
-    const float Gb = float(kp.Gb), Gt = float(kp.Gt), Hf = float(kp.H), HEf = float(kp.HE);
+    const float Gb = kp.f.Gb, Gt = kp.f.Gt, Hf = kp.f.H, HEf = kp.f.HE;
     for (int t = tid; t < JE * CB; t += bs) {
         const int c = t / JE, a = t - c * JE, col = col0 + c;
         if (col >= M) continue;
@@ -1031,16 +1032,16 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
             dox = fmaf(w, ypi[2 * r + 1].x, dox);
             doy = fmaf(w, ypi[2 * r + 1].y, doy);
         }
-        const float sz = float(2.0 / Hbar);
+        const float sz = kp.f.sz;
         for (int side = 0; side < 2; ++side) {
             const int j = side ? m - a : a;
             if (side && j == a) break;
             const float sg = side ? -1.f : 1.f;
             float2 ps = make_float2(ex + sg * ox, ey + sg * oy);
             float2 dps = make_float2((dex + sg * dox) * sz, (dey + sg * doy) * sz);
-            const float z = float(kp.zn[j]);
+            const float z = kp.zn32[j];
             if (s_corr[c] && z >= -HEf && z <= Hf + HEf) {
-                const float k = float(s_k[c]), ekH = s_ekH[c], iden = 1.f / s_den[c];
+                const float k = s_k[c], ekH = s_ekH[c], iden = 1.f / s_den[c];
                 const float e1 = expf(-k * z), e3 = expf(k * (z - Hf));
                 const float e2 = e3 * ekH, e4 = e1 * ekH;
                 const float2 P = s_P[c], Q = s_Q[c];
@@ -1057,8 +1058,11 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
             sp[size_t(N + j) * M + col] = dps;
         }
     }
-    const double g = block_sum(tid < CB ? s_gauge[tid] : 0.0);
-    if (tid == 0) kp.part_gauge_far[blockIdx.x] = g;
+    if (tid == 0) {
+        double g = 0.0;
+        for (int c = 0; c < CB; ++c) g += s_gauge[c];
+        kp.part_gauge_far[blockIdx.x] = g;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1237,6 +1241,88 @@ __global__ void k_interp(KP kp) {
         b0 = warp_sum(double(a0)); b1 = warp_sum(double(a1)); b2 = warp_sum(double(a2)); b3 = warp_sum(double(a3));
     }
     if (lane == 0) kp.far[k] = make_double4_32a(b0, b1, b2, b3);
+}
+
+// Mixed precision, in two kernels. k_interp_setup (one thread per charge)
+// takes the support of each charge with the index rule of the spreading in
+// double; k_interp_f32 (one warp per charge) gives each lane an (x, y) column
+// of the support and walks down z with one pointer step per node, all in
+// float. Node distances use z and z_j as float pairs, exact to ~1e-7.
+__global__ void k_interp_setup(KP kp) {
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= kp.n) return;
+    const double4_32a p = kp.near_on ? kp.sorted[slot] : kp.part[slot];
+    const double HE = kp.HE;
+    IRec r;
+    r.xlo = int(ceil((p.x - HE) / kp.hx));
+    r.ylo = int(ceil((p.y - HE) / kp.hy));
+    r.sx = short(int(floor((p.x + HE) / kp.hx)) - r.xlo + 1);
+    r.sy = short(int(floor((p.y + HE) / kp.hy)) - r.ylo + 1);
+    r.d0x = float(double(r.xlo) * kp.hx - p.x);
+    r.d0y = float(double(r.ylo) * kp.hy - p.y);
+    int j0, j1;
+    node_range(kp, p.z, j0, j1);
+    r.j0 = short(j0);
+    r.j1 = short(j1);
+    r.zhi = float(p.z);
+    r.zlo = float(p.z - double(r.zhi));
+    kp.irec[slot] = r;
+}
+
+__global__ void __launch_bounds__(32 * kInterpWarps) k_interp_f32(KP kp) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* smi = reinterpret_cast<float*>(smraw);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* wx = smi + w * (2 * kMaxSupport + kMaxNz);
+    float* wy = wx + kMaxSupport;
+    float* wzz = wy + kMaxSupport;
+    const int slot = blockIdx.x * kInterpWarps + w;
+    if (slot >= kp.n) return;
+    const int k = kp.near_on ? kp.sorted_idx[slot] : slot;
+    const IRec r = kp.irec[slot];
+    const int sx = r.sx, sy = r.sy, j0 = r.j0, sz = r.j1 - r.j0 + 1;
+    const float ig2 = kp.f.ig2, s1 = kp.f.s1norm;
+    for (int i = lane; i < sx; i += 32) {
+        const float d = r.d0x + float(i) * kp.f.hx;
+        wx[i] = s1 * expf(-d * d * ig2);
+    }
+    for (int i = lane; i < sy; i += 32) {
+        const float d = r.d0y + float(i) * kp.f.hy;
+        wy[i] = s1 * expf(-d * d * ig2);
+    }
+    for (int i = lane; i < sz; i += 32) {
+        const int j = j0 + i;
+        const float d = (kp.zn32[j] - r.zhi) + (kp.znlo32[j] - r.zlo);
+        wzz[i] = kp.wzh32[j] * (s1 * expf(-d * d * ig2));
+    }
+    __syncwarp();
+    const float4* fields = static_cast<const float4*>(kp.fields);
+    const int nx = kp.nx, ny = kp.ny;
+    const size_t plane = size_t(ny) * nx;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const int sxy = sx * sy;
+    for (int t = lane; t < sxy; t += 32) {
+        const int iy = t / sx, ix = t - iy * sx;
+        const int gx = wrap_index(r.xlo + ix, nx), gy = wrap_index(r.ylo + iy, ny);
+        const float wxy = wx[ix] * wy[iy];
+        const float4* f = fields + (size_t(j0) * ny + gy) * nx + gx;
+        for (int jz = 0; jz < sz; ++jz, f += plane) {
+            const float4 v = __ldg(f);
+            const float wt = wxy * wzz[jz];
+            a0 = fmaf(wt, v.x, a0);
+            a1 = fmaf(wt, v.y, a1);
+            a2 = fmaf(wt, v.z, a2);
+            a3 = fmaf(wt, v.w, a3);
+        }
+    }
+    a0 = warp_sum_f(a0);
+    a1 = warp_sum_f(a1);
+    a2 = warp_sum_f(a2);
+    a3 = warp_sum_f(a3);
+    if (lane < 4) {
+        const float v = lane == 0 ? a0 : lane == 1 ? a1 : lane == 2 ? a2 : a3;
+        reinterpret_cast<double*>(kp.far + k)[lane] = double(v);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1626,6 +1712,15 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
     kp.s1norm = std::pow(2.0 * 3.14159265358979323846 * d.gt * d.gt, -0.5);
     kp.sigma2 = std::isinf(d.xi) ? 0.0 : (0.5 / d.xi) * (0.5 / d.xi);
     kp.inv_nxny = 1.0 / (double(nx) * double(ny));
+    kp.f.kxs = float(2.0 * 3.14159265358979323846 / p->Lx);
+    kp.f.kys = float(2.0 * 3.14159265358979323846 / p->Ly);
+    kp.f.H = float(p->H); kp.f.HE = float(d.HE); kp.f.Hbar = float(d.Hbar); kp.f.sz = float(2.0 / d.Hbar);
+    kp.f.scale = float(-(0.5 * d.Hbar) * (0.5 * d.Hbar) / p->eps);
+    kp.f.Gb = float(kp.Gb); kp.f.Gt = float(kp.Gt); kp.f.cb = float(kp.cb); kp.f.db = float(kp.db);
+    kp.f.ct = float(kp.ct); kp.f.dt = float(kp.dt); kp.f.tb = float(kp.tb); kp.f.tt = float(kp.tt);
+    kp.f.rtb = float(kp.rtb); kp.f.rtt = float(kp.rtt); kp.f.sigma2 = float(kp.sigma2);
+    kp.f.hx = float(d.hx); kp.f.hy = float(d.hy); kp.f.ig2 = float(1.0 / (2.0 * d.gt * d.gt));
+    kp.f.s1norm = float(kp.s1norm);
     kp.near_on = d.r_cut > 0.0 && std::isfinite(d.xi);
     kp.na1 = 2.0 * p->gw;
     kp.pa1 = std::sqrt(2.0) * p->gw;
@@ -1723,6 +1818,14 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
             cudaMemcpy(dp, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
             dst = dp;
         };
+        upf(t.zn, kp.zn32);
+        {
+            std::vector<double> lo(t.zn.size()), wzh(t.wz.size());
+            for (size_t j = 0; j < t.zn.size(); ++j) lo[j] = t.zn[j] - double(float(t.zn[j]));
+            for (size_t j = 0; j < t.wz.size(); ++j) wzh[j] = t.wz[j] * d.hx * d.hy;
+            upf(lo, kp.znlo32);
+            upf(wzh, kp.wzh32);
+        }
         upf(t.cft, kp.cft32); upf(t.tie, kp.tie32); upf(t.tio, kp.tio32);
         upf(t.j2l, kp.j2l32); upf(t.j2d, kp.j2d32); upf(t.j2u, kp.j2u32);
         upf(t.u1, kp.u132); upf(t.u2, kp.u232); upf(t.v1, kp.v132); upf(t.v2, kp.v232);
@@ -1750,6 +1853,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         bytes += 2 * align_up(n * sizeof(int));               // cell_of, sorted_idx
         bytes += align_up(n * sizeof(double4_32a));               // sorted
         bytes += align_up(n * sizeof(float4));                    // sorted_rel
+        bytes += align_up(n * sizeof(IRec));                      // irec
         bytes += 3 * align_up((size_t(kp.nbuckets) + 1) * sizeof(int));   // bucket count/start/fill
         bytes += align_up(size_t(3 * n) * size_t(kp.nslabs) * sizeof(SrcRec));   // worst case: every source in every slab
         bytes += 3 * align_up((size_t(kp.ncells) + 1) * sizeof(int));
@@ -1773,6 +1877,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         kp.sorted_idx = carve<int>(cur, n);
         kp.sorted = carve<double4_32a>(cur, n);
         kp.sorted_rel = carve<float4>(cur, n);
+        kp.irec = carve<IRec>(cur, n);
         kp.tile_count = carve<int>(cur, size_t(kp.nbuckets) + 1);
         kp.tile_start = carve<int>(cur, size_t(kp.nbuckets) + 1);
         kp.tile_fill = carve<int>(cur, size_t(kp.nbuckets) + 1);
@@ -1825,7 +1930,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         cudaFuncSetAttribute(k_ffty_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
         cudaFuncSetAttribute(k_fftx_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
         cudaFuncSetAttribute(k_column_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
-        cudaFuncSetAttribute(k_interp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
+        cudaFuncSetAttribute(k_interp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
         cudaFuncSetAttribute(k_spread_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_spread));
     } else {
         cudaFuncSetAttribute(k_fftx_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
@@ -1960,7 +2065,8 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         mark(6);
         LAUNCH(k_fftx_inv<float><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(7);
-        LAUNCH(k_interp<float><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
+        LAUNCH(k_interp_setup<<<nb, kChargeThreads, 0, st>>>(kp));
+        LAUNCH(k_interp_f32<<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     } else {
         LAUNCH(k_fftx_fwd<double><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
         mark(3);
