@@ -12,6 +12,7 @@ namespace dps {
 enum : int {
     kStatusOutOfSlab = 1,
     kStatusNonFinite = 2,
+    kStatusCapacity = 4,      // a bucketed-source buffer would overflow (not reachable within the bound)
 };
 
 // One spreading source with its support precomputed: grid indices
@@ -26,6 +27,16 @@ struct IRec {
     float zhi, zlo;           // z = zhi + zlo
     int xlo, ylo;
     short sx, sy, j0, j1;     // support sizes, first and last z node
+};
+
+// A source of the mixed-precision spreading (float offsets and strength,
+// z as a float pair), stored once per (tile, slab) block it touches.
+struct SrcF {
+    float d0x, d0y;           // x_lo h_x - x, y_lo h_y - y
+    float zhi, zlo;           // z = zhi + zlo
+    float q;                  // strength (image strengths for images)
+    int xlo, ylo;             // first support index in x and y (unwrapped)
+    unsigned pack;            // sx | sy << 6 | j0 << 12 | j1 << 21 | over << 30
 };
 
 struct SrcRec {
@@ -105,6 +116,8 @@ struct KP {
     int* tile_start;          // nbuckets + 1
     int* tile_fill;
     struct SrcRec* srcs;      // bucketed source records
+    SrcF* srcsf;              // the same storage, mixed-precision records
+    size_t src_cap;           // capacity of srcsf in records
     // cell list
     int ncx, ncy, ncz, ncells;
     double cwx, cwy, cwz;     // cell widths

@@ -90,6 +90,64 @@ __global__ void k_prepare(KP kp) {
     }
 }
 
+// Multi-block exclusive scan of count[0..n) into start[0..n]: block sums of
+// kScanChunk elements, a one-block scan of those sums (k_scan), then each
+// block scans its chunk and adds its offset.
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanBlock * kScanItems;
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(const int* count, int n, int* part) {
+    __shared__ int red[32];
+    const int base = blockIdx.x * kScanChunk;
+    int s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        const int idx = base + i * kScanBlock + threadIdx.x;
+        if (idx < n) s += count[idx];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = red[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_apply(const int* count, int* start, int n, const int* offs) {
+    __shared__ int red[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int base = blockIdx.x * kScanChunk + tid * kScanItems;
+    int v[kScanItems], t = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? count[base + i] : 0;
+        t += v[i];
+    }
+    int inc = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) red[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = red[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        red[lane] = w;
+    }
+    __syncthreads();
+    int run = offs[blockIdx.x] + (warp ? red[warp - 1] : 0) + inc - t;
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) start[base + i] = run;
+        run += v[i];
+    }
+    if (blockIdx.x == gridDim.x - 1 && tid == 0) start[n] = offs[gridDim.x];
+}
+
 // exclusive scan of count[0..n) into start[0..n], one block of 1024 threads
 __global__ void k_scan(const int* count, int* start, int n) {
     __shared__ int sums[1024];
@@ -342,6 +400,187 @@ __global__ void __launch_bounds__(kTile * kTile) k_spread_tiled(KP kp) {
             const size_t g = (size_t(j) * kp.ny + gy) * kp.nx + gx;
             rho[g] = acc_i[(j - js) * kTile * kTile + tid];
             rho[G + g] = acc_o[(j - js) * kTile * kTile + tid];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// spreading, mixed precision (Sec. 5.2.2 steps 2-3, same support rule as
+// above): each source is stored in every (tile, slab) block it touches, so a
+// block reads exactly the sources that reach it. The block's 256 threads own
+// its 16 x 16 grid columns and keep their kSlabM z values of rho_i and rho_o
+// in registers; per batch of sources the threads first fill the separable
+// weight tables (x, y, and z times the strength) in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kSlabM = 8;
+constexpr int kSpreadBatchM = 128;
+constexpr int kWzStride = 12;      // z-table row stride (16-byte rows, fewer bank conflicts)
+
+// Distinct tiles along one axis touched by support indices lo .. lo + s - 1
+// (wrapped mod n; s <= n); returns their number (<= 6 for s < 64).
+__device__ __forceinline__ int axis_tiles(int lo, int s, int n, int* out) {
+    int col = wrap_index(lo, n), rem = s, cnt = 0;
+    while (rem > 0) {
+        const int t = col / kTile;
+        const int take = min(rem, min(n, (t + 1) * kTile) - col);
+        bool dup = false;
+        for (int i = 0; i < cnt; ++i) dup |= out[i] == t;
+        if (!dup) out[cnt++] = t;
+        rem -= take;
+        col += take;
+        if (col >= n) col -= n;
+    }
+    return cnt;
+}
+
+// Source s of charge p as a mixed-precision record; false if it does not
+// exist. Index rule and node range as make_source.
+__device__ __forceinline__ bool make_source_f(const KP& kp, const double4_32a& p, int s, SrcF& r, int& sx, int& sy,
+                                              int& j0, int& j1) {
+    double z = p.z, q = p.w;
+    const bool nb = p.z <= 2.0 * kp.HE, nt = p.z >= kp.H - 2.0 * kp.HE;
+    if (s == 1) {
+        if (!nb || kp.Gb == 0.0) return false;
+        z = -p.z; q = -kp.Gb * p.w;
+    } else if (s == 2) {
+        if (!nt || kp.Gt == 0.0) return false;
+        z = 2.0 * kp.H - p.z; q = -kp.Gt * p.w;
+    }
+    if (q == 0.0) return false;
+    const double HE = kp.HE;
+    r.xlo = int(ceil((p.x - HE) / kp.hx));
+    r.ylo = int(ceil((p.y - HE) / kp.hy));
+    sx = int(floor((p.x + HE) / kp.hx)) - r.xlo + 1;
+    sy = int(floor((p.y + HE) / kp.hy)) - r.ylo + 1;
+    r.d0x = float(double(r.xlo) * kp.hx - p.x);
+    r.d0y = float(double(r.ylo) * kp.hy - p.y);
+    node_range(kp, z, j0, j1);
+    if (j0 > j1) return false;
+    r.zhi = float(z);
+    r.zlo = float(z - double(r.zhi));
+    r.q = float(q);
+    const unsigned over = (s == 0) && (nb || nt);
+    r.pack = unsigned(sx) | (unsigned(sy) << 6) | (unsigned(j0) << 12) | (unsigned(j1) << 21) | (over << 30);
+    return true;
+}
+
+template <bool kScatter>
+__global__ void k_bucket_sources_f(KP kp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kp.n) return;
+    const double4_32a p = kp.part[k];
+    for (int s = 0; s < 3; ++s) {
+        SrcF r;
+        int sx, sy, j0, j1;
+        if (!make_source_f(kp, p, s, r, sx, sy, j0, j1)) continue;
+        int tx[6], ty[6];
+        const int ntx = axis_tiles(r.xlo, sx, kp.nx, tx);
+        const int nty = axis_tiles(r.ylo, sy, kp.ny, ty);
+        for (int sl = j0 / kSlabM; sl <= j1 / kSlabM; ++sl)
+            for (int a = 0; a < nty; ++a)
+                for (int c = 0; c < ntx; ++c) {
+                    const int b = sl * kp.ntiles + ty[a] * kp.ntx + tx[c];
+                    if (kScatter) {
+                        const size_t at = size_t(kp.tile_start[b]) + atomicAdd(&kp.tile_fill[b], 1);
+                        if (at < kp.src_cap) kp.srcsf[at] = r;
+                        else atomicOr(kp.status, kStatusCapacity);
+                    } else {
+                        atomicAdd(&kp.tile_count[b], 1);
+                    }
+                }
+    }
+}
+
+__global__ void __launch_bounds__(kTile * kTile) k_spread_f32(KP kp) {
+    constexpr int B = kSpreadBatchM;
+    __shared__ float s_wx[B][kTile + 1];
+    __shared__ float s_wy[B][kTile + 1];
+    __shared__ __align__(16) float s_wz[B][kWzStride];
+    __shared__ int s_over[B];
+    const int tid = threadIdx.x, lx = tid % kTile, ly = tid / kTile;
+    const int tile = blockIdx.x, txi = tile % kp.ntx, tyi = tile / kp.ntx;
+    const int slab = blockIdx.y, js = slab * kSlabM;
+    const int gx0 = txi * kTile, gy0 = tyi * kTile;
+    const int bk = slab * kp.ntiles + tile;
+    const int first = kp.tile_start[bk], total = kp.tile_start[bk + 1] - first;
+    const SrcF* src = kp.srcsf + first;
+    const float ig2 = kp.f.ig2, s1 = kp.f.s1norm;
+    float ai[kSlabM], ao[kSlabM];
+#pragma unroll
+    for (int j = 0; j < kSlabM; ++j) ai[j] = ao[j] = 0.f;
+    for (int base = 0; base < total; base += B) {
+        const int nb = min(B, total - base);
+        {
+            const int b = tid % B;
+            if (b < nb) {
+                const SrcF r = src[base + b];
+                if (tid < B) {
+                    // x weights of the tile's columns, then z weights times q
+                    const int sx = r.pack & 63;
+                    int i = wrap_index(gx0 - r.xlo, kp.nx);
+                    for (int l = 0; l < kTile; ++l) {
+                        float w = 0.f;
+                        if (i < sx) {
+                            const float d = r.d0x + float(i) * kp.f.hx;
+                            w = s1 * expf(-d * d * ig2);
+                        }
+                        s_wx[b][l] = w;
+                        if (++i >= kp.nx) i -= kp.nx;
+                    }
+                    const int j0 = (r.pack >> 12) & 511, j1 = (r.pack >> 21) & 511;
+                    for (int jj = 0; jj < kSlabM; ++jj) {
+                        const int j = js + jj;
+                        float w = 0.f;
+                        if (j >= j0 && j <= j1) {
+                            const float d = (kp.zn32[j] - r.zhi) + (kp.znlo32[j] - r.zlo);
+                            w = r.q * (s1 * expf(-d * d * ig2));
+                        }
+                        s_wz[b][jj] = w;
+                    }
+                    s_over[b] = int(r.pack >> 30);
+                } else {
+                    const int sy = (r.pack >> 6) & 63;
+                    int i = wrap_index(gy0 - r.ylo, kp.ny);
+                    for (int l = 0; l < kTile; ++l) {
+                        float w = 0.f;
+                        if (i < sy) {
+                            const float d = r.d0y + float(i) * kp.f.hy;
+                            w = s1 * expf(-d * d * ig2);
+                        }
+                        s_wy[b][l] = w;
+                        if (++i >= kp.ny) i -= kp.ny;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int b = 0; b < nb; ++b) {
+            const float w = s_wx[b][lx] * s_wy[b][ly];
+            if (w != 0.f) {
+                const float4 z0 = *reinterpret_cast<const float4*>(&s_wz[b][0]);
+                const float4 z1 = *reinterpret_cast<const float4*>(&s_wz[b][4]);
+                const float wz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+                for (int j = 0; j < kSlabM; ++j) ai[j] = fmaf(w, wz[j], ai[j]);
+                if (s_over[b]) {
+#pragma unroll
+                    for (int j = 0; j < kSlabM; ++j) ao[j] = fmaf(w, wz[j], ao[j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int gx = gx0 + lx, gy = gy0 + ly;
+    if (gx < kp.nx && gy < kp.ny) {
+        float* rho = static_cast<float*>(kp.rho);
+        const size_t G = size_t(kp.nz) * kp.ny * kp.nx;
+#pragma unroll
+        for (int j = 0; j < kSlabM; ++j) {
+            if (js + j < kp.nz) {
+                const size_t g = (size_t(js + j) * kp.ny + gy) * kp.nx + gx;
+                rho[g] = ai[j];
+                rho[G + g] = ao[j];
+            }
         }
     }
 }
@@ -1606,6 +1845,7 @@ struct dpslab_plan {
     double* d_force = nullptr;
     double* h_scal = nullptr;   // pinned
     int* h_status = nullptr;
+    int* scan_part = nullptr;     // block sums and offsets of the multi-block scans
     int64_t last_n = 0;
     int launches = 0;
     int profiling = 0;
@@ -1772,7 +2012,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
     }
     const int M = ny * nxh;
     const bool mixed = p->precision == DPSLAB_MIXED;
-    kp.slab = mixed ? 32 : 16;
+    kp.slab = mixed ? kSlabM : 16;
     kp.nslabs = (nz + kp.slab - 1) / kp.slab;
     kp.nbuckets = kp.ntiles * kp.nslabs;
     kp.supx = d.support_x;
@@ -1855,12 +2095,33 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         bytes += align_up(n * sizeof(float4));                    // sorted_rel
         bytes += align_up(n * sizeof(IRec));                      // irec
         bytes += 3 * align_up((size_t(kp.nbuckets) + 1) * sizeof(int));   // bucket count/start/fill
-        bytes += align_up(size_t(3 * n) * size_t(kp.nslabs) * sizeof(SrcRec));   // worst case: every source in every slab
+        // source records, worst case. FP64: every source in every slab.
+        // Mixed: a source is stored once per (tile, slab) block it touches.
+        size_t src_bytes = size_t(3 * n) * size_t(kp.nslabs) * sizeof(SrcRec);
+        if (mixed) {
+            const int spc = p->H <= 4.0 * d.HE ? 3 : 2;     // charge and its images
+            auto axis = [](int sup, int nn) {
+                const int tl = (sup - 1 + kTile - 1) / kTile + 1 + (nn % kTile ? 1 : 0);
+                return std::min(tl, (nn + kTile - 1) / kTile);
+            };
+            int maxnodes = 1;                                 // nodes in any window of width 2 H_E
+            for (int j0 = 0, j1 = 0; j0 < nz; ++j0) {
+                while (j1 + 1 < nz && t.zn[j0] - t.zn[j1 + 1] <= 2.0 * d.HE * (1.0 + 1e-12)) ++j1;
+                maxnodes = std::max(maxnodes, j1 - j0 + 1);
+            }
+            const int sl = std::min(kp.nslabs, (maxnodes - 1) / kSlabM + 2);
+            const size_t recs = n * size_t(spc) * size_t(axis(d.support_x, nx)) * size_t(axis(d.support_y, ny)) * size_t(sl);
+            src_bytes = recs * sizeof(SrcF);
+            kp.src_cap = recs;
+        }
+        bytes += align_up(src_bytes);
         bytes += 3 * align_up((size_t(kp.ncells) + 1) * sizeof(int));
         bytes += align_up(size_t(kp.ncells) * sizeof(int));
         bytes += align_up(size_t(kp.n_col_blocks) * sizeof(double));
         bytes += 4 * align_up(size_t(kp.n_charge_blocks) * 2 * sizeof(double));
         bytes += align_up(16 * sizeof(double)) + align_up(16 * sizeof(int));
+        const size_t scan_n = 2 * ((std::max<size_t>(kp.nbuckets, kp.ncells) + kScanChunk - 1) / kScanChunk + 1);
+        bytes += align_up(scan_n * sizeof(int));
         bytes += align_up(n * 3 * sizeof(double)) * 2 + align_up(n * sizeof(double)) * 2;   // host-call staging
         cudaError_t e = cudaMalloc(&pl->work, bytes);
         if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
@@ -1881,7 +2142,8 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         kp.tile_count = carve<int>(cur, size_t(kp.nbuckets) + 1);
         kp.tile_start = carve<int>(cur, size_t(kp.nbuckets) + 1);
         kp.tile_fill = carve<int>(cur, size_t(kp.nbuckets) + 1);
-        kp.srcs = carve<SrcRec>(cur, size_t(3 * n) * size_t(kp.nslabs));
+        kp.srcs = reinterpret_cast<SrcRec*>(carve<char>(cur, src_bytes));
+        kp.srcsf = reinterpret_cast<SrcF*>(kp.srcs);
         kp.cell_count = carve<int>(cur, size_t(kp.ncells) + 1);
         kp.cell_start = carve<int>(cur, size_t(kp.ncells) + 1);
         kp.cell_fill = carve<int>(cur, size_t(kp.ncells) + 1);
@@ -1893,6 +2155,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
         kp.scal = carve<double>(cur, 16);
         kp.status = carve<int>(cur, 16);
+        pl->scan_part = carve<int>(cur, scan_n);
         pl->d_pos = carve<double>(cur, 3 * n);
         pl->d_force = carve<double>(cur, 3 * n);
         pl->d_q = carve<double>(cur, n);
@@ -1931,7 +2194,6 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         cudaFuncSetAttribute(k_fftx_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
         cudaFuncSetAttribute(k_column_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
         cudaFuncSetAttribute(k_interp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
-        cudaFuncSetAttribute(k_spread_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_spread));
     } else {
         cudaFuncSetAttribute(k_fftx_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
         cudaFuncSetAttribute(k_ffty_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
@@ -2026,6 +2288,20 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         ++launches;                                  \
         if (cudaGetLastError() != cudaSuccess) return DPSLAB_ERR_CUDA; \
     } while (0)
+    // exclusive scan count[0..m) -> start[0..m] (m >= 1)
+    auto scan = [&](const int* count, int* start, int m) -> int {
+        const int nbs = (m + kScanChunk - 1) / kScanChunk;
+        int* sums = pl->scan_part;
+        int* offs = pl->scan_part + nbs + 1;
+        LAUNCH(k_scan_sums<<<nbs, kScanBlock, 0, st>>>(count, m, sums));
+        LAUNCH(k_scan<<<1, 1024, 0, st>>>(sums, offs, nbs));
+        LAUNCH(k_scan_apply<<<nbs, kScanBlock, 0, st>>>(count, start, m, offs));
+        return 0;
+    };
+#define SCAN(c, s_, m)                          \
+    do {                                        \
+        if (const int e_ = scan(c, s_, m)) return e_; \
+    } while (0)
 
     DPS_CUDA(cudaMemsetAsync(kp.status, 0, sizeof(int), st));
     DPS_CUDA(cudaMemsetAsync(kp.tile_count, 0, (size_t(kp.nbuckets) + 1) * sizeof(int), st));
@@ -2037,16 +2313,22 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     mark(0);
     LAUNCH(k_prepare<<<nb, kChargeThreads, 0, st>>>(kp));
     if (kp.near_on) {   // cell list: the near field's pairs and the interpolation's order
-        LAUNCH(k_scan_cells<<<1, 1024, 0, st>>>(kp));
+        SCAN(kp.cell_count, kp.cell_start, kp.ncells);
         LAUNCH(k_scatter_cells<<<nb, kChargeThreads, 0, st>>>(kp));
     }
     mark(1);
-    LAUNCH(k_count_sources<<<nb, kChargeThreads, 0, st>>>(kp));
-    LAUNCH(k_scan<<<1, 1024, 0, st>>>(kp.tile_count, kp.tile_start, kp.nbuckets));
-    LAUNCH(k_scatter_sources<<<nb, kChargeThreads, 0, st>>>(kp));
     const dim3 gs(kp.ntiles, kp.nslabs);
-    if (kp.mixed) LAUNCH(k_spread_tiled<float><<<gs, kTile * kTile, pl->sm_spread, st>>>(kp));
-    else LAUNCH(k_spread_tiled<double><<<gs, kTile * kTile, pl->sm_spread, st>>>(kp));
+    if (kp.mixed) {
+        LAUNCH(k_bucket_sources_f<false><<<nb, kChargeThreads, 0, st>>>(kp));
+        SCAN(kp.tile_count, kp.tile_start, kp.nbuckets);
+        LAUNCH(k_bucket_sources_f<true><<<nb, kChargeThreads, 0, st>>>(kp));
+        LAUNCH(k_spread_f32<<<gs, kTile * kTile, 0, st>>>(kp));
+    } else {
+        LAUNCH(k_count_sources<<<nb, kChargeThreads, 0, st>>>(kp));
+        SCAN(kp.tile_count, kp.tile_start, kp.nbuckets);
+        LAUNCH(k_scatter_sources<<<nb, kChargeThreads, 0, st>>>(kp));
+        LAUNCH(k_spread_tiled<double><<<gs, kTile * kTile, pl->sm_spread, st>>>(kp));
+    }
     mark(2);
     const int npairs = kp.nz * kp.ny;
     const dim3 gy_fwd((kp.nxh + pl->tk_fwd - 1) / pl->tk_fwd, 2 * kp.nz);
@@ -2092,6 +2374,7 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     LAUNCH(k_final_energy<<<1, 1024, 0, st>>>(kp));
     mark(10);
 #undef LAUNCH
+#undef SCAN
     DPS_CUDA(cudaMemcpyAsync(pl->h_scal, kp.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     DPS_CUDA(cudaMemcpyAsync(pl->h_status, kp.status, sizeof(int), cudaMemcpyDeviceToHost, st));
     pl->launches = launches;
@@ -2108,6 +2391,7 @@ int finish(dpslab_plan* pl, cudaStream_t st, double* U) {
         }
     }
     if (U) *U = pl->h_scal[4];
+    if (*pl->h_status & kStatusCapacity) return DPSLAB_ERR_CAPACITY;
     if (*pl->h_status) return DPSLAB_ERR_OUT_OF_SLAB;
     const double sq = pl->h_scal[5], saq = pl->h_scal[6];
     if (std::fabs(sq) > 1e-12 * saq) return DPSLAB_ERR_NOT_NEUTRAL;
