@@ -36,7 +36,7 @@ struct SrcF {
     float zhi, zlo;           // z = zhi + zlo
     float q;                  // strength (image strengths for images)
     int xlo, ylo;             // first support index in x and y (unwrapped)
-    unsigned pack;            // sx | sy << 6 | j0 << 12 | j1 << 21 | over << 30
+    unsigned pack;            // sx | sy << 6 | j0 << 12 | j1 << 21 | over << 30 | spread << 31
 };
 
 struct SrcRec {
@@ -76,6 +76,7 @@ struct KP {
         float Gb, Gt, cb, db, ct, dt, tb, tt, rtb, rtt;
         float sigma2;
         float hx, hy, ig2, s1norm;        // grid steps, 1/(2 g_t^2), (2 pi g_t^2)^{-1/2}
+        float a;                          // lower end of the Chebyshev interval
     } f;
     // charges
     int n;
@@ -127,7 +128,8 @@ struct KP {
     int* cell_fill;
     double4_32a* sorted;
     float4* sorted_rel;       // float offsets from the cell corner, and q (mixed near field)
-    IRec* irec;               // [n] interpolation windows, in interpolation order (mixed)
+    IRec* irec;               // [n] interpolation windows by charge (mixed)
+    SrcF* srcs_tmp;           // [3n] sources of each charge before bucketing (mixed)
     int* sorted_idx;
     // reductions
     double* part_gauge_far;   // one per column block

@@ -433,60 +433,105 @@ __device__ __forceinline__ int axis_tiles(int lo, int s, int n, int* out) {
     return cnt;
 }
 
-// Source s of charge p as a mixed-precision record; false if it does not
-// exist. Index rule and node range as make_source.
-__device__ __forceinline__ bool make_source_f(const KP& kp, const double4_32a& p, int s, SrcF& r, int& sx, int& sy,
-                                              int& j0, int& j1) {
-    double z = p.z, q = p.w;
-    const bool nb = p.z <= 2.0 * kp.HE, nt = p.z >= kp.H - 2.0 * kp.HE;
-    if (s == 1) {
-        if (!nb || kp.Gb == 0.0) return false;
-        z = -p.z; q = -kp.Gb * p.w;
-    } else if (s == 2) {
-        if (!nt || kp.Gt == 0.0) return false;
-        z = 2.0 * kp.H - p.z; q = -kp.Gt * p.w;
-    }
-    if (q == 0.0) return false;
-    const double HE = kp.HE;
-    r.xlo = int(ceil((p.x - HE) / kp.hx));
-    r.ylo = int(ceil((p.y - HE) / kp.hy));
-    sx = int(floor((p.x + HE) / kp.hx)) - r.xlo + 1;
-    sy = int(floor((p.y + HE) / kp.hy)) - r.ylo + 1;
-    r.d0x = float(double(r.xlo) * kp.hx - p.x);
-    r.d0y = float(double(r.ylo) * kp.hy - p.y);
-    node_range(kp, z, j0, j1);
-    if (j0 > j1) return false;
-    r.zhi = float(z);
-    r.zlo = float(z - double(r.zhi));
-    r.q = float(q);
-    const unsigned over = (s == 0) && (nb || nt);
-    r.pack = unsigned(sx) | (unsigned(sy) << 6) | (unsigned(j0) << 12) | (unsigned(j1) << 21) | (over << 30);
-    return true;
+// Node range |z_j - z| <= H_E (same rule and result as node_range): an
+// arccos estimate, then the membership test in float on z and z_j as float
+// pairs, falling back to the double test only within 1e-5 H_E of the edge.
+__device__ __forceinline__ void node_range_f(const KP& kp, double z, float zhi, float zlo, int& j0, int& j1) {
+    const int N = kp.nz;
+    const float HE = kp.f.HE, sc = float(N - 1) * 0.318309886183790672f;
+    auto jof = [&](float zz) {
+        const float sv = fminf(1.f, fmaxf(-1.f, (zz - kp.f.a) * kp.f.sz - 1.f));
+        return acosf(sv) * sc;
+    };
+    auto inside = [&](int j) -> bool {
+        const float d = fabsf((kp.zn32[j] - zhi) + (kp.znlo32[j] - zlo));
+        if (fabsf(d - HE) > 1e-5f * HE) return d <= HE;
+        return fabs(kp.zn[j] - z) <= kp.HE;
+    };
+    j0 = max(0, int(floorf(jof(zhi + HE))) - 1);
+    j1 = min(N - 1, int(ceilf(jof(zhi - HE))) + 1);
+    while (j0 <= j1 && !inside(j0)) ++j0;
+    while (j1 >= j0 && !inside(j1)) --j1;
+    while (j0 > 0 && inside(j0 - 1)) --j0;
+    while (j1 < N - 1 && inside(j1 + 1)) ++j1;
 }
 
-template <bool kScatter>
-__global__ void k_bucket_sources_f(KP kp) {
+// Support window of a point in x or y: first index ceil((x - H_E)/h), size,
+// and the float offset of the first index (double arithmetic).
+__device__ __forceinline__ void axis_window(double x, double HE, double h, int& lo, int& sz, float& d0) {
+    lo = int(ceil((x - HE) / h));
+    sz = int(floor((x + HE) / h)) - lo + 1;
+    d0 = float(double(lo) * h - x);
+}
+
+// One thread per charge: the interpolation window of the charge (irec[k]),
+// its spreading sources (the charge and its images, Eq. (ims)) as records
+// srcs_tmp[3k + s], and the bucket counts of every (tile, slab) block each
+// source touches.
+__global__ void k_sources_f(KP kp) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= kp.n) return;
     const double4_32a p = kp.part[k];
+    SrcF r;
+    int sx, sy;
+    axis_window(p.x, kp.HE, kp.hx, r.xlo, sx, r.d0x);
+    axis_window(p.y, kp.HE, kp.hy, r.ylo, sy, r.d0y);
+    const bool nb = p.z <= 2.0 * kp.HE, nt = p.z >= kp.H - 2.0 * kp.HE;
+    int tx[6], ty[6];
+    const int ntx = axis_tiles(r.xlo, sx, kp.nx, tx);
+    const int nty = axis_tiles(r.ylo, sy, kp.ny, ty);
     for (int s = 0; s < 3; ++s) {
-        SrcF r;
-        int sx, sy, j0, j1;
-        if (!make_source_f(kp, p, s, r, sx, sy, j0, j1)) continue;
-        int tx[6], ty[6];
-        const int ntx = axis_tiles(r.xlo, sx, kp.nx, tx);
-        const int nty = axis_tiles(r.ylo, sy, kp.ny, ty);
+        double z = p.z, q = p.w;
+        bool exists = true;
+        if (s == 1) { exists = nb && kp.Gb != 0.0; z = -p.z; q = -kp.Gb * p.w; }
+        if (s == 2) { exists = nt && kp.Gt != 0.0; z = 2.0 * kp.H - p.z; q = -kp.Gt * p.w; }
+        unsigned pack = 0u;
+        if (exists) {
+            r.zhi = float(z);
+            r.zlo = float(z - double(r.zhi));
+            r.q = float(q);
+            int j0, j1;
+            node_range_f(kp, z, r.zhi, r.zlo, j0, j1);
+            if (s == 0) {
+                IRec ir;
+                ir.d0x = r.d0x; ir.d0y = r.d0y; ir.zhi = r.zhi; ir.zlo = r.zlo;
+                ir.xlo = r.xlo; ir.ylo = r.ylo;
+                ir.sx = short(sx); ir.sy = short(sy); ir.j0 = short(j0); ir.j1 = short(j1);
+                kp.irec[k] = ir;
+            }
+            if (j0 <= j1 && q != 0.0) {
+                const unsigned over = (s == 0) && (nb || nt);
+                pack = unsigned(sx) | (unsigned(sy) << 6) | (unsigned(j0) << 12) | (unsigned(j1) << 21) | (over << 30) |
+                       (1u << 31);
+                for (int sl = j0 / kSlabM; sl <= j1 / kSlabM; ++sl)
+                    for (int a = 0; a < nty; ++a)
+                        for (int c = 0; c < ntx; ++c) atomicAdd(&kp.tile_count[sl * kp.ntiles + ty[a] * kp.ntx + tx[c]], 1);
+            }
+        }
+        r.pack = pack;
+        kp.srcs_tmp[3 * size_t(k) + s] = r;
+    }
+}
+
+__global__ void k_scatter_sources_f(KP kp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kp.n) return;
+    int tx[6], ty[6], ntx = 0, nty = 0;
+    for (int s = 0; s < 3; ++s) {
+        const SrcF r = kp.srcs_tmp[3 * size_t(k) + s];
+        if (!(r.pack >> 31)) continue;
+        if (!ntx) {
+            ntx = axis_tiles(r.xlo, r.pack & 63, kp.nx, tx);
+            nty = axis_tiles(r.ylo, (r.pack >> 6) & 63, kp.ny, ty);
+        }
+        const int j0 = (r.pack >> 12) & 511, j1 = (r.pack >> 21) & 511;
         for (int sl = j0 / kSlabM; sl <= j1 / kSlabM; ++sl)
             for (int a = 0; a < nty; ++a)
                 for (int c = 0; c < ntx; ++c) {
                     const int b = sl * kp.ntiles + ty[a] * kp.ntx + tx[c];
-                    if (kScatter) {
-                        const size_t at = size_t(kp.tile_start[b]) + atomicAdd(&kp.tile_fill[b], 1);
-                        if (at < kp.src_cap) kp.srcsf[at] = r;
-                        else atomicOr(kp.status, kStatusCapacity);
-                    } else {
-                        atomicAdd(&kp.tile_count[b], 1);
-                    }
+                    const size_t at = size_t(kp.tile_start[b]) + atomicAdd(&kp.tile_fill[b], 1);
+                    if (at < kp.src_cap) kp.srcsf[at] = r;
+                    else atomicOr(kp.status, kStatusCapacity);
                 }
     }
 }
@@ -537,7 +582,7 @@ __global__ void __launch_bounds__(kTile * kTile) k_spread_f32(KP kp) {
                         }
                         s_wz[b][jj] = w;
                     }
-                    s_over[b] = int(r.pack >> 30);
+                    s_over[b] = int((r.pack >> 30) & 1u);
                 } else {
                     const int sy = (r.pack >> 6) & 63;
                     int i = wrap_index(gy0 - r.ylo, kp.ny);
@@ -1482,32 +1527,10 @@ __global__ void k_interp(KP kp) {
     if (lane == 0) kp.far[k] = make_double4_32a(b0, b1, b2, b3);
 }
 
-// Mixed precision, in two kernels. k_interp_setup (one thread per charge)
-// takes the support of each charge with the index rule of the spreading in
-// double; k_interp_f32 (one warp per charge) gives each lane an (x, y) column
-// of the support and walks down z with one pointer step per node, all in
-// float. Node distances use z and z_j as float pairs, exact to ~1e-7.
-__global__ void k_interp_setup(KP kp) {
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= kp.n) return;
-    const double4_32a p = kp.near_on ? kp.sorted[slot] : kp.part[slot];
-    const double HE = kp.HE;
-    IRec r;
-    r.xlo = int(ceil((p.x - HE) / kp.hx));
-    r.ylo = int(ceil((p.y - HE) / kp.hy));
-    r.sx = short(int(floor((p.x + HE) / kp.hx)) - r.xlo + 1);
-    r.sy = short(int(floor((p.y + HE) / kp.hy)) - r.ylo + 1);
-    r.d0x = float(double(r.xlo) * kp.hx - p.x);
-    r.d0y = float(double(r.ylo) * kp.hy - p.y);
-    int j0, j1;
-    node_range(kp, p.z, j0, j1);
-    r.j0 = short(j0);
-    r.j1 = short(j1);
-    r.zhi = float(p.z);
-    r.zlo = float(p.z - double(r.zhi));
-    kp.irec[slot] = r;
-}
-
+// Mixed precision: one warp per charge, on the window k_sources_f stored for
+// it (the support of the charge's own source). Each lane takes (x, y)
+// columns of the support and walks down z with one pointer step per node,
+// all in float; node distances use z and z_j as float pairs (~1e-7).
 __global__ void __launch_bounds__(32 * kInterpWarps) k_interp_f32(KP kp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float* smi = reinterpret_cast<float*>(smraw);
@@ -1518,7 +1541,7 @@ __global__ void __launch_bounds__(32 * kInterpWarps) k_interp_f32(KP kp) {
     const int slot = blockIdx.x * kInterpWarps + w;
     if (slot >= kp.n) return;
     const int k = kp.near_on ? kp.sorted_idx[slot] : slot;
-    const IRec r = kp.irec[slot];
+    const IRec r = kp.irec[k];
     const int sx = r.sx, sy = r.sy, j0 = r.j0, sz = r.j1 - r.j0 + 1;
     const float ig2 = kp.f.ig2, s1 = kp.f.s1norm;
     for (int i = lane; i < sx; i += 32) {
@@ -1539,10 +1562,16 @@ __global__ void __launch_bounds__(32 * kInterpWarps) k_interp_f32(KP kp) {
     const int nx = kp.nx, ny = kp.ny;
     const size_t plane = size_t(ny) * nx;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    const int sxy = sx * sy;
-    for (int t = lane; t < sxy; t += 32) {
-        const int iy = t / sx, ix = t - iy * sx;
-        const int gx = wrap_index(r.xlo + ix, nx), gy = wrap_index(r.ylo + iy, ny);
+    // column t = lane + 32 i of the sx x sy support, as (ix, iy), advanced
+    // incrementally; the support fits the grid, so one wrap suffices
+    int iy = lane / max(sx, 1), ix = lane - iy * sx;
+    const int xw = wrap_index(r.xlo, nx), yw = wrap_index(r.ylo, ny);
+    for (; sx > 0 && iy < sy; ix += 32) {
+        while (ix >= sx) { ix -= sx; ++iy; }
+        if (iy >= sy) break;
+        int gx = xw + ix, gy = yw + iy;
+        if (gx >= nx) gx -= nx;
+        if (gy >= ny) gy -= ny;
         const float wxy = wx[ix] * wy[iy];
         const float4* f = fields + (size_t(j0) * ny + gy) * nx + gx;
         for (int jz = 0; jz < sz; ++jz, f += plane) {
@@ -1961,6 +1990,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
     kp.f.rtb = float(kp.rtb); kp.f.rtt = float(kp.rtt); kp.f.sigma2 = float(kp.sigma2);
     kp.f.hx = float(d.hx); kp.f.hy = float(d.hy); kp.f.ig2 = float(1.0 / (2.0 * d.gt * d.gt));
     kp.f.s1norm = float(kp.s1norm);
+    kp.f.a = float(d.a);
     kp.near_on = d.r_cut > 0.0 && std::isfinite(d.xi);
     kp.na1 = 2.0 * p->gw;
     kp.pa1 = std::sqrt(2.0) * p->gw;
@@ -2094,6 +2124,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         bytes += align_up(n * sizeof(double4_32a));               // sorted
         bytes += align_up(n * sizeof(float4));                    // sorted_rel
         bytes += align_up(n * sizeof(IRec));                      // irec
+        bytes += mixed ? align_up(3 * n * sizeof(SrcF)) : 0;      // srcs_tmp
         bytes += 3 * align_up((size_t(kp.nbuckets) + 1) * sizeof(int));   // bucket count/start/fill
         // source records, worst case. FP64: every source in every slab.
         // Mixed: a source is stored once per (tile, slab) block it touches.
@@ -2139,6 +2170,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         kp.sorted = carve<double4_32a>(cur, n);
         kp.sorted_rel = carve<float4>(cur, n);
         kp.irec = carve<IRec>(cur, n);
+        if (mixed) kp.srcs_tmp = carve<SrcF>(cur, 3 * n);
         kp.tile_count = carve<int>(cur, size_t(kp.nbuckets) + 1);
         kp.tile_start = carve<int>(cur, size_t(kp.nbuckets) + 1);
         kp.tile_fill = carve<int>(cur, size_t(kp.nbuckets) + 1);
@@ -2319,9 +2351,9 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     mark(1);
     const dim3 gs(kp.ntiles, kp.nslabs);
     if (kp.mixed) {
-        LAUNCH(k_bucket_sources_f<false><<<nb, kChargeThreads, 0, st>>>(kp));
+        LAUNCH(k_sources_f<<<nb, kChargeThreads, 0, st>>>(kp));
         SCAN(kp.tile_count, kp.tile_start, kp.nbuckets);
-        LAUNCH(k_bucket_sources_f<true><<<nb, kChargeThreads, 0, st>>>(kp));
+        LAUNCH(k_scatter_sources_f<<<nb, kChargeThreads, 0, st>>>(kp));
         LAUNCH(k_spread_f32<<<gs, kTile * kTile, 0, st>>>(kp));
     } else {
         LAUNCH(k_count_sources<<<nb, kChargeThreads, 0, st>>>(kp));
@@ -2347,7 +2379,6 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         mark(6);
         LAUNCH(k_fftx_inv<float><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(7);
-        LAUNCH(k_interp_setup<<<nb, kChargeThreads, 0, st>>>(kp));
         LAUNCH(k_interp_f32<<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     } else {
         LAUNCH(k_fftx_fwd<double><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
