@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="c3_jumps_n1048576")
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_simt"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=150.0)
@@ -245,7 +245,7 @@ def main():
     # each rank solves its own system (independent seed)
     if world > 1:
         pos, q = synth.electrolyte(n, p["Lx"], p["Ly"], 1.0, p["H"] - 1.0, wl["seed"] + 1000 * rank)
-    prec = dpslab.MIXED if args.precision == "mixed" else dpslab.FP64
+    prec = {"mixed": dpslab.MIXED, "mixed_simt": dpslab.MIXED_SIMT, "fp64": dpslab.FP64}[args.precision]
     plan = dpslab.Plan(dpslab.make_params(precision=prec, **p), n)
     d = plan.derived
     pos_t = torch.tensor(pos, dtype=torch.float64, device=dev)
@@ -319,7 +319,7 @@ def main():
     # accuracy of the timed path against the FP64 path on the same inputs, and
     # the FP64 path's own step time (outside the timed region)
     accuracy, fp64_ms = None, None
-    if args.precision == "mixed":
+    if args.precision != "fp64":
         plan64 = dpslab.Plan(dpslab.make_params(precision=dpslab.FP64, **p), n)
         phi64 = torch.empty_like(phi)
         force64 = torch.empty_like(force)
@@ -343,8 +343,8 @@ def main():
 
     # roofline of the dominant stage
     over = int(np.sum((pos[:, 2] <= 2 * d["HE"]) | (pos[:, 2] >= p["H"] - 2 * d["HE"])))
-    work, fft_flops = stage_work(d, n, over, wbytes=4 if args.precision == "mixed" else 8)
-    if args.precision == "mixed":
+    work, fft_flops = stage_work(d, n, over, wbytes=4 if args.precision != "fp64" else 8)
+    if args.precision != "fp64":
         # the mixed path's column work is 2 spectra in and 2 out; on the tensor
         # cores or in FP32 the stage is bounded by that traffic
         S = d["nz"] * d["ny"] * (d["nx"] // 2 + 1)

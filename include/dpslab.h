@@ -51,7 +51,12 @@ extern "C" {
 
 /* ------------------------------------------------------------- precision */
 #define DPSLAB_FP64   0   /* every stage in double precision */
-#define DPSLAB_MIXED  1   /* reserved: FP32 grids, BF16-split tensor-core z transform */
+#define DPSLAB_MIXED  1   /* FP32 spreading, FFT, interpolation and near field; the z Chebyshev
+                             transforms as tensor-core GEMMs on three-piece BF16 splits with FP32
+                             accumulation (Nz <= 128 and ny (nx/2+1) even; otherwise as
+                             DPSLAB_MIXED_SIMT); per-mode boundary-condition coefficients, the
+                             k = 0 mode and the energy reduction accumulated in double */
+#define DPSLAB_MIXED_SIMT 2  /* DPSLAB_MIXED with the z transforms in FP32 on the CUDA cores */
 
 /* Bits of dpslab_derived.violations (Sec. 5.3): */
 #define DPSLAB_VIOL_FAR_FIELD   1  /* 2 H_E >= H: images of images reach [-H_E, H+H_E] (Eq. (farconstraint), with h = 0) */

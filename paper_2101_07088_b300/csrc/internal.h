@@ -14,6 +14,18 @@ constexpr int kMaxFft = 4096;      // xy grid size per direction
 constexpr int kMaxRadix = 64;      // largest prime factor of nx, ny
 constexpr int kMaxStages = 24;
 
+// Tensor-core z transforms (Nz <= 128): canonical K-major, no-swizzle
+// operand image of a rows x 128 bf16 operand, element (r, k) at
+// r/8 * 2048 B + k/8 * 128 B + (r%8) * 16 B + (k%8) * 2 B (8 x 16-byte core
+// matrices; K-direction stride 128 B, row-group stride 2048 B).
+#ifdef __CUDACC__
+#define DPS_HD __host__ __device__
+#else
+#define DPS_HD
+#endif
+constexpr int kZMaxNz = 128;
+DPS_HD inline constexpr int zimg_index(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7); }
+
 struct Complex {
     double re, im;
 };
@@ -40,6 +52,10 @@ struct Tables {
     std::vector<double> wg;          // gauge weights int G_sigma(z) T_n(s(z)) dz
     std::vector<Complex> twx, twy;   // e^{-2 pi i k/n}
     std::vector<int> radx, rady;     // FFT radices (Stockham stages)
+    // three bf16 pieces (x1 + x2 + x3) of the dense z transforms, 128 x 128
+    // padded, as zimg_index images (empty when Nz > 128): coefficients from
+    // node values (DCT-I form) and node values from coefficients
+    std::vector<unsigned short> zimg_fwd, zimg_inv;
 };
 
 int derive(const dpslab_params& p, dpslab_derived& d);

@@ -13,6 +13,7 @@ enum : int {
     kStatusOutOfSlab = 1,
     kStatusNonFinite = 2,
     kStatusCapacity = 4,      // a bucketed-source buffer would overflow (not reachable within the bound)
+    kStatusTimeout = 8,       // a bounded wait on the tensor-core pipeline gave up
 };
 
 // One spreading source with its support precomputed: grid indices
@@ -37,6 +38,16 @@ struct SrcF {
     float q;                  // strength (image strengths for images)
     int xlo, ylo;             // first support index in x and y (unwrapped)
     unsigned pack;            // sx | sy << 6 | j0 << 12 | j1 << 21 | over << 30 | spread << 31
+};
+
+// Correction parameters of one k-mode for the node-value GEMM epilogue
+// (mixed precision, normalised form of Eq. (inphisc)): the correction is
+// iden (P (-(e1 - Gt e2)) + Q (e3 - Gb e4)) with e1 = e^{-kz}, e3 = e^{k(z-H)},
+// e2 = e3 ekH, e4 = e1 ekH; corr = 0 for modes without one.
+struct ColP {
+    float2 P, Q;
+    float k, ekH, iden;
+    int corr;
 };
 
 struct SrcRec {
@@ -130,6 +141,9 @@ struct KP {
     float4* sorted_rel;       // float offsets from the cell corner, and q (mixed near field)
     IRec* irec;               // [n] interpolation windows by charge (mixed)
     SrcF* srcs_tmp;           // [3n] sources of each charge before bucketing (mixed)
+    ColP* colp;               // [ny nxh] correction parameters per mode (tensor-core z transforms)
+    const unsigned short* zimg_fwd;   // split bf16 images of the z transforms (tensor cores)
+    const unsigned short* zimg_inv;
     int* sorted_idx;
     // reductions
     double* part_gauge_far;   // one per column block

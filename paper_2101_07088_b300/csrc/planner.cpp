@@ -76,7 +76,8 @@ int derive(const dpslab_params& p, dpslab_derived& d) {
     if (!(p.eps_b > 0.0) || !(p.eps_t > 0.0)) return DPSLAB_ERR_INVALID_ARG;   // may be +inf
     if (p.nx < 4 || p.ny < 4 || p.nx > kMaxFft || p.ny > kMaxFft) return DPSLAB_ERR_GRID;
     if (p.nz != 0 && (p.nz < 4 || p.nz > kMaxNz)) return DPSLAB_ERR_GRID;
-    if (p.precision != DPSLAB_FP64 && p.precision != DPSLAB_MIXED) return DPSLAB_ERR_UNSUPPORTED;
+    if (p.precision != DPSLAB_FP64 && p.precision != DPSLAB_MIXED && p.precision != DPSLAB_MIXED_SIMT)
+        return DPSLAB_ERR_UNSUPPORTED;
     if (!(p.xi >= 0.0) || !(p.r_cut >= 0.0) || !(p.n_sigma >= 0.0)) return DPSLAB_ERR_INVALID_ARG;
 
     // Table (ewconstraints)
@@ -186,6 +187,67 @@ int build_tables(const dpslab_params& p, const dpslab_derived& d, Tables& t) {
             for (int q = 0; q < JO; ++q) t.cft[size_t(a) * N + JE + q] = fwd(2 * q + 1, a);
         for (int r = 0; r < JE; ++r) t.tie[size_t(r) * JE + a] = cs[(size_t(2 * r) * a) % (2 * m)];
         for (int r = 0; r < JO; ++r) t.tio[size_t(r) * JE + a] = cs[(size_t(2 * r + 1) * a) % (2 * m)];
+    }
+
+    // dense transforms for the tensor-core path: each entry x as three bf16
+    // pieces x1 + x2 + x3 (round to nearest even at each step)
+    if (N <= kZMaxNz) {
+        auto bf16 = [](double x) -> unsigned short {
+            const float f = float(x);
+            uint32_t u;
+            std::memcpy(&u, &f, 4);
+            u += 0x7FFFu + ((u >> 16) & 1u);
+            return static_cast<unsigned short>(u >> 16);
+        };
+        auto bf16v = [](unsigned short h) -> double {
+            const uint32_t u = uint32_t(h) << 16;
+            float f;
+            std::memcpy(&f, &u, 4);
+            return double(f);
+        };
+        // piece 1 on a fixed-point grid: rint(x 128/s) s/128 with s the power
+        // of two at or above the row's largest |entry| (an integer of at most
+        // 8 bits times a power of two, exact in bf16); pieces 2 and 3 the bf16
+        // roundings of what remains
+        auto image = [&](std::vector<unsigned short>& img, const std::function<double(int, int)>& A) {
+            img.assign(3 * size_t(kZMaxNz) * kZMaxNz, 0);
+            for (int r = 0; r < kZMaxNz; ++r) {
+                double amax = 0.0;
+                for (int k = 0; k < kZMaxNz; ++k) amax = std::max(amax, std::fabs(A(r, k)));
+                int e = 0;
+                if (amax > 0.0) std::frexp(amax, &e);
+                const double sc = std::ldexp(1.0, e);     // > amax
+                for (int k = 0; k < kZMaxNz; ++k) {
+                    double x = A(r, k);
+                    const double p1 = std::rint(x * 128.0 / sc) * (sc / 128.0);
+                    img[zimg_index(r, k)] = bf16(p1);
+                    x -= p1;
+                    for (int piece = 1; piece < 3; ++piece) {
+                        const unsigned short h = bf16(x);
+                        img[size_t(piece) * kZMaxNz * kZMaxNz + zimg_index(r, k)] = h;
+                        x -= bf16v(h);
+                    }
+                }
+            }
+        };
+        // even/odd split (the symmetry used above), halves at row and K
+        // offset H2 = 64: forward rows r < JE give coefficient 2r from
+        // S_k = v_k + v_{m-k} (K columns k < JE), rows H2 + q give coefficient
+        // 2q + 1 from D_k = v_k - v_{m-k} (K columns H2 + k); inverse rows
+        // a < JE give E_a = sum_r cos(pi 2r a/m) y_{2r} (K columns r), rows
+        // H2 + a give O_a = sum_r cos(pi (2r+1) a/m) y_{2r+1} (K columns H2 + r);
+        // then v_a = E_a + O_a, v_{m-a} = E_a - O_a
+        constexpr int H2 = kZMaxNz / 2;
+        image(t.zimg_fwd, [&](int r, int k) {
+            if (r < H2) return (r < JE && k < JE) ? fwd(2 * r, k) : 0.0;
+            const int q = r - H2, kk = k - H2;
+            return (q < JO && kk >= 0 && kk < JO) ? fwd(2 * q + 1, kk) : 0.0;
+        });
+        image(t.zimg_inv, [&](int r, int k) {
+            if (r < H2) return (r < JE && k < JE) ? cs[(size_t(2 * k) * r) % (2 * m)] : 0.0;
+            const int a = r - H2, kk = k - H2;
+            return (a < JE && kk >= 0 && kk < JO) ? cs[(size_t(2 * kk + 1) * a) % (2 * m)] : 0.0;
+        });
     }
 
     // Appendix A: J maps coefficients of a function to those of its integral

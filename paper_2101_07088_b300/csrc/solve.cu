@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "zgemm.cuh"
 
 using namespace dps;
 
@@ -715,6 +716,204 @@ __global__ void k_ffty_fwd(KP kp, int TK) {
 }
 
 // ---------------------------------------------------------------------------
+// xy FFT for power-of-two nx, ny (32..4096): the same four transforms with
+// the register radix-16 routine. Rows: P sequences per block; columns: TK
+// neighbouring kx columns per block (neighbouring threads on neighbouring
+// columns, so every row segment is read and written whole).
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void k_fftx_fwd_p2(KP kp, int P, int logn) {
+    using C = typename Prec<R>::C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = kp.nx, nxh = kp.nxh, np = n + (n >> 4);
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* buf = tw + n;
+    const C* twg = twx_of<R>(kp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    __syncthreads();
+    const R* rho = static_cast<const R*>(kp.rho);
+    C* spec = static_cast<C*>(kp.spec);
+    const int npairs = kp.nz * kp.ny;
+    const int p0 = blockIdx.x * P;
+    auto load = [&](int q, int i) {
+        C v;
+        v.x = R(0);
+        v.y = R(0);
+        if (p0 + q < npairs) {
+            const size_t r0 = 2 * size_t(p0 + q);
+            v.x = rho[r0 * n + i];
+            v.y = rho[(r0 + 1) * n + i];
+        }
+        return v;
+    };
+    auto store = [&](int q, int i, C v) { buf[q * np + pad16(i)] = v; };
+    fft_pow2<false>(buf, tw, n, logn, P, -1, load, store);
+    __syncthreads();
+    for (int t = threadIdx.x; t < P * nxh; t += blockDim.x) {
+        const int p = t / nxh, k = t - p * nxh, pr = p0 + p;
+        if (pr >= npairs) continue;
+        const C Z = buf[p * np + pad16(k)];
+        const C Zm = cconj(buf[p * np + pad16((n - k) & (n - 1))]);
+        const C sum = cadd(Z, Zm), d = csub(Z, Zm);
+        const size_t r0 = 2 * size_t(pr);
+        spec[r0 * nxh + k] = cscale(sum, R(0.5));
+        C b;
+        b.x = R(0.5) * d.y;
+        b.y = R(-0.5) * d.x;
+        spec[(r0 + 1) * nxh + k] = b;
+    }
+}
+
+template <class R>
+__global__ void k_ffty_fwd_p2(KP kp, int TK, int logn) {
+    using C = typename Prec<R>::C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = kp.ny, nxh = kp.nxh;
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* buf = tw + n;
+    const C* twg = twy_of<R>(kp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    __syncthreads();
+    C* base = static_cast<C*>(kp.spec) + size_t(blockIdx.y) * n * nxh;
+    const int k0 = blockIdx.x * TK;
+    auto load = [&](int q, int i) {
+        C v;
+        v.x = R(0);
+        v.y = R(0);
+        if (k0 + q < nxh) v = base[size_t(i) * nxh + k0 + q];
+        return v;
+    };
+    auto store = [&](int q, int i, C v) {
+        if (k0 + q < nxh) base[size_t(i) * nxh + k0 + q] = v;
+    };
+    fft_pow2<true>(buf, tw, n, logn, TK, -1, load, store);
+}
+
+// one of the three inverse column transforms: F = 0: -i k_y psi (psi -> specB),
+// F = 1: psi (in place), F = 2: dpsi/dz (in place)
+template <int F, class R>
+__device__ __forceinline__ void ffty_inv_field(const KP& kp, typename Prec<R>::C* buf, const typename Prec<R>::C* tw,
+                                               int TK, int logn) {
+    using C = typename Prec<R>::C;
+    const int n = kp.ny, nxh = kp.nxh;
+    const size_t plane = size_t(n) * nxh;
+    C* src = static_cast<C*>(kp.spec) + size_t((F == 2 ? kp.nz : 0) + blockIdx.y) * plane;
+    C* dst = F == 0 ? static_cast<C*>(kp.specB) + size_t(blockIdx.y) * plane : src;
+    const R kys = R(kTwoPi / kp.Ly);
+    const int k0 = blockIdx.x * TK;
+    auto load = [&](int c, int i) {
+        C v;
+        v.x = R(0);
+        v.y = R(0);
+        if (k0 + c >= nxh) return v;
+        const C ps = src[size_t(i) * nxh + k0 + c];
+        if constexpr (F != 0) return ps;
+        const int my = i < (n + 1) / 2 ? i : i - n;
+        const R ky = (i == n / 2) ? R(0) : (sizeof(R) == sizeof(double) ? R(kTwoPi * my / kp.Ly) : kys * R(my));
+        v.x = ky * ps.y;
+        v.y = -ky * ps.x;
+        return v;
+    };
+    auto store = [&](int c, int i, C v) {
+        if (k0 + c < nxh) dst[size_t(i) * nxh + k0 + c] = v;
+    };
+    fft_pow2<true>(buf, tw, n, logn, TK, +1, load, store);
+}
+
+template <class R>
+__global__ void __launch_bounds__(512, sizeof(R) == sizeof(float) ? 2 : 1) k_ffty_inv_p2(KP kp, int TK, int logn) {
+    using C = typename Prec<R>::C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = kp.ny;
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* buf = tw + n;
+    const C* twg = twy_of<R>(kp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    __syncthreads();
+    // -i k_y psi first: it reads psi before the psi transform overwrites it
+    ffty_inv_field<0, R>(kp, buf, tw, TK, logn);
+    __syncthreads();
+    ffty_inv_field<1, R>(kp, buf, tw, TK, logn);
+    __syncthreads();
+    ffty_inv_field<2, R>(kp, buf, tw, TK, logn);
+}
+
+template <class R>
+__global__ void k_fftx_inv_p2(KP kp, int P, int logn) {
+    using C = typename Prec<R>::C;
+    using V4 = typename Prec<R>::V4;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = kp.nx, nxh = kp.nxh, np = n + (n >> 4);
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* buf = tw + n;
+    const C* twg = twx_of<R>(kp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    const C* spec = static_cast<const C*>(kp.spec);
+    const C* specB = static_cast<const C*>(kp.specB);
+    V4* fields = static_cast<V4*>(kp.fields);
+    const int nrows = kp.nz * kp.ny;
+    const size_t S = size_t(nrows) * nxh;
+    const R kxs = R(kTwoPi / kp.Lx);
+    const int r0 = blockIdx.x * P;
+    // stage the half spectra of the block's rows, st[(3 p + a) nxh + k] with
+    // a = 0 psi, 1 E_y (specB), 2 dpsi/dz (3 nxh <= 2 (n + n/16): fits buf)
+    C* st = buf;
+    for (int t = threadIdx.x; t < 3 * P * nxh; t += blockDim.x) {
+        const int pa = t / nxh, k = t - pa * nxh, p = pa / 3, a = pa - 3 * p, row = r0 + p;
+        C v;
+        v.x = R(0);
+        v.y = R(0);
+        if (row < nrows) {
+            const size_t g = size_t(row) * nxh + k;
+            v = a == 0 ? spec[g] : (a == 1 ? specB[g] : spec[S + g]);
+        }
+        st[t] = v;
+    }
+    __syncthreads();
+    // sequence q = 2 p + w: row r0 + p; w = 0 packs (phi, E_x), w = 1 (E_y, E_z)
+    auto load = [&](int q, int k) {
+        const int p = q >> 1, w = q & 1;
+        const bool hi = k >= nxh;
+        const int kk = hi ? n - k : k;
+        const bool edge = kk == 0 || kk == n / 2;
+        const C* row = st + 3 * p * nxh + kk;
+        C z;
+        if (w == 0) {
+            C a = row[0];
+            if (edge) a.y = R(0);
+            const R kxd = edge ? R(0) : (sizeof(R) == sizeof(double) ? R(kTwoPi * kk / kp.Lx) : kxs * R(kk));
+            C r;
+            r.x = kxd * a.y;                     // -i k_x psi
+            r.y = -kxd * a.x;
+            if (hi) { a = cconj(a); r = cconj(r); }
+            z.x = a.x - r.y;                     // phi + i E_x
+            z.y = a.y + r.x;
+        } else {
+            C b = row[nxh];
+            C c = row[2 * nxh];
+            if (edge) { b.y = R(0); c.y = R(0); }
+            C mc;
+            mc.x = -c.x;                         // E_z = -dpsi/dz
+            mc.y = -c.y;
+            if (hi) { b = cconj(b); mc = cconj(mc); }
+            z.x = b.x - mc.y;                    // E_y + i E_z
+            z.y = b.y + mc.x;
+        }
+        return z;
+    };
+    auto store = [&](int q, int i, C v) { buf[q * np + pad16(i)] = v; };
+    fft_pow2<false, true>(buf, tw, n, logn, 2 * P, +1, load, store);
+    __syncthreads();
+    const R s = R(kp.inv_nxny);
+    for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
+        const int p = t / n, x = t - p * n, row = r0 + p;
+        if (row >= nrows) continue;
+        const C u = buf[(2 * p) * np + pad16(x)], v = buf[(2 * p + 1) * np + pad16(x)];
+        fields[size_t(row) * n + x] = Prec<R>::v4(u.x * s, u.y * s, v.x * s, v.y * s);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // per-mode column work: z Chebyshev transform, the Appendix-A BVP for both
 // densities, mismatches and correction (Sec. 5.2.2 step 4), the k = 0 slope
 // (step 5), the gauge partial sum, and the values of psi_i and dpsi_i/dz at
@@ -1042,6 +1241,11 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
 constexpr int kColBlockM = 8;
 constexpr int kColThreadsM = 32 * kColBlockM;
 
+// kTensor: the z transforms run as tensor-core GEMMs around this kernel
+// (k_zgemm); it then reads the coefficients of both densities and writes
+// the coefficients of psi_i and dpsi_i/dz and each mode's correction
+// parameters, instead of transforming itself.
+template <bool kTensor>
 __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int CB = kColBlockM;
@@ -1077,6 +1281,7 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         s_gauge[c] = 0.0;
     }
     if (tid == 0) s_Ai = 0.0;
+    const float scale = kp.f.scale;
     for (int t = tid; t < N * CB; t += bs) {
         const int j = t / CB, c = t - j * CB, col = col0 + c;
         float2 vi = make_float2(0.f, 0.f), vo = vi;
@@ -1084,12 +1289,18 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
             vi = sp[size_t(j) * M + col];
             vo = sp[size_t(N + j) * M + col];
         }
-        Vi[c * NP + j] = vi;
-        Vo[c * NP + j] = vo;
+        if (kTensor) {                       // coefficients: right-hand sides of Eq. (blocksys)
+            Ci[c * NP + j] = cscale(vi, scale);
+            Co[c * NP + j] = cscale(vo, scale);
+        } else {
+            Vi[c * NP + j] = vi;
+            Vo[c * NP + j] = vo;
+        }
     }
     __syncthreads();
 
     const int m = N - 1, JE = (N + 1) / 2, JO = N / 2;
+    if (!kTensor) {
     for (int t = tid; t < 2 * CB * JE; t += bs) {
         const int f = t / (CB * JE), r = t - f * CB * JE, c = r / JE, a = r - c * JE;
         if (a < m - a) {
@@ -1100,7 +1311,6 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         }
     }
     __syncthreads();
-    const float scale = kp.f.scale;
     for (int t = tid; t < CB * N; t += bs) {
         const int c = t / N, q = t - c * N;
         const bool odd = q >= JE;
@@ -1122,6 +1332,7 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         Co[c * NP + n] = make_float2(ox * scale, oy * scale);
     }
     __syncthreads();
+    }
 
     // Appendix A banded solve (even and odd chains), float
     if (tid < 2 * CB) {
@@ -1271,6 +1482,9 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
                 s_ekH[c] = ekH;
                 s_den[c] = den;
                 corr0 = (-P.x * (1.f - kp.f.Gt * ekH * ekH) + Q.x * (ekH - kp.f.Gb * ekH)) / den;
+                if (kTensor) kp.colp[col0 + c] = ColP{P, Q, k, ekH, 1.f / den, 1};
+            } else if (kTensor) {
+                kp.colp[col0 + c] = ColP{make_float2(0.f, 0.f), make_float2(0.f, 0.f), k, 0.f, 0.f, 0};
             }
             if (col0 + c == 0) {
                 const double ddz = 2.0 / kp.Hbar;
@@ -1293,6 +1507,20 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     }
     __syncthreads();
 
+    if (kTensor) {
+        // coefficients of psi_i (plane 0) and dpsi_i/dz (plane 1, before the
+        // factor 2/Hbar), for the node-value GEMM
+        for (int t = tid; t < 2 * CB * N; t += bs) {
+            const int f = t / (CB * N), r = t - f * CB * N, n = r / CB, c = r - n * CB, col = col0 + c;
+            if (col < M) sp[size_t(f * N + n) * M + col] = (f ? Vi : Ci)[c * NP + n];
+        }
+        if (tid == 0) {
+            double g = 0.0;
+            for (int c = 0; c < CB; ++c) g += s_gauge[c];
+            kp.part_gauge_far[blockIdx.x] = g;
+        }
+        return;
+    }
     // node values (float), correction at the nodes (float)
     const float Ai = float(s_Ai);
     const float Gb = kp.f.Gb, Gt = kp.f.Gt, Hf = kp.f.H, HEf = kp.f.HE;
@@ -1347,6 +1575,71 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         for (int c = 0; c < CB; ++c) g += s_gauge[c];
         kp.part_gauge_far[blockIdx.x] = g;
     }
+}
+
+// ---------------------------------------------------------------------------
+// z transforms on the tensor cores (zgemm.cuh), mixed precision, Nz <= 128:
+// k_zgemm_fwd turns the node values of both densities (planes 0, 1 of the
+// spectrum) into Chebyshev coefficients in place; k_column_mixed<true> solves
+// the BVPs on them; k_zgemm_inv turns the coefficients of psi_i and
+// dpsi_i/dz back into node values, adding in its epilogue the factor 2/Hbar
+// of the derivative, the correction of Eq. (inphisc) at the node
+// (normalised form, float) and the k = 0 linear term A_i z (Sec. 5.2.2
+// steps 4-6).
+// ---------------------------------------------------------------------------
+// 32 consecutive floats of an output row (w valid), 16-byte stores
+__device__ __forceinline__ void store_row(float* dst, const float* v, int w) {
+    if (w == 32) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    } else {
+        for (int i = 0; i < w; ++i) dst[i] = v[i];
+    }
+}
+
+__global__ void __launch_bounds__(kZThreads, 1) k_zgemm_fwd(KP kp) {
+    float* base = static_cast<float*>(kp.spec);
+    const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
+    auto epi = [&](int plane, int row, int c0, float* v, int w) {
+        store_row(base + plane * pstride + size_t(row) * ld + c0, v, w);
+    };
+    zgemm_run<false>(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
+}
+
+__global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
+    float* base = static_cast<float*>(kp.spec);
+    const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
+    const float Gb = kp.f.Gb, Gt = kp.f.Gt, H = kp.f.H, HE = kp.f.HE, sz = kp.f.sz;
+    const float Ai = float(kp.scal[1]);
+    auto epi = [&](int plane, int row, int c0, float* v, int w) {
+        const float z = kp.zn32[row];
+        const bool zin = z >= -HE && z <= H + HE;
+        for (int i = 0; i < w; i += 2) {
+            const int col = (c0 + i) >> 1;
+            float re = v[i], im = v[i + 1];
+            if (plane == 1) { re *= sz; im *= sz; }
+            const ColP cp = kp.colp[col];
+            if (cp.corr && zin) {
+                const float e1 = expf(-cp.k * z), e3 = expf(cp.k * (z - H));
+                const float e2 = e3 * cp.ekH, e4 = e1 * cp.ekH;
+                float a, b;
+                if (plane == 0) {
+                    a = -(e1 - Gt * e2) * cp.iden;
+                    b = (e3 - Gb * e4) * cp.iden;
+                } else {
+                    a = (e1 + Gt * e2) * cp.k * cp.iden;
+                    b = (e3 + Gb * e4) * cp.k * cp.iden;
+                }
+                re += cp.P.x * a + cp.Q.x * b;
+                im += cp.P.y * a + cp.Q.y * b;
+            }
+            if (col == 0) re += plane == 0 ? Ai * z : Ai;
+            v[i] = re;
+            v[i + 1] = im;
+        }
+        store_row(base + plane * pstride + size_t(row) * ld + c0, v, w);
+    };
+    zgemm_run<true>(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
 }
 
 // ---------------------------------------------------------------------------
@@ -1862,6 +2155,10 @@ struct dpslab_plan {
     int nxh = 0;
     size_t G = 0, S = 0;
     int px_fwd = 1, tk_fwd = 1, tk_inv = 1, px_inv = 1;
+    int p2x = 0, p2y = 0, lognx = 0, logny = 0;        // power-of-two FFT kernels in x, y
+    bool ztensor = false;                              // z transforms as tensor-core GEMMs
+    int zgrid = 0;                                     // persistent CTAs of the z GEMMs
+    int thr_x_fwd = 256, thr_x_inv = 256, thr_y_fwd = 256, thr_y_inv = 256;
     size_t sm_fftx_fwd = 0, sm_ffty_fwd = 0, sm_ffty_inv = 0, sm_fftx_inv = 0, sm_col = 0, sm_interp = 0, sm_spread = 0;
     KP kp{};
     // allocations
@@ -2041,7 +2338,10 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         if (kp.tile_r > 3) { delete pl; return DPSLAB_ERR_GRID; }
     }
     const int M = ny * nxh;
-    const bool mixed = p->precision == DPSLAB_MIXED;
+    const bool mixed = p->precision == DPSLAB_MIXED || p->precision == DPSLAB_MIXED_SIMT;
+    // z transforms on the tensor cores: Nz <= 128, and rows of a spectrum
+    // plane (2 ny (nx/2+1) floats) a multiple of 16 bytes for the bulk copies
+    pl->ztensor = p->precision == DPSLAB_MIXED && nz <= kZMaxNz && (M % 2) == 0 && !t.zimg_fwd.empty();
     kp.slab = mixed ? kSlabM : 16;
     kp.nslabs = (nz + kp.slab - 1) / kp.slab;
     kp.nbuckets = kp.ntiles * kp.nslabs;
@@ -2060,7 +2360,9 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         const size_t vec = align_up(N * sizeof(double));
         bytes += 2 * vec + 4 * align_up(N * N * sizeof(double)) + 11 * vec;
         bytes += align_up(nx * sizeof(double2)) + align_up(ny * sizeof(double2));
-        bytes += 2 * align_up(N * N * sizeof(float)) + 12 * align_up(N * sizeof(float));   // float copies
+        // float copies: cft, tie, tio (together <= 2 N^2) and 13 vectors
+        bytes += 3 * align_up(N * N * sizeof(float)) + 13 * align_up(N * sizeof(float));
+        if (pl->ztensor) bytes += 2 * align_up(t.zimg_fwd.size() * sizeof(unsigned short));   // bf16 images
         bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
         cudaError_t e = cudaMalloc(&pl->tables, bytes);
         if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
@@ -2089,6 +2391,15 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
             dst = dp;
         };
         upf(t.zn, kp.zn32);
+        if (pl->ztensor) {
+            auto upimg = [&](const std::vector<unsigned short>& v, const unsigned short*& dst) {
+                unsigned short* dp = carve<unsigned short>(cur, v.size());
+                cudaMemcpy(dp, v.data(), v.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
+                dst = dp;
+            };
+            upimg(t.zimg_fwd, kp.zimg_fwd);
+            upimg(t.zimg_inv, kp.zimg_inv);
+        }
         {
             std::vector<double> lo(t.zn.size()), wzh(t.wz.size());
             for (size_t j = 0; j < t.zn.size(); ++j) lo[j] = t.zn[j] - double(float(t.zn[j]));
@@ -2125,6 +2436,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         bytes += align_up(n * sizeof(float4));                    // sorted_rel
         bytes += align_up(n * sizeof(IRec));                      // irec
         bytes += mixed ? align_up(3 * n * sizeof(SrcF)) : 0;      // srcs_tmp
+        bytes += pl->ztensor ? align_up(size_t(M) * sizeof(ColP)) : 0;   // colp
         bytes += 3 * align_up((size_t(kp.nbuckets) + 1) * sizeof(int));   // bucket count/start/fill
         // source records, worst case. FP64: every source in every slab.
         // Mixed: a source is stored once per (tile, slab) block it touches.
@@ -2171,6 +2483,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         kp.sorted_rel = carve<float4>(cur, n);
         kp.irec = carve<IRec>(cur, n);
         if (mixed) kp.srcs_tmp = carve<SrcF>(cur, 3 * n);
+        if (pl->ztensor) kp.colp = carve<ColP>(cur, size_t(M));
         kp.tile_count = carve<int>(cur, size_t(kp.nbuckets) + 1);
         kp.tile_start = carve<int>(cur, size_t(kp.nbuckets) + 1);
         kp.tile_fill = carve<int>(cur, size_t(kp.nbuckets) + 1);
@@ -2209,6 +2522,55 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
     pl->sm_ffty_fwd = (size_t(ny) + 2 * size_t(pl->tk_fwd) * ny) * csz;
     pl->sm_ffty_inv = (size_t(ny) + 6 * size_t(pl->tk_inv) * ny) * csz;
     pl->sm_fftx_inv = (size_t(nx) + 4 * size_t(pl->px_inv) * nx) * csz;
+    // power-of-two sizes: register radix-16 kernels, one slot of 16 values
+    // per thread, one padded buffer (n + n/16 elements) per sequence
+    {
+        const size_t cap = 200 * 1024;
+        auto pow2 = [](int v) { return v >= 32 && v <= kMaxFft && (v & (v - 1)) == 0; };
+        // largest block each kernel can launch with (its register count)
+        auto maxthr = [](const void* f) {
+            cudaFuncAttributes fa{};
+            return cudaFuncGetAttributes(&fa, f) == cudaSuccess ? fa.maxThreadsPerBlock : 0;
+        };
+        const int mxf = maxthr(mixed ? (const void*)k_fftx_fwd_p2<float> : (const void*)k_fftx_fwd_p2<double>);
+        const int mxi = maxthr(mixed ? (const void*)k_fftx_inv_p2<float> : (const void*)k_fftx_inv_p2<double>);
+        const int myf = maxthr(mixed ? (const void*)k_ffty_fwd_p2<float> : (const void*)k_ffty_fwd_p2<double>);
+        const int myi = maxthr(mixed ? (const void*)k_ffty_inv_p2<float> : (const void*)k_ffty_inv_p2<double>);
+        auto lg = [](int v) { int l = 0; while ((1 << l) < v) ++l; return l; };
+        if (pow2(nx)) {
+            const int n16 = nx / 16;
+            const size_t seq = size_t(nx + n16) * csz;
+            const int P = std::max(1, std::min(256, mxf) / n16), Pi = std::max(1, std::min(256, mxi) / (2 * n16));
+            const size_t fwd = size_t(nx) * csz + P * seq, inv = size_t(nx) * csz + 2 * Pi * seq;
+            if (fwd <= cap && inv <= cap && P * n16 <= mxf && 2 * Pi * n16 <= mxi) {
+                pl->p2x = 1;
+                pl->lognx = lg(nx);
+                pl->px_fwd = P;
+                pl->px_inv = Pi;
+                pl->sm_fftx_fwd = fwd;
+                pl->sm_fftx_inv = inv;
+                pl->thr_x_fwd = P * n16;
+                pl->thr_x_inv = 2 * Pi * n16;
+            }
+        }
+        if (pow2(ny)) {
+            const int n16 = ny / 16;
+            const size_t seq = size_t(ny + n16) * csz, tw = size_t(ny) * csz;
+            int T = std::max(1, std::min(8, myf / n16)), Ti = std::max(1, std::min(8, myi / n16));
+            while (T > 1 && tw + T * seq > cap) T /= 2;
+            while (Ti > 1 && tw + Ti * seq > cap) Ti /= 2;
+            if (tw + T * seq <= cap && tw + Ti * seq <= cap && T * n16 <= myf && Ti * n16 <= myi) {
+                pl->p2y = 1;
+                pl->logny = lg(ny);
+                pl->tk_fwd = T;
+                pl->tk_inv = Ti;
+                pl->sm_ffty_fwd = tw + T * seq;
+                pl->sm_ffty_inv = tw + Ti * seq;
+                pl->thr_y_fwd = T * n16;
+                pl->thr_y_inv = Ti * n16;
+            }
+        }
+    }
     pl->sm_col = size_t(col_block) * (nz + (mixed ? 1 : 0)) * (4 * csz + 2 * rsz);
     pl->sm_interp = size_t(kInterpWarps) * (2 * kMaxSupport + kMaxNz) * rsz;
     pl->sm_spread = (2 * size_t(kp.slab) * kTile * kTile +
@@ -2220,13 +2582,30 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         return DPSLAB_ERR_GRID;
     }
     if (mixed) {
+        cudaFuncSetAttribute(k_fftx_fwd_p2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
+        cudaFuncSetAttribute(k_ffty_fwd_p2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
+        cudaFuncSetAttribute(k_ffty_inv_p2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
+        cudaFuncSetAttribute(k_fftx_inv_p2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
         cudaFuncSetAttribute(k_fftx_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
         cudaFuncSetAttribute(k_ffty_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
         cudaFuncSetAttribute(k_ffty_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
         cudaFuncSetAttribute(k_fftx_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
-        cudaFuncSetAttribute(k_column_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
+        if (pl->ztensor) {
+            cudaFuncSetAttribute(k_zgemm_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kZSmem));
+            cudaFuncSetAttribute(k_zgemm_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kZSmem));
+            int nsm = 0;
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->device);
+            const int ntiles = 2 * int((2 * size_t(M) + kZN - 1) / kZN);   // both planes
+            pl->zgrid = std::max(1, std::min(ntiles, nsm));
+        }
+        cudaFuncSetAttribute(k_column_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
+        cudaFuncSetAttribute(k_column_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
         cudaFuncSetAttribute(k_interp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
     } else {
+        cudaFuncSetAttribute(k_fftx_fwd_p2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
+        cudaFuncSetAttribute(k_ffty_fwd_p2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
+        cudaFuncSetAttribute(k_ffty_inv_p2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
+        cudaFuncSetAttribute(k_fftx_inv_p2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
         cudaFuncSetAttribute(k_fftx_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
         cudaFuncSetAttribute(k_ffty_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
         cudaFuncSetAttribute(k_ffty_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
@@ -2369,27 +2748,41 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     const int gx_inv = (kp.nz * kp.ny + pl->px_inv - 1) / pl->px_inv;
     const int gi = (n + kInterpWarps - 1) / kInterpWarps;
     if (kp.mixed) {
-        LAUNCH(k_fftx_fwd<float><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
+        if (pl->p2x) LAUNCH(k_fftx_fwd_p2<float><<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
+        else LAUNCH(k_fftx_fwd<float><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
         mark(3);
-        LAUNCH(k_ffty_fwd<float><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
+        if (pl->p2y) LAUNCH(k_ffty_fwd_p2<float><<<gy_fwd, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny));
+        else LAUNCH(k_ffty_fwd<float><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
         mark(4);
-        LAUNCH(k_column_mixed<<<kp.n_col_blocks, kColThreadsM, pl->sm_col, st>>>(kp));
+        if (pl->ztensor) {
+            LAUNCH(k_zgemm_fwd<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
+            LAUNCH(k_column_mixed<true><<<kp.n_col_blocks, kColThreadsM, pl->sm_col, st>>>(kp));
+            LAUNCH(k_zgemm_inv<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
+        } else {
+            LAUNCH(k_column_mixed<false><<<kp.n_col_blocks, kColThreadsM, pl->sm_col, st>>>(kp));
+        }
         mark(5);
-        LAUNCH(k_ffty_inv<float><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
+        if (pl->p2y) LAUNCH(k_ffty_inv_p2<float><<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
+        else LAUNCH(k_ffty_inv<float><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
         mark(6);
-        LAUNCH(k_fftx_inv<float><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
+        if (pl->p2x) LAUNCH(k_fftx_inv_p2<float><<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
+        else LAUNCH(k_fftx_inv<float><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(7);
         LAUNCH(k_interp_f32<<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     } else {
-        LAUNCH(k_fftx_fwd<double><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
+        if (pl->p2x) LAUNCH(k_fftx_fwd_p2<double><<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
+        else LAUNCH(k_fftx_fwd<double><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
         mark(3);
-        LAUNCH(k_ffty_fwd<double><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
+        if (pl->p2y) LAUNCH(k_ffty_fwd_p2<double><<<gy_fwd, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny));
+        else LAUNCH(k_ffty_fwd<double><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
         mark(4);
         LAUNCH(k_column<<<kp.n_col_blocks, kColThreads, pl->sm_col, st>>>(kp));
         mark(5);
-        LAUNCH(k_ffty_inv<double><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
+        if (pl->p2y) LAUNCH(k_ffty_inv_p2<double><<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
+        else LAUNCH(k_ffty_inv<double><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
         mark(6);
-        LAUNCH(k_fftx_inv<double><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
+        if (pl->p2x) LAUNCH(k_fftx_inv_p2<double><<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
+        else LAUNCH(k_fftx_inv<double><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(7);
         LAUNCH(k_interp<double><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     }
@@ -2423,6 +2816,7 @@ int finish(dpslab_plan* pl, cudaStream_t st, double* U) {
     }
     if (U) *U = pl->h_scal[4];
     if (*pl->h_status & kStatusCapacity) return DPSLAB_ERR_CAPACITY;
+    if (*pl->h_status & kStatusTimeout) return DPSLAB_ERR_CUDA;
     if (*pl->h_status) return DPSLAB_ERR_OUT_OF_SLAB;
     const double sq = pl->h_scal[5], saq = pl->h_scal[6];
     if (std::fabs(sq) > 1e-12 * saq) return DPSLAB_ERR_NOT_NEUTRAL;

@@ -1,0 +1,333 @@
+// z-direction Chebyshev transforms as tensor-core GEMMs (sm_103a, tcgen05).
+//
+// Sec. 5.2.2 steps 3 and 6 apply one dense Nz x Nz matrix to every k-mode
+// column: coefficients from node values (the DCT-I form of the extrema-grid
+// transform) and node values from coefficients (T_n(s_j) = cos(pi n j/m)).
+// With the columns of a spectrum plane as the N dimension this is
+//     D[128 x N] = A[128 x 128] . B[128 x N]      (rows and K padded to 128)
+// over N = 2 ny (nx/2+1) real columns per plane (real and imaginary parts).
+// Both transforms use the even/odd split of the extrema grid, halves at row
+// and K offset 64: forward, K = (S_k = v_k + v_{m-k}, D_k = v_k - v_{m-k}) and
+// rows = (even, odd) coefficients, block diagonal; inverse, K = (even, odd)
+// coefficients and rows = (E_a, O_a), combined to v_a = E_a + O_a,
+// v_{m-a} = E_a - O_a in the epilogue. Each output is a sum of Nz/2 terms.
+//
+// Precision: A and B are split into three bf16 pieces each, x = x1 + x2 + x3,
+// and the six products with piece orders summing to at most 4 (11, 12, 21,
+// 13, 22, 31) are kept; the dropped terms are below 2^-24 of the largest
+// entry. The tensor core adds into its FP32 accumulator with truncation (a
+// bias toward zero of up to one ulp per K step), which a plain split turns
+// into a systematic error of ~1e-6. Hence x1 lies on a fixed-point grid,
+// rint(x 128/s) s/128, with s the power of two above the largest |x| of the
+// row of A (host) or of the column of B (per tile, here): x1 128/s is an
+// integer of at most 8 bits, so every partial sum of the dominant product 11
+// is an integer multiple of one unit below 2^20 units, exact in FP32 - it is
+// never truncated. It has its own accumulator; the five small products share
+// a second one (their truncation is 2^-7 smaller), and the two are added on
+// the CUDA cores in round-to-nearest. x2 and x3 are bf16 roundings of the rest.
+//
+// One persistent CTA of 512 threads per SM keeps A (three pieces, 96 KB) in
+// shared memory and loops over N tiles of 128 columns:
+//   1. the threads split the tile's values (held in registers, loaded during
+//      the previous tile's MMAs) into the three bf16 B pieces, canonical
+//      K-major layout (8 x 16-byte core matrices, no swizzle);
+//   2. one thread issues the 6 x 8 tcgen05.mma (M=128, N=128, K=16,
+//      kind::f16, bf16 inputs, FP32 accumulators) and commits them to an
+//      mbarrier; meanwhile the threads load the next tile (coalesced along
+//      columns, in even/odd row pairs);
+//   3. each warp reads its quarter of the accumulator lanes, 32 columns, with
+//      tcgen05.ld, adds the two accumulators and stores the rows through an
+//      epilogue functor.
+// The wait on the MMAs is bounded; on a timeout the kernel records
+// kStatusTimeout, stops, waits (bounded) once more and frees its tensor memory.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace dps {
+
+constexpr int kZK = 128;          // K and M of the GEMM (Nz padded)
+constexpr int kZH = kZK / 2;      // offset of the odd half (rows and K)
+constexpr int kZN = 128;          // N tile (floats)
+constexpr int kZThreads = 512;
+constexpr int kZPieceA = kZK * kZK;         // bf16 elements per A piece
+constexpr int kZPieceB = kZN * kZK;         // bf16 elements per B piece
+constexpr size_t kZSmemA = 3 * size_t(kZPieceA) * 2;
+constexpr size_t kZSmemB = 3 * size_t(kZPieceB) * 2;
+constexpr size_t kZSmem = kZSmemA + kZSmemB + 64;
+constexpr int kZTmemCols = 2 * kZN;         // exact product 11 | the other five
+constexpr int kZXStride = kZN + 1;          // padded row stride of the inverse epilogue exchange
+constexpr int kZPairs = 16;                 // even/odd row pairs per thread and tile
+constexpr long kZSpinLimit = 1L << 26;      // polls of an mbarrier before giving up
+static_assert(kZThreads == kZN * (kZH / kZPairs), "one (column, pair group) per thread");
+static_assert(size_t(kZK) * kZXStride * 4 <= kZSmemB, "exchange fits the B pieces");
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N)
+// byte offsets >> 4, descriptor version 1 (bits 46-47), no swizzle
+__device__ __forceinline__ uint64_t zdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// bf16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t zidesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long i = 0; i < kZSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+// 16 consecutive 32-bit accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// x = x1 + x2 + x3: x1 = rint(x q) / q on the fixed-point grid of step 1/q
+// (q = 128/s, a power of two), x2, x3 bf16 roundings of the rest (each
+// residual exact in FP32)
+__device__ __forceinline__ void split3(float x, float q, float iq, __nv_bfloat16& a, __nv_bfloat16& b,
+                                       __nv_bfloat16& c) {
+    const float x1 = rintf(x * q) * iq;
+    a = __float2bfloat16_rn(x1);
+    const float r1 = x - x1;
+    b = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(b);
+    c = __float2bfloat16_rn(r2);
+}
+
+// 8 values at K entries k0..k0+7 of column n, three pieces, one 16-byte
+// store each
+__device__ __forceinline__ void put8(unsigned short* sB, int n, int k0, const float* x, float q, float iq) {
+    __align__(16) __nv_bfloat16 p1[8], p2[8], p3[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) split3(x[i], q, iq, p1[i], p2[i], p3[i]);
+    const int e = zimg_index(n, k0);
+    *reinterpret_cast<uint4*>(sB + e) = *reinterpret_cast<const uint4*>(p1);
+    *reinterpret_cast<uint4*>(sB + kZPieceB + e) = *reinterpret_cast<const uint4*>(p2);
+    *reinterpret_cast<uint4*>(sB + 2 * kZPieceB + e) = *reinterpret_cast<const uint4*>(p3);
+}
+
+// The GEMM over nplanes planes of rows (= Nz) x ncols floats (row stride ld,
+// plane stride pstride floats). kInv = false: forward (node values ->
+// coefficients); true: inverse. A image: three pieces, zimg_index layout,
+// halves at 64. epi(plane, row, col0, v[32], nvalid) stores 32 columns of
+// output row `row` (coefficient index, or node index) from column col0.
+template <bool kInv, class Epi>
+__device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aimg, const float* base, int nplanes,
+                                          size_t pstride, int rows, int ncols, size_t ld, int* status, Epi epi) {
+    extern __shared__ __align__(1024) unsigned char zsm[];
+    unsigned short* sA = reinterpret_cast<unsigned short*>(zsm);
+    unsigned short* sB = reinterpret_cast<unsigned short*>(zsm + kZSmemA);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(zsm + kZSmemA + kZSmemB);
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+    __shared__ int s_abort;
+    __shared__ float s_colmax[kZH / kZPairs][kZN];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_per_plane = (ncols + kZN - 1) / kZN;
+    const int ntiles = nplanes * tiles_per_plane;
+    const int m = rows - 1, JE = (rows + 1) >> 1, JO = rows >> 1;
+    // this thread's column of the tile and its group of even/odd pairs
+    const int n = tid & (kZN - 1), g = tid / kZN, p0 = g * kZPairs;
+
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(aimg);
+        uint4* dst = reinterpret_cast<uint4*>(sA);
+        for (int i = tid; i < int(kZSmemA / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
+                     "r"(kZTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    // the pairs of tile t: forward (v_p, v_{m-p}), inverse (y_{2p}, y_{2p+1})
+    float ra[kZPairs], rb[kZPairs];
+    auto load = [&](int t) {
+        const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
+        const bool ok = c0 + n < ncols;
+        const float* col = base + size_t(plane) * pstride + c0 + n;
+#pragma unroll
+        for (int i = 0; i < kZPairs; ++i) {
+            const int p = p0 + i;
+            const int r0 = kInv ? 2 * p : p, r1 = kInv ? 2 * p + 1 : m - p;
+            ra[i] = (ok && p < JE) ? __ldg(col + size_t(r0) * ld) : 0.f;
+            rb[i] = (ok && p < JE && r1 < rows) ? __ldg(col + size_t(r1) * ld) : 0.f;
+        }
+    };
+
+    uint32_t ph = 0u;
+    bool pend = false;
+    if (int(blockIdx.x) < ntiles) load(blockIdx.x);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
+        const int w = min(kZN, ncols - c0);
+        // B operand: K entries p (S_p or y_{2p}) and kZH + p (D_p or y_{2p+1})
+        float xs[kZPairs], xd[kZPairs];
+        float amax = 0.f;
+#pragma unroll
+        for (int i = 0; i < kZPairs; ++i) {
+            const int p = p0 + i;
+            if (kInv) {
+                xs[i] = ra[i];
+                xd[i] = p < JO ? rb[i] : 0.f;
+            } else {
+                const bool mid = p == m - p;                   // the middle node (Nz odd)
+                xs[i] = mid ? ra[i] : ra[i] + rb[i];
+                xd[i] = (p < JO && !mid) ? ra[i] - rb[i] : 0.f;
+            }
+            amax = fmaxf(amax, fmaxf(fabsf(xs[i]), fabsf(xd[i])));
+        }
+        s_colmax[g][n] = amax;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kZH / kZPairs; ++i) amax = fmaxf(amax, s_colmax[i][n]);
+        int e = 0;
+        if (amax > 0.f) frexpf(amax, &e);
+        const float q = ldexpf(1.f, 7 - e), iq = ldexpf(1.f, e - 7);   // 128/s, s/128 with s = 2^e > amax
+        put8(sB, n, p0, xs, q, iq);
+        put8(sB, n, p0 + 8, xs + 8, q, iq);
+        put8(sB, n, kZH + p0, xd, q, iq);
+        put8(sB, n, kZH + p0 + 8, xd + 8, q, iq);
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            constexpr uint32_t idesc = zidesc(kZK, kZN);
+            const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+            const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+            for (int qd = 0; qd < 6; ++qd)
+#pragma unroll
+                for (int s = 0; s < kZK / 16; ++s) {
+                    const uint64_t ad = zdesc(a0 + uint32_t(pa[qd]) * kZPieceA * 2 + uint32_t(s) * 256u, 128u, 2048u);
+                    const uint64_t bd = zdesc(b0 + uint32_t(pb[qd]) * kZPieceB * 2 + uint32_t(s) * 256u, 128u, 2048u);
+                    const bool first = s == 0 && qd <= 1;      // first K step of either accumulator
+                    tc_mma(tmem + (qd == 0 ? 0u : uint32_t(kZN)), ad, bd, idesc, first ? 0u : 1u);
+                }
+            tc_commit(bar);
+        }
+        pend = true;
+        // the next tile's values, while the tensor cores work
+        if (t + int(gridDim.x) < ntiles) load(t + gridDim.x);
+        if (mbar_wait(bar, ph)) {
+            ph ^= 1u;
+            pend = false;
+        } else {
+            s_abort = 1;
+        }
+        __syncthreads();
+        tc_fence_after();
+        if (s_abort) break;
+        {
+            // warp: TMEM lane quarter (warp % 4), 32 columns ((warp / 4) * 32)
+            const int qtr = warp & 3, cc = (warp >> 2) * 32;
+            const int r = qtr * 32 + lane;
+            const uint32_t lb = tmem + (uint32_t(qtr * 32) << 16) + uint32_t(cc);
+            float v[32], u[16];
+#pragma unroll
+            for (int h = 0; h < 32; h += 16) {
+                tc_ld16(lb + uint32_t(h), v + h);
+                tc_ld16(lb + uint32_t(kZN + h), u);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[h + i] += u[i];
+            }
+            if (!kInv) {
+                // row r: coefficient 2r (r < kZH) or 2 (r - kZH) + 1
+                const int nc = r < kZH ? 2 * r : 2 * (r - kZH) + 1;
+                const bool ok = r < kZH ? r < JE : r - kZH < JO;
+                const int wv = min(32, w - cc);
+                if (ok && wv > 0) epi(plane, nc, c0 + cc, v, wv);
+            } else {
+                // rows a and kZH + a hold E_a and O_a: exchange through shared
+                // memory (the B pieces are free once the MMAs completed)
+                float* X = reinterpret_cast<float*>(sB);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) X[r * kZXStride + cc + i] = v[i];
+                __syncthreads();
+                const int a = tid & (kZH - 1), side = (tid >> 6) & 1, ch = (tid >> 7) * 32;
+                const int j = side ? m - a : a;
+                const int wc = min(32, w - ch);
+                if (a < JE && !(side && j == a) && wc > 0) {
+                    const float sg = side ? -1.f : 1.f;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        v[i] = X[a * kZXStride + ch + i] + sg * X[(kZH + a) * kZXStride + ch + i];
+                    epi(plane, j, c0 + ch, v, wc);
+                }
+            }
+        }
+        tc_fence_before();
+        fence_async_smem();
+        __syncthreads();
+    }
+    if (s_abort && tid == 0) {
+        atomicOr(status, kStatusTimeout);
+        if (pend) mbar_wait(bar, ph);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kZTmemCols) : "memory");
+}
+
+}  // namespace dps

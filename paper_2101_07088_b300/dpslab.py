@@ -19,7 +19,7 @@ ERRORS = {
     -1: "INVALID_ARG", -2: "NOT_NEUTRAL", -3: "OUT_OF_SLAB", -4: "CUTOFF_TOO_LARGE",
     -5: "SPLIT_CONSTRAINT", -6: "CAPACITY", -7: "CUDA", -8: "NO_DEVICE", -9: "GRID", -10: "UNSUPPORTED",
 }
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_SIMT = 0, 1, 2   # DPSLAB_FP64, DPSLAB_MIXED, DPSLAB_MIXED_SIMT
 NSTAGES = 10
 
 

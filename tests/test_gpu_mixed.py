@@ -48,14 +48,32 @@ CASES = [
 ]
 
 
+PRECISIONS = [(dpslab.MIXED, "tensor-z"), (dpslab.MIXED_SIMT, "simt-z")]
+
+
+@pytest.mark.parametrize("prec,plabel", PRECISIONS, ids=[p[1] for p in PRECISIONS])
 @pytest.mark.parametrize("name,_", CASES, ids=[c[0] for c in CASES])
-def test_mixed_against_oracle(name, _):
+def test_mixed_against_oracle(name, _, prec, plabel):
     pos, q, p = synth.workload(name)
     P = oracle_params(p["Lx"], p["Ly"], p["H"], p["gw"], p["tol"], p["nx"], p["ny"], nz=p["nz"],
                       eps_b=p["eps_b"], eps_t=p["eps_t"], r_cut=p["r_cut"])
     ref = osolver.solve(pos, q, P)
-    out = gpu_solve(plan_for(P, len(q), precision=dpslab.MIXED), pos, q)
-    _check(ref, out, name, TOL_MIXED_ENERGY if len(q) >= 16384 else TOL_MIXED_ENERGY_SMALL)
+    out = gpu_solve(plan_for(P, len(q), precision=prec), pos, q)
+    _check(ref, out, f"{name} {plabel}", TOL_MIXED_ENERGY if len(q) >= 16384 else TOL_MIXED_ENERGY_SMALL)
+
+
+def test_tensor_z_transform_runs():
+    # Nz <= 128 with ny (nx/2+1) even: the z transforms run as two tensor-core
+    # GEMM launches around the BVP kernel (two launches more than the SIMT form)
+    pos, q, p = synth.workload("c2_jumps_n16384")
+    P = oracle_params(p["Lx"], p["Ly"], p["H"], p["gw"], p["tol"], p["nx"], p["ny"], nz=p["nz"],
+                      eps_b=p["eps_b"], eps_t=p["eps_t"], r_cut=p["r_cut"])
+    counts = {}
+    for prec in (dpslab.MIXED, dpslab.MIXED_SIMT):
+        plan = plan_for(P, len(q), precision=prec)
+        gpu_solve(plan, pos, q)
+        counts[prec] = plan.last_launch_count()
+    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 2, counts
 
 
 def test_mixed_small_ragged_and_paper_rule():
