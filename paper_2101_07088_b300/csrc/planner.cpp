@@ -230,24 +230,8 @@ int build_tables(const dpslab_params& p, const dpslab_derived& d, Tables& t) {
                 }
             }
         };
-        // even/odd split (the symmetry used above), halves at row and K
-        // offset H2 = 64: forward rows r < JE give coefficient 2r from
-        // S_k = v_k + v_{m-k} (K columns k < JE), rows H2 + q give coefficient
-        // 2q + 1 from D_k = v_k - v_{m-k} (K columns H2 + k); inverse rows
-        // a < JE give E_a = sum_r cos(pi 2r a/m) y_{2r} (K columns r), rows
-        // H2 + a give O_a = sum_r cos(pi (2r+1) a/m) y_{2r+1} (K columns H2 + r);
-        // then v_a = E_a + O_a, v_{m-a} = E_a - O_a
-        constexpr int H2 = kZMaxNz / 2;
-        image(t.zimg_fwd, [&](int r, int k) {
-            if (r < H2) return (r < JE && k < JE) ? fwd(2 * r, k) : 0.0;
-            const int q = r - H2, kk = k - H2;
-            return (q < JO && kk >= 0 && kk < JO) ? fwd(2 * q + 1, kk) : 0.0;
-        });
-        image(t.zimg_inv, [&](int r, int k) {
-            if (r < H2) return (r < JE && k < JE) ? cs[(size_t(2 * k) * r) % (2 * m)] : 0.0;
-            const int a = r - H2, kk = k - H2;
-            return (a < JE && kk >= 0 && kk < JO) ? cs[(size_t(2 * kk + 1) * a) % (2 * m)] : 0.0;
-        });
+        image(t.zimg_fwd, [&](int n, int j) { return (n < N && j < N) ? fwd(n, j) : 0.0; });
+        image(t.zimg_inv, [&](int j, int n) { return (n < N && j < N) ? cs[(size_t(n) * j) % (2 * m)] : 0.0; });
     }
 
     // Appendix A: J maps coefficients of a function to those of its integral

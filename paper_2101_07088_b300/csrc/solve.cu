@@ -1603,7 +1603,7 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_fwd(KP kp) {
     auto epi = [&](int plane, int row, int c0, float* v, int w) {
         store_row(base + plane * pstride + size_t(row) * ld + c0, v, w);
     };
-    zgemm_run<false>(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
+    zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
 }
 
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
@@ -1639,7 +1639,7 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
         }
         store_row(base + plane * pstride + size_t(row) * ld + c0, v, w);
     };
-    zgemm_run<true>(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
+    zgemm_run(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
 }
 
 // ---------------------------------------------------------------------------

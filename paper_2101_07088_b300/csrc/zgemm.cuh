@@ -6,11 +6,6 @@
 // With the columns of a spectrum plane as the N dimension this is
 //     D[128 x N] = A[128 x 128] . B[128 x N]      (rows and K padded to 128)
 // over N = 2 ny (nx/2+1) real columns per plane (real and imaginary parts).
-// Both transforms use the even/odd split of the extrema grid, halves at row
-// and K offset 64: forward, K = (S_k = v_k + v_{m-k}, D_k = v_k - v_{m-k}) and
-// rows = (even, odd) coefficients, block diagonal; inverse, K = (even, odd)
-// coefficients and rows = (E_a, O_a), combined to v_a = E_a + O_a,
-// v_{m-a} = E_a - O_a in the epilogue. Each output is a sum of Nz/2 terms.
 //
 // Precision: A and B are split into three bf16 pieces each, x = x1 + x2 + x3,
 // and the six products with piece orders summing to at most 4 (11, 12, 21,
@@ -21,7 +16,7 @@
 // rint(x 128/s) s/128, with s the power of two above the largest |x| of the
 // row of A (host) or of the column of B (per tile, here): x1 128/s is an
 // integer of at most 8 bits, so every partial sum of the dominant product 11
-// is an integer multiple of one unit below 2^20 units, exact in FP32 - it is
+// is an integer multiple of one unit below 2^21 units, exact in FP32 - it is
 // never truncated. It has its own accumulator; the five small products share
 // a second one (their truncation is 2^-7 smaller), and the two are added on
 // the CUDA cores in round-to-nearest. x2 and x3 are bf16 roundings of the rest.
@@ -29,12 +24,12 @@
 // One persistent CTA of 512 threads per SM keeps A (three pieces, 96 KB) in
 // shared memory and loops over N tiles of 128 columns:
 //   1. the threads split the tile's values (held in registers, loaded during
-//      the previous tile's MMAs) into the three bf16 B pieces, canonical
-//      K-major layout (8 x 16-byte core matrices, no swizzle);
+//      the previous tile's MMAs, 16-byte loads of 4 columns x 8 rows per
+//      thread) into the three bf16 B pieces, canonical K-major layout
+//      (8 x 16-byte core matrices, no swizzle);
 //   2. one thread issues the 6 x 8 tcgen05.mma (M=128, N=128, K=16,
 //      kind::f16, bf16 inputs, FP32 accumulators) and commits them to an
-//      mbarrier; meanwhile the threads load the next tile (coalesced along
-//      columns, in even/odd row pairs);
+//      mbarrier; meanwhile the threads load the next tile;
 //   3. each warp reads its quarter of the accumulator lanes, 32 columns, with
 //      tcgen05.ld, adds the two accumulators and stores the rows through an
 //      epilogue functor.
@@ -52,7 +47,6 @@
 namespace dps {
 
 constexpr int kZK = 128;          // K and M of the GEMM (Nz padded)
-constexpr int kZH = kZK / 2;      // offset of the odd half (rows and K)
 constexpr int kZN = 128;          // N tile (floats)
 constexpr int kZThreads = 512;
 constexpr int kZPieceA = kZK * kZK;         // bf16 elements per A piece
@@ -61,11 +55,10 @@ constexpr size_t kZSmemA = 3 * size_t(kZPieceA) * 2;
 constexpr size_t kZSmemB = 3 * size_t(kZPieceB) * 2;
 constexpr size_t kZSmem = kZSmemA + kZSmemB + 64;
 constexpr int kZTmemCols = 2 * kZN;         // exact product 11 | the other five
-constexpr int kZXStride = kZN + 1;          // padded row stride of the inverse epilogue exchange
-constexpr int kZPairs = 16;                 // even/odd row pairs per thread and tile
+constexpr int kZRows = 8;                   // rows per thread and tile (4 columns each)
+constexpr int kZGroups = kZK / kZRows;      // row groups of a tile
 constexpr long kZSpinLimit = 1L << 26;      // polls of an mbarrier before giving up
-static_assert(kZThreads == kZN * (kZH / kZPairs), "one (column, pair group) per thread");
-static_assert(size_t(kZK) * kZXStride * 4 <= kZSmemB, "exchange fits the B pieces");
+static_assert(kZThreads == (kZN / 4) * kZGroups, "one (column quad, row group) per thread");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -156,11 +149,10 @@ __device__ __forceinline__ void put8(unsigned short* sB, int n, int k0, const fl
 }
 
 // The GEMM over nplanes planes of rows (= Nz) x ncols floats (row stride ld,
-// plane stride pstride floats). kInv = false: forward (node values ->
-// coefficients); true: inverse. A image: three pieces, zimg_index layout,
-// halves at 64. epi(plane, row, col0, v[32], nvalid) stores 32 columns of
-// output row `row` (coefficient index, or node index) from column col0.
-template <bool kInv, class Epi>
+// plane stride pstride floats; ld and the plane base multiples of 4 floats).
+// A image: three pieces, zimg_index layout. epi(plane, row, col0, v[32],
+// nvalid) stores 32 columns of output row `row` from column col0.
+template <class Epi>
 __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aimg, const float* base, int nplanes,
                                           size_t pstride, int rows, int ncols, size_t ld, int* status, Epi epi) {
     extern __shared__ __align__(1024) unsigned char zsm[];
@@ -169,13 +161,12 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     uint64_t* bar = reinterpret_cast<uint64_t*>(zsm + kZSmemA + kZSmemB);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
     __shared__ int s_abort;
-    __shared__ float s_colmax[kZH / kZPairs][kZN];
+    __shared__ float s_colmax[kZGroups][kZN];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_per_plane = (ncols + kZN - 1) / kZN;
     const int ntiles = nplanes * tiles_per_plane;
-    const int m = rows - 1, JE = (rows + 1) >> 1, JO = rows >> 1;
-    // this thread's column of the tile and its group of even/odd pairs
-    const int n = tid & (kZN - 1), g = tid / kZN, p0 = g * kZPairs;
+    // this thread's 4 columns (4 cq .. 4 cq + 3) and 8 rows (8 g .. 8 g + 7)
+    const int cq = tid & (kZN / 4 - 1), g = tid / (kZN / 4), r0 = g * kZRows;
 
     {
         const uint4* src = reinterpret_cast<const uint4*>(aimg);
@@ -199,18 +190,16 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
-    // the pairs of tile t: forward (v_p, v_{m-p}), inverse (y_{2p}, y_{2p+1})
-    float ra[kZPairs], rb[kZPairs];
+    float4 rv[kZRows];
     auto load = [&](int t) {
         const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
-        const bool ok = c0 + n < ncols;
-        const float* col = base + size_t(plane) * pstride + c0 + n;
+        const int c = c0 + 4 * cq;
+        const float* src = base + size_t(plane) * pstride + c;
 #pragma unroll
-        for (int i = 0; i < kZPairs; ++i) {
-            const int p = p0 + i;
-            const int r0 = kInv ? 2 * p : p, r1 = kInv ? 2 * p + 1 : m - p;
-            ra[i] = (ok && p < JE) ? __ldg(col + size_t(r0) * ld) : 0.f;
-            rb[i] = (ok && p < JE && r1 < rows) ? __ldg(col + size_t(r1) * ld) : 0.f;
+        for (int i = 0; i < kZRows; ++i) {
+            const int r = r0 + i;
+            rv[i] = (r < rows && c < ncols) ? __ldg(reinterpret_cast<const float4*>(src + size_t(r) * ld))
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
 
@@ -220,33 +209,33 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
         const int w = min(kZN, ncols - c0);
-        // B operand: K entries p (S_p or y_{2p}) and kZH + p (D_p or y_{2p+1})
-        float xs[kZPairs], xd[kZPairs];
-        float amax = 0.f;
+        // per column, the largest |entry| (fixed-point scale of piece 1), then
+        // the split into the three pieces at K entries r0 .. r0 + 7
+        float cm[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < kZPairs; ++i) {
-            const int p = p0 + i;
-            if (kInv) {
-                xs[i] = ra[i];
-                xd[i] = p < JO ? rb[i] : 0.f;
-            } else {
-                const bool mid = p == m - p;                   // the middle node (Nz odd)
-                xs[i] = mid ? ra[i] : ra[i] + rb[i];
-                xd[i] = (p < JO && !mid) ? ra[i] - rb[i] : 0.f;
-            }
-            amax = fmaxf(amax, fmaxf(fabsf(xs[i]), fabsf(xd[i])));
+        for (int i = 0; i < kZRows; ++i) {
+            cm[0] = fmaxf(cm[0], fabsf(rv[i].x));
+            cm[1] = fmaxf(cm[1], fabsf(rv[i].y));
+            cm[2] = fmaxf(cm[2], fabsf(rv[i].z));
+            cm[3] = fmaxf(cm[3], fabsf(rv[i].w));
         }
-        s_colmax[g][n] = amax;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s_colmax[g][4 * cq + j] = cm[j];
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < kZH / kZPairs; ++i) amax = fmaxf(amax, s_colmax[i][n]);
-        int e = 0;
-        if (amax > 0.f) frexpf(amax, &e);
-        const float q = ldexpf(1.f, 7 - e), iq = ldexpf(1.f, e - 7);   // 128/s, s/128 with s = 2^e > amax
-        put8(sB, n, p0, xs, q, iq);
-        put8(sB, n, p0 + 8, xs + 8, q, iq);
-        put8(sB, n, kZH + p0, xd, q, iq);
-        put8(sB, n, kZH + p0 + 8, xd + 8, q, iq);
+        for (int j = 0; j < 4; ++j) {
+            const int n = 4 * cq + j;
+            float amax = 0.f;
+#pragma unroll
+            for (int i = 0; i < kZGroups; ++i) amax = fmaxf(amax, s_colmax[i][n]);
+            int e = 0;
+            if (amax > 0.f) frexpf(amax, &e);
+            const float q = ldexpf(1.f, 7 - e), iq = ldexpf(1.f, e - 7);   // 128/s, s/128 with s = 2^e > amax
+            float x[kZRows];
+#pragma unroll
+            for (int i = 0; i < kZRows; ++i) x[i] = j == 0 ? rv[i].x : j == 1 ? rv[i].y : j == 2 ? rv[i].z : rv[i].w;
+            put8(sB, n, r0, x, q, iq);
+        }
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -278,7 +267,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
         tc_fence_after();
         if (s_abort) break;
         {
-            // warp: TMEM lane quarter (warp % 4), 32 columns ((warp / 4) * 32)
+            // warp: TMEM lane quarter (warp % 4) = rows, 32 columns ((warp / 4) * 32)
             const int qtr = warp & 3, cc = (warp >> 2) * 32;
             const int r = qtr * 32 + lane;
             const uint32_t lb = tmem + (uint32_t(qtr * 32) << 16) + uint32_t(cc);
@@ -290,30 +279,8 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[h + i] += u[i];
             }
-            if (!kInv) {
-                // row r: coefficient 2r (r < kZH) or 2 (r - kZH) + 1
-                const int nc = r < kZH ? 2 * r : 2 * (r - kZH) + 1;
-                const bool ok = r < kZH ? r < JE : r - kZH < JO;
-                const int wv = min(32, w - cc);
-                if (ok && wv > 0) epi(plane, nc, c0 + cc, v, wv);
-            } else {
-                // rows a and kZH + a hold E_a and O_a: exchange through shared
-                // memory (the B pieces are free once the MMAs completed)
-                float* X = reinterpret_cast<float*>(sB);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) X[r * kZXStride + cc + i] = v[i];
-                __syncthreads();
-                const int a = tid & (kZH - 1), side = (tid >> 6) & 1, ch = (tid >> 7) * 32;
-                const int j = side ? m - a : a;
-                const int wc = min(32, w - ch);
-                if (a < JE && !(side && j == a) && wc > 0) {
-                    const float sg = side ? -1.f : 1.f;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        v[i] = X[a * kZXStride + ch + i] + sg * X[(kZH + a) * kZXStride + ch + i];
-                    epi(plane, j, c0 + ch, v, wc);
-                }
-            }
+            const int wv = min(32, w - cc);
+            if (r < rows && wv > 0) epi(plane, r, c0 + cc, v, wv);
         }
         tc_fence_before();
         fence_async_smem();
