@@ -1587,22 +1587,10 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
 // (normalised form, float) and the k = 0 linear term A_i z (Sec. 5.2.2
 // steps 4-6).
 // ---------------------------------------------------------------------------
-// 32 consecutive floats of an output row (w valid), 16-byte stores
-__device__ __forceinline__ void store_row(float* dst, const float* v, int w) {
-    if (w == 32) {
-#pragma unroll
-        for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-    } else {
-        for (int i = 0; i < w; ++i) dst[i] = v[i];
-    }
-}
-
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_fwd(KP kp) {
     float* base = static_cast<float*>(kp.spec);
     const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
-    auto epi = [&](int plane, int row, int c0, float* v, int w) {
-        store_row(base + plane * pstride + size_t(row) * ld + c0, v, w);
-    };
+    auto epi = [](int, int, int, float*, int) {};
     zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
 }
 
@@ -1614,7 +1602,9 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
     auto epi = [&](int plane, int row, int c0, float* v, int w) {
         const float z = kp.zn32[row];
         const bool zin = z >= -HE && z <= H + HE;
-        for (int i = 0; i < w; i += 2) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 2) {
+            if (i >= w) break;
             const int col = (c0 + i) >> 1;
             float re = v[i], im = v[i + 1];
             if (plane == 1) { re *= sz; im *= sz; }
@@ -1637,7 +1627,6 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
             v[i] = re;
             v[i + 1] = im;
         }
-        store_row(base + plane * pstride + size_t(row) * ld + c0, v, w);
     };
     zgemm_run(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
 }

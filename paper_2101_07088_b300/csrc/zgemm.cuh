@@ -149,11 +149,15 @@ __device__ __forceinline__ void put8(unsigned short* sB, int n, int k0, const fl
 }
 
 // The GEMM over nplanes planes of rows (= Nz) x ncols floats (row stride ld,
-// plane stride pstride floats; ld and the plane base multiples of 4 floats).
-// A image: three pieces, zimg_index layout. epi(plane, row, col0, v[32],
-// nvalid) stores 32 columns of output row `row` from column col0.
+// plane stride pstride floats; ld and the plane base multiples of 4 floats),
+// written back in place. A image: three pieces, zimg_index layout.
+// epi(plane, row, col0, v[32], nvalid) may change the 32 outputs of row `row`
+// from column col0 before they are stored (the tile is staged in shared
+// memory so that each warp store writes 512 contiguous bytes of one row).
+constexpr int kZOStride = kZN + 4;          // staged output row stride (16-byte rows, conflict-free)
+static_assert(size_t(kZK) * kZOStride * 4 <= kZSmemB, "staged outputs fit the B pieces");
 template <class Epi>
-__device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aimg, const float* base, int nplanes,
+__device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aimg, float* base, int nplanes,
                                           size_t pstride, int rows, int ncols, size_t ld, int* status, Epi epi) {
     extern __shared__ __align__(1024) unsigned char zsm[];
     unsigned short* sA = reinterpret_cast<unsigned short*>(zsm);
@@ -257,13 +261,14 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
         pend = true;
         // the next tile's values, while the tensor cores work
         if (t + int(gridDim.x) < ntiles) load(t + gridDim.x);
-        if (mbar_wait(bar, ph)) {
+        // one thread polls the MMA barrier (polls from every warp would
+        // compete with the loads for the memory pipes); the rest wait here
+        if (tid == 0 && !mbar_wait(bar, ph)) s_abort = 1;
+        __syncthreads();
+        if (!s_abort) {
             ph ^= 1u;
             pend = false;
-        } else {
-            s_abort = 1;
         }
-        __syncthreads();
         tc_fence_after();
         if (s_abort) break;
         {
@@ -281,6 +286,19 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
             }
             const int wv = min(32, w - cc);
             if (r < rows && wv > 0) epi(plane, r, c0 + cc, v, wv);
+            // stage (the B pieces are free once the MMAs completed)
+            float* O = reinterpret_cast<float*>(sB);
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+                *reinterpret_cast<float4*>(O + r * kZOStride + cc + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            __syncthreads();
+            // warp w stores rows w, w + 16, ...: lane l writes columns 4l .. 4l + 3
+            float* dst = base + size_t(plane) * pstride + c0 + 4 * lane;
+            if (4 * lane < w) {
+                for (int rr = warp; rr < rows; rr += kZThreads / 32)
+                    __stcs(reinterpret_cast<float4*>(dst + size_t(rr) * ld),
+                           *reinterpret_cast<const float4*>(O + rr * kZOStride + 4 * lane));
+            }
         }
         tc_fence_before();
         fence_async_smem();
