@@ -1334,7 +1334,8 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     __syncthreads();
     }
 
-    // Appendix A banded solve (even and odd chains), float
+    // Appendix A banded solve (even and odd chains), float; the previous
+    // step's pivot and right-hand sides stay in registers
     if (tid < 2 * CB) {
         const int c = tid >> 1, ch = tid & 1;
         const float K2 = s_K[c] * s_K[c];
@@ -1342,30 +1343,34 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         float2* Fo = Co + c * NP;
         float* cq = cpv + c * NP;
         float* xc = xe + c * NP;
-        int prev = -1;
+        float cqp = 0.f, xcp = 0.f;
+        float2 fip = make_float2(0.f, 0.f), fop = fip;
+        int last = ch;
         for (int n = ch; n < N; n += 2) {
             const float an = n >= 2 ? -K2 * kp.j2l32[n] : 0.f;
             const float bn = 1.f - K2 * kp.j2d32[n];
             const float cn = n + 2 < N ? -K2 * kp.j2u32[n] : 0.f;
-            float mm = bn, rn = (n == ch) ? K2 : 0.f;
-            float2 fi = Fi[n], fo = Fo[n];
-            if (prev >= 0) {
-                mm -= an * cq[prev];
-                fi = csub(fi, cscale(Fi[prev], an));
-                fo = csub(fo, cscale(Fo[prev], an));
-                rn -= an * xc[prev];
-            }
+            const float mm = bn - an * cqp;
             const float inv = 1.f / mm;
-            cq[n] = cn * inv;
-            Fi[n] = cscale(fi, inv);
-            Fo[n] = cscale(fo, inv);
-            xc[n] = rn * inv;
-            prev = n;
+            const float rn = (n == ch) ? K2 : 0.f;
+            fip = cscale(csub(Fi[n], cscale(fip, an)), inv);
+            fop = cscale(csub(Fo[n], cscale(fop, an)), inv);
+            xcp = (rn - an * xcp) * inv;
+            cqp = cn * inv;
+            cq[n] = cqp;
+            Fi[n] = fip;
+            Fo[n] = fop;
+            xc[n] = xcp;
+            last = n;
         }
-        for (int n = prev - 2; n >= ch; n -= 2) {
-            Fi[n] = csub(Fi[n], cscale(Fi[n + 2], cq[n]));
-            Fo[n] = csub(Fo[n], cscale(Fo[n + 2], cq[n]));
-            xc[n] -= cq[n] * xc[n + 2];
+        for (int n = last - 2; n >= ch; n -= 2) {
+            const float q = cq[n];
+            fip = csub(Fi[n], cscale(fip, q));
+            fop = csub(Fo[n], cscale(fop, q));
+            xcp = xc[n] - q * xcp;
+            Fi[n] = fip;
+            Fo[n] = fop;
+            xc[n] = xcp;
         }
     }
     __syncthreads();
@@ -1409,31 +1414,39 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         }
     }
     __syncthreads();
-    for (int t = tid; t < 2 * CB * N; t += bs) {
-        const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
+    // (field, column) pairs over the warps, n over the lanes
+    const int warp_id = tid >> 5, lane_id = tid & 31, nwarps = bs >> 5;
+    for (int fc = warp_id; fc < 2 * CB; fc += nwarps) {
+        const int f = fc / CB, c = fc % CB;
         float2* X = (f ? Co : Ci) + c * NP;
-        const float2 mm = (n & 1) ? s_d[f][c] : s_c[f][c];
-        X[n] = cadd(X[n], cscale(mm, xe[c * NP + n]));
+        const float2 mc = s_c[f][c], md = s_d[f][c];
+        for (int n = lane_id; n < N; n += 32) X[n] = cadd(X[n], cscale((n & 1) ? md : mc, xe[c * NP + n]));
     }
     __syncthreads();
-    for (int t = tid; t < 2 * CB * N; t += bs) {
-        const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
+    for (int fc = warp_id; fc < 2 * CB; fc += nwarps) {
+        const int f = fc / CB, c = fc % CB;
         const float2* Y = (f ? Co : Ci) + c * NP;
-        float2 v;
-        if (n == 0) v = s_d[f][c];
-        else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
-        else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
-        (f ? Vo : Vi)[c * NP + n] = v;
+        float2* V = (f ? Vo : Vi) + c * NP;
+        for (int n = lane_id; n < N; n += 32) {
+            float2 v;
+            if (n == 0) v = s_d[f][c];
+            else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
+            else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
+            V[n] = v;
+        }
     }
     __syncthreads();
-    for (int t = tid; t < 2 * CB * N; t += bs) {
-        const int f = t / (CB * N), r = t - f * CB * N, c = r / N, n = r - c * N;
+    for (int fc = warp_id; fc < 2 * CB; fc += nwarps) {
+        const int f = fc / CB, c = fc % CB;
         const float2* Y = (f ? Vo : Vi) + c * NP;
-        float2 v;
-        if (n == 0) v = s_c[f][c];
-        else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
-        else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
-        (f ? Co : Ci)[c * NP + n] = v;
+        float2* X = (f ? Co : Ci) + c * NP;
+        for (int n = lane_id; n < N; n += 32) {
+            float2 v;
+            if (n == 0) v = s_c[f][c];
+            else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
+            else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
+            X[n] = v;
+        }
     }
     __syncthreads();
 
@@ -1511,8 +1524,9 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         // coefficients of psi_i (plane 0) and dpsi_i/dz (plane 1, before the
         // factor 2/Hbar), for the node-value GEMM
         for (int t = tid; t < 2 * CB * N; t += bs) {
-            const int f = t / (CB * N), r = t - f * CB * N, n = r / CB, c = r - n * CB, col = col0 + c;
-            if (col < M) sp[size_t(f * N + n) * M + col] = (f ? Vi : Ci)[c * NP + n];
+            const int c = t % CB, fn = t / CB, col = col0 + c;       // fn = f N + n (CB a power of two)
+            const int f = fn >= N, n = fn - f * N;
+            if (col < M) sp[size_t(fn) * M + col] = (f ? Vi : Ci)[c * NP + n];
         }
         if (tid == 0) {
             double g = 0.0;
