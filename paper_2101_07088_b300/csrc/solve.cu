@@ -49,6 +49,13 @@ __device__ double block_sum(double v) {
     return v;
 }
 
+// Cell list index, z fastest: the cell-sorted charge order then sweeps thin
+// y-slabs of the box, whose grid neighbourhood stays in L2 while the
+// interpolation gathers from it.
+__device__ __forceinline__ int cell_index(const KP& kp, int cx, int cy, int cz) {
+    return (cy * kp.ncx + cx) * kp.ncz + cz;
+}
+
 __device__ __forceinline__ int wrap_index(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
@@ -78,7 +85,7 @@ __global__ void k_prepare(KP kp) {
             const int cx = min(kp.ncx - 1, max(0, int(x / kp.cwx)));
             const int cy = min(kp.ncy - 1, max(0, int(y / kp.cwy)));
             const int cz = min(kp.ncz - 1, max(0, int(z / kp.cwz)));
-            const int c = (cz * kp.ncy + cy) * kp.ncx + cx;
+            const int c = cell_index(kp, cx, cy, cz);
             kp.cell_of[k] = c;
             atomicAdd(&kp.cell_count[c], 1);
         }
@@ -1924,7 +1931,7 @@ __global__ void k_scatter_cells(KP kp) {
     const double4_32a p = kp.part[k];
     kp.sorted[slot] = p;
     kp.sorted_idx[slot] = k;
-    const int cx = c % kp.ncx, cy = (c / kp.ncx) % kp.ncy, cz = c / (kp.ncx * kp.ncy);
+    const int cz = c % kp.ncz, cx = (c / kp.ncz) % kp.ncx, cy = c / (kp.ncz * kp.ncx);
     kp.sorted_rel[slot] = make_float4(float(p.x - cx * kp.cwx), float(p.y - cy * kp.cwy), float(p.z - cz * kp.cwz),
                                       float(p.w));
 }
@@ -1988,7 +1995,7 @@ __global__ void k_near(KP kp) {
                 const int yc = kp.ncy >= 3 ? wrap_index(cy - 1 + oy, kp.ncy) : oy;
                 for (int ox = 0; ox < nxc; ++ox) {
                     const int xc = kp.ncx >= 3 ? wrap_index(cx - 1 + ox, kp.ncx) : ox;
-                    near_cell<R>(kp, (zc * kp.ncy + yc) * kp.ncx + xc, x, y, z, zsign, zoff, st, rc2, phi, ex, ey, ez);
+                    near_cell<R>(kp, cell_index(kp, xc, yc, zc), x, y, z, zsign, zoff, st, rc2, phi, ex, ey, ez);
                 }
             }
         }
@@ -2046,7 +2053,7 @@ __global__ void k_near_f32(KP kp) {
                 for (int ox = 0; ox < nxc; ++ox) {
                     const int xu = wrap3x ? cx - 1 + ox : ox;
                     const int xc = wrap3x ? wrap_index(xu, kp.ncx) : ox;
-                    const int cell = (zc * kp.ncy + yc) * kp.ncx + xc;
+                    const int cell = cell_index(kp, xc, yc, zc);
                     const float sxh = float(cx - xu) * cwx, syh = float(cy - yu) * cwy;
                     for (int q = kp.cell_start[cell]; q < kp.cell_start[cell + 1]; ++q) {
                         const float4 src = kp.sorted_rel[q];
