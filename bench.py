@@ -67,9 +67,13 @@ def stage_work(d, n, n_over, wbytes=8):
         "spread": ("hbm", (G + G * n_over / max(n, 1)) * wbytes + n * 4 * wbytes),
         "fft_x_fwd": ("hbm", 2 * G * wbytes + 2 * S * c),
         "fft_y_fwd": ("hbm", 2 * 2 * S * c),
-        # dense z transforms, even/odd split: 4 transforms of N/2 x N/2 blocks,
-        # twice (even/odd), real matrix x complex vector = 4 flops per entry
-        "column": ("alu", M * 4 * (2 * (nz // 2 + 1) ** 2) * 4.0),
+        # z transforms: both spectra in and out (tensor cores; FP32 storage)
+        "z_fwd": ("hbm", 4 * S * c),
+        "z_inv": ("hbm", 4 * S * c),
+        # per-mode BVP: coefficients of both densities in, psi and dpsi/dz
+        # coefficients out (mixed); the FP64 form also transforms in z, dense
+        # N/2 x N/2 blocks, even/odd, real x complex = 4 flops per entry
+        "bvp": ("hbm", 4 * S * c) if wbytes == 4 else ("alu", M * 4 * (2 * (nz // 2 + 1) ** 2) * 4.0),
         "fft_y_inv": ("hbm", 2 * S * c + 3 * S * c),
         "fft_x_inv": ("hbm", 3 * S * c + 4 * G * wbytes),
         "interp": ("hbm", 4 * G * wbytes + n * 8 * wbytes),
@@ -85,6 +89,18 @@ def stage_work(d, n, n_over, wbytes=8):
         "fft_x_inv": 2 * nz * ny * 5 * nx * lg(nx),
     }
     return out, fft_flops
+
+
+# Stages that are one kernel each (the roofline names one kernel)
+SINGLE_KERNEL_STAGES = ("fft_x_fwd", "fft_y_fwd", "z_fwd", "bvp", "z_inv", "fft_y_inv", "fft_x_inv", "interp", "near")
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch,
+# from one ncu capture of the mixed path on the 262144-charge quarter box
+# (512 x 512 x 128 grid, 131584 columns); scaled to another grid by its column
+# count. Only kernels unchanged since their capture are listed.
+NCU_TRAFFIC_C3Q = {"bvp": 269547520 + 219080448, "interp": 393451520 + 10385408,
+                   "fft_x_inv": 404271360 + 485672704}
+NCU_TRAFFIC_COLUMNS = 512 * 257
 
 
 def peaks():
@@ -115,30 +131,50 @@ class Clocks:
         self.lines = []
 
     def start(self):
+        """Start sampling (every 100 ms) and wait for the first sample, so
+        that the sampler is running when the timed region begins."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
+            return
+        t0 = time.monotonic()
+        while not self.lines and time.monotonic() - t0 < 5.0:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def begin(self):
+        self.t_begin = time.monotonic()
+
+    def end(self):
+        self.t_end = time.monotonic()
 
     def stop(self):
+        """Samples taken during [begin, end] (the nearest one after begin if
+        none fell inside)."""
         if not self.proc:
-            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        time.sleep(0.15)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        t0, t1 = getattr(self, "t_begin", 0.0), getattr(self, "t_end", float("inf"))
+        inside = [ln for (t, ln) in self.lines if t0 <= t <= t1 + 0.1]
+        if not inside:
+            after = [ln for (t, ln) in self.lines if t >= t0]
+            inside = after[:1]
         sm, smax, reasons = [], [], set()
         names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in inside:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -259,10 +295,11 @@ def main():
         plan.solve(pos_t, q_t, phi, force)
     plan.profile(True)
     clocks = Clocks(local)
+    clocks.start()
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    clocks.start()
+    clocks.begin()
     step_ms, stage_sum = [], {}
     t_wall = time.perf_counter()
     for _ in range(args.steps):
@@ -278,6 +315,7 @@ def main():
             stage_sum[k] = stage_sum.get(k, 0.0) + v
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t_wall
+    clocks.end()
     clk = clocks.stop()
     launches = plan.last_launch_count() * args.steps
     plan.profile(False)
@@ -344,20 +382,18 @@ def main():
     # roofline of the dominant stage
     over = int(np.sum((pos[:, 2] <= 2 * d["HE"]) | (pos[:, 2] >= p["H"] - 2 * d["HE"])))
     work, fft_flops = stage_work(d, n, over, wbytes=4 if args.precision != "fp64" else 8)
-    if args.precision != "fp64":
-        # the mixed path's column work is 2 spectra in and 2 out; on the tensor
-        # cores or in FP32 the stage is bounded by that traffic
-        S = d["nz"] * d["ny"] * (d["nx"] // 2 + 1)
-        work["column"] = ("hbm", 4 * S * 8)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
-    top = max(stage_ms, key=stage_ms.get)
+    top = max(SINGLE_KERNEL_STAGES, key=lambda k: stage_ms.get(k, 0.0))
     pk = peaks()
     bound, amount = work[top]
     secs = stage_ms[top] * 1e-3
     if bound == "hbm":
         achieved = amount / secs / 1e9
+        traffic = None
+        if args.precision == "mixed" and top in NCU_TRAFFIC_C3Q:
+            traffic = NCU_TRAFFIC_C3Q[top] * (d["ny"] * (d["nx"] // 2 + 1)) / NCU_TRAFFIC_COLUMNS
         roof = dict(bound="hbm", achieved=achieved, peak=pk["hbm_gbs"], unit="GB/s",
-                    frac=achieved / pk["hbm_gbs"], traffic=None, kernel=top,
+                    frac=achieved / pk["hbm_gbs"], traffic=traffic, algorithmic_bytes=amount, kernel=top,
                     peak_source=pk["source"] + " (MEASURED_PEAKS hbm_gbs)")
     else:
         achieved = amount / secs / 1e12

@@ -181,12 +181,15 @@ int dpslab_last_launch_count(const dpslab_plan* plan);
  * Per-stage timing. With profiling on, every solve records CUDA events on its
  * stream around each stage; dpslab_stage_times writes the last solve's
  * stage durations in milliseconds (device time) to ms[0 .. DPSLAB_NSTAGES-1].
- * Stage i is named by dpslab_stage_name(i): prepare, spread, fft_x_fwd,
- * fft_y_fwd, column (z transform + BVP + correction + inverse z), fft_y_inv,
- * fft_x_inv, interp, near (cell list + pairs), finish (gauge + assembly +
- * energy).
+ * Stage i is named by dpslab_stage_name(i): prepare (validation, cell
+ * list), spread (sources, buckets, spreading), fft_x_fwd, fft_y_fwd, z_fwd
+ * (tensor-core z transform; 0 when the z transforms run inside the BVP
+ * kernel), bvp (per-mode BVP, correction coefficients, k = 0 mode), z_inv
+ * (tensor-core inverse z transform with the correction at the nodes; 0 as
+ * z_fwd), fft_y_inv, fft_x_inv, interp, near (pairs), finish (gauge +
+ * assembly + energy).
  */
-#define DPSLAB_NSTAGES 10
+#define DPSLAB_NSTAGES 12
 int dpslab_profile(dpslab_plan* plan, int on);
 int dpslab_stage_times(const dpslab_plan* plan, double* ms, int n);
 const char* dpslab_stage_name(int stage);

@@ -2663,8 +2663,8 @@ extern "C" int dpslab_stage_times(const dpslab_plan* plan, double* ms, int n) {
 }
 
 extern "C" const char* dpslab_stage_name(int stage) {
-    static const char* names[DPSLAB_NSTAGES] = {"prepare", "spread", "fft_x_fwd", "fft_y_fwd", "column",
-                                                "fft_y_inv", "fft_x_inv", "interp", "near", "finish"};
+    static const char* names[DPSLAB_NSTAGES] = {"prepare", "spread", "fft_x_fwd", "fft_y_fwd", "z_fwd", "bvp",
+                                                "z_inv", "fft_y_inv", "fft_x_inv", "interp", "near", "finish"};
     return (stage >= 0 && stage < DPSLAB_NSTAGES) ? names[stage] : "";
 }
 
@@ -2766,18 +2766,22 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         mark(4);
         if (pl->ztensor) {
             LAUNCH(k_zgemm_fwd<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
+            mark(5);
             LAUNCH(k_column_mixed<true><<<kp.n_col_blocks, kColThreadsM, pl->sm_col, st>>>(kp));
+            mark(6);
             LAUNCH(k_zgemm_inv<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
         } else {
+            mark(5);
             LAUNCH(k_column_mixed<false><<<kp.n_col_blocks, kColThreadsM, pl->sm_col, st>>>(kp));
+            mark(6);
         }
-        mark(5);
+        mark(7);
         if (pl->p2y) LAUNCH(k_ffty_inv_p2<float><<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
         else LAUNCH(k_ffty_inv<float><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
-        mark(6);
+        mark(8);
         if (pl->p2x) LAUNCH(k_fftx_inv_p2<float><<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
         else LAUNCH(k_fftx_inv<float><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
-        mark(7);
+        mark(9);
         LAUNCH(k_interp_f32<<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     } else {
         if (pl->p2x) LAUNCH(k_fftx_fwd_p2<double><<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
@@ -2786,27 +2790,29 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         if (pl->p2y) LAUNCH(k_ffty_fwd_p2<double><<<gy_fwd, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny));
         else LAUNCH(k_ffty_fwd<double><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
         mark(4);
-        LAUNCH(k_column<<<kp.n_col_blocks, kColThreads, pl->sm_col, st>>>(kp));
         mark(5);
+        LAUNCH(k_column<<<kp.n_col_blocks, kColThreads, pl->sm_col, st>>>(kp));
+        mark(6);
+        mark(7);
         if (pl->p2y) LAUNCH(k_ffty_inv_p2<double><<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
         else LAUNCH(k_ffty_inv<double><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
-        mark(6);
+        mark(8);
         if (pl->p2x) LAUNCH(k_fftx_inv_p2<double><<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
         else LAUNCH(k_fftx_inv<double><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
-        mark(7);
+        mark(9);
         LAUNCH(k_interp<double><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     }
-    mark(8);
+    mark(10);
     if (kp.near_on) {
         if (kp.mixed) LAUNCH(k_near_f32<<<(n + 127) / 128, 128, 0, st>>>(kp));
         else LAUNCH(k_near<double><<<(n + 127) / 128, 128, 0, st>>>(kp));
     }
-    mark(9);
+    mark(11);
     LAUNCH(k_origin<<<nb, kChargeThreads, 0, st>>>(kp));
     LAUNCH(k_final_gauge<<<1, 1024, 0, st>>>(kp));
     LAUNCH(k_assemble<<<nb, kChargeThreads, 0, st>>>(kp));
     LAUNCH(k_final_energy<<<1, 1024, 0, st>>>(kp));
-    mark(10);
+    mark(12);
 #undef LAUNCH
 #undef SCAN
     DPS_CUDA(cudaMemcpyAsync(pl->h_scal, kp.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -50,7 +50,10 @@ constexpr int kZK = 128;          // K and M of the GEMM (Nz padded)
 constexpr int kZN = 128;          // N tile (floats)
 constexpr int kZThreads = 512;
 constexpr int kZPieceA = kZK * kZK;         // bf16 elements per A piece
-constexpr int kZPieceB = kZN * kZK;         // bf16 elements per B piece
+// B row groups (8 columns, all K) 2064 B apart instead of 2048: a warp's
+// 16-byte stores into 16 groups then fall on different banks
+constexpr int kZSboB = 2048 + 16;           // bytes between B row groups
+constexpr int kZPieceB = (kZN / 8) * (kZSboB / 2);   // bf16 elements per B piece
 constexpr size_t kZSmemA = 3 * size_t(kZPieceA) * 2;
 constexpr size_t kZSmemB = 3 * size_t(kZPieceB) * 2;
 constexpr size_t kZSmem = kZSmemA + kZSmemB + 64;
@@ -142,7 +145,7 @@ __device__ __forceinline__ void put8(unsigned short* sB, int n, int k0, const fl
     __align__(16) __nv_bfloat16 p1[8], p2[8], p3[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) split3(x[i], q, iq, p1[i], p2[i], p3[i]);
-    const int e = zimg_index(n, k0);
+    const int e = (n >> 3) * (kZSboB / 2) + (k0 >> 3) * 64 + (n & 7) * 8;   // canonical layout, padded row groups
     *reinterpret_cast<uint4*>(sB + e) = *reinterpret_cast<const uint4*>(p1);
     *reinterpret_cast<uint4*>(sB + kZPieceB + e) = *reinterpret_cast<const uint4*>(p2);
     *reinterpret_cast<uint4*>(sB + 2 * kZPieceB + e) = *reinterpret_cast<const uint4*>(p3);
@@ -252,7 +255,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
 #pragma unroll
                 for (int s = 0; s < kZK / 16; ++s) {
                     const uint64_t ad = zdesc(a0 + uint32_t(pa[qd]) * kZPieceA * 2 + uint32_t(s) * 256u, 128u, 2048u);
-                    const uint64_t bd = zdesc(b0 + uint32_t(pb[qd]) * kZPieceB * 2 + uint32_t(s) * 256u, 128u, 2048u);
+                    const uint64_t bd = zdesc(b0 + uint32_t(pb[qd]) * kZPieceB * 2 + uint32_t(s) * 256u, 128u, kZSboB);
                     const bool first = s == 0 && qd <= 1;      // first K step of either accumulator
                     tc_mma(tmem + (qd == 0 ? 0u : uint32_t(kZN)), ad, bd, idesc, first ? 0u : 1u);
                 }

@@ -20,7 +20,7 @@ ERRORS = {
     -5: "SPLIT_CONSTRAINT", -6: "CAPACITY", -7: "CUDA", -8: "NO_DEVICE", -9: "GRID", -10: "UNSUPPORTED",
 }
 FP64, MIXED, MIXED_SIMT = 0, 1, 2   # DPSLAB_FP64, DPSLAB_MIXED, DPSLAB_MIXED_SIMT
-NSTAGES = 10
+NSTAGES = 12
 
 
 class DpslabError(RuntimeError):
