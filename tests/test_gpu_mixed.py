@@ -103,3 +103,19 @@ def test_mixed_against_fp64_gpu_at_one_million_charges():
     # zero net lateral force (walls push only along z) holds at any size
     s = np.sum(np.abs(out["force"][:, :2]))
     assert abs(np.sum(out["force"][:, 0])) < 1e-6 * s and abs(np.sum(out["force"][:, 1])) < 1e-6 * s
+
+
+@pytest.mark.parametrize("ny,nz", [(39, 37), (40, 160)], ids=["odd-columns", "nz-160"])
+def test_mixed_fallback_to_cuda_core_z_transform(ny, nz):
+    # ny (nx/2+1) odd, or Nz > 128: DPSLAB_MIXED runs the z transforms on the
+    # CUDA cores (same launch count as DPSLAB_MIXED_SIMT) and meets the same bar
+    P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, ny, nz=nz, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
+    pos, q = synth.electrolyte(102, 24.0, 20.0, 1.0, 19.0, seed=4)
+    ref = osolver.solve(pos, q, P)
+    counts = {}
+    for prec in (dpslab.MIXED, dpslab.MIXED_SIMT):
+        plan = plan_for(P, 102, precision=prec)
+        out = gpu_solve(plan, pos, q)
+        counts[prec] = plan.last_launch_count()
+        _check(ref, out, f"fallback ny={ny} nz={nz} prec={prec}", TOL_MIXED_ENERGY_SMALL)
+    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT], counts
