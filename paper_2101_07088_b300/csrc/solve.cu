@@ -20,7 +20,7 @@ namespace {
 constexpr int kColBlock = 4;        // k_par columns per block of the column kernel (one warp each)
 constexpr int kColThreads = 32 * kColBlock;
 constexpr int kChargeThreads = 256;
-constexpr int kInterpWarps = 8;
+constexpr int kInterpWarps = 2;
 constexpr int kTile = 16;           // spreading tile: kTile x kTile xy grid points, one thread each
 constexpr int kSpreadBatch = 32;    // sources per batch in the tiled spreading
 constexpr double kTwoPi = 6.283185307179586476925286766559;
