@@ -862,31 +862,20 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int logn) {
     const size_t S = size_t(nrows) * nxh;
     const R kxs = R(kTwoPi / kp.Lx);
     const int r0 = blockIdx.x * P;
-    // stage the half spectra of the block's rows, st[(3 p + a) nxh + k] with
-    // a = 0 psi, 1 E_y (specB), 2 dpsi/dz (3 nxh <= 2 (n + n/16): fits buf)
-    C* st = buf;
-    for (int t = threadIdx.x; t < 3 * P * nxh; t += blockDim.x) {
-        const int pa = t / nxh, k = t - pa * nxh, p = pa / 3, a = pa - 3 * p, row = r0 + p;
-        C v;
-        v.x = R(0);
-        v.y = R(0);
-        if (row < nrows) {
-            const size_t g = size_t(row) * nxh + k;
-            v = a == 0 ? spec[g] : (a == 1 ? specB[g] : spec[S + g]);
-        }
-        st[t] = v;
-    }
     __syncthreads();
     // sequence q = 2 p + w: row r0 + p; w = 0 packs (phi, E_x), w = 1 (E_y, E_z)
     auto load = [&](int q, int k) {
-        const int p = q >> 1, w = q & 1;
+        const int p = q >> 1, w = q & 1, row = r0 + p;
+        C z;
+        z.x = R(0);
+        z.y = R(0);
+        if (row >= nrows) return z;
         const bool hi = k >= nxh;
         const int kk = hi ? n - k : k;
         const bool edge = kk == 0 || kk == n / 2;
-        const C* row = st + 3 * p * nxh + kk;
-        C z;
+        const size_t g = size_t(row) * nxh + kk;
         if (w == 0) {
-            C a = row[0];
+            C a = spec[g];
             if (edge) a.y = R(0);
             const R kxd = edge ? R(0) : (sizeof(R) == sizeof(double) ? R(kTwoPi * kk / kp.Lx) : kxs * R(kk));
             C r;
@@ -896,8 +885,8 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int logn) {
             z.x = a.x - r.y;                     // phi + i E_x
             z.y = a.y + r.x;
         } else {
-            C b = row[nxh];
-            C c = row[2 * nxh];
+            C b = specB[g];
+            C c = spec[S + g];
             if (edge) { b.y = R(0); c.y = R(0); }
             C mc;
             mc.x = -c.x;                         // E_z = -dpsi/dz
@@ -909,7 +898,7 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int logn) {
         return z;
     };
     auto store = [&](int q, int i, C v) { buf[q * np + pad16(i)] = v; };
-    fft_pow2<false, true>(buf, tw, n, logn, 2 * P, +1, load, store);
+    fft_pow2<false>(buf, tw, n, logn, 2 * P, +1, load, store);
     __syncthreads();
     const R s = R(kp.inv_nxny);
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
@@ -2550,7 +2539,7 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         if (pow2(nx)) {
             const int n16 = nx / 16;
             const size_t seq = size_t(nx + n16) * csz;
-            const int P = std::max(1, std::min(256, mxf) / n16), Pi = std::max(1, std::min(256, mxi) / (2 * n16));
+            const int P = std::max(1, std::min(256, mxf) / n16), Pi = std::max(1, std::min(128, mxi) / (2 * n16));
             const size_t fwd = size_t(nx) * csz + P * seq, inv = size_t(nx) * csz + 2 * Pi * seq;
             if (fwd <= cap && inv <= cap && P * n16 <= mxf && 2 * Pi * n16 <= mxi) {
                 pl->p2x = 1;
