@@ -1330,43 +1330,82 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
     __syncthreads();
     }
 
-    // Appendix A banded solve (even and odd chains), float; the previous
-    // step's pivot and right-hand sides stay in registers
-    if (tid < 2 * CB) {
-        const int c = tid >> 1, ch = tid & 1;
+    // Appendix A banded solve (even and odd chains), float, eliminated from
+    // both ends at once: lane side 0 sweeps rows 0 .. m-1 downward (row i
+    // becomes y_i + c'_i y_{i+1} = f'_i), lane side 1 sweeps rows L-1 .. m
+    // upward (a''_i y_{i-1} + y_i = f''_i); the two meet in a 2 x 2 system at
+    // rows m-1, m, then substitute back outward. One instruction stream for
+    // both directions (per-lane start, step and coefficient roles). The
+    // 4 CB lanes of warp 0: (mode c, chain ch, side).
+    static_assert(4 * CB <= 32, "the two-way sweeps run in one warp");
+    if (tid < 4 * CB) {
+        const int c = tid >> 2, ch = (tid >> 1) & 1, side = tid & 1;
         const float K2 = s_K[c] * s_K[c];
         float2* Fi = Ci + c * NP;
         float2* Fo = Co + c * NP;
-        float* cq = cpv + c * NP;
+        float* cq = cpv + c * NP;          // c'_i (side 0 rows), a''_i (side 1 rows)
         float* xc = xe + c * NP;
-        float cqp = 0.f, xcp = 0.f;
+        const int L = (N - ch + 1) / 2, m = L / 2;
+        const int cnt = side ? L - m : m, i0 = side ? L - 1 : 0, di = side ? -1 : 1;
+        const int cmax = L - m;            // >= m: the longer sweep
+        float qp = 0.f, xcp = 0.f;
         float2 fip = make_float2(0.f, 0.f), fop = fip;
-        int last = ch;
-        for (int n = ch; n < N; n += 2) {
-            const float an = n >= 2 ? -K2 * kp.j2l32[n] : 0.f;
-            const float bn = 1.f - K2 * kp.j2d32[n];
-            const float cn = n + 2 < N ? -K2 * kp.j2u32[n] : 0.f;
-            const float mm = bn - an * cqp;
-            const float inv = 1.f / mm;
-            const float rn = (n == ch) ? K2 : 0.f;
-            fip = cscale(csub(Fi[n], cscale(fip, an)), inv);
-            fop = cscale(csub(Fo[n], cscale(fop, an)), inv);
-            xcp = (rn - an * xcp) * inv;
-            cqp = cn * inv;
-            cq[n] = cqp;
-            Fi[n] = fip;
-            Fo[n] = fop;
-            xc[n] = xcp;
-            last = n;
+        for (int k = 0; k < cmax; ++k) {
+            if (k < cnt) {
+                const int i = i0 + di * k, n = ch + 2 * i;
+                const float an = n >= 2 ? -K2 * kp.j2l32[n] : 0.f;
+                const float bn = 1.f - K2 * kp.j2d32[n];
+                const float cn = n + 2 < N ? -K2 * kp.j2u32[n] : 0.f;
+                const float lo = side ? cn : an, up = side ? an : cn;   // toward / away from the sweep
+                const float inv = 1.f / (bn - lo * qp);
+                const float rn = (i == 0) ? K2 : 0.f;
+                fip = cscale(csub(Fi[n], cscale(fip, lo)), inv);
+                fop = cscale(csub(Fo[n], cscale(fop, lo)), inv);
+                xcp = (rn - lo * xcp) * inv;
+                qp = up * inv;
+                cq[n] = qp;
+                Fi[n] = fip;
+                Fo[n] = fop;
+                xc[n] = xcp;
+            }
         }
-        for (int n = last - 2; n >= ch; n -= 2) {
-            const float q = cq[n];
-            fip = csub(Fi[n], cscale(fip, q));
-            fop = csub(Fo[n], cscale(fop, q));
-            xcp = xc[n] - q * xcp;
-            Fi[n] = fip;
-            Fo[n] = fop;
-            xc[n] = xcp;
+        __syncwarp();
+        if (side == 1 && m > 0) {
+            // rows m-1 (y + c' y_m = f') and m (a'' y_{m-1} + y = f'')
+            const int nA = ch + 2 * (m - 1), nB = ch + 2 * m;
+            const float cA = cq[nA], aB = cq[nB];
+            const float den = 1.f / (1.f - aB * cA);
+            const float2 yBi = cscale(csub(Fi[nB], cscale(Fi[nA], aB)), den);
+            const float2 yBo = cscale(csub(Fo[nB], cscale(Fo[nA], aB)), den);
+            const float yBx = (xc[nB] - aB * xc[nA]) * den;
+            Fi[nA] = csub(Fi[nA], cscale(yBi, cA));
+            Fo[nA] = csub(Fo[nA], cscale(yBo, cA));
+            xc[nA] = xc[nA] - cA * yBx;
+            Fi[nB] = yBi;
+            Fo[nB] = yBo;
+            xc[nB] = yBx;
+        }
+        __syncwarp();
+        // substitute outward from the interface: side 0 rows m-2 .. 0,
+        // side 1 rows m+1 .. L-1
+        const int bcnt = side ? L - m - 1 : m - 1, b0 = side ? m + 1 : m - 2, bdi = -di;
+        if (bcnt > 0) {
+            const int nprev = ch + 2 * (b0 - bdi);
+            fip = Fi[nprev];
+            fop = Fo[nprev];
+            xcp = xc[nprev];
+        }
+        for (int k = 0; k < cmax; ++k) {
+            if (k < bcnt) {
+                const int i = b0 + bdi * k, n = ch + 2 * i;
+                const float q = cq[n];
+                fip = csub(Fi[n], cscale(fip, q));
+                fop = csub(Fo[n], cscale(fop, q));
+                xcp = xc[n] - q * xcp;
+                Fi[n] = fip;
+                Fo[n] = fop;
+                xc[n] = xcp;
+            }
         }
     }
     __syncthreads();

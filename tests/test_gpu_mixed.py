@@ -105,7 +105,7 @@ def test_mixed_against_fp64_gpu_at_one_million_charges():
     assert abs(np.sum(out["force"][:, 0])) < 1e-6 * s and abs(np.sum(out["force"][:, 1])) < 1e-6 * s
 
 
-@pytest.mark.parametrize("ny,nz", [(39, 37), (40, 160)], ids=["odd-columns", "nz-160"])
+@pytest.mark.parametrize("ny,nz", [(39, 37), (40, 136)], ids=["odd-columns", "nz-136"])
 def test_mixed_fallback_to_cuda_core_z_transform(ny, nz):
     # ny (nx/2+1) odd, or Nz > 128: DPSLAB_MIXED runs the z transforms on the
     # CUDA cores (same launch count as DPSLAB_MIXED_SIMT) and meets the same bar
