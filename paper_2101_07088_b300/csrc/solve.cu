@@ -1639,8 +1639,9 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_fwd(KP kp) {
     float* base = static_cast<float*>(kp.spec);
     const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
+    auto prep = [](int, int) {};
     auto epi = [](int, int, int, float*, int) {};
-    zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
+    zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi);
 }
 
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
@@ -1648,6 +1649,14 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
     const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
     const float Gb = kp.f.Gb, Gt = kp.f.Gt, H = kp.f.H, HE = kp.f.HE, sz = kp.f.sz;
     const float Ai = float(kp.scal[1]);
+    // the tile's 64 modes' correction parameters, staged once per tile
+    __shared__ ColP s_cp[kZN / 2];
+    int s_c0 = 0;
+    auto prep = [&](int, int c0) {
+        const int i = threadIdx.x, col = c0 / 2 + i;
+        if (i < kZN / 2 && col < kp.ny * kp.nxh) s_cp[i] = kp.colp[col];
+        s_c0 = c0;
+    };
     auto epi = [&](int plane, int row, int c0, float* v, int w) {
         const float z = kp.zn32[row];
         const bool zin = z >= -HE && z <= H + HE;
@@ -1657,8 +1666,10 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
             const int col = (c0 + i) >> 1;
             float re = v[i], im = v[i + 1];
             if (plane == 1) { re *= sz; im *= sz; }
-            const ColP cp = kp.colp[col];
-            if (cp.corr && zin) {
+            const ColP cp = s_cp[col - s_c0 / 2];
+            // both exponentials below e^-80 (k z and k (H - z) large): the
+            // correction is below FP32 resolution of psi there
+            if (cp.corr && zin && (cp.k * z < 80.f || cp.k * (H - z) < 80.f)) {
                 const float e1 = expf(-cp.k * z), e3 = expf(cp.k * (z - H));
                 const float e2 = e3 * cp.ekH, e4 = e1 * cp.ekH;
                 float a, b;
@@ -1677,7 +1688,7 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
             v[i + 1] = im;
         }
     };
-    zgemm_run(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, epi);
+    zgemm_run(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi);
 }
 
 // ---------------------------------------------------------------------------

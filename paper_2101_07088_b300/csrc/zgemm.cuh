@@ -159,9 +159,13 @@ __device__ __forceinline__ void put8(unsigned short* sB, int n, int k0, const fl
 // memory so that each warp store writes 512 contiguous bytes of one row).
 constexpr int kZOStride = kZN + 4;          // staged output row stride (16-byte rows, conflict-free)
 static_assert(size_t(kZK) * kZOStride * 4 <= kZSmemB, "staged outputs fit the B pieces");
-template <class Epi>
+// prep(plane, col0) runs on every thread once per tile while the MMAs are in
+// flight (before the barrier that precedes the epilogue): it may stage
+// per-tile data in shared memory for epi.
+template <class Prep, class Epi>
 __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aimg, float* base, int nplanes,
-                                          size_t pstride, int rows, int ncols, size_t ld, int* status, Epi epi) {
+                                          size_t pstride, int rows, int ncols, size_t ld, int* status, Prep prep,
+                                          Epi epi) {
     extern __shared__ __align__(1024) unsigned char zsm[];
     unsigned short* sA = reinterpret_cast<unsigned short*>(zsm);
     unsigned short* sB = reinterpret_cast<unsigned short*>(zsm + kZSmemA);
@@ -264,6 +268,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
         pend = true;
         // the next tile's values, while the tensor cores work
         if (t + int(gridDim.x) < ntiles) load(t + gridDim.x);
+        prep(plane, c0);
         // one thread polls the MMA barrier (polls from every warp would
         // compete with the loads for the memory pipes); the rest wait here
         if (tid == 0 && !mbar_wait(bar, ph)) s_abort = 1;
