@@ -267,7 +267,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_2101_07088_b300 import build, dpslab
+    from paper_2101_07088_b300 import build, dpslab, replicas
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -280,7 +280,7 @@ def main():
         dist.barrier()
     # each rank solves its own system (independent seed)
     if world > 1:
-        pos, q = synth.electrolyte(n, p["Lx"], p["Ly"], 1.0, p["H"] - 1.0, wl["seed"] + 1000 * rank)
+        pos, q = synth.electrolyte(n, p["Lx"], p["Ly"], 1.0, p["H"] - 1.0, replicas.replica_seed(wl["seed"], rank))
     prec = {"mixed": dpslab.MIXED, "mixed_simt": dpslab.MIXED_SIMT, "fp64": dpslab.FP64}[args.precision]
     plan = dpslab.Plan(dpslab.make_params(precision=prec, **p), n)
     d = plan.derived
@@ -319,13 +319,9 @@ def main():
     clk = clocks.stop()
     launches = plan.last_launch_count() * args.steps
     plan.profile(False)
-    mean_ms = sum(step_ms) / len(step_ms)
+    mean_ms, value = replicas.job_rate(sum(step_ms) / len(step_ms), n, dist, dev)
     if dist:
-        t = torch.tensor([mean_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = float(t.item())
         dist.barrier()
-    value = n * world / (mean_ms * 1e-3)
     srt = sorted(step_ms)
     p50 = srt[len(srt) // 2]
     p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
@@ -348,11 +344,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_mean = sum(e2e_ms) / len(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_mean], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_mean = float(t.item())
+    e2e_mean, e2e_value = replicas.job_rate(sum(e2e_ms) / len(e2e_ms), n, dist, dev)
 
     # accuracy of the timed path against the FP64 path on the same inputs, and
     # the FP64 path's own step time (outside the timed region)
@@ -406,7 +398,7 @@ def main():
                 ms_per_step=mean_ms, p50_ms=p50, p99_ms=p99, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64" if args.precision == "fp64" else "f32+f64", data="synthetic (seeded +-1 electrolyte)",
                 config=config,
-                e2e=dict(value=n * world / (e2e_mean * 1e-3), unit=UNIT, ms_per_step=e2e_mean,
+                e2e=dict(value=e2e_value, unit=UNIT, ms_per_step=e2e_mean,
                          h2d_bytes_per_step=n * 4 * 8, d2h_bytes_per_step=n * 4 * 8 + 8 + 8 * 8 + 4),
                 gpu_launches=launches, roofline=roof, clocks=clk, wall_s=wall,
                 energy=U, plan_device_bytes=plan.device_bytes)
