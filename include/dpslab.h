@@ -178,6 +178,41 @@ int dpslab_debug_fetch(dpslab_plan* plan, int which, void* host_dst, size_t byte
 int dpslab_last_launch_count(const dpslab_plan* plan);
 
 /*
+ * Batches of independent systems, each with its own box, walls, grid and
+ * charge count (the paper's solve, per system; systems never interact).
+ *
+ * dpslab_batch_create makes one plan per system (params[i], max_n[i]: as
+ * dpslab_plan_create) and nstreams CUDA streams (1 <= nstreams; at most
+ * count are used). System i runs on stream i mod nstreams. The plans of one
+ * stream share one workspace sized for the largest of them, since they run
+ * one after another. The batch's device footprint is therefore the tables of
+ * every system plus nstreams workspaces (dpslab_batch_device_bytes). Errors
+ * are as dpslab_plan_create, for the first system that fails; nothing is
+ * left allocated then.
+ *
+ * dpslab_batch_solve solves every system. It forks the caller's stream into
+ * the batch's streams, enqueues each system's solve there, and joins them
+ * back. The first call with a given set of arguments (the n[i] and every
+ * pointer) captures this into a CUDA graph; later calls with the same
+ * arguments replay it (new values in the same buffers are fine). It returns
+ * when the batch is done.
+ *   n[count]; pos[count] ([n_i][3] device), q[count] ([n_i] device): the
+ *   inputs of system i, as dpslab_solve.
+ *   U[count]: host, may be NULL; phi, force: arrays of count device
+ *   pointers, may be NULL, and so may their entries (that output is skipped).
+ *   status[count]: host, may be NULL; the dpslab_solve code of each system.
+ * Returns DPSLAB_OK if every system succeeded, else the code of the first
+ * failing one. A batch is not thread-safe; one call at a time per batch.
+ */
+typedef struct dpslab_batch dpslab_batch;
+int dpslab_batch_create(const dpslab_params* params, const int64_t* max_n, int count, int nstreams,
+                        dpslab_batch** out);
+int dpslab_batch_solve(dpslab_batch* batch, const int64_t* n, const double* const* pos, const double* const* q,
+                       double* U, double* const* phi, double* const* force, int* status, void* stream);
+int64_t dpslab_batch_device_bytes(const dpslab_batch* batch);
+int dpslab_batch_destroy(dpslab_batch* batch);
+
+/*
  * Per-stage timing. With profiling on, every solve records CUDA events on its
  * stream around each stage; dpslab_stage_times writes the last solve's
  * stage durations in milliseconds (device time) to ms[0 .. DPSLAB_NSTAGES-1].

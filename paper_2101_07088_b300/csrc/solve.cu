@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -2212,7 +2213,9 @@ struct dpslab_plan {
     KP kp{};
     // allocations
     void* tables = nullptr;
-    void* work = nullptr;
+    void* work = nullptr;             // owned workspace (null when bound to a shared one)
+    size_t work_bytes = 0;            // size of the workspace this plan needs
+    size_t src_bytes = 0, scan_n = 0, rsz = 8;
     int64_t device_bytes = 0;
     double* d_pos = nullptr;    // staging for dpslab_solve_host
     double* d_q = nullptr;
@@ -2234,10 +2237,35 @@ int cuda_err(cudaError_t e) {
     return e == cudaSuccess ? DPSLAB_OK : DPSLAB_ERR_CUDA;
 }
 
-#define DPS_CUDA(call)                            \
-    do {                                          \
-        cudaError_t e_ = (call);                  \
-        if (e_ != cudaSuccess) return cuda_err(e_); \
+// The dynamic shared-memory cap of a kernel is a property of the kernel, not
+// of a plan: raise it to what this plan needs, never lower it (a plan created
+// later with smaller grids must not break an earlier one).
+void raise_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return;
+    if (size_t(fa.maxDynamicSharedSizeBytes) < bytes)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
+// DPSLAB_TRACE set in the environment: failing CUDA calls are reported on
+// stderr with the call and its line (the return codes carry no detail)
+bool trace_on() {
+    static const bool on = std::getenv("DPSLAB_TRACE") != nullptr;
+    return on;
+}
+void trace(const char* what, cudaError_t e, int line) {
+    if (trace_on()) std::fprintf(stderr, "dpslab: %s failed at solve.cu:%d: %s\n", what, line, cudaGetErrorString(e));
+}
+
+#define DPS_CUDA(call)                                \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            trace(#call, e_, __LINE__);               \
+            return cuda_err(e_);                      \
+        }                                             \
     } while (0)
 
 constexpr size_t align_up_c(size_t v) { return (v + 255) & ~size_t(255); }
@@ -2254,6 +2282,52 @@ int floor_pow2(int v) {
     int p = 1;
     while (p * 2 <= v) p *= 2;
     return p;
+}
+
+// Carve the plan's workspace from base (every per-solve device array: grids,
+// charge arrays, buckets, cell list, partial sums); with base == nullptr it
+// only measures. Returns the bytes used.
+size_t bind_work(dpslab_plan* pl, char* base) {
+    KP& kp = pl->kp;
+    const size_t n = size_t(pl->max_n), rsz = pl->rsz;
+    const size_t M = size_t(kp.ny) * kp.nxh;
+    char* cur = base;
+    kp.rho = carve<char>(cur, 2 * pl->G * rsz);
+    kp.spec = carve<char>(cur, 2 * pl->S * 2 * rsz);
+    kp.specB = carve<char>(cur, pl->S * 2 * rsz);
+    kp.fields = carve<char>(cur, pl->G * 4 * rsz);
+    kp.part = carve<double4_32a>(cur, n);
+    kp.far = carve<double4_32a>(cur, n);
+    kp.nearv = carve<double4_32a>(cur, n);
+    kp.cell_of = carve<int>(cur, n);
+    kp.sorted_idx = carve<int>(cur, n);
+    kp.sorted = carve<double4_32a>(cur, n);
+    kp.sorted_rel = carve<float4>(cur, n);
+    kp.irec = carve<IRec>(cur, n);
+    kp.srcs_tmp = kp.mixed ? carve<SrcF>(cur, 3 * n) : nullptr;
+    kp.colp = pl->ztensor ? carve<ColP>(cur, M) : nullptr;
+    kp.tile_count = carve<int>(cur, size_t(kp.nbuckets) + 1);
+    kp.tile_start = carve<int>(cur, size_t(kp.nbuckets) + 1);
+    kp.tile_fill = carve<int>(cur, size_t(kp.nbuckets) + 1);
+    kp.srcs = reinterpret_cast<SrcRec*>(carve<char>(cur, pl->src_bytes));
+    kp.srcsf = reinterpret_cast<SrcF*>(kp.srcs);
+    kp.cell_count = carve<int>(cur, size_t(kp.ncells) + 1);
+    kp.cell_start = carve<int>(cur, size_t(kp.ncells) + 1);
+    kp.cell_fill = carve<int>(cur, size_t(kp.ncells) + 1);
+    carve<int>(cur, size_t(kp.ncells));
+    kp.part_gauge_far = carve<double>(cur, kp.n_col_blocks);
+    kp.part_gauge_near = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
+    kp.part_u = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
+    kp.part_q = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
+    carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
+    kp.scal = carve<double>(cur, 16);
+    kp.status = carve<int>(cur, 16);
+    pl->scan_part = carve<int>(cur, pl->scan_n);
+    pl->d_pos = carve<double>(cur, 3 * n);
+    pl->d_force = carve<double>(cur, 3 * n);
+    pl->d_q = carve<double>(cur, n);
+    pl->d_phi = carve<double>(cur, n);
+    return size_t(cur - base);
 }
 
 void release(dpslab_plan* pl) {
@@ -2289,7 +2363,16 @@ extern "C" int dpslab_table(const dpslab_params* p, int which, double* out, int 
     return DPSLAB_OK;
 }
 
+namespace {
+int plan_create_impl(const dpslab_params* p, int64_t max_n, bool defer_work, dpslab_plan** out);
+}
+
 extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_plan** out) {
+    return plan_create_impl(p, max_n, false, out);
+}
+
+namespace {
+int plan_create_impl(const dpslab_params* p, int64_t max_n, bool defer_work, dpslab_plan** out) {
     if (!out) return DPSLAB_ERR_INVALID_ARG;
     *out = nullptr;
     if (!p || max_n < 1 || max_n > (int64_t(1) << 28)) return DPSLAB_ERR_INVALID_ARG;
@@ -2471,22 +2554,11 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         upc(t.twy, kp.twy32);
         if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
     }
-    // work space (one allocation)
+    // work space: sizes of the worst-case arrays, then one allocation (or,
+    // for plans of a batch, a workspace shared with the other plans of its
+    // stream, bound later)
     {
         const size_t n = size_t(max_n);
-        size_t bytes = 0;
-        bytes += align_up(2 * pl->G * rsz);                   // rho
-        bytes += align_up(2 * pl->S * 2 * rsz);               // spec
-        bytes += align_up(pl->S * 2 * rsz);                   // specB
-        bytes += align_up(pl->G * 4 * rsz);                   // fields
-        bytes += 3 * align_up(n * sizeof(double4_32a));           // part, far, nearv
-        bytes += 2 * align_up(n * sizeof(int));               // cell_of, sorted_idx
-        bytes += align_up(n * sizeof(double4_32a));               // sorted
-        bytes += align_up(n * sizeof(float4));                    // sorted_rel
-        bytes += align_up(n * sizeof(IRec));                      // irec
-        bytes += mixed ? align_up(3 * n * sizeof(SrcF)) : 0;      // srcs_tmp
-        bytes += pl->ztensor ? align_up(size_t(M) * sizeof(ColP)) : 0;   // colp
-        bytes += 3 * align_up((size_t(kp.nbuckets) + 1) * sizeof(int));   // bucket count/start/fill
         // source records, worst case. FP64: every source in every slab.
         // Mixed: a source is stored once per (tile, slab) block it touches.
         size_t src_bytes = size_t(3 * n) * size_t(kp.nslabs) * sizeof(SrcRec);
@@ -2506,54 +2578,16 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
             src_bytes = recs * sizeof(SrcF);
             kp.src_cap = recs;
         }
-        bytes += align_up(src_bytes);
-        bytes += 3 * align_up((size_t(kp.ncells) + 1) * sizeof(int));
-        bytes += align_up(size_t(kp.ncells) * sizeof(int));
-        bytes += align_up(size_t(kp.n_col_blocks) * sizeof(double));
-        bytes += 4 * align_up(size_t(kp.n_charge_blocks) * 2 * sizeof(double));
-        bytes += align_up(16 * sizeof(double)) + align_up(16 * sizeof(int));
-        const size_t scan_n = 2 * ((std::max<size_t>(kp.nbuckets, kp.ncells) + kScanChunk - 1) / kScanChunk + 1);
-        bytes += align_up(scan_n * sizeof(int));
-        bytes += align_up(n * 3 * sizeof(double)) * 2 + align_up(n * sizeof(double)) * 2;   // host-call staging
-        cudaError_t e = cudaMalloc(&pl->work, bytes);
-        if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
-        pl->device_bytes += int64_t(bytes);
-        char* cur = static_cast<char*>(pl->work);
-        kp.rho = carve<char>(cur, 2 * pl->G * rsz);
-        kp.spec = carve<char>(cur, 2 * pl->S * 2 * rsz);
-        kp.specB = carve<char>(cur, pl->S * 2 * rsz);
-        kp.fields = carve<char>(cur, pl->G * 4 * rsz);
-        kp.part = carve<double4_32a>(cur, n);
-        kp.far = carve<double4_32a>(cur, n);
-        kp.nearv = carve<double4_32a>(cur, n);
-        kp.cell_of = carve<int>(cur, n);
-        kp.sorted_idx = carve<int>(cur, n);
-        kp.sorted = carve<double4_32a>(cur, n);
-        kp.sorted_rel = carve<float4>(cur, n);
-        kp.irec = carve<IRec>(cur, n);
-        if (mixed) kp.srcs_tmp = carve<SrcF>(cur, 3 * n);
-        if (pl->ztensor) kp.colp = carve<ColP>(cur, size_t(M));
-        kp.tile_count = carve<int>(cur, size_t(kp.nbuckets) + 1);
-        kp.tile_start = carve<int>(cur, size_t(kp.nbuckets) + 1);
-        kp.tile_fill = carve<int>(cur, size_t(kp.nbuckets) + 1);
-        kp.srcs = reinterpret_cast<SrcRec*>(carve<char>(cur, src_bytes));
-        kp.srcsf = reinterpret_cast<SrcF*>(kp.srcs);
-        kp.cell_count = carve<int>(cur, size_t(kp.ncells) + 1);
-        kp.cell_start = carve<int>(cur, size_t(kp.ncells) + 1);
-        kp.cell_fill = carve<int>(cur, size_t(kp.ncells) + 1);
-        carve<int>(cur, size_t(kp.ncells));
-        kp.part_gauge_far = carve<double>(cur, kp.n_col_blocks);
-        kp.part_gauge_near = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
-        kp.part_u = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
-        kp.part_q = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
-        carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
-        kp.scal = carve<double>(cur, 16);
-        kp.status = carve<int>(cur, 16);
-        pl->scan_part = carve<int>(cur, scan_n);
-        pl->d_pos = carve<double>(cur, 3 * n);
-        pl->d_force = carve<double>(cur, 3 * n);
-        pl->d_q = carve<double>(cur, n);
-        pl->d_phi = carve<double>(cur, n);
+        pl->src_bytes = src_bytes;
+        pl->rsz = rsz;
+        pl->scan_n = 2 * ((std::max<size_t>(kp.nbuckets, kp.ncells) + kScanChunk - 1) / kScanChunk + 1);
+        pl->work_bytes = bind_work(pl, nullptr);
+        if (!defer_work) {
+            cudaError_t e = cudaMalloc(&pl->work, pl->work_bytes);
+            if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
+            pl->device_bytes += int64_t(pl->work_bytes);
+            bind_work(pl, static_cast<char*>(pl->work));
+        }
     }
     if (cudaMallocHost(&pl->h_scal, 16 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&pl->h_status, 16 * sizeof(int)) != cudaSuccess) {
@@ -2631,42 +2665,43 @@ extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_
         return DPSLAB_ERR_GRID;
     }
     if (mixed) {
-        cudaFuncSetAttribute(k_fftx_fwd_p2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
-        cudaFuncSetAttribute(k_ffty_fwd_p2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
-        cudaFuncSetAttribute(k_ffty_inv_p2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
-        cudaFuncSetAttribute(k_fftx_inv_p2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
-        cudaFuncSetAttribute(k_fftx_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
-        cudaFuncSetAttribute(k_ffty_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
-        cudaFuncSetAttribute(k_ffty_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
-        cudaFuncSetAttribute(k_fftx_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
+        raise_smem(reinterpret_cast<const void*>(k_fftx_fwd_p2<float>), size_t(pl->sm_fftx_fwd));
+        raise_smem(reinterpret_cast<const void*>(k_ffty_fwd_p2<float>), size_t(pl->sm_ffty_fwd));
+        raise_smem(reinterpret_cast<const void*>(k_ffty_inv_p2<float>), size_t(pl->sm_ffty_inv));
+        raise_smem(reinterpret_cast<const void*>(k_fftx_inv_p2<float>), size_t(pl->sm_fftx_inv));
+        raise_smem(reinterpret_cast<const void*>(k_fftx_fwd<float>), size_t(pl->sm_fftx_fwd));
+        raise_smem(reinterpret_cast<const void*>(k_ffty_fwd<float>), size_t(pl->sm_ffty_fwd));
+        raise_smem(reinterpret_cast<const void*>(k_ffty_inv<float>), size_t(pl->sm_ffty_inv));
+        raise_smem(reinterpret_cast<const void*>(k_fftx_inv<float>), size_t(pl->sm_fftx_inv));
         if (pl->ztensor) {
-            cudaFuncSetAttribute(k_zgemm_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kZSmem));
-            cudaFuncSetAttribute(k_zgemm_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kZSmem));
+            raise_smem(reinterpret_cast<const void*>(k_zgemm_fwd), size_t(kZSmem));
+            raise_smem(reinterpret_cast<const void*>(k_zgemm_inv), size_t(kZSmem));
             int nsm = 0;
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->device);
             const int ntiles = 2 * int((2 * size_t(M) + kZN - 1) / kZN);   // both planes
             pl->zgrid = std::max(1, std::min(ntiles, nsm));
         }
-        cudaFuncSetAttribute(k_column_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
-        cudaFuncSetAttribute(k_column_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
-        cudaFuncSetAttribute(k_interp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
+        raise_smem(reinterpret_cast<const void*>(k_column_mixed<false>), size_t(pl->sm_col));
+        raise_smem(reinterpret_cast<const void*>(k_column_mixed<true>), size_t(pl->sm_col));
+        raise_smem(reinterpret_cast<const void*>(k_interp_f32), size_t(pl->sm_interp));
     } else {
-        cudaFuncSetAttribute(k_fftx_fwd_p2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
-        cudaFuncSetAttribute(k_ffty_fwd_p2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
-        cudaFuncSetAttribute(k_ffty_inv_p2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
-        cudaFuncSetAttribute(k_fftx_inv_p2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
-        cudaFuncSetAttribute(k_fftx_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_fwd));
-        cudaFuncSetAttribute(k_ffty_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_fwd));
-        cudaFuncSetAttribute(k_ffty_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_ffty_inv));
-        cudaFuncSetAttribute(k_fftx_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_fftx_inv));
-        cudaFuncSetAttribute(k_column, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_col));
-        cudaFuncSetAttribute(k_interp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_interp));
-        cudaFuncSetAttribute(k_spread_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl->sm_spread));
+        raise_smem(reinterpret_cast<const void*>(k_fftx_fwd_p2<double>), size_t(pl->sm_fftx_fwd));
+        raise_smem(reinterpret_cast<const void*>(k_ffty_fwd_p2<double>), size_t(pl->sm_ffty_fwd));
+        raise_smem(reinterpret_cast<const void*>(k_ffty_inv_p2<double>), size_t(pl->sm_ffty_inv));
+        raise_smem(reinterpret_cast<const void*>(k_fftx_inv_p2<double>), size_t(pl->sm_fftx_inv));
+        raise_smem(reinterpret_cast<const void*>(k_fftx_fwd<double>), size_t(pl->sm_fftx_fwd));
+        raise_smem(reinterpret_cast<const void*>(k_ffty_fwd<double>), size_t(pl->sm_ffty_fwd));
+        raise_smem(reinterpret_cast<const void*>(k_ffty_inv<double>), size_t(pl->sm_ffty_inv));
+        raise_smem(reinterpret_cast<const void*>(k_fftx_inv<double>), size_t(pl->sm_fftx_inv));
+        raise_smem(reinterpret_cast<const void*>(k_column), size_t(pl->sm_col));
+        raise_smem(reinterpret_cast<const void*>(k_interp<double>), size_t(pl->sm_interp));
+        raise_smem(reinterpret_cast<const void*>(k_spread_tiled<double>), size_t(pl->sm_spread));
     }
     if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
     *out = pl;
     return DPSLAB_OK;
 }
+}  // namespace
 
 extern "C" int dpslab_plan_derived(const dpslab_plan* plan, dpslab_derived* out) {
     if (!plan || !out) return DPSLAB_ERR_INVALID_ARG;
@@ -2746,7 +2781,11 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     do {                                             \
         __VA_ARGS__;                                 \
         ++launches;                                  \
-        if (cudaGetLastError() != cudaSuccess) return DPSLAB_ERR_CUDA; \
+        const cudaError_t le_ = cudaGetLastError();  \
+        if (le_ != cudaSuccess) {                    \
+            trace(#__VA_ARGS__, le_, __LINE__);      \
+            return DPSLAB_ERR_CUDA;                  \
+        }                                            \
     } while (0)
     // exclusive scan count[0..m) -> start[0..m] (m >= 1)
     auto scan = [&](const int* count, int* start, int m) -> int {
@@ -2860,6 +2899,17 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     return DPSLAB_OK;
 }
 
+// the result of a completed solve: U and the status bits copied back
+int collect(dpslab_plan* pl, double* U) {
+    if (U) *U = pl->h_scal[4];
+    if (*pl->h_status & kStatusCapacity) return DPSLAB_ERR_CAPACITY;
+    if (*pl->h_status & kStatusTimeout) return DPSLAB_ERR_CUDA;
+    if (*pl->h_status) return DPSLAB_ERR_OUT_OF_SLAB;
+    const double sq = pl->h_scal[5], saq = pl->h_scal[6];
+    if (std::fabs(sq) > 1e-12 * saq) return DPSLAB_ERR_NOT_NEUTRAL;
+    return DPSLAB_OK;
+}
+
 int finish(dpslab_plan* pl, cudaStream_t st, double* U) {
     DPS_CUDA(cudaStreamSynchronize(st));
     if (pl->profiling) {
@@ -2869,13 +2919,7 @@ int finish(dpslab_plan* pl, cudaStream_t st, double* U) {
             pl->stage_ms[i] = ms;
         }
     }
-    if (U) *U = pl->h_scal[4];
-    if (*pl->h_status & kStatusCapacity) return DPSLAB_ERR_CAPACITY;
-    if (*pl->h_status & kStatusTimeout) return DPSLAB_ERR_CUDA;
-    if (*pl->h_status) return DPSLAB_ERR_OUT_OF_SLAB;
-    const double sq = pl->h_scal[5], saq = pl->h_scal[6];
-    if (std::fabs(sq) > 1e-12 * saq) return DPSLAB_ERR_NOT_NEUTRAL;
-    return DPSLAB_OK;
+    return collect(pl, U);
 }
 
 }  // namespace
@@ -3056,4 +3100,170 @@ extern "C" int dpslab_near_field_static(const dpslab_params* p, int64_t n, const
     DPS_CUDA(cudaMemcpyAsync(&status, kp.status, sizeof(int), cudaMemcpyDeviceToHost, st));
     DPS_CUDA(cudaStreamSynchronize(st));
     return status ? DPSLAB_ERR_OUT_OF_SLAB : DPSLAB_OK;
+}
+
+// ===========================================================================
+// batches of independent systems
+// ===========================================================================
+struct dpslab_batch {
+    int device = 0;
+    std::vector<dpslab_plan*> plans;
+    std::vector<cudaStream_t> streams;
+    std::vector<void*> work;               // one shared workspace per stream
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    // the graph is captured and launched on `head` (the caller's stream may be
+    // the legacy default stream, which cannot be captured), ordered after the
+    // caller's prior work (`in`) and before its later work (`out`)
+    cudaStream_t head = nullptr;
+    cudaEvent_t in = nullptr, out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> g_n;              // arguments the graph was captured with
+    std::vector<const void*> g_ptr;
+    int64_t device_bytes = 0;
+};
+
+namespace {
+void batch_release(dpslab_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto* pl : b->plans) release(pl);
+    for (void* w : b->work)
+        if (w) cudaFree(w);
+    for (auto st : b->streams) cudaStreamDestroy(st);
+    for (auto e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->head) cudaStreamDestroy(b->head);
+    if (b->in) cudaEventDestroy(b->in);
+    if (b->out) cudaEventDestroy(b->out);
+    delete b;
+}
+}  // namespace
+
+extern "C" int dpslab_batch_create(const dpslab_params* params, const int64_t* max_n, int count, int nstreams,
+                                   dpslab_batch** out) {
+    if (!params || !max_n || !out || count < 1 || nstreams < 1) return DPSLAB_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return DPSLAB_ERR_NO_DEVICE;
+    auto* b = new (std::nothrow) dpslab_batch;
+    if (!b) return DPSLAB_ERR_CUDA;
+    cudaGetDevice(&b->device);
+    const int S = std::min(nstreams, count);
+    for (int i = 0; i < count; ++i) {
+        dpslab_plan* pl = nullptr;
+        const int rc = plan_create_impl(&params[i], max_n[i], true, &pl);
+        if (rc) { batch_release(b); return rc; }
+        b->plans.push_back(pl);
+        b->device_bytes += pl->device_bytes;
+    }
+    b->work.assign(S, nullptr);
+    for (int s = 0; s < S; ++s) {
+        size_t need = 0;
+        for (int i = s; i < count; i += S) need = std::max(need, b->plans[i]->work_bytes);
+        if (cudaMalloc(&b->work[s], need) != cudaSuccess) { batch_release(b); return DPSLAB_ERR_CUDA; }
+        b->device_bytes += int64_t(need);
+        for (int i = s; i < count; i += S) bind_work(b->plans[i], static_cast<char*>(b->work[s]));
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { batch_release(b); return DPSLAB_ERR_CUDA; }
+        b->streams.push_back(st);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { batch_release(b); return DPSLAB_ERR_CUDA; }
+        b->joins.push_back(ev);
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->head, cudaStreamNonBlocking) != cudaSuccess) {
+        batch_release(b);
+        return DPSLAB_ERR_CUDA;
+    }
+    *out = b;
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_batch_solve(dpslab_batch* b, const int64_t* n, const double* const* pos, const double* const* q,
+                                  double* U, double* const* phi, double* const* force, int* status, void* stream) {
+    if (!b || !n || !pos || !q) return DPSLAB_ERR_INVALID_ARG;
+    const int count = int(b->plans.size()), S = int(b->streams.size());
+    std::vector<const void*> ptr;
+    ptr.reserve(4 * size_t(count));
+    for (int i = 0; i < count; ++i) {
+        if (!pos[i] || !q[i] || n[i] < 1) return DPSLAB_ERR_INVALID_ARG;
+        if (n[i] > b->plans[i]->max_n) return DPSLAB_ERR_CAPACITY;
+        ptr.push_back(pos[i]);
+        ptr.push_back(q[i]);
+        ptr.push_back(phi ? phi[i] : nullptr);
+        ptr.push_back(force ? force[i] : nullptr);
+    }
+    DPS_CUDA(cudaSetDevice(b->device));
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    cudaStream_t st = b->head;
+    DPS_CUDA(cudaEventRecord(b->in, caller));
+    DPS_CUDA(cudaStreamWaitEvent(st, b->in, 0));
+    const bool same = b->exec && b->g_ptr == ptr && int(b->g_n.size()) == count &&
+                      std::equal(b->g_n.begin(), b->g_n.end(), n);
+    if (!same) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        DPS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = DPSLAB_OK;
+        if (cudaEventRecord(b->fork, st) != cudaSuccess) rc = DPSLAB_ERR_CUDA;
+        for (int s = 0; s < S && !rc; ++s)
+            if (cudaStreamWaitEvent(b->streams[s], b->fork, 0) != cudaSuccess) rc = DPSLAB_ERR_CUDA;
+        for (int i = 0; i < count && !rc; ++i) {
+            dpslab_plan* pl = b->plans[i];
+            pl->profiling = 0;
+            rc = enqueue(pl, n[i], pos[i], q[i], phi ? phi[i] : nullptr, force ? force[i] : nullptr, b->streams[i % S]);
+            pl->last_n = n[i];
+        }
+        for (int s = 0; s < S && !rc; ++s) {
+            if (cudaEventRecord(b->joins[s], b->streams[s]) != cudaSuccess ||
+                cudaStreamWaitEvent(st, b->joins[s], 0) != cudaSuccess)
+                rc = DPSLAB_ERR_CUDA;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (e != cudaSuccess) trace("cudaStreamEndCapture", e, __LINE__);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc ? rc : DPSLAB_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&b->exec, g, 0);
+        if (ie != cudaSuccess) {
+            trace("cudaGraphInstantiate", ie, __LINE__);
+            cudaGraphDestroy(g);
+            b->exec = nullptr;
+            return DPSLAB_ERR_CUDA;
+        }
+        b->graph = g;
+        b->g_ptr = ptr;
+        b->g_n.assign(n, n + count);
+    }
+    DPS_CUDA(cudaGraphLaunch(b->exec, st));
+    DPS_CUDA(cudaEventRecord(b->out, st));
+    DPS_CUDA(cudaStreamWaitEvent(caller, b->out, 0));
+    DPS_CUDA(cudaStreamSynchronize(st));
+    int first = DPSLAB_OK;
+    for (int i = 0; i < count; ++i) {
+        const int rc = collect(b->plans[i], U ? &U[i] : nullptr);
+        if (rc && trace_on()) std::fprintf(stderr, "dpslab: batch system %d: code %d, status bits %d\n", i, rc, *b->plans[i]->h_status);
+        if (status) status[i] = rc;
+        if (rc && !first) first = rc;
+    }
+    return first;
+}
+
+extern "C" int64_t dpslab_batch_device_bytes(const dpslab_batch* b) { return b ? b->device_bytes : 0; }
+
+extern "C" int dpslab_batch_destroy(dpslab_batch* b) {
+    if (!b) return DPSLAB_ERR_INVALID_ARG;
+    cudaSetDevice(b->device);
+    batch_release(b);
+    return DPSLAB_OK;
 }

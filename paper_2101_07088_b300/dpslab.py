@@ -19,6 +19,8 @@ ERRORS = {
     -1: "INVALID_ARG", -2: "NOT_NEUTRAL", -3: "OUT_OF_SLAB", -4: "CUTOFF_TOO_LARGE",
     -5: "SPLIT_CONSTRAINT", -6: "CAPACITY", -7: "CUDA", -8: "NO_DEVICE", -9: "GRID", -10: "UNSUPPORTED",
 }
+(ERR_INVALID_ARG, ERR_NOT_NEUTRAL, ERR_OUT_OF_SLAB, ERR_CUTOFF_TOO_LARGE, ERR_SPLIT_CONSTRAINT, ERR_CAPACITY,
+ ERR_CUDA, ERR_NO_DEVICE, ERR_GRID, ERR_UNSUPPORTED) = range(-1, -11, -1)
 FP64, MIXED, MIXED_SIMT = 0, 1, 2   # DPSLAB_FP64, DPSLAB_MIXED, DPSLAB_MIXED_SIMT
 NSTAGES = 12
 
@@ -73,6 +75,13 @@ def lib():
             "dpslab_last_launch_count": (ctypes.c_int, [vp]),
             "dpslab_plan_destroy": (ctypes.c_int, [vp]),
             "dpslab_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "dpslab_batch_create": (ctypes.c_int, [P, ctypes.POINTER(i64), ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(vp)]),
+            "dpslab_batch_solve": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp), dp,
+                                                  ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                  ctypes.POINTER(ctypes.c_int), vp]),
+            "dpslab_batch_device_bytes": (i64, [vp]),
+            "dpslab_batch_destroy": (ctypes.c_int, [vp]),
             "dpslab_profile": (ctypes.c_int, [vp, ctypes.c_int]),
             "dpslab_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
             "dpslab_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
@@ -213,3 +222,53 @@ class Plan:
         ms = (ctypes.c_double * NSTAGES)()
         _check(lib().dpslab_stage_times(self._h, ms, NSTAGES))
         return {lib().dpslab_stage_name(i).decode(): ms[i] for i in range(NSTAGES)}
+
+
+class Batch:
+    """dpslab_batch_create / dpslab_batch_solve / dpslab_batch_destroy: many
+    independent systems solved by one call (one CUDA graph, replayed while
+    the buffers stay the same)."""
+
+    def __init__(self, params_list, max_n_list, nstreams=8):
+        self.count = len(params_list)
+        self._params = (Params * self.count)(*[_as_params(p) for p in params_list])
+        mx = (ctypes.c_int64 * self.count)(*[int(v) for v in max_n_list])
+        h = ctypes.c_void_p()
+        _check(lib().dpslab_batch_create(self._params, mx, self.count, int(nstreams), ctypes.byref(h)))
+        self._h = h
+        self.device_bytes = lib().dpslab_batch_device_bytes(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dpslab_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, pos, q, phi=None, force=None, stream=None, check=True):
+        """pos, q: lists of float64 contiguous CUDA tensors ([n_i, 3], [n_i]);
+        phi, force: lists of output tensors (or None). Returns (U [count],
+        status [count]) as numpy arrays."""
+        import torch
+        c = self.count
+        vp = ctypes.c_void_p
+        for t in list(pos) + list(q):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("pos and q must be contiguous float64 CUDA tensors")
+        n = (ctypes.c_int64 * c)(*[int(t.shape[0]) for t in q])
+        P = (vp * c)(*[t.data_ptr() for t in pos])
+        Q = (vp * c)(*[t.data_ptr() for t in q])
+        PH = (vp * c)(*[t.data_ptr() if t is not None else None for t in phi]) if phi is not None else None
+        FO = (vp * c)(*[t.data_ptr() if t is not None else None for t in force]) if force is not None else None
+        U = np.zeros(c)
+        status = np.zeros(c, dtype=np.int32)
+        st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc = lib().dpslab_batch_solve(self._h, n, P, Q, U.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), PH, FO,
+                                      status.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), st)
+        if check:
+            _check(rc)
+        return U, status

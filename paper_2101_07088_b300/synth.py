@@ -7,6 +7,8 @@ charges -1 assigned by a random permutation, positions uniform in
 depends on the solver. Both the CUDA path's tests and the oracle's take
 their inputs from this module.
 """
+import math
+
 import numpy as np
 
 
@@ -50,3 +52,40 @@ def workload(name):
     params = dict(Lx=w["Lx"], Ly=w["Ly"], H=w["H"], eps=1.0, eps_b=w["eps_b"], eps_t=w["eps_t"],
                   gw=1.0, tol=1e-4, nx=w["nx"], ny=w["ny"], nz=w["nz"], r_cut=4.0)
     return pos, q, params
+
+
+def smooth7(v):
+    """Smallest integer >= v whose prime factors are 2, 3, 5, 7."""
+    v = max(1, int(math.ceil(v)))
+    while True:
+        r = v
+        for f in (2, 3, 5, 7):
+            while r % f == 0:
+                r //= f
+        if r == 1:
+            return v
+        v += 1
+
+
+def batch_systems(count, seed, n_range=(256, 65536), l_range=(32.0, 256.0), h_range=(16.0, 128.0),
+                  ratios=(1.0 / 80.0, 1.0, math.inf), h=0.5, gw=1.0, tol=1e-4, r_cut=4.0):
+    """Independent slab systems of the batched workload: N log-uniform in
+    n_range (even), Lx = Ly log-uniform in l_range, H uniform in h_range, each
+    wall's eps_w/eps drawn from `ratios`, grid spacing h (2 points per width
+    at g_w = 1; nx rounded up to a 7-smooth size and Lx = nx h), N_z from the
+    paper's rule (0 here). Returns a list of (pos, q, params) with the same
+    params keys as workload(); system i uses seed + i for its charges."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))) // 2 * 2)
+        L = math.exp(rng.uniform(math.log(l_range[0]), math.log(l_range[1])))
+        H = float(rng.uniform(*h_range))
+        eb, et = (float(ratios[j]) for j in rng.integers(0, len(ratios), 2))
+        nx = smooth7(L / h)
+        L = nx * h
+        pos, q = electrolyte(n, L, L, 1.0, H - 1.0, seed + i)
+        params = dict(Lx=L, Ly=L, H=H, eps=1.0, eps_b=eb, eps_t=et, gw=gw, tol=tol, nx=nx, ny=nx, nz=0,
+                      r_cut=r_cut)
+        out.append((pos, q, params))
+    return out

@@ -1,0 +1,93 @@
+"""Batches of independent systems (dpslab_batch_*): every system's result in
+the batch equals its result alone (the same kernels; only the order of
+floating-point additions inside the spreading buckets may differ), also when
+the captured graph is replayed with new values in the same buffers, and a
+bad system reports its own status without affecting the others."""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL_MIXED_ENERGY, TOL_MIXED_FORCE, rel_l2
+from paper_2101_07088_b300 import build, dpslab, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def _systems(count, seed):
+    # the batched workload's recipe at small sizes (N_z from the paper's rule)
+    return synth.batch_systems(count, seed, n_range=(64, 2048), l_range=(16.0, 40.0), h_range=(12.0, 30.0))
+
+
+def _tensors(pos, q):
+    dev = torch.device("cuda:0")
+    return (torch.tensor(pos, dtype=torch.float64, device=dev), torch.tensor(q, dtype=torch.float64, device=dev),
+            torch.empty(len(q), dtype=torch.float64, device=dev),
+            torch.empty((len(q), 3), dtype=torch.float64, device=dev))
+
+
+def _alone(pos, q, p, prec):
+    plan = dpslab.Plan(dpslab.make_params(precision=prec, **p), len(q))
+    pt, qt, phi, f = _tensors(pos, q)
+    U, _ = plan.solve(pt, qt, phi, f)
+    plan.close()
+    return U, phi.cpu().numpy(), f.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec,ftol,utol", [(dpslab.FP64, 1e-12, 1e-12), (dpslab.MIXED, TOL_MIXED_FORCE, TOL_MIXED_ENERGY)],
+                         ids=["fp64", "mixed"])
+def test_batch_equals_alone_and_replays(prec, ftol, utol):
+    systems = _systems(7, 11)
+    params = [dpslab.make_params(precision=prec, **p) for _, _, p in systems]
+    batch = dpslab.Batch(params, [len(q) for _, q, _ in systems], nstreams=3)
+    bufs = [_tensors(pos, q) for pos, q, _ in systems]
+    for rnd in range(2):
+        if rnd == 1:
+            # new charges in the same buffers: the captured graph is replayed
+            systems = [(synth.electrolyte(len(q), p["Lx"], p["Ly"], 1.0, p["H"] - 1.0, 100 + i)[0], q, p)
+                       for i, (_, q, p) in enumerate(systems)]
+            for (pos, _, _), (pt, _, _, _) in zip(systems, bufs):
+                pt.copy_(torch.tensor(pos, dtype=torch.float64))
+        U, status = batch.solve([b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs],
+                                [b[3] for b in bufs])
+        assert (status == 0).all(), status
+        for i, (pos, q, p) in enumerate(systems):
+            U1, phi1, f1 = _alone(pos, q, p, prec)
+            assert abs(U[i] - U1) <= utol * abs(U1), (rnd, i, U[i], U1)
+            assert rel_l2(bufs[i][3].cpu().numpy(), f1) <= ftol, (rnd, i)
+            assert np.max(np.abs(bufs[i][2].cpu().numpy() - phi1)) <= max(ftol, 1e-6) * np.max(np.abs(phi1)), (rnd, i)
+    batch.close()
+
+
+def test_batch_reports_each_systems_status():
+    systems = _systems(3, 5)
+    params = [dpslab.make_params(precision=dpslab.MIXED, **p) for _, _, p in systems]
+    batch = dpslab.Batch(params, [len(q) for _, q, _ in systems], nstreams=2)
+    bufs = [_tensors(pos, q) for pos, q, _ in systems]
+    bufs[1][0][0, 2] = -1.0                       # system 1: a charge below the slab
+    U, status = batch.solve([b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs],
+                            [b[3] for b in bufs], check=False)
+    assert status[0] == dpslab.OK and status[2] == dpslab.OK
+    assert status[1] == dpslab.ERR_OUT_OF_SLAB, status
+    assert np.isfinite(U[0]) and np.isfinite(U[2])
+    batch.close()
+
+
+def test_batch_shares_workspaces_by_stream():
+    systems = _systems(8, 7)
+    params = [dpslab.make_params(precision=dpslab.MIXED, **p) for _, _, p in systems]
+    mx = [len(q) for _, q, _ in systems]
+    one = sum(dpslab.Plan(pp, m).device_bytes for pp, m in zip(params, mx))
+    b2 = dpslab.Batch(params, mx, nstreams=2)
+    b8 = dpslab.Batch(params, mx, nstreams=8)
+    # two shared workspaces need less than eight, and eight (one per system)
+    # need about what eight separate plans do
+    assert b2.device_bytes < b8.device_bytes <= one * 1.01 + 1
+    b2.close()
+    b8.close()
