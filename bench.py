@@ -230,8 +230,80 @@ def cpu_model():
 
 
 # ---------------------------------------------------------------------------
+BATCH_WORKLOADS = {"c4_batch256": dict(count=256, seed=3, nstreams=8)}
+
+
+def bench_batch(args):
+    """The batched workload: 256 independent systems (N log-uniform in
+    [256, 65536], L in [32, 256], H in [16, 128], walls from {1/80, 1, metal},
+    2 grid points per width, N_z from the paper's rule) solved by one
+    dpslab_batch_solve call (a replayed CUDA graph). Reports total charges/s
+    of the mixed form, the FP64 batch beside it, and the same mixed plans
+    solved one system after another (no graph, one stream)."""
+    import numpy as np
+    import torch
+    from paper_2101_07088_b300 import build, dpslab, synth
+    cfg = BATCH_WORKLOADS[args.workload]
+    build.build()
+    dev = torch.device("cuda:0")
+    systems = synth.batch_systems(cfg["count"], cfg["seed"])
+    total = sum(len(q) for _, q, _ in systems)
+    bufs = [(torch.tensor(pos, dtype=torch.float64, device=dev), torch.tensor(q, dtype=torch.float64, device=dev),
+             torch.empty(len(q), dtype=torch.float64, device=dev),
+             torch.empty((len(q), 3), dtype=torch.float64, device=dev)) for pos, q, _ in systems]
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    out = {}
+    for name, prec in (("mixed", dpslab.MIXED), ("fp64", dpslab.FP64)):
+        params = [dpslab.make_params(precision=prec, **p) for _, _, p in systems]
+        batch = dpslab.Batch(params, [len(q) for _, q, _ in systems], nstreams=cfg["nstreams"])
+        args_ = ([b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs], [b[3] for b in bufs])
+        ms = timed(lambda: batch.solve(*args_), max(1, args.steps), max(3, args.warmup))
+        U, _ = batch.solve(*args_)
+        out[name] = dict(ms=ms, U=U.copy(), bytes=batch.device_bytes)
+        batch.close()
+    # the mixed plans one after another (no graph, no concurrency)
+    plans = [dpslab.Plan(dpslab.make_params(precision=dpslab.MIXED, **p), len(q)) for _, q, p in systems]
+    seq = timed(lambda: [pl.solve(b[0], b[1], b[2], b[3]) for pl, b in zip(plans, bufs)], 3, 1)
+    for pl in plans:
+        pl.close()
+    ms = sorted(out["mixed"]["ms"])
+    mean = sum(ms) / len(ms)
+    f64 = sum(out["fp64"]["ms"]) / len(out["fp64"]["ms"])
+    uerr = float(np.max(np.abs(out["mixed"]["U"] - out["fp64"]["U"]) / np.abs(out["fp64"]["U"])))
+    line = dict(metric=METRIC, value=total / (mean * 1e-3), unit=UNIT, n_gpus=1, steps=len(ms),
+                warmup=max(3, args.warmup), ms_per_step=mean, p50_ms=ms[len(ms) // 2],
+                p99_ms=ms[min(len(ms) - 1, int(math.ceil(0.99 * len(ms))) - 1)], higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32+f64", data="synthetic (seeded +-1 electrolytes)",
+                config=dict(workload=args.workload, systems=cfg["count"], charges=total, streams=cfg["nstreams"],
+                            form="one dpslab_batch_solve call (CUDA graph replay)",
+                            l2="512 MiB memset between timed steps"),
+                fp64_value=total / (f64 * 1e-3), fp64_ms_per_step=f64,
+                mixed_over_fp64=f64 / mean, sequential_ms_per_step=sum(seq) / len(seq),
+                max_energy_rel_vs_fp64=uerr, device_bytes=dict(mixed=out["mixed"]["bytes"], fp64=out["fp64"]["bytes"]))
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload in BATCH_WORKLOADS:
+        return bench_batch(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
