@@ -113,6 +113,7 @@ struct KP {
     const float2* twy32;
     // float copies of the column tables (mixed precision)
     const float* zn32;        // z_j rounded to float
+    const float* hinv32;      // 1/(2n), n >= 1 (integration recurrence)
     const float* znlo32;      // z_j - zn32[j] (z_j as a float pair)
     const float* wzh32;       // Clenshaw-Curtis weight times h_x h_y
     const float *cft32, *tie32, *tio32, *j2l32, *j2d32, *j2u32, *u132, *u232, *v132, *v232, *t032, *tH32, *wg32;

@@ -1450,38 +1450,36 @@ __global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
         }
     }
     __syncthreads();
-    // (field, column) pairs over the warps, n over the lanes
-    const int warp_id = tid >> 5, lane_id = tid & 31, nwarps = bs >> 5;
-    for (int fc = warp_id; fc < 2 * CB; fc += nwarps) {
-        const int f = fc / CB, c = fc % CB;
-        float2* X = (f ? Co : Ci) + c * NP;
-        const float2 mc = s_c[f][c], md = s_d[f][c];
-        for (int n = lane_id; n < N; n += 32) X[n] = cadd(X[n], cscale((n & 1) ? md : mc, xe[c * NP + n]));
-    }
-    __syncthreads();
-    for (int fc = warp_id; fc < 2 * CB; fc += nwarps) {
-        const int f = fc / CB, c = fc % CB;
-        const float2* Y = (f ? Co : Ci) + c * NP;
-        float2* V = (f ? Vo : Vi) + c * NP;
-        for (int n = lane_id; n < N; n += 32) {
-            float2 v;
-            if (n == 0) v = s_d[f][c];
-            else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
-            else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
-            V[n] = v;
-        }
-    }
-    __syncthreads();
-    for (int fc = warp_id; fc < 2 * CB; fc += nwarps) {
-        const int f = fc / CB, c = fc % CB;
-        const float2* Y = (f ? Vo : Vi) + c * NP;
-        float2* X = (f ? Co : Ci) + c * NP;
-        for (int n = lane_id; n < N; n += 32) {
-            float2 v;
-            if (n == 0) v = s_c[f][c];
-            else if (n == 1) v = csub(Y[0], cscale(Y[2], 0.5f));
-            else v = cscale(csub(Y[n - 1], n + 1 < N ? Y[n + 1] : make_float2(0.f, 0.f)), 0.5f / n);
-            X[n] = v;
+    // (field, column) pairs over the warps, n over the lanes; the three
+    // passes of a pair depend only on that pair's arrays, so a warp runs them
+    // back to back (warp barriers only): X += (c or d) xe gives y'', then
+    // y' = J y'' + d e0 and y = J y' + c e0 (Appendix A integration:
+    // entry n of J v is (v_{n-1} - v_{n+1})/(2n), entry 1 is v_0 - v_2/2)
+    {
+        const int warp_id = tid >> 5, lane_id = tid & 31, nwarps = bs >> 5;
+        for (int fc = warp_id; fc < 2 * CB; fc += nwarps) {
+            const int f = fc / CB, c = fc % CB;
+            float2* X = (f ? Co : Ci) + c * NP;
+            float2* V = (f ? Vo : Vi) + c * NP;
+            const float2 mc = s_c[f][c], md = s_d[f][c];
+            for (int n = lane_id; n < N; n += 32) X[n] = cadd(X[n], cscale((n & 1) ? md : mc, xe[c * NP + n]));
+            __syncwarp();
+            for (int n = lane_id; n < N; n += 32) {
+                float2 v;
+                if (n == 0) v = md;
+                else if (n == 1) v = csub(X[0], cscale(X[2], 0.5f));
+                else v = cscale(csub(X[n - 1], n + 1 < N ? X[n + 1] : make_float2(0.f, 0.f)), kp.hinv32[n]);
+                V[n] = v;
+            }
+            __syncwarp();
+            for (int n = lane_id; n < N; n += 32) {
+                float2 v;
+                if (n == 0) v = mc;
+                else if (n == 1) v = csub(V[0], cscale(V[2], 0.5f));
+                else v = cscale(csub(V[n - 1], n + 1 < N ? V[n + 1] : make_float2(0.f, 0.f)), kp.hinv32[n]);
+                X[n] = v;
+            }
+            __syncwarp();
         }
     }
     __syncthreads();
@@ -2492,8 +2490,8 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, bool defer_work, dps
         const size_t vec = align_up(N * sizeof(double));
         bytes += 2 * vec + 4 * align_up(N * N * sizeof(double)) + 11 * vec;
         bytes += align_up(nx * sizeof(double2)) + align_up(ny * sizeof(double2));
-        // float copies: cft, tie, tio (together <= 2 N^2) and 13 vectors
-        bytes += 3 * align_up(N * N * sizeof(float)) + 13 * align_up(N * sizeof(float));
+        // float copies: cft, tie, tio (together <= 2 N^2) and 14 vectors
+        bytes += 3 * align_up(N * N * sizeof(float)) + 14 * align_up(N * sizeof(float));
         if (pl->ztensor) bytes += 2 * align_up(t.zimg_fwd.size() * sizeof(unsigned short));   // bf16 images
         bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
         cudaError_t e = cudaMalloc(&pl->tables, bytes);
@@ -2523,6 +2521,11 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, bool defer_work, dps
             dst = dp;
         };
         upf(t.zn, kp.zn32);
+        {
+            std::vector<double> hinv(t.zn.size(), 0.0);
+            for (size_t j = 1; j < hinv.size(); ++j) hinv[j] = 0.5 / double(j);
+            upf(hinv, kp.hinv32);
+        }
         if (pl->ztensor) {
             auto upimg = [&](const std::vector<unsigned short>& v, const unsigned short*& dst) {
                 unsigned short* dp = carve<unsigned short>(cur, v.size());
