@@ -1243,7 +1243,7 @@ constexpr int kColThreadsM = 32 * kColBlockM;
 // the coefficients of psi_i and dpsi_i/dz and each mode's correction
 // parameters, instead of transforming itself.
 template <bool kTensor>
-__global__ void __launch_bounds__(kColThreadsM) k_column_mixed(KP kp) {
+__global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(KP kp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int CB = kColBlockM;
     const int N = kp.nz;
