@@ -300,10 +300,114 @@ def bench_batch(args):
     return 0
 
 
+SERVE_WORKLOADS = {"c5_serve1000": dict(replicas=1000, seed=4, rate=20000.0, per_step=100, nstreams=8,
+                                         budget_frac=0.6)}
+
+
+def bench_serve(args):
+    """The served workload: 1000 Brownian-dynamics replicas (N log-uniform in
+    [512, 262144], H in [16, 128], both walls at 1/80, the charge density of
+    the 2^20-charge workload, 2 grid points per width, N_z from the paper's
+    rule), requests for uniformly drawn replicas arriving as a Poisson stream
+    of 20,000 per second (far above what one device serves: the run is in
+    overload and shows queueing and admission). Replica plans are registered
+    up front; workspaces are admitted under a budget of 60% of the free
+    device memory. `warmup` x 100 requests are served first (filling the
+    resident set), then `steps` x 100 requests are timed. Reports charges/s,
+    p50/p99 latency (arrival to completion) and service time (start to
+    completion), admission counters, and the first 100 timed requests solved
+    one after another on one stream for comparison."""
+    os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
+    import numpy as np
+    import torch
+    from paper_2101_07088_b300 import build, dpslab, synth
+    from paper_2101_07088_b300.serve import Request, Server, latency_stats
+    cfg = SERVE_WORKLOADS[args.workload]
+    build.build()
+    dev = torch.device("cuda:0")
+    reps = synth.serve_replicas(cfg["replicas"], cfg["seed"])
+    # one input set per replica (a replica has one solve in flight at a time)
+    bufs = []
+    for i, r in enumerate(reps):
+        pos, q = synth.electrolyte(r["n"], r["Lx"], r["Ly"], 1.0, r["H"] - 1.0, cfg["seed"] + 1 + i)
+        bufs.append((torch.tensor(pos, dtype=torch.float64, device=dev), torch.tensor(q, dtype=torch.float64, device=dev),
+                     torch.empty(r["n"], dtype=torch.float64, device=dev),
+                     torch.empty((r["n"], 3), dtype=torch.float64, device=dev)))
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(cfg["budget_frac"] * free)
+    prec = {"fp64": dpslab.FP64, "mixed": dpslab.MIXED, "mixed_simt": dpslab.MIXED_SIMT}[args.precision]
+    srv = Server(budget, nstreams=cfg["nstreams"], precision=prec)
+    t0 = time.perf_counter()
+    for i, r in enumerate(reps):
+        srv.register(i, {k: v for k, v in r.items() if k != "n"}, r["n"])
+    t_register = time.perf_counter() - t0
+    warm, steps = max(3, args.warmup), max(1, args.steps)
+    rep_ids, t_arr = synth.serve_arrivals((warm + steps) * cfg["per_step"], len(reps), cfg["rate"], cfg["seed"])
+
+    def requests(lo, hi):
+        t_base = t_arr[lo]
+        return [Request(int(rep_ids[k]), *bufs[rep_ids[k]], t_arrival=float(t_arr[k] - t_base)) for k in range(lo, hi)]
+
+    nw = warm * cfg["per_step"]
+    srv.run(requests(0, nw))
+    torch.cuda.synchronize()
+    stats0 = dict(srv.stats)
+    clocks = Clocks(0)
+    clocks.start()
+    clocks.begin()
+    t0 = time.perf_counter()
+    done = srv.run(requests(nw, len(rep_ids)))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks.end()
+    ck = clocks.stop()
+    st = latency_stats(done)
+    svc = sorted((r.t_done - r.t_start) * 1e3 for r in done)
+    counters = {k: srv.stats[k] - stats0.get(k, 0) for k in ("admissions", "evictions", "resident_hits", "rejected")}
+    # the first 100 timed requests again, one after another on one stream
+    subset = done[:cfg["per_step"]]
+    for r in list(srv.ws):
+        srv._evict(r)
+    one = srv.alloc(max(srv.plans[r.replica].work_bytes for r in subset))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    seq_charges = 0
+    for r in subset:
+        pl = srv.plans[r.replica]
+        pl.bind_work(one)
+        pl.solve(r.pos, r.q, r.phi, r.force)
+        pl.bind_work(None)
+        seq_charges += r.n
+    torch.cuda.synchronize()
+    seq_rate = seq_charges / (time.perf_counter() - t1)
+    line = dict(metric=METRIC, value=st["charges"] / wall, unit=UNIT, n_gpus=1, steps=steps, warmup=warm,
+                ms_per_step=wall * 1e3 / steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype={"fp64": "f64", "mixed": "f32+f64", "mixed_simt": "f32+f64"}[args.precision],
+                data="synthetic (seeded +-1 electrolytes)",
+                config=dict(workload=args.workload, replicas=len(reps), requests_per_step=cfg["per_step"],
+                            arrival_rate_per_s=cfg["rate"], streams=cfg["nstreams"],
+                            workspace_budget_gb=budget / 1e9,
+                            l2="grids of 10 MB to 2 GB per request, requests interleaved; no flush"),
+                latency_ms=dict(p50=st["p50_ms"], p99=st["p99_ms"]),
+                service_ms=dict(p50=svc[len(svc) // 2], p99=svc[min(len(svc) - 1, int(0.99 * len(svc)))]),
+                requests=st["requests"], failed=st.get("failed", 0), charges=st["charges"],
+                admission=dict(counters, peak_workspace_gb=srv.peak_ws_bytes / 1e9,
+                               resident_plans_gb=srv.plan_bytes() / 1e9, register_s=t_register),
+                sequential_value=seq_rate, served_over_sequential=(st["charges"] / wall) / seq_rate,
+                clocks=ck)
+    print(json.dumps(line))
+    del one
+    srv.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.workload in BATCH_WORKLOADS:
         return bench_batch(args)
+    if args.workload in SERVE_WORKLOADS:
+        return bench_serve(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -48,6 +48,7 @@ extern "C" {
 #define DPSLAB_ERR_NO_DEVICE         -8  /* no usable CUDA device */
 #define DPSLAB_ERR_GRID              -9  /* grid too small for the Gaussian support, or a size the kernels do not support */
 #define DPSLAB_ERR_UNSUPPORTED      -10  /* option not built into this library */
+#define DPSLAB_PENDING                1  /* dpslab_solve_poll: the enqueued solve has not finished yet */
 
 /* ------------------------------------------------------------- precision */
 #define DPSLAB_FP64   0   /* every stage in double precision */
@@ -138,6 +139,40 @@ int dpslab_plan_derived(const dpslab_plan* plan, dpslab_derived* out);
 int64_t dpslab_plan_device_bytes(const dpslab_plan* plan);
 
 /*
+ * A plan without a workspace: tables and derived parameters only (a few MB);
+ * the caller binds a workspace of at least dpslab_plan_work_bytes bytes with
+ * dpslab_plan_bind_work before solving. Serving loops keep many such plans
+ * resident and give the large per-solve arrays (grids, cell list) only to
+ * the solves admitted at a time. Errors as dpslab_plan_create.
+ */
+int dpslab_plan_create_unbound(const dpslab_params* p, int64_t max_n, dpslab_plan** out);
+
+/* Bytes of the per-solve workspace the plan needs (grids, spectra, field
+ * grids, charge arrays, buckets, cell list, partial sums). */
+int64_t dpslab_plan_work_bytes(const dpslab_plan* plan);
+
+/*
+ * Bind the caller's device workspace to an unbound plan: `work` (256-byte
+ * aligned, at least dpslab_plan_work_bytes bytes) is carved into the plan's
+ * per-solve arrays and used by every later solve until rebound; work == NULL
+ * unbinds (solves then fail with DPSLAB_ERR_INVALID_ARG). The caller keeps
+ * ownership and must not free or reuse it while a solve of the plan is in
+ * flight; nothing in it needs to survive between solves, so plans may take
+ * turns on one workspace. DPSLAB_ERR_INVALID_ARG for a plan that owns its
+ * workspace (dpslab_plan_create), one with a solve in flight, a misaligned
+ * pointer or too few bytes.
+ */
+int dpslab_plan_bind_work(dpslab_plan* plan, void* work, int64_t bytes);
+
+/*
+ * Bytes of device memory dpslab_plan_create(p, max_n) would take, computed on
+ * the host without a device and without allocating (for admission control
+ * by memory footprint). Errors as dpslab_plan_create's parameter checks;
+ * *bytes is 0 on error.
+ */
+int dpslab_plan_footprint(const dpslab_params* p, int64_t max_n, int64_t* bytes);
+
+/*
  * One solve (Sec. 5.2.2 far field + Sec. 4.2 near field + gauge + energy).
  *   n        number of charges, 1 <= n <= max_n;
  *   pos      device, [n][3] (x, y, z); x and y are wrapped into [0, L);
@@ -176,6 +211,21 @@ int dpslab_debug_fetch(dpslab_plan* plan, int which, void* host_dst, size_t byte
 
 /* Number of kernels the last solve launched. */
 int dpslab_last_launch_count(const dpslab_plan* plan);
+
+/*
+ * Asynchronous form of dpslab_solve, for serving loops that overlap many
+ * solves. dpslab_solve_enqueue validates the arguments and enqueues the
+ * whole solve on `stream` (the same work as dpslab_solve), then returns
+ * without waiting. dpslab_solve_poll never blocks. It returns DPSLAB_PENDING
+ * while the enqueued solve runs, and then the solve's own result code, as
+ * dpslab_solve would have returned it, with *U set (U may be NULL). At most
+ * one solve per plan may be in flight; enqueueing another before the poll
+ * has returned a result gives DPSLAB_ERR_INVALID_ARG. The output buffers
+ * must stay valid until then.
+ */
+int dpslab_solve_enqueue(dpslab_plan* plan, int64_t n, const double* pos, const double* q, double* phi,
+                         double* force, void* stream);
+int dpslab_solve_poll(dpslab_plan* plan, double* U);
 
 /*
  * Batches of independent systems, each with its own box, walls, grid and

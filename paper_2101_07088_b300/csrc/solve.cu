@@ -2222,6 +2222,9 @@ struct dpslab_plan {
     double* h_scal = nullptr;   // pinned
     int* h_status = nullptr;
     int* scan_part = nullptr;     // block sums and offsets of the multi-block scans
+    cudaEvent_t done = nullptr;   // end of an enqueued (asynchronous) solve
+    bool in_flight = false;
+    bool bound = false;           // a workspace is bound (owned, a batch's, or the caller's)
     int64_t last_n = 0;
     int launches = 0;
     int profiling = 0;
@@ -2325,11 +2328,13 @@ size_t bind_work(dpslab_plan* pl, char* base) {
     pl->d_force = carve<double>(cur, 3 * n);
     pl->d_q = carve<double>(cur, n);
     pl->d_phi = carve<double>(cur, n);
+    if (base) pl->bound = true;
     return size_t(cur - base);
 }
 
 void release(dpslab_plan* pl) {
     if (!pl) return;
+    if (pl->done) cudaEventDestroy(pl->done);
     for (auto& e : pl->ev)
         if (e) cudaEventDestroy(e);
     if (pl->tables) cudaFree(pl->tables);
@@ -2362,15 +2367,17 @@ extern "C" int dpslab_table(const dpslab_params* p, int which, double* out, int 
 }
 
 namespace {
-int plan_create_impl(const dpslab_params* p, int64_t max_n, bool defer_work, dpslab_plan** out);
+enum PlanMode { kPlanFull = 0, kPlanDeferWork = 1, kPlanMeasure = 2 };
+int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_plan** out);
 }
 
 extern "C" int dpslab_plan_create(const dpslab_params* p, int64_t max_n, dpslab_plan** out) {
-    return plan_create_impl(p, max_n, false, out);
+    return plan_create_impl(p, max_n, kPlanFull, out);
 }
 
 namespace {
-int plan_create_impl(const dpslab_params* p, int64_t max_n, bool defer_work, dpslab_plan** out) {
+int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_plan** out) {
+    const bool measure = mode == kPlanMeasure, defer_work = mode != kPlanFull;
     if (!out) return DPSLAB_ERR_INVALID_ARG;
     *out = nullptr;
     if (!p || max_n < 1 || max_n > (int64_t(1) << 28)) return DPSLAB_ERR_INVALID_ARG;
@@ -2383,9 +2390,11 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, bool defer_work, dps
     dps::Tables t;
     rc = dps::build_tables(*p, pl->d, t);
     if (rc) { delete pl; return rc; }
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) { delete pl; return DPSLAB_ERR_NO_DEVICE; }
-    cudaGetDevice(&pl->device);
+    if (!measure) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) { delete pl; return DPSLAB_ERR_NO_DEVICE; }
+        cudaGetDevice(&pl->device);
+    }
 
     const dpslab_derived& d = pl->d;
     const int nx = d.nx, ny = d.ny, nz = d.nz, nxh = nx / 2 + 1;
@@ -2494,6 +2503,11 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, bool defer_work, dps
         bytes += 3 * align_up(N * N * sizeof(float)) + 14 * align_up(N * sizeof(float));
         if (pl->ztensor) bytes += 2 * align_up(t.zimg_fwd.size() * sizeof(unsigned short));   // bf16 images
         bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
+        pl->device_bytes += int64_t(bytes);   // table bytes, taken up again below
+    }
+    if (!measure) {
+        const size_t bytes = size_t(pl->device_bytes);
+        pl->device_bytes = 0;
         cudaError_t e = cudaMalloc(&pl->tables, bytes);
         if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
         pl->device_bytes += int64_t(bytes);
@@ -2585,6 +2599,11 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, bool defer_work, dps
         pl->rsz = rsz;
         pl->scan_n = 2 * ((std::max<size_t>(kp.nbuckets, kp.ncells) + kScanChunk - 1) / kScanChunk + 1);
         pl->work_bytes = bind_work(pl, nullptr);
+        if (measure) {
+            pl->device_bytes += int64_t(pl->work_bytes);
+            *out = pl;
+            return DPSLAB_OK;
+        }
         if (!defer_work) {
             cudaError_t e = cudaMalloc(&pl->work, pl->work_bytes);
             if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
@@ -2714,6 +2733,34 @@ extern "C" int dpslab_plan_derived(const dpslab_plan* plan, dpslab_derived* out)
 
 extern "C" int64_t dpslab_plan_device_bytes(const dpslab_plan* plan) { return plan ? plan->device_bytes : 0; }
 
+extern "C" int dpslab_plan_create_unbound(const dpslab_params* p, int64_t max_n, dpslab_plan** out) {
+    return plan_create_impl(p, max_n, kPlanDeferWork, out);
+}
+
+extern "C" int64_t dpslab_plan_work_bytes(const dpslab_plan* plan) { return plan ? int64_t(plan->work_bytes) : 0; }
+
+extern "C" int dpslab_plan_bind_work(dpslab_plan* plan, void* work, int64_t bytes) {
+    if (!plan || plan->work || plan->in_flight) return DPSLAB_ERR_INVALID_ARG;   // owned workspace, or busy
+    if (!work) {
+        plan->bound = false;
+        return DPSLAB_OK;
+    }
+    if (reinterpret_cast<uintptr_t>(work) % 256 != 0 || bytes < int64_t(plan->work_bytes)) return DPSLAB_ERR_INVALID_ARG;
+    bind_work(plan, static_cast<char*>(work));
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_plan_footprint(const dpslab_params* p, int64_t max_n, int64_t* bytes) {
+    if (!bytes) return DPSLAB_ERR_INVALID_ARG;
+    *bytes = 0;
+    dpslab_plan* pl = nullptr;
+    const int rc = plan_create_impl(p, max_n, kPlanMeasure, &pl);
+    if (rc) return rc;
+    *bytes = pl->device_bytes;
+    delete pl;        // measure mode holds no device or pinned memory
+    return DPSLAB_OK;
+}
+
 extern "C" int dpslab_plan_destroy(dpslab_plan* plan) {
     if (!plan) return DPSLAB_OK;
     cudaSetDevice(plan->device);
@@ -2758,6 +2805,7 @@ extern "C" const char* dpslab_strerror(int code) {
         case DPSLAB_ERR_NO_DEVICE: return "no CUDA device";
         case DPSLAB_ERR_GRID: return "grid too small for the Gaussian support or unsupported size";
         case DPSLAB_ERR_UNSUPPORTED: return "unsupported option";
+        case DPSLAB_PENDING: return "the solve has not finished yet";
         default: return "unknown error";
     }
 }
@@ -2929,7 +2977,7 @@ int finish(dpslab_plan* pl, cudaStream_t st, double* U) {
 
 extern "C" int dpslab_solve(dpslab_plan* plan, int64_t n, const double* pos, const double* q, double* U,
                             double* phi, double* force, void* stream) {
-    if (!plan || !pos || !q || n < 1) return DPSLAB_ERR_INVALID_ARG;
+    if (!plan || !pos || !q || n < 1 || plan->in_flight || !plan->bound) return DPSLAB_ERR_INVALID_ARG;
     if (n > plan->max_n) return DPSLAB_ERR_CAPACITY;
     DPS_CUDA(cudaSetDevice(plan->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -2939,9 +2987,39 @@ extern "C" int dpslab_solve(dpslab_plan* plan, int64_t n, const double* pos, con
     return finish(plan, st, U);
 }
 
+extern "C" int dpslab_solve_enqueue(dpslab_plan* plan, int64_t n, const double* pos, const double* q, double* phi,
+                                    double* force, void* stream) {
+    if (!plan || !pos || !q || n < 1 || plan->in_flight || !plan->bound) return DPSLAB_ERR_INVALID_ARG;
+    if (n > plan->max_n) return DPSLAB_ERR_CAPACITY;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    if (!plan->done) DPS_CUDA(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int prof = plan->profiling;
+    plan->profiling = 0;
+    const int rc = enqueue(plan, n, pos, q, phi, force, st);
+    plan->profiling = prof;
+    if (rc) return rc;
+    DPS_CUDA(cudaEventRecord(plan->done, st));
+    plan->last_n = n;
+    plan->in_flight = true;
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_solve_poll(dpslab_plan* plan, double* U) {
+    if (!plan || !plan->in_flight) return DPSLAB_ERR_INVALID_ARG;
+    const cudaError_t e = cudaEventQuery(plan->done);
+    if (e == cudaErrorNotReady) return DPSLAB_PENDING;
+    plan->in_flight = false;
+    if (e != cudaSuccess) {
+        trace("cudaEventQuery", e, __LINE__);
+        return DPSLAB_ERR_CUDA;
+    }
+    return collect(plan, U);
+}
+
 extern "C" int dpslab_solve_host(dpslab_plan* plan, int64_t n, const double* pos, const double* q, double* U,
                                  double* phi, double* force, void* stream) {
-    if (!plan || !pos || !q || n < 1) return DPSLAB_ERR_INVALID_ARG;
+    if (!plan || !pos || !q || n < 1 || plan->in_flight || !plan->bound) return DPSLAB_ERR_INVALID_ARG;
     if (n > plan->max_n) return DPSLAB_ERR_CAPACITY;
     DPS_CUDA(cudaSetDevice(plan->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -3157,7 +3235,7 @@ extern "C" int dpslab_batch_create(const dpslab_params* params, const int64_t* m
     const int S = std::min(nstreams, count);
     for (int i = 0; i < count; ++i) {
         dpslab_plan* pl = nullptr;
-        const int rc = plan_create_impl(&params[i], max_n[i], true, &pl);
+        const int rc = plan_create_impl(&params[i], max_n[i], kPlanDeferWork, &pl);
         if (rc) { batch_release(b); return rc; }
         b->plans.push_back(pl);
         b->device_bytes += pl->device_bytes;

@@ -21,6 +21,7 @@ ERRORS = {
 }
 (ERR_INVALID_ARG, ERR_NOT_NEUTRAL, ERR_OUT_OF_SLAB, ERR_CUTOFF_TOO_LARGE, ERR_SPLIT_CONSTRAINT, ERR_CAPACITY,
  ERR_CUDA, ERR_NO_DEVICE, ERR_GRID, ERR_UNSUPPORTED) = range(-1, -11, -1)
+PENDING = 1                          # DPSLAB_PENDING
 FP64, MIXED, MIXED_SIMT = 0, 1, 2   # DPSLAB_FP64, DPSLAB_MIXED, DPSLAB_MIXED_SIMT
 NSTAGES = 12
 
@@ -75,6 +76,12 @@ def lib():
             "dpslab_last_launch_count": (ctypes.c_int, [vp]),
             "dpslab_plan_destroy": (ctypes.c_int, [vp]),
             "dpslab_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "dpslab_plan_footprint": (ctypes.c_int, [P, i64, ctypes.POINTER(i64)]),
+            "dpslab_plan_create_unbound": (ctypes.c_int, [P, i64, ctypes.POINTER(vp)]),
+            "dpslab_plan_work_bytes": (i64, [vp]),
+            "dpslab_plan_bind_work": (ctypes.c_int, [vp, vp, i64]),
+            "dpslab_solve_enqueue": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, vp]),
+            "dpslab_solve_poll": (ctypes.c_int, [vp, dp]),
             "dpslab_batch_create": (ctypes.c_int, [P, ctypes.POINTER(i64), ctypes.c_int, ctypes.c_int,
                                                    ctypes.POINTER(vp)]),
             "dpslab_batch_solve": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp), dp,
@@ -140,19 +147,41 @@ def near_field_static(params, pos, q, out, stream=None, check=True):
     return rc
 
 
-class Plan:
-    """dpslab_plan_create / dpslab_solve / dpslab_plan_destroy."""
+def plan_bytes(params, max_n):
+    """dpslab_plan_footprint: device bytes a plan for (params, max_n) takes."""
+    p = _as_params(params)
+    b = ctypes.c_int64(0)
+    _check(lib().dpslab_plan_footprint(ctypes.byref(p), int(max_n), ctypes.byref(b)))
+    return b.value
 
-    def __init__(self, params, max_n):
+
+class Plan:
+    """dpslab_plan_create / dpslab_solve / dpslab_plan_destroy. With
+    own_work=False the plan is created unbound (dpslab_plan_create_unbound):
+    bind a workspace with bind_work() before solving."""
+
+    def __init__(self, params, max_n, own_work=True):
         self.params = _as_params(params)
         h = ctypes.c_void_p()
-        _check(lib().dpslab_plan_create(ctypes.byref(self.params), int(max_n), ctypes.byref(h)))
+        create = lib().dpslab_plan_create if own_work else lib().dpslab_plan_create_unbound
+        _check(create(ctypes.byref(self.params), int(max_n), ctypes.byref(h)))
         self._h = h
         self.max_n = int(max_n)
         d = Derived()
         _check(lib().dpslab_plan_derived(self._h, ctypes.byref(d)))
         self.derived = {name: getattr(d, name) for name, _ in Derived._fields_}
         self.device_bytes = lib().dpslab_plan_device_bytes(self._h)
+        self.work_bytes = lib().dpslab_plan_work_bytes(self._h)
+        self.work = None
+
+    def bind_work(self, work):
+        """dpslab_plan_bind_work: `work` a CUDA uint8 tensor of at least
+        work_bytes bytes (kept referenced while bound), or None to unbind."""
+        if work is None:
+            _check(lib().dpslab_plan_bind_work(self._h, None, 0))
+        else:
+            _check(lib().dpslab_plan_bind_work(self._h, work.data_ptr(), work.numel() * work.element_size()))
+        self.work = work
 
     def close(self):
         if getattr(self, "_h", None):
@@ -183,6 +212,24 @@ class Plan:
         if check:
             _check(rc)
         return (U.value if energy else None), rc
+
+    def enqueue(self, pos, q, phi=None, force=None, stream=None):
+        """dpslab_solve_enqueue: start the solve on `stream` and return at
+        once (poll() tells when it is done)."""
+        import torch
+        for t in (pos, q):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("pos and q must be contiguous float64 CUDA tensors")
+        st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(lib().dpslab_solve_enqueue(self._h, q.shape[0], pos.data_ptr(), q.data_ptr(),
+                                          phi.data_ptr() if phi is not None else None,
+                                          force.data_ptr() if force is not None else None, st))
+
+    def poll(self):
+        """dpslab_solve_poll: (PENDING, None) while running, then (code, U)."""
+        U = ctypes.c_double(math.nan)
+        rc = lib().dpslab_solve_poll(self._h, ctypes.byref(U))
+        return (rc, None) if rc == PENDING else (rc, U.value)
 
     def solve_host(self, pos, q, want_phi=True, want_force=True, stream=None, check=True):
         """Host (numpy) buffers; copies happen inside the library call.

@@ -89,3 +89,41 @@ def batch_systems(count, seed, n_range=(256, 65536), l_range=(32.0, 256.0), h_ra
                       r_cut=r_cut)
         out.append((pos, q, params))
     return out
+
+
+# Smallest box side of the served workload: twice the larger of the cutoff
+# (4) and the Gaussian support half-width (about 4.3 at g_w = 1, tolerance
+# 1e-4), plus one grid spacing, rounded up.
+SERVE_L_MIN = 10.0
+
+
+def serve_replicas(count, seed, n_range=(512, 262144), h_range=(16.0, 128.0), ratio=1.0 / 80.0,
+                   rho=1.0 / 32.0, h=0.5, gw=1.0, tol=1e-4, r_cut=4.0):
+    """Replicas of the served workload: N log-uniform in n_range (even), H
+    uniform in h_range, both walls at eps_w/eps = ratio, square box side
+    L = sqrt(N / (rho H)) (the charge density of the 2^20-charge workload,
+    2^20 / (512^2 128) = 1/32 per unit volume) but at least SERVE_L_MIN, grid
+    spacing h (nx 7-smooth, Lx = nx h), N_z from the paper's rule. Returns a
+    list of params dicts (the keys of workload()) with "n" added."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))) // 2 * 2)
+        H = float(rng.uniform(*h_range))
+        L = max(SERVE_L_MIN, math.sqrt(n / (rho * H)))
+        nx = smooth7(L / h)
+        L = nx * h
+        out.append(dict(n=n, Lx=L, Ly=L, H=H, eps=1.0, eps_b=ratio, eps_t=ratio, gw=gw, tol=tol, nx=nx, ny=nx,
+                        nz=0, r_cut=r_cut))
+    return out
+
+
+def serve_arrivals(count, n_replicas, rate, seed):
+    """Request stream of the served workload: `count` requests, each for a
+    replica drawn uniformly, Poisson arrivals at `rate` per second. Returns
+    (replica ids, arrival times in seconds from the start); request k's
+    charges come from electrolyte(..., seed + 1 + k)."""
+    rng = np.random.default_rng(seed)
+    rep = rng.integers(0, n_replicas, count)
+    t = np.cumsum(rng.exponential(1.0 / rate, count))
+    return rep, t
