@@ -31,6 +31,10 @@ d_w = 1/(1 + r_w) (metal: G_w = c_w = 1, d_w = 0).
 
 k_par = 0 -- Sec. 4.3.4, Eq. (CE), (ai1), (ai2) and Sec. 5.2.2 step 5 (A_i is
 the mean of the two expressions).
+
+Wall charges sigma_b, sigma_t (Eq. (rho), Sec. 4.3.1) enter only here: through
+the displacement mismatches Eq. (mm2), (mm4) for k_par != 0 and the sigma
+terms of Eq. (ai1), (ai2) for k_par = 0.
 """
 import numpy as np
 
@@ -47,16 +51,17 @@ def wall_factors(eps, eps_w):
 
 
 def mismatches(psi_i0, dpsi_i0, psi_iH, dpsi_iH, psi_o0, dpsi_o0, psi_oH, dpsi_oH,
-               eps, eps_b, eps_t):
-    """Eq. (mm1)-(mm4) with sigma_b = sigma_t = 0 and psi_b* = tau_b psi_o*,
-    psi_t* = tau_t psi_o* (Eq. (phibst), (phitst)). Returned m_E are divided by
-    eps: (m_phi^b, m_E^b/eps, m_phi^t, m_E^t/eps)."""
+               eps, eps_b, eps_t, sigma_b=0.0, sigma_t=0.0):
+    """Eq. (mm1)-(mm4) with psi_b* = tau_b psi_o*, psi_t* = tau_t psi_o*
+    (Eq. (phibst), (phitst)) and the wall charges' transforms sigma_b, sigma_t
+    (+sigma_b in m_E^b, -sigma_t in m_E^t). Returned m_E are divided by eps:
+    (m_phi^b, m_E^b/eps, m_phi^t, m_E^t/eps)."""
     _, _, _, tb, rtb = wall_factors(eps, eps_b)
     _, _, _, tt, rtt = wall_factors(eps, eps_t)
     m_phi_b = psi_i0 - tb * psi_o0
-    m_E_b = dpsi_i0 - rtb * dpsi_o0
+    m_E_b = dpsi_i0 - rtb * dpsi_o0 + sigma_b / eps
     m_phi_t = psi_iH - tt * psi_oH
-    m_E_t = dpsi_iH - rtt * dpsi_oH
+    m_E_t = dpsi_iH - rtt * dpsi_oH - sigma_t / eps
     return m_phi_b, m_E_b, m_phi_t, m_E_t
 
 
@@ -79,20 +84,21 @@ def correction(k, z, m_phi_b, m_E_b, m_phi_t, m_E_t, H, eps, eps_b, eps_t):
 
 
 def zero_mode_slope(dpsi_i0, dpsi_iH, dpsi_o_a, dpsi_o0, dpsi_oH, dpsi_o_b,
-                    psi_i0, psi_iH, H, eps, eps_b, eps_t):
-    """A_i(0) of Sec. 4.3.4 (sigma = 0), from the k=0 Dirichlet solutions
-    psi_i*, psi_o* (derivatives d/dz at a, 0, H, b).
+                    psi_i0, psi_iH, H, eps, eps_b, eps_t, sigma_b0=0.0, sigma_t0=0.0):
+    """A_i(0) of Sec. 4.3.4, from the k=0 Dirichlet solutions psi_i*, psi_o*
+    (derivatives d/dz at a, 0, H, b) and the k=0 transforms of the wall
+    charges sigma_b0, sigma_t0.
 
     Eq. (CE): A_b = -d psi_b*/dz (a), A_t = -d psi_t*/dz (b);
-    Eq. (ai1): A_i = (eps_b/eps) tau_b (psi_o*'(0) - psi_o*'(a)) - psi_i*'(0);
-    Eq. (ai2): A_i = (eps_t/eps) tau_t (psi_o*'(H) - psi_o*'(b)) - psi_i*'(H).
+    Eq. (ai1): A_i = (eps_b/eps) tau_b (psi_o*'(0) - psi_o*'(a)) - psi_i*'(0) - sigma_b0/eps;
+    Eq. (ai2): A_i = (eps_t/eps) tau_t (psi_o*'(H) - psi_o*'(b)) - psi_i*'(H) + sigma_t0/eps.
     Both dielectric: the mean (Sec. 5.2.2 step 5). A metallic wall only enters
     through the other wall's equation; two metallic walls are held at equal
     potential, A_i = -(psi_i*(H) - psi_i*(0))/H."""
     _, _, _, _, rtb = wall_factors(eps, eps_b)
     _, _, _, _, rtt = wall_factors(eps, eps_t)
-    ai1 = rtb * (dpsi_o0 - dpsi_o_a) - dpsi_i0
-    ai2 = rtt * (dpsi_oH - dpsi_o_b) - dpsi_iH
+    ai1 = rtb * (dpsi_o0 - dpsi_o_a) - dpsi_i0 - sigma_b0 / eps
+    ai2 = rtt * (dpsi_oH - dpsi_o_b) - dpsi_iH + sigma_t0 / eps
     mb, mt = np.isinf(eps_b), np.isinf(eps_t)
     if mb and mt:
         return -(psi_iH - psi_i0) / H

@@ -215,9 +215,43 @@ def gauge_weights(P):
     return (w @ T) / np.sqrt(np.pi)
 
 
-def solve(pos, q, P, near_method="auto"):
-    """Full solve. pos (n, 3), q (n,). Returns a dict with U, phi, force and
-    the intermediate quantities the GPU path is compared with stage by stage."""
+def gauge_weights_at(P, z0):
+    """gauge_weights at height z0 instead of 0: the z part of the average of
+    the Chebyshev series with gamma^{1/2} at z = z0."""
+    Q = dict(P)
+    Q["a"], Q["b"] = P["a"] - z0, P["b"] - z0
+    return gauge_weights(Q)
+
+
+def wall_near_planar(d, P):
+    """Integral over the wall plane of the pointwise near-field kernel
+    Eq. (Gnear) of a unit charge at distance d from it, truncated at r_cut
+    like the near field: (1/(2 eps)) int_d^{r_cut} [erf(r/a1) - erf(r/a2)] dr
+    with a1 = sqrt2 g_w, a2 = sqrt(2 g_w^2 + xi^-2), written with
+    I(x, a) = int_x^inf erfc(r/a) dr = a (e^{-(x/a)^2}/sqrt(pi) - (x/a) erfc(x/a))."""
+    from scipy.special import erfc
+    d = np.abs(np.asarray(d, dtype=np.float64))
+    if P["r_cut"] <= 0.0 or np.isinf(P["xi"]):
+        return np.zeros_like(d)
+    a1 = np.sqrt(2.0) * P["gw"]
+    a2 = np.sqrt(2.0 * P["gw"] ** 2 + (1.0 / P["xi"] ** 2 if P["xi"] > 0 else np.inf))
+
+    def I(x, a):
+        if np.isinf(a):
+            return np.zeros_like(x)
+        u = x / a
+        return a * (np.exp(-u * u) / np.sqrt(np.pi) - u * erfc(u))
+
+    rc = P["r_cut"]
+    val = (I(d, a2) - I(d, a1)) - (I(np.full_like(d, rc), a2) - I(np.full_like(d, rc), a1))
+    return np.where(d < rc, val, 0.0) / (2.0 * P["eps"])
+
+
+def solve(pos, q, P, near_method="auto", sigma_b=None, sigma_t=None):
+    """Full solve. pos (n, 3), q (n,). sigma_b, sigma_t: wall charge
+    densities sampled on the xy grid, arrays (ny, nx) with [j, i] at
+    (i h_x, j h_y), or None. Returns a dict with U, phi, force and the
+    intermediate quantities the GPU path is compared with stage by stage."""
     pos = np.asarray(pos, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     Lx, Ly, H, HE = P["Lx"], P["Ly"], P["H"], P["HE"]
@@ -283,8 +317,16 @@ def solve(pos, q, P, near_method="auto"):
     corr = np.zeros((nz, M), complex)
     dcorr = np.zeros((nz, M), complex)
     corr0 = np.zeros(M, complex)
+    # wall charges (Eq. (rho)): their xy transforms, unnormalised like rho's
+    with_sigma = sigma_b is not None or sigma_t is not None
+    zero = np.zeros((ny, nx))
+    sb_hat = np.fft.rfft2(np.asarray(sigma_b if sigma_b is not None else zero, np.float64)).reshape(M)
+    st_hat = np.fft.rfft2(np.asarray(sigma_t if sigma_t is not None else zero, np.float64)).reshape(M)
+    if with_sigma and ((np.isinf(eps_b) and np.any(sb_hat != 0)) or (np.isinf(eps_t) and np.any(st_hat != 0))):
+        raise ValueError("a wall charge on a metallic wall is not part of the method")
     mm = mismatches(psi_i_at[1], dpsi_i_at[1], psi_i_at[2], dpsi_i_at[2],
-                    psi_o_at[1], dpsi_o_at[1], psi_o_at[2], dpsi_o_at[2], eps, eps_b, eps_t)
+                    psi_o_at[1], dpsi_o_at[1], psi_o_at[2], dpsi_o_at[2], eps, eps_b, eps_t,
+                    sb_hat, st_hat)
     if np.any(cmask):
         c = np.nonzero(cmask)[0]
         args = [m_[c] for m_ in mm]
@@ -299,7 +341,8 @@ def solve(pos, q, P, near_method="auto"):
     Ai = zero_mode_slope(dpsi_i_at[1, k0].real, dpsi_i_at[2, k0].real,
                          dpsi_o_at[0, k0].real, dpsi_o_at[1, k0].real,
                          dpsi_o_at[2, k0].real, dpsi_o_at[3, k0].real,
-                         psi_i_at[1, k0].real, psi_i_at[2, k0].real, H, eps, eps_b, eps_t)
+                         psi_i_at[1, k0].real, psi_i_at[2, k0].real, H, eps, eps_b, eps_t,
+                         sb_hat[k0].real, st_hat[k0].real)
 
     # step 6: values at the nodes, derivatives, inverse transforms
     psi = cheb.coeffs_to_values(yi, nz) + corr
@@ -341,7 +384,70 @@ def solve(pos, q, P, near_method="auto"):
     Ebar = far[:, 1:4] + En
     force = q[:, None] * Ebar
     U = 0.5 * float(np.sum(q * phibar))
-    return dict(U=U, phi=phibar, force=force, B=B, Ai=Ai, phi_f0=phi_f0, phi_n0=phi_n0,
+    wall = {}
+    if with_sigma:
+        wall = wall_charge_energy(x, y, z, q, P, sb_hat, st_hat, yi[:, k0].real, Ai, B, kf, cmask, zn, wz, full)
+        U += wall["U_wall"]
+    return dict(U=U, phi=phibar, force=force, B=B, Ai=Ai, phi_f0=phi_f0, phi_n0=phi_n0, wall=wall,
                 corr0=corr0, psi0=psi_i_at[1],
                 rho_i=rho_i, rho_o=rho_o, fields=fields, far=far, phin=phin, En=En,
                 psi=psi, dpsi=dpsi, over=over, zn=zn, wz=wz)
+
+
+def wall_charge_energy(x, y, z, q, P, sb_hat, st_hat, y0, Ai, B, kf, cmask, zn, wz, full):
+    """The wall term of Eq. (Ufinal), 1/2 int (sigma_b phi(x, y, 0) + sigma_t phi(x, y, H)) dx dy,
+    split by xy mode.
+
+    k_par = 0: the mean wall charge times the plane average of the pointwise
+    potential at the wall. Its far part is the k=0 column averaged with
+    gamma^{1/2} in z (the series with the weights of gauge_weights at z = 0 or
+    H) plus A_i z, plus the gauge B; its near part is wall_near_planar summed
+    over the charges and their images (the near field's sources).
+
+    k_par != 0: by Green's reciprocity int sigma phi_q = sum_k q_k phibar_sigma(z_k),
+    with phi_sigma the correction driven by the wall charges alone (Eq. (mm2),
+    (mm4) with psi* = 0), interpolated at the charges like the far field; plus
+    the wall charges' own term int sigma phi_sigma by Parseval. On these modes
+    the correction is the exact per-mode solution of the jump conditions, so
+    the energy's derivative is the force the solve returns. (A direct
+    quadrature of the charges' near potential on the wall would need the scale
+    g_w there; the reciprocity form needs none.)"""
+    Lx, Ly, H = P["Lx"], P["Ly"], P["H"]
+    eps, eps_b, eps_t = P["eps"], P["eps_b"], P["eps_t"]
+    nx, ny, nz = P["nx"], P["ny"], P["nz"]
+    M = kf.size
+    k0 = int(np.nonzero(kf == 0.0)[0][0])
+    hxhy = P["hx"] * P["hy"]
+    # k_par = 0
+    far0 = float(gauge_weights_at(P, 0.0) @ y0) / (nx * ny) + B
+    farH = float(gauge_weights_at(P, H) @ y0 + Ai * H) / (nx * ny) + B
+    sx, sy, sz, sq = near_sources(x, y, z, q, P)
+    area = Lx * Ly
+    near0 = float(np.sum(sq * wall_near_planar(sz, P))) / area
+    nearH = float(np.sum(sq * wall_near_planar(H - sz, P))) / area
+    Qb, Qt = hxhy * sb_hat[k0].real, hxhy * st_hat[k0].real
+    U0 = 0.5 * (Qb * (far0 + near0) + Qt * (farH + nearH))
+    # k_par != 0: the wall charges' own correction
+    sb = np.where(cmask, sb_hat, 0.0)
+    st = np.where(cmask, st_hat, 0.0)
+    corr = np.zeros((nz, M), complex)
+    wall0 = np.zeros(M, complex)
+    wallH = np.zeros(M, complex)
+    if np.any(cmask):
+        c = np.nonzero(cmask)[0]
+        zsel = (zn >= -P["HE"]) & (zn <= H + P["HE"])
+        zero = np.zeros(c.size)
+        args = (zero, sb[c] / eps, zero, -st[c] / eps)
+        v, _ = correction(kf[c], zn[zsel], *args, H, eps, eps_b, eps_t)
+        corr[np.ix_(zsel, c)] = v.T
+        v0, _ = correction(kf[c], np.array([0.0, H]), *args, H, eps, eps_b, eps_t)
+        wall0[c], wallH[c] = v0[:, 0], v0[:, 1]
+    grid = np.fft.irfft2(corr.reshape(nz, ny, nx // 2 + 1), s=(ny, nx), axes=(1, 2))
+    zeros = np.zeros_like(grid)
+    phis = interpolate(np.stack([grid, zeros, zeros, zeros]), x, y, z, P, zn, wz)[:, 0]
+    cross = float(np.sum(q * phis))
+    fullv = full.reshape(M)
+    self_ = hxhy / (nx * ny) * float(np.sum(fullv * (np.conj(sb) * wall0 + np.conj(st) * wallH).real))
+    Uk = 0.5 * (cross + self_)
+    return dict(U_wall=U0 + Uk, U_wall0=U0, U_wall_cross=0.5 * cross, U_wall_self=0.5 * self_,
+                phi_wall0=far0 + near0, phi_wallH=farH + nearH, phi_sigma=phis)
