@@ -139,6 +139,32 @@ int dpslab_plan_derived(const dpslab_plan* plan, dpslab_derived* out);
 int64_t dpslab_plan_device_bytes(const dpslab_plan* plan);
 
 /*
+ * Wall charge densities (Eq. (rho) and Sec. 4.3.1, the paper's sigma_b at
+ * z = 0 and sigma_t at z = H), fixed for every later solve of the plan.
+ *   sigma_b, sigma_t  host arrays of ny*nx doubles, [j*nx + i] the density at
+ *                     (i*hx, j*hy) (nx, ny the plan's grid); NULL for an
+ *                     uncharged wall. Both NULL removes the wall charges.
+ *   stream            CUDA stream (cudaStream_t) for the set-up work.
+ * They enter the displacement mismatches Eq. (mm2), (mm4) for 0 < |k| <= pi/h
+ * (modes above are dropped: the density must be resolved by the grid) and
+ * Eq. (ai1), (ai2) for k = 0, so potentials and forces include their field.
+ * The energy gains 1/2 int (sigma_b phi(x, y, 0) + sigma_t phi(x, y, H)),
+ * evaluated per xy mode: for k = 0 from the plane-averaged potential at the
+ * walls (far field plus the near field's planar integral in closed form), for
+ * k != 0 by Green's reciprocity (the wall charges' own correction averaged
+ * at the charges, plus its Parseval self term), so -dU/dz_k is the force.
+ * Electroneutrality (Eq. (elecneu)) then covers charges and wall charges
+ * together. The set-up runs once: two xy transforms, the correction grid
+ * (one grid of the plan's precision, held by the plan) and its self term;
+ * each solve adds one gather kernel. Needs a bound workspace (its arrays are
+ * used as scratch) and no solve in flight. Errors: DPSLAB_ERR_INVALID_ARG
+ * (no workspace, a solve in flight, non-finite values),
+ * DPSLAB_ERR_UNSUPPORTED (a charge density on a metallic wall),
+ * DPSLAB_ERR_CUDA.
+ */
+int dpslab_plan_set_wall_charge(dpslab_plan* plan, const double* sigma_b, const double* sigma_t, void* stream);
+
+/*
  * A plan without a workspace: tables and derived parameters only (a few MB);
  * the caller binds a workspace of at least dpslab_plan_work_bytes bytes with
  * dpslab_plan_bind_work before solving. Serving loops keep many such plans

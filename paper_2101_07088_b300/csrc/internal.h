@@ -50,6 +50,7 @@ struct Tables {
     std::vector<double> u1, u2, v1, v2;  // 1^T J, 1^T J^2, (-1)^T J, (-1)^T J^2
     std::vector<double> t0, tH;      // T_n(s(0)), T_n(s(H))
     std::vector<double> wg;          // gauge weights int G_sigma(z) T_n(s(z)) dz
+    std::vector<double> wgH;         // the same at z = H (wall-charge energy)
     std::vector<Complex> twx, twy;   // e^{-2 pi i k/n}
     std::vector<int> radx, rady;     // FFT radices (Stockham stages)
     // three bf16 pieces (x1 + x2 + x3) of the dense z transforms, 128 x 128

@@ -151,7 +151,18 @@ struct KP {
     double* part_gauge_near;  // one per charge block
     double* part_u;           // one per charge block
     double* part_q;           // [2 * nblocks]: sum q, sum |q|
-    double* scal;             // [8]: B, A_i, phi_f0, phi_n0, U, sumq, sumabsq, spare
+    double* scal;             // [16]: B, A_i, phi_f0, phi_n0, U, sumq, sumabsq, k=0 far potential at
+                              // z = 0 and z = H (unnormalised; wall charges), spare
+    // wall charge densities (Eq. (rho)): their xy transforms, the potential
+    // grid of their k != 0 correction, per-charge terms of the wall energy
+    int sigma_on;
+    const double2* sig_hat;   // [2][ny nxh]: sigma_b, sigma_t transforms (unnormalised)
+    const void* sig_grid;     // R [nz][ny][nx]: correction driven by the wall charges alone
+    double* wall_phi;         // [n] phibar of that correction at each charge
+    double* part_wall;        // [3 * nblocks]: q phibar_sigma, near planar sums at z = 0, H
+    const double* wgH;        // gauge weights at z = H
+    double sig_Qb, sig_Qt;    // total wall charges int sigma dx dy
+    double sig_self;          // 1/2 int sigma phi_sigma over both walls (k != 0)
     int* status;
     int n_col_blocks, n_charge_blocks;
     // user outputs

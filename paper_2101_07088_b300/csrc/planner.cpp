@@ -294,23 +294,26 @@ int build_tables(const dpslab_params& p, const dpslab_derived& d, Tables& t) {
     cheb_row(s0, t.t0);
     cheb_row(sH, t.tH);
 
-    // gauge weights: int G_sigma(z) T_n(s0 + 2 z/Hbar) dz, sigma = 1/(2 xi),
+    // gauge weights: int G_sigma(z) T_n(sc + 2 z/Hbar) dz, sigma = 1/(2 xi),
     // by the trapezoid rule on [-14 sigma, 14 sigma] (spectrally accurate for a
-    // Gaussian times a polynomial)
-    if (std::isinf(d.xi)) {
-        t.wg = t.t0;
-    } else {
+    // Gaussian times a polynomial): the z part of the gamma^{1/2} average of a
+    // Chebyshev series at the height whose scaled coordinate is sc (z = 0 for
+    // the gauge; z = 0 and z = H for the wall-charge energy)
+    auto gauge_row = [&](long double sc, const std::vector<double>& plain, std::vector<double>& out) {
+        if (std::isinf(d.xi)) {
+            out = plain;
+            return;
+        }
         const long double sig = 0.5L / d.xi;
         const int M = 601;   // step 0.047 sigma: the aliasing error exp(-2 pi^2 sigma^2 / dz^2) is far below 1e-16
         const long double zlo = -14.0L * sig, dzs = 28.0L * sig / (M - 1);
         std::vector<long double> acc(N, 0.0L);
-        std::vector<double> row;
         for (int i = 0; i < M; ++i) {
             const long double z = zlo + dzs * i;
             const long double g = expl(-z * z / (2.0L * sig * sig)) /
                                   (sig * sqrtl(2.0L * 3.141592653589793238462643383279503L));
             const long double w = (i == 0 || i == M - 1) ? 0.5L : 1.0L;
-            long double tm = 1.0L, s = s0 + 2.0L * z / d.Hbar, tc = s;
+            long double tm = 1.0L, s = sc + 2.0L * z / d.Hbar, tc = s;
             acc[0] += w * g;
             if (N > 1) acc[1] += w * g * s;
             for (int n = 2; n < N; ++n) {
@@ -320,9 +323,11 @@ int build_tables(const dpslab_params& p, const dpslab_derived& d, Tables& t) {
                 tc = tn;
             }
         }
-        t.wg.resize(N);
-        for (int n = 0; n < N; ++n) t.wg[n] = double(acc[n] * dzs);
-    }
+        out.resize(N);
+        for (int n = 0; n < N; ++n) out[n] = double(acc[n] * dzs);
+    };
+    gauge_row(s0, t.t0, t.wg);
+    gauge_row(sH, t.tH, t.wgH);
 
     // FFT twiddles and radices
     auto tw = [](int n, std::vector<Complex>& out) {

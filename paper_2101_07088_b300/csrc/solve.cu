@@ -1142,9 +1142,13 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
             double2 corr0 = make_double2(0.0, 0.0);
             if (s_corr[c]) {
                 const double2 mpb = csub(pi0, cscale(po0, kp.tb));
-                const double2 meb = csub(dpi0, cscale(dpo0, kp.rtb));
+                double2 meb = csub(dpi0, cscale(dpo0, kp.rtb));
                 const double2 mpt = csub(piH, cscale(poH, kp.tt));
-                const double2 met = csub(dpiH, cscale(dpoH, kp.rtt));
+                double2 met = csub(dpiH, cscale(dpoH, kp.rtt));
+                if (kp.sigma_on) {   // Eq. (mm2), (mm4): +sigma_b, -sigma_t (over eps)
+                    meb = cadd(meb, cscale(kp.sig_hat[col0 + c], 1.0 / kp.eps));
+                    met = csub(met, cscale(kp.sig_hat[M + col0 + c], 1.0 / kp.eps));
+                }
                 const double2 P = csub(cscale(mpb, kp.cb), cscale(meb, kp.db / k));
                 const double2 Q = csub(cscale(mpt, -kp.ct), cscale(met, kp.dt / k));
                 const double ekH = exp(-k * kp.H);
@@ -1158,8 +1162,12 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
             if (col0 + c == 0) {
                 // Sec. 4.3.4: Eq. (CE), (ai1), (ai2); mean, or the non-metal wall's
                 // equation, or equal wall potentials for two metal walls
-                const double ai1 = kp.rtb * (dpo0.x - dpoa) - dpi0.x;
-                const double ai2 = kp.rtt * (dpoH.x - dpob) - dpiH.x;
+                double ai1 = kp.rtb * (dpo0.x - dpoa) - dpi0.x;
+                double ai2 = kp.rtt * (dpoH.x - dpob) - dpiH.x;
+                if (kp.sigma_on) {
+                    ai1 -= kp.sig_hat[0].x / kp.eps;
+                    ai2 += kp.sig_hat[M].x / kp.eps;
+                }
                 double Ai;
                 if (kp.metal_b && kp.metal_t) Ai = -(piH.x - pi0.x) / kp.H;
                 else if (kp.metal_b) Ai = ai2;
@@ -1167,6 +1175,15 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
                 else Ai = 0.5 * (ai1 + ai2);
                 s_Ai = Ai;
                 kp.scal[1] = Ai;
+                if (kp.sigma_on) {   // k = 0 far potential at the walls, gamma^{1/2}-averaged in z
+                    double f0 = 0.0, fH = 0.0;
+                    for (int n = 0; n < N; ++n) {
+                        f0 = fma(kp.wg[n], yi[n].x, f0);
+                        fH = fma(kp.wgH[n], yi[n].x, fH);
+                    }
+                    kp.scal[7] = f0;
+                    kp.scal[8] = fH + Ai * kp.H;
+                }
             }
             const double damp = exp(-0.5 * kp.sigma2 * k * k);
             s_gauge[c] = s_mult[c] * (damp * acc[18] + corr0.x);
@@ -1516,9 +1533,15 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
             float corr0 = 0.f;
             if (s_corr[c]) {
                 const float2 mpb = csub(pi0, cscale(po0, kp.f.tb));
-                const float2 meb = csub(dpi0, cscale(dpo0, kp.f.rtb));
+                float2 meb = csub(dpi0, cscale(dpo0, kp.f.rtb));
                 const float2 mpt = csub(piH, cscale(poH, kp.f.tt));
-                const float2 met = csub(dpiH, cscale(dpoH, kp.f.rtt));
+                float2 met = csub(dpiH, cscale(dpoH, kp.f.rtt));
+                if (kp.sigma_on) {   // Eq. (mm2), (mm4): +sigma_b, -sigma_t (over eps)
+                    const double2 sb = kp.sig_hat[col0 + c], st = kp.sig_hat[M + col0 + c];
+                    const double ie = 1.0 / kp.eps;
+                    meb = cadd(meb, make_float2(float(sb.x * ie), float(sb.y * ie)));
+                    met = csub(met, make_float2(float(st.x * ie), float(st.y * ie)));
+                }
                 const float ik = 1.f / k;
                 const float2 P = csub(cscale(mpb, kp.f.cb), cscale(meb, kp.f.db * ik));
                 const float2 Q = csub(cscale(mpt, -kp.f.ct), cscale(met, kp.f.dt * ik));
@@ -1538,8 +1561,12 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
                 const double dpi0x = double(da[2]) * ddz, dpiHx = double(da[6]) * ddz;
                 const double dpo0x = double(da[10]) * ddz, dpoHx = double(da[14]) * ddz;
                 const double dpoa = double(da[16]) * ddz, dpob = double(da[17]) * ddz;
-                const double ai1 = kp.rtb * (dpo0x - dpoa) - dpi0x;
-                const double ai2 = kp.rtt * (dpoHx - dpob) - dpiHx;
+                double ai1 = kp.rtb * (dpo0x - dpoa) - dpi0x;
+                double ai2 = kp.rtt * (dpoHx - dpob) - dpiHx;
+                if (kp.sigma_on) {
+                    ai1 -= kp.sig_hat[0].x / kp.eps;
+                    ai2 += kp.sig_hat[M].x / kp.eps;
+                }
                 double Ai;
                 if (kp.metal_b && kp.metal_t) Ai = -(double(da[4]) - double(da[0])) / kp.H;
                 else if (kp.metal_b) Ai = ai2;
@@ -1547,6 +1574,15 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
                 else Ai = 0.5 * (ai1 + ai2);
                 s_Ai = Ai;
                 kp.scal[1] = Ai;
+                if (kp.sigma_on) {   // k = 0 far potential at the walls, gamma^{1/2}-averaged in z
+                    double f0 = 0.0, fH = 0.0;
+                    for (int n = 0; n < N; ++n) {
+                        f0 = fma(kp.wg[n], double(yi[n].x), f0);
+                        fH = fma(kp.wgH[n], double(yi[n].x), fH);
+                    }
+                    kp.scal[7] = f0;
+                    kp.scal[8] = fH + Ai * kp.H;
+                }
             }
             const float damp = expf(-0.5f * kp.f.sigma2 * k * k);
             s_gauge[c] = double(s_mult[c] * (damp * da[18] + corr0));
@@ -2111,9 +2147,48 @@ __global__ void k_near_f32(KP kp) {
     kp.nearv[kp.sorted_idx[s]] = make_double4_32a(phi, ex, ey, ez);
 }
 
-// pointwise near-field potential at the origin (gauge of Sec. 5.2.2)
+// Integral over a wall plane of the pointwise near-field kernel Eq. (Gnear)
+// of a unit charge at distance d from it, truncated at r_cut like the near
+// field: (1/(2 eps)) int_d^{r_cut} [erf(r/a1) - erf(r/a2)] dr, written with
+// I(x, a) = int_x^inf erfc(r/a) dr = a (e^{-(x/a)^2}/sqrt(pi) - (x/a) erfc(x/a)).
+__device__ double wall_near_planar(double d, const KP& kp) {
+    d = fabs(d);
+    if (d >= kp.r_cut) return 0.0;
+    auto I = [](double x, double a) {
+        const double u = x / a;
+        return a * (exp(-u * u) * 0.56418958354775628695 - u * erfc(u));
+    };
+    const double a1 = kp.pa1, a2 = kp.pa2, rc = kp.r_cut;
+    return ((I(d, a2) - I(d, a1)) - (I(rc, a2) - I(rc, a1))) / (2.0 * kp.eps);
+}
+
+// pointwise near-field potential at the origin (gauge of Sec. 5.2.2); with
+// wall charges also the per-charge terms of their energy: q phibar_sigma and
+// the near field's planar integrals at z = 0 and z = H (charge and one image
+// per wall, the near field's sources)
 __global__ void k_origin(KP kp) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kp.sigma_on) {
+        double c = 0.0, n0 = 0.0, nH = 0.0;
+        if (k < kp.n) {
+            const double4_32a p = kp.part[k];
+            const double q = p.w, z = p.z, H = kp.H;
+            c = q * kp.wall_phi[k];
+            if (kp.near_on) {
+                n0 = q * ((1.0 - kp.Gb) * wall_near_planar(z, kp) - kp.Gt * wall_near_planar(2.0 * H - z, kp));
+                nH = q * ((1.0 - kp.Gt) * wall_near_planar(H - z, kp) - kp.Gb * wall_near_planar(H + z, kp));
+            }
+        }
+        c = block_sum(c);
+        n0 = block_sum(n0);
+        nH = block_sum(nH);
+        if (threadIdx.x == 0) {
+            const int nb = kp.n_charge_blocks;
+            kp.part_wall[blockIdx.x] = c;
+            kp.part_wall[nb + blockIdx.x] = n0;
+            kp.part_wall[2 * nb + blockIdx.x] = nH;
+        }
+    }
     double v = 0.0;
     if (k < kp.n && kp.near_on) {
         const double4_32a p = kp.part[k];
@@ -2183,11 +2258,188 @@ __global__ void k_assemble(KP kp) {
     if (threadIdx.x == 0) kp.part_u[blockIdx.x] = s;
 }
 
+// U = 1/2 sum q phibar (Eq. (Ufinal)); with wall charges plus the wall term
+// 1/2 int (sigma_b phi(x, y, 0) + sigma_t phi(x, y, H)): for k = 0 the total
+// wall charge times the plane-averaged pointwise potential at the wall (far
+// part from the k = 0 column, near part from the planar sums, gauge B), for
+// k != 0 by Green's reciprocity 1/2 sum q phibar_sigma plus the wall charges'
+// own term fixed when they were set
 __global__ void k_final_energy(KP kp) {
-    double u = 0.0;
-    for (int i = threadIdx.x; i < kp.n_charge_blocks; i += blockDim.x) u += kp.part_u[i];
+    const int nb = kp.n_charge_blocks;
+    double u = 0.0, c = 0.0, n0 = 0.0, nH = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        u += kp.part_u[i];
+        if (kp.sigma_on) {
+            c += kp.part_wall[i];
+            n0 += kp.part_wall[nb + i];
+            nH += kp.part_wall[2 * nb + i];
+        }
+    }
     u = block_sum(u);
-    if (threadIdx.x == 0) kp.scal[4] = 0.5 * u;
+    if (kp.sigma_on) {
+        c = block_sum(c);
+        n0 = block_sum(n0);
+        nH = block_sum(nH);
+    }
+    if (threadIdx.x == 0) {
+        double U = 0.5 * u;
+        if (kp.sigma_on) {
+            const double B = kp.scal[0], area = kp.Lx * kp.Ly;
+            const double phi0 = kp.scal[7] * kp.inv_nxny + B + n0 / area;
+            const double phiH = kp.scal[8] * kp.inv_nxny + B + nH / area;
+            U += 0.5 * (kp.sig_Qb * phi0 + kp.sig_Qt * phiH) + 0.5 * c + kp.sig_self;
+        }
+        kp.scal[4] = U;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// wall charges: set-up kernels (run once per dpslab_plan_set_wall_charge) and
+// the per-solve gather of their correction at the charges
+// ---------------------------------------------------------------------------
+// sigma_b into plane 0 and sigma_t into plane 1 of rho_i (the rest zeroed
+// before), for the forward xy transform
+template <class R>
+__global__ void k_wall_fill(KP kp, const double* sig) {
+    const size_t plane = size_t(kp.ny) * kp.nx;
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < 2 * plane) static_cast<R*>(kp.rho)[i] = R(sig[i]);
+}
+
+// the two transformed planes -> sig_hat (double)
+template <class R>
+__global__ void k_wall_hat(KP kp, double2* hat) {
+    using C = typename Prec<R>::C;
+    const int M = kp.ny * kp.nxh;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 2 * M) {
+        const C v = static_cast<const C*>(kp.spec)[i];
+        hat[i] = make_double2(double(v.x), double(v.y));
+    }
+}
+
+// node values of the wall charges' own correction (Eq. (inphisc) with
+// m_phi = 0, m_E = +sigma_b, -sigma_t) for 0 < k <= pi/h at nodes in
+// [-H_E, H + H_E], zero elsewhere, and zero derivative planes, laid out as
+// the inverse transforms read psi and dpsi/dz
+template <class R>
+__global__ void k_wall_nodes(KP kp, const double2* hat) {
+    using C = typename Prec<R>::C;
+    const int M = kp.ny * kp.nxh;
+    const size_t S = size_t(kp.nz) * M;
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    const int j = int(i / M), col = int(i - size_t(j) * M);
+    C* spec = static_cast<C*>(kp.spec);
+    C zero;
+    zero.x = zero.y = R(0);
+    spec[S + i] = zero;
+    const int iy = col / kp.nxh, ix = col - iy * kp.nxh;
+    const int my = iy < (kp.ny + 1) / 2 ? iy : iy - kp.ny;
+    const double kx = kTwoPi * ix / kp.Lx, ky = kTwoPi * my / kp.Ly;
+    const double k = sqrt(kx * kx + ky * ky), z = kp.zn[j];
+    C out = zero;
+    if (k > 0.0 && k <= kp.kmax && z >= -kp.HE && z <= kp.H + kp.HE) {
+        const double ie = 1.0 / (kp.eps * k);
+        const double2 P = cscale(hat[col], -kp.db * ie);
+        const double2 Q = cscale(hat[M + col], kp.dt * ie);
+        const double ekH = exp(-k * kp.H);
+        const double den = 1.0 - kp.Gb * kp.Gt * ekH * ekH;
+        const double e1 = exp(-k * z), e2 = exp(k * (z - 2.0 * kp.H)), e3 = exp(k * (z - kp.H)), e4 = exp(-k * (z + kp.H));
+        const double2 v = cscale(cadd(cscale(P, -(e1 - kp.Gt * e2)), cscale(Q, e3 - kp.Gb * e4)), 1.0 / den);
+        out.x = R(v.x);
+        out.y = R(v.y);
+    }
+    spec[i] = out;
+}
+
+// phi component of the inverse-transformed field grid -> sig_grid
+template <class R>
+__global__ void k_wall_grid(KP kp, R* grid) {
+    using V4 = typename Prec<R>::V4;
+    const size_t G = size_t(kp.nz) * kp.ny * kp.nx;
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < G) grid[i] = static_cast<const V4*>(kp.fields)[i].x;
+}
+
+// 1/2 int sigma phi_sigma over both walls for k != 0, by Parseval on the
+// half spectrum (single block)
+__global__ void k_wall_self(KP kp, const double2* hat, double* out) {
+    const int M = kp.ny * kp.nxh;
+    double acc = 0.0;
+    for (int col = threadIdx.x; col < M; col += blockDim.x) {
+        const int iy = col / kp.nxh, ix = col - iy * kp.nxh;
+        const int my = iy < (kp.ny + 1) / 2 ? iy : iy - kp.ny;
+        const double kx = kTwoPi * ix / kp.Lx, ky = kTwoPi * my / kp.Ly;
+        const double k = sqrt(kx * kx + ky * ky);
+        if (!(k > 0.0 && k <= kp.kmax)) continue;
+        const double ie = 1.0 / (kp.eps * k);
+        const double2 sb = hat[col], st = hat[M + col];
+        const double2 P = cscale(sb, -kp.db * ie), Q = cscale(st, kp.dt * ie);
+        const double ekH = exp(-k * kp.H);
+        const double den = 1.0 - kp.Gb * kp.Gt * ekH * ekH;
+        // correction at z = 0 and z = H
+        const double2 v0 = cscale(cadd(cscale(P, -(1.0 - kp.Gt * ekH * ekH)), cscale(Q, ekH - kp.Gb * ekH)), 1.0 / den);
+        const double2 vH = cscale(cadd(cscale(P, -(ekH - kp.Gt * ekH)), cscale(Q, 1.0 - kp.Gb * ekH * ekH)), 1.0 / den);
+        const double mult = (ix == 0 || (kp.nx % 2 == 0 && ix == kp.nx / 2)) ? 1.0 : 2.0;
+        acc += mult * (sb.x * v0.x + sb.y * v0.y + st.x * vH.x + st.y * vH.y);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *out = 0.5 * acc * kp.hx * kp.hy * kp.inv_nxny;
+}
+
+// phibar of the wall charges' correction at each charge: the far field's
+// interpolation (Sec. 5.2.2 step 7) of one scalar grid; one warp per charge
+template <class R>
+__global__ void k_wall_cross(KP kp) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R* smi = reinterpret_cast<R*>(smraw);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    R* wx = smi + w * (2 * kMaxSupport + kMaxNz);
+    R* wy = wx + kMaxSupport;
+    R* wzz = wy + kMaxSupport;
+    const int k = blockIdx.x * (blockDim.x >> 5) + w;
+    if (k >= kp.n) return;
+    const R* grid = static_cast<const R*>(kp.sig_grid);
+    const double4_32a p = kp.part[k];
+    const double x = p.x, y = p.y, z = p.z, HE = kp.HE;
+    const int ix0 = int(ceil((x - HE) / kp.hx)), ix1 = int(floor((x + HE) / kp.hx));
+    const int iy0 = int(ceil((y - HE) / kp.hy)), iy1 = int(floor((y + HE) / kp.hy));
+    const int sx = ix1 - ix0 + 1, sy = iy1 - iy0 + 1;
+    int j0 = kp.nz, j1 = -1;
+    for (int j = lane; j < kp.nz; j += 32) {
+        if (fabs(kp.zn[j] - z) <= HE) { j0 = min(j0, j); j1 = max(j1, j); }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        j0 = min(j0, __shfl_xor_sync(0xffffffffu, j0, o));
+        j1 = max(j1, __shfl_xor_sync(0xffffffffu, j1, o));
+    }
+    const int sz = j1 - j0 + 1;
+    const double ig2 = 1.0 / (2.0 * kp.gt * kp.gt);
+    const double s1 = kp.s1norm;
+    for (int i = lane; i < sx; i += 32) {
+        const double d = double(ix0 + i) * kp.hx - x;
+        wx[i] = R(s1 * exp(-d * d * ig2));
+    }
+    for (int i = lane; i < sy; i += 32) {
+        const double d = double(iy0 + i) * kp.hy - y;
+        wy[i] = R(s1 * exp(-d * d * ig2));
+    }
+    for (int i = lane; i < sz; i += 32) {
+        const double d = kp.zn[j0 + i] - z;
+        wzz[i] = R(kp.wz[j0 + i] * (s1 * exp(-d * d * ig2)));
+    }
+    __syncwarp();
+    const R wxy = R(kp.hx * kp.hy);
+    R a = 0;
+    const int sxy = sx * sy;
+    for (int t = lane; t < sz * sxy; t += 32) {
+        const int jz = t / sxy, r = t - jz * sxy, iy = r / sx, ix = r - iy * sx;
+        const size_t g = (size_t(j0 + jz) * kp.ny + wrap_index(iy0 + iy, kp.ny)) * kp.nx + wrap_index(ix0 + ix, kp.nx);
+        a = fma(wxy * wzz[jz] * wy[iy] * wx[ix], grid[g], a);
+    }
+    const double b = warp_sum(double(a));
+    if (lane == 0) kp.wall_phi[k] = b;
 }
 
 }  // namespace
@@ -2222,6 +2474,8 @@ struct dpslab_plan {
     double* h_scal = nullptr;   // pinned
     int* h_status = nullptr;
     int* scan_part = nullptr;     // block sums and offsets of the multi-block scans
+    void* sig_mem = nullptr;      // wall charges: transforms, correction grid, scratch
+    size_t sig_bytes = 0;
     cudaEvent_t done = nullptr;   // end of an enqueued (asynchronous) solve
     bool in_flight = false;
     bool bound = false;           // a workspace is bound (owned, a batch's, or the caller's)
@@ -2320,7 +2574,8 @@ size_t bind_work(dpslab_plan* pl, char* base) {
     kp.part_gauge_near = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
     kp.part_u = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
     kp.part_q = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
-    carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
+    kp.part_wall = carve<double>(cur, 3 * size_t(kp.n_charge_blocks));
+    kp.wall_phi = carve<double>(cur, n);
     kp.scal = carve<double>(cur, 16);
     kp.status = carve<int>(cur, 16);
     pl->scan_part = carve<int>(cur, pl->scan_n);
@@ -2339,6 +2594,7 @@ void release(dpslab_plan* pl) {
         if (e) cudaEventDestroy(e);
     if (pl->tables) cudaFree(pl->tables);
     if (pl->work) cudaFree(pl->work);
+    if (pl->sig_mem) cudaFree(pl->sig_mem);
     if (pl->h_scal) cudaFreeHost(pl->h_scal);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     delete pl;
@@ -2497,7 +2753,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         const size_t N = nz;
         size_t bytes = 0;
         const size_t vec = align_up(N * sizeof(double));
-        bytes += 2 * vec + 4 * align_up(N * N * sizeof(double)) + 11 * vec;
+        bytes += 2 * vec + 4 * align_up(N * N * sizeof(double)) + 12 * vec;
         bytes += align_up(nx * sizeof(double2)) + align_up(ny * sizeof(double2));
         // float copies: cft, tie, tio (together <= 2 N^2) and 14 vectors
         bytes += 3 * align_up(N * N * sizeof(float)) + 14 * align_up(N * sizeof(float));
@@ -2521,7 +2777,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         up(t.cft, kp.cft); up(t.tie, kp.tie); up(t.tio, kp.tio);
         up(t.j2l, kp.j2l); up(t.j2d, kp.j2d); up(t.j2u, kp.j2u);
         up(t.u1, kp.u1); up(t.u2, kp.u2); up(t.v1, kp.v1); up(t.v2, kp.v2);
-        up(t.t0, kp.t0); up(t.tH, kp.tH); up(t.wg, kp.wg);
+        up(t.t0, kp.t0); up(t.tH, kp.tH); up(t.wg, kp.wg); up(t.wgH, kp.wgH);
         double2* tx = carve<double2>(cur, nx);
         double2* ty = carve<double2>(cur, ny);
         cudaMemcpy(tx, t.twx.data(), nx * sizeof(double2), cudaMemcpyHostToDevice);
@@ -2750,6 +3006,112 @@ extern "C" int dpslab_plan_bind_work(dpslab_plan* plan, void* work, int64_t byte
     return DPSLAB_OK;
 }
 
+namespace {
+// forward and inverse xy transforms of the plan's grids, launched as a solve
+// launches them (used by the wall-charge set-up)
+template <class R>
+int xy_transforms(dpslab_plan* pl, const KP& kp, cudaStream_t st, bool inverse) {
+    const int npairs = kp.nz * kp.ny;
+    if (!inverse) {
+        const dim3 gy((kp.nxh + pl->tk_fwd - 1) / pl->tk_fwd, 2 * kp.nz);
+        const int gx = (npairs + pl->px_fwd - 1) / pl->px_fwd;
+        if (pl->p2x) k_fftx_fwd_p2<R><<<gx, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx);
+        else k_fftx_fwd<R><<<gx, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd);
+        if (pl->p2y) k_ffty_fwd_p2<R><<<gy, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny);
+        else k_ffty_fwd<R><<<gy, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd);
+    } else {
+        const dim3 gy((kp.nxh + pl->tk_inv - 1) / pl->tk_inv, kp.nz);
+        const int gx = (npairs + pl->px_inv - 1) / pl->px_inv;
+        if (pl->p2y) k_ffty_inv_p2<R><<<gy, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny);
+        else k_ffty_inv<R><<<gy, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv);
+        if (pl->p2x) k_fftx_inv_p2<R><<<gx, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx);
+        else k_fftx_inv<R><<<gx, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        trace("xy_transforms", e, __LINE__);
+        return DPSLAB_ERR_CUDA;
+    }
+    return DPSLAB_OK;
+}
+
+// transforms of the wall charges, the potential grid of their correction and
+// its own energy term, on the plan's workspace (Eq. (mm2), (mm4), (Ufinal))
+template <class R>
+int wall_setup(dpslab_plan* pl, const double* planes, cudaStream_t st) {
+    KP kp = pl->kp;
+    const int M = kp.ny * kp.nxh;
+    const size_t G = size_t(kp.nz) * kp.ny * kp.nx, P2 = 2 * size_t(kp.ny) * kp.nx;
+    char* base = static_cast<char*>(pl->sig_mem);
+    double2* hat = reinterpret_cast<double2*>(base);
+    R* grid = reinterpret_cast<R*>(base + align_up(2 * size_t(M) * sizeof(double2)));
+    double* tmp = reinterpret_cast<double*>(reinterpret_cast<char*>(grid) + align_up(G * sizeof(R)));
+    double* self = tmp + P2;
+    DPS_CUDA(cudaMemcpyAsync(tmp, planes, P2 * sizeof(double), cudaMemcpyHostToDevice, st));
+    DPS_CUDA(cudaMemsetAsync(kp.rho, 0, 2 * G * sizeof(R), st));
+    k_wall_fill<R><<<unsigned((P2 + 255) / 256), 256, 0, st>>>(kp, tmp);
+    if (int rc = xy_transforms<R>(pl, kp, st, false)) return rc;
+    k_wall_hat<R><<<(2 * M + 255) / 256, 256, 0, st>>>(kp, hat);
+    k_wall_nodes<R><<<unsigned((size_t(kp.nz) * M + 255) / 256), 256, 0, st>>>(kp, hat);
+    if (int rc = xy_transforms<R>(pl, kp, st, true)) return rc;
+    k_wall_grid<R><<<unsigned((G + 255) / 256), 256, 0, st>>>(kp, grid);
+    k_wall_self<<<1, 1024, 0, st>>>(kp, hat, self);
+    DPS_CUDA(cudaGetLastError());
+    double h[3];
+    DPS_CUDA(cudaMemcpyAsync(&h[0], &hat[0].x, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DPS_CUDA(cudaMemcpyAsync(&h[1], &hat[M].x, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DPS_CUDA(cudaMemcpyAsync(&h[2], self, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DPS_CUDA(cudaStreamSynchronize(st));
+    pl->kp.sig_hat = hat;
+    pl->kp.sig_grid = grid;
+    pl->kp.sig_Qb = kp.hx * kp.hy * h[0];
+    pl->kp.sig_Qt = kp.hx * kp.hy * h[1];
+    pl->kp.sig_self = h[2];
+    pl->kp.sigma_on = 1;
+    return DPSLAB_OK;
+}
+}  // namespace
+
+extern "C" int dpslab_plan_set_wall_charge(dpslab_plan* plan, const double* sigma_b, const double* sigma_t,
+                                           void* stream) {
+    if (!plan || plan->in_flight || !plan->bound) return DPSLAB_ERR_INVALID_ARG;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    KP& kp = plan->kp;
+    if (!sigma_b && !sigma_t) {
+        kp.sigma_on = 0;
+        if (plan->sig_mem) {
+            DPS_CUDA(cudaStreamSynchronize(st));
+            cudaFree(plan->sig_mem);
+            plan->sig_mem = nullptr;
+            plan->device_bytes -= int64_t(plan->sig_bytes);
+            plan->sig_bytes = 0;
+        }
+        return DPSLAB_OK;
+    }
+    if ((sigma_b && kp.metal_b) || (sigma_t && kp.metal_t)) return DPSLAB_ERR_UNSUPPORTED;
+    const size_t P1 = size_t(kp.ny) * kp.nx, G = size_t(kp.nz) * P1, M = size_t(kp.ny) * kp.nxh;
+    std::vector<double> planes(2 * P1, 0.0);
+    for (size_t i = 0; i < P1; ++i) {
+        const double b = sigma_b ? sigma_b[i] : 0.0, t = sigma_t ? sigma_t[i] : 0.0;
+        if (!std::isfinite(b) || !std::isfinite(t)) return DPSLAB_ERR_INVALID_ARG;
+        planes[i] = b;
+        planes[P1 + i] = t;
+    }
+    if (!plan->sig_mem) {
+        const size_t bytes = align_up(2 * M * sizeof(double2)) + align_up(G * plan->rsz) + align_up(2 * P1 * sizeof(double)) +
+                             align_up(sizeof(double));
+        if (cudaMalloc(&plan->sig_mem, bytes) != cudaSuccess) {
+            plan->sig_mem = nullptr;
+            return DPSLAB_ERR_CUDA;
+        }
+        plan->sig_bytes = bytes;
+        plan->device_bytes += int64_t(bytes);
+    }
+    kp.sigma_on = 0;
+    return kp.mixed ? wall_setup<float>(plan, planes.data(), st) : wall_setup<double>(plan, planes.data(), st);
+}
+
 extern "C" int dpslab_plan_footprint(const dpslab_params* p, int64_t max_n, int64_t* bytes) {
     if (!bytes) return DPSLAB_ERR_INVALID_ARG;
     *bytes = 0;
@@ -2912,6 +3274,7 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         else LAUNCH(k_fftx_inv<float><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(9);
         LAUNCH(k_interp_f32<<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
+        if (kp.sigma_on) LAUNCH(k_wall_cross<float><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     } else {
         if (pl->p2x) LAUNCH(k_fftx_fwd_p2<double><<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
         else LAUNCH(k_fftx_fwd<double><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
@@ -2930,6 +3293,7 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         else LAUNCH(k_fftx_inv<double><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(9);
         LAUNCH(k_interp<double><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
+        if (kp.sigma_on) LAUNCH(k_wall_cross<double><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     }
     mark(10);
     if (kp.near_on) {
@@ -2956,7 +3320,11 @@ int collect(dpslab_plan* pl, double* U) {
     if (*pl->h_status & kStatusCapacity) return DPSLAB_ERR_CAPACITY;
     if (*pl->h_status & kStatusTimeout) return DPSLAB_ERR_CUDA;
     if (*pl->h_status) return DPSLAB_ERR_OUT_OF_SLAB;
-    const double sq = pl->h_scal[5], saq = pl->h_scal[6];
+    double sq = pl->h_scal[5], saq = pl->h_scal[6];
+    if (pl->kp.sigma_on) {   // Eq. (elecneu): charges and wall charges together
+        sq += pl->kp.sig_Qb + pl->kp.sig_Qt;
+        saq += std::fabs(pl->kp.sig_Qb) + std::fabs(pl->kp.sig_Qt);
+    }
     if (std::fabs(sq) > 1e-12 * saq) return DPSLAB_ERR_NOT_NEUTRAL;
     return DPSLAB_OK;
 }

@@ -78,6 +78,7 @@ def lib():
             "dpslab_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "dpslab_plan_footprint": (ctypes.c_int, [P, i64, ctypes.POINTER(i64)]),
             "dpslab_plan_create_unbound": (ctypes.c_int, [P, i64, ctypes.POINTER(vp)]),
+            "dpslab_plan_set_wall_charge": (ctypes.c_int, [vp, vp, vp, vp]),
             "dpslab_plan_work_bytes": (i64, [vp]),
             "dpslab_plan_bind_work": (ctypes.c_int, [vp, vp, i64]),
             "dpslab_solve_enqueue": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, vp]),
@@ -173,6 +174,27 @@ class Plan:
         self.device_bytes = lib().dpslab_plan_device_bytes(self._h)
         self.work_bytes = lib().dpslab_plan_work_bytes(self._h)
         self.work = None
+
+    def set_wall_charge(self, sigma_b=None, sigma_t=None, stream=None):
+        """dpslab_plan_set_wall_charge: numpy arrays (ny, nx) of the wall
+        charge densities at (i hx, j hy) ([j, i]), or None."""
+        import numpy as np
+        import torch
+        keep = []
+
+        def ptr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            d = self.derived
+            if a.shape != (d["ny"], d["nx"]):
+                raise ValueError(f"wall charge grid must be (ny, nx) = ({d['ny']}, {d['nx']})")
+            keep.append(a)
+            return a.ctypes.data
+
+        st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(lib().dpslab_plan_set_wall_charge(self._h, ptr(sigma_b), ptr(sigma_t), st))
+        self.device_bytes = lib().dpslab_plan_device_bytes(self._h)
 
     def bind_work(self, work):
         """dpslab_plan_bind_work: `work` a CUDA uint8 tensor of at least
