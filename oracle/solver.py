@@ -4,8 +4,10 @@ Problem (Sec. 2): N Gaussian charges (Eq. (gcharge)) at z_k = (x_k, y_k, z_k)
 with 0 < z_k < H, periodic on [0, Lx) x [0, Ly), permittivity eps in the
 slab, eps_b below z = 0, eps_t above z = H. Outputs: the averaged potential
 phibar_k (Eq. (pbar)), the force F_k = q_k Ebar(z_k) (Eq. (fqE)) and the
-energy U = 1/2 sum q_k phibar_k (Eq. (Ufinal), no wall charge). The gauge is
-phi(0) = 0 (Eq. (phi00)).
+energy U = 1/2 sum q_k phibar_k plus, with wall charges sigma_b, sigma_t,
+1/2 int (sigma_b phi(x, y, 0) + sigma_t phi(x, y, H)) (Eq. (Ufinal); see
+wall_charge_energy). The gauge is phi(0) = 0 (Eq. (phi00)). This module is
+test infrastructure: only tests and the benchmark's CPU baseline use it.
 
 Far field, Sec. 5.2.2 steps 1-7 (figure "ffsolve"):
  1. C_over = charges within 2 H_E of a wall (z <= 2H_E or z >= H - 2H_E),
