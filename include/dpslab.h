@@ -39,7 +39,7 @@ extern "C" {
 /* ------------------------------------------------------------------ codes */
 #define DPSLAB_OK                     0
 #define DPSLAB_ERR_INVALID_ARG       -1  /* a parameter is out of range or a pointer is NULL */
-#define DPSLAB_ERR_NOT_NEUTRAL       -2  /* |sum q| > 1e-12 sum |q| (Eq. (elecneu), no wall charge) */
+#define DPSLAB_ERR_NOT_NEUTRAL       -2  /* |sum q + wall charges| > 1e-12 (sum |q| + |wall charges|) (Eq. (elecneu)) */
 #define DPSLAB_ERR_OUT_OF_SLAB       -3  /* a charge has z outside (0, H) or a non-finite value */
 #define DPSLAB_ERR_CUTOFF_TOO_LARGE  -4  /* r_cut >= min(Lx, Ly)/2: nearest-image rule of Sec. 4.2 fails */
 #define DPSLAB_ERR_SPLIT_CONSTRAINT  -5  /* strict mode: 2 H_E >= H or r_cut >= H (Sec. 5.3, Table (ewconstraints)) */
@@ -48,6 +48,7 @@ extern "C" {
 #define DPSLAB_ERR_NO_DEVICE         -8  /* no usable CUDA device */
 #define DPSLAB_ERR_GRID              -9  /* grid too small for the Gaussian support, or a size the kernels do not support */
 #define DPSLAB_ERR_UNSUPPORTED      -10  /* option not built into this library */
+#define DPSLAB_ERR_BD_REJECTED      -11  /* every proposal of a Brownian-dynamics step left the slab */
 #define DPSLAB_PENDING                1  /* dpslab_solve_poll: the enqueued solve has not finished yet */
 
 /* ------------------------------------------------------------- precision */
@@ -163,6 +164,61 @@ int64_t dpslab_plan_device_bytes(const dpslab_plan* plan);
  * DPSLAB_ERR_CUDA.
  */
 int dpslab_plan_set_wall_charge(dpslab_plan* plan, const double* sigma_b, const double* sigma_t, void* stream);
+
+/*
+ * Brownian dynamics of the ions (Sec. 7.1): one step of Eq. (leimkuhler)
+ *   z^{n+1} = z^n + mu (F_steric(z^n) + F(z^n)) dt + sqrt(kT mu dt / 2) (W^n + W^{n+1})
+ * with F the electrostatic force of a solve with this plan (Eq. (fqE)) and
+ * F_steric the capped Lennard-Jones repulsion of Eq. (steric), (lj) between
+ * ions (nearest periodic image in x, y) and between each ion and its own
+ * mirror image in each wall.
+ */
+typedef struct dpslab_bd_params {
+    double dt;          /* time step */
+    double mu;          /* scalar mobility */
+    double kT;          /* thermal energy */
+    double a;           /* ion radius: the repulsion acts below 2^(1/p) 2a */
+    double U0;          /* strength of Eq. (lj) */
+    double r_m;         /* below r_m the force is F_LJ(r_m) */
+    int p;              /* exponent of Eq. (lj), >= 1 */
+    int max_retries;    /* proposals per step, 1 .. DPSLAB_BD_MAX_RETRIES */
+    double max_disp;    /* > 0: an ion's displacement per step is capped at this length */
+    uint64_t seed;      /* key of the noise generator */
+} dpslab_bd_params;
+
+#define DPSLAB_BD_MAX_RETRIES 32
+
+/*
+ * The noise W_i = (W_x, W_y, W_z) of ion i at (step, retry): Philox4x32-10
+ * (Salmon et al., SC 2011) with key = seed and counter = (i, step low word,
+ * step high word, retry); its four words u_k = (w_k + 1/2) 2^-32 give two
+ * Box-Muller pairs, of which the first three numbers are used. W^{n+1} of step
+ * n is drawn with step index n + 1. This call writes W^0 (step 0, retry 0)
+ * for n ions into the device array W [n][3] on `stream`.
+ */
+int dpslab_bd_init_noise(uint64_t seed, int64_t n, double* W, void* stream);
+
+/*
+ * Enqueue step `step` (n -> n + 1) on `stream` and return at once; completion
+ * and errors through dpslab_solve_poll (the plan is in flight until then).
+ *   pos    device [n][3] positions z^n, replaced by z^{n+1} (x, y wrapped into
+ *          the box) when the step is accepted
+ *   q      device [n] charges (electroneutral with any wall charges)
+ *   W      device [n][3] noise W^n, replaced by the accepted W^{n+1}
+ *   force  device [n][3] receives the electrostatic force at z^n, or NULL
+ * The solve at z^n, the steric forces (on the solve's cell list) and up to
+ * max_retries proposals run as kernels in stream order. A proposal with any
+ * ion outside 0 < z < H is discarded and the next one (new W^{n+1}) tried;
+ * if all are discarded nothing changes and the poll returns
+ * DPSLAB_ERR_BD_REJECTED. Requires the near field (xi finite) with
+ * 2^(1/p) 2a <= r_cut; the energy is computed as in dpslab_solve.
+ * Errors at enqueue: DPSLAB_ERR_INVALID_ARG, DPSLAB_ERR_CAPACITY, DPSLAB_ERR_CUDA.
+ */
+int dpslab_bd_step_enqueue(dpslab_plan* plan, const dpslab_bd_params* bp, int64_t n, double* pos, const double* q,
+                           double* W, uint64_t step, double* force, void* stream);
+
+/* Proposals discarded by the last completed step (0 .. max_retries). */
+int dpslab_bd_last_retries(const dpslab_plan* plan);
 
 /*
  * A plan without a workspace: tables and derived parameters only (a few MB);

@@ -97,15 +97,16 @@ def steric_forces(pos, P, bp):
     return F
 
 
-def step(pos, q, W, n_step, P, bp, force=None):
+def step(pos, q, W, n_step, P, bp, force=None, sigma_b=None, sigma_t=None):
     """One step of Eq. (leimkuhler) from step n_step. pos (n, 3), W = W^n
     (n, 3). bp: dict with dt, mu, kT, a, U0, p, r_m, max_disp (<= 0: none),
     max_retries (>= 1), seed. force: the electrostatic force at pos, or None
-    to compute it with the oracle solve. Returns (pos', W', retries used,
-    ok); on failure pos and W unchanged."""
+    to compute it with the oracle solve (with the wall charges sigma_b,
+    sigma_t if given). Returns (pos', W', retries used, ok); on failure pos
+    and W unchanged."""
     pos = np.asarray(pos, dtype=np.float64)
     if force is None:
-        force = solver.solve(pos, q, P)["force"]
+        force = solver.solve(pos, q, P, sigma_b=sigma_b, sigma_t=sigma_t)["force"]
     drift = bp["mu"] * (force + steric_forces(pos, P, bp)) * bp["dt"]
     amp = np.sqrt(bp["kT"] * bp["mu"] * bp["dt"] / 2.0)
     for r in range(bp["max_retries"]):

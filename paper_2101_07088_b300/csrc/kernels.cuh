@@ -14,6 +14,7 @@ enum : int {
     kStatusNonFinite = 2,
     kStatusCapacity = 4,      // a bucketed-source buffer would overflow (not reachable within the bound)
     kStatusTimeout = 8,       // a bounded wait on the tensor-core pipeline gave up
+    kStatusRejected = 16,     // every proposal of a Brownian-dynamics step left the slab
 };
 
 // One spreading source with its support precomputed: grid indices
@@ -163,6 +164,9 @@ struct KP {
     const double* wgH;        // gauge weights at z = H
     double sig_Qb, sig_Qt;    // total wall charges int sigma dx dy
     double sig_self;          // 1/2 int sigma phi_sigma over both walls (k != 0)
+    // Brownian dynamics scratch: steric forces, proposal, proposed noise [n][3]; flags per retry
+    double *bd_steric, *bd_prop, *bd_wnew;
+    int* bd_flags;
     int* status;
     int n_col_blocks, n_charge_blocks;
     // user outputs

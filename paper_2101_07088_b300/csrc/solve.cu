@@ -2576,6 +2576,10 @@ size_t bind_work(dpslab_plan* pl, char* base) {
     kp.part_q = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
     kp.part_wall = carve<double>(cur, 3 * size_t(kp.n_charge_blocks));
     kp.wall_phi = carve<double>(cur, n);
+    kp.bd_steric = carve<double>(cur, 3 * n);
+    kp.bd_prop = carve<double>(cur, 3 * n);
+    kp.bd_wnew = carve<double>(cur, 3 * n);
+    kp.bd_flags = carve<int>(cur, DPSLAB_BD_MAX_RETRIES);
     kp.scal = carve<double>(cur, 16);
     kp.status = carve<int>(cur, 16);
     pl->scan_part = carve<int>(cur, pl->scan_n);
@@ -3112,6 +3116,235 @@ extern "C" int dpslab_plan_set_wall_charge(dpslab_plan* plan, const double* sigm
     return kp.mixed ? wall_setup<float>(plan, planes.data(), st) : wall_setup<double>(plan, planes.data(), st);
 }
 
+// ---------------------------------------------------------------------------
+// Brownian dynamics, Sec. 7.1: Eq. (leimkuhler), (steric), (lj)
+// ---------------------------------------------------------------------------
+namespace {
+int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, double* phi, double* force,
+            cudaStream_t st);
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;   // Philox4x32 multipliers
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;   // key increments
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011)
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
+        }
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c[0]), lo0 = kPhiloxM0 * c[0];
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c[2]), lo1 = kPhiloxM1 * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// W_i at (step, retry): the generator's four words as uniforms (w + 1/2) 2^-32,
+// two Box-Muller pairs, the first three numbers
+__device__ __forceinline__ double3 bd_normals(uint32_t i, uint64_t step, uint32_t retry, uint64_t seed) {
+    uint32_t c[4] = {i, uint32_t(step), uint32_t(step >> 32), retry};
+    philox4x32_10(c, uint32_t(seed), uint32_t(seed >> 32));
+    const double s = 2.3283064365386962890625e-10;   // 2^-32
+    const double u0 = (double(c[0]) + 0.5) * s, u1 = (double(c[1]) + 0.5) * s;
+    const double u2 = (double(c[2]) + 0.5) * s, u3 = (double(c[3]) + 0.5) * s;
+    const double r1 = sqrt(-2.0 * log(u0)), r2 = sqrt(-2.0 * log(u2));
+    return make_double3(r1 * cos(kTwoPi * u1), r1 * sin(kTwoPi * u1), r2 * cos(kTwoPi * u3));
+}
+
+struct BdConst {
+    double dt, mu, amp, a2, U0, r_m, rs2, max_disp;
+    int p, R;
+    uint64_t seed, step;
+};
+
+// Eq. (steric): F_LJ(max(r, r_m)) for r <= 2^(1/p) 2a (caller checks the range)
+__device__ __forceinline__ double bd_steric_mag(double r, const BdConst& b) {
+    const double rr = fmax(r, b.r_m);
+    double s = 1.0;
+    const double t = b.a2 / rr;
+    for (int k = 0; k < b.p; ++k) s *= t;
+    return 4.0 * b.U0 * b.p / rr * (2.0 * s * s - s);
+}
+
+__global__ void k_bd_init(uint64_t seed, int n, double* W) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double3 w = bd_normals(uint32_t(i), 0, 0, seed);
+    W[3 * i] = w.x;
+    W[3 * i + 1] = w.y;
+    W[3 * i + 2] = w.z;
+}
+
+// steric forces at z^n on the solve's cell list (cells are at least r_cut >=
+// 2^(1/p) 2a wide), plus each ion's own wall images
+__global__ void k_bd_steric(KP kp, BdConst b) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= kp.n) return;
+    const double4_32a t = kp.sorted[s];
+    const int cx = min(kp.ncx - 1, max(0, int(t.x / kp.cwx)));
+    const int cy = min(kp.ncy - 1, max(0, int(t.y / kp.cwy)));
+    const int cz = min(kp.ncz - 1, max(0, int(t.z / kp.cwz)));
+    const int nxc = kp.ncx >= 3 ? 3 : kp.ncx, nyc = kp.ncy >= 3 ? 3 : kp.ncy;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    for (int zc = max(0, cz - 1); zc <= min(kp.ncz - 1, cz + 1); ++zc) {
+        for (int oy = 0; oy < nyc; ++oy) {
+            const int yc = kp.ncy >= 3 ? wrap_index(cy - 1 + oy, kp.ncy) : oy;
+            for (int ox = 0; ox < nxc; ++ox) {
+                const int xc = kp.ncx >= 3 ? wrap_index(cx - 1 + ox, kp.ncx) : ox;
+                const int cell = cell_index(kp, xc, yc, zc);
+                for (int u = kp.cell_start[cell]; u < kp.cell_start[cell + 1]; ++u) {
+                    if (u == s) continue;
+                    const double4_32a o = kp.sorted[u];
+                    const double dx = min_image(t.x - o.x, kp.Lx), dy = min_image(t.y - o.y, kp.Ly), dz = t.z - o.z;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 <= b.rs2) {
+                        const double r = sqrt(r2), f = bd_steric_mag(r, b) / r;
+                        fx = fma(f, dx, fx);
+                        fy = fma(f, dy, fy);
+                        fz = fma(f, dz, fz);
+                    }
+                }
+            }
+        }
+    }
+    const double db = 2.0 * t.z, dt = 2.0 * (kp.H - t.z);
+    if (db * db <= b.rs2) fz += bd_steric_mag(db, b);
+    if (dt * dt <= b.rs2) fz -= bd_steric_mag(dt, b);
+    const int k = kp.sorted_idx[s];
+    kp.bd_steric[3 * k] = fx;
+    kp.bd_steric[3 * k + 1] = fy;
+    kp.bd_steric[3 * k + 2] = fz;
+}
+
+__device__ __forceinline__ bool bd_skip(const KP& kp, int r) {
+    if (*kp.status & (kStatusOutOfSlab | kStatusNonFinite)) return true;   // the solve refused z^n
+    for (int rr = 0; rr < r; ++rr)
+        if (kp.bd_flags[rr] == 0) return true;                             // an earlier proposal was accepted
+    return false;
+}
+
+// proposal r of Eq. (leimkuhler) from the sanitised z^n; flags it if an ion leaves 0 < z < H
+__global__ void k_bd_propose(KP kp, BdConst b, const double* F, const double* W, int r) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kp.n || bd_skip(kp, r)) return;
+    const double4_32a p = kp.part[i];
+    const double3 wn = bd_normals(uint32_t(i), b.step + 1, uint32_t(r), b.seed);
+    const double* fs = kp.bd_steric + 3 * i;
+    double dx = b.mu * (F[3 * i] + fs[0]) * b.dt + b.amp * (W[3 * i] + wn.x);
+    double dy = b.mu * (F[3 * i + 1] + fs[1]) * b.dt + b.amp * (W[3 * i + 1] + wn.y);
+    double dz = b.mu * (F[3 * i + 2] + fs[2]) * b.dt + b.amp * (W[3 * i + 2] + wn.z);
+    if (b.max_disp > 0.0) {
+        const double nrm = sqrt(dx * dx + dy * dy + dz * dz);
+        if (nrm > b.max_disp) {
+            const double sc = b.max_disp / nrm;
+            dx *= sc;
+            dy *= sc;
+            dz *= sc;
+        }
+    }
+    const double z = p.z + dz;
+    kp.bd_prop[3 * i] = np_mod(p.x + dx, kp.Lx);
+    kp.bd_prop[3 * i + 1] = np_mod(p.y + dy, kp.Ly);
+    kp.bd_prop[3 * i + 2] = z;
+    kp.bd_wnew[3 * i] = wn.x;
+    kp.bd_wnew[3 * i + 1] = wn.y;
+    kp.bd_wnew[3 * i + 2] = wn.z;
+    if (!(z > 0.0 && z < kp.H)) atomicOr(&kp.bd_flags[r], 1);
+}
+
+// accept proposal r if no ion left the slab (and none before was accepted)
+__global__ void k_bd_commit(KP kp, BdConst b, double* pos, double* W, int r) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bd_skip(kp, r)) return;
+    if (kp.bd_flags[r] != 0) {
+        if (r == b.R - 1 && i == 0) {
+            atomicOr(kp.status, kStatusRejected);
+            kp.scal[9] = double(b.R);
+        }
+        return;
+    }
+    if (i == 0) kp.scal[9] = double(r);
+    if (i >= kp.n) return;
+    for (int c = 0; c < 3; ++c) {
+        pos[3 * i + c] = kp.bd_prop[3 * i + c];
+        W[3 * i + c] = kp.bd_wnew[3 * i + c];
+    }
+}
+}  // namespace
+
+extern "C" int dpslab_bd_init_noise(uint64_t seed, int64_t n, double* W, void* stream) {
+    if (!W || n < 1 || n > (int64_t(1) << 31) - 1) return DPSLAB_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_bd_init<<<unsigned((n + 255) / 256), 256, 0, st>>>(seed, int(n), W);
+    DPS_CUDA(cudaGetLastError());
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_bd_step_enqueue(dpslab_plan* plan, const dpslab_bd_params* bp, int64_t n, double* pos,
+                                      const double* q, double* W, uint64_t step, double* force, void* stream) {
+    if (!plan || !bp || !pos || !q || !W || n < 1 || plan->in_flight || !plan->bound) return DPSLAB_ERR_INVALID_ARG;
+    if (n > plan->max_n) return DPSLAB_ERR_CAPACITY;
+    const KP& kp0 = plan->kp;
+    const double rs = std::pow(2.0, 1.0 / std::max(1, bp->p)) * 2.0 * bp->a;
+    if (!(bp->dt > 0.0) || !(bp->mu > 0.0) || !(bp->kT >= 0.0) || !(bp->a > 0.0) || !(bp->U0 >= 0.0) ||
+        !(bp->r_m > 0.0) || bp->p < 1 || bp->max_retries < 1 || bp->max_retries > DPSLAB_BD_MAX_RETRIES ||
+        !(bp->max_disp >= 0.0) || !kp0.near_on || rs > kp0.r_cut)
+        return DPSLAB_ERR_INVALID_ARG;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    if (!plan->done) DPS_CUDA(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* F = force ? force : plan->d_force;
+    const int prof = plan->profiling;
+    plan->profiling = 0;
+    int rc = enqueue(plan, n, pos, q, nullptr, F, st);
+    plan->profiling = prof;
+    if (rc) return rc;
+    KP kp = plan->kp;
+    kp.n = int(n);
+    kp.pos = pos;
+    kp.q = q;
+    BdConst b;
+    b.dt = bp->dt;
+    b.mu = bp->mu;
+    b.amp = std::sqrt(bp->kT * bp->mu * bp->dt / 2.0);
+    b.a2 = 2.0 * bp->a;
+    b.U0 = bp->U0;
+    b.r_m = bp->r_m;
+    b.rs2 = rs * rs;
+    b.max_disp = bp->max_disp;
+    b.p = bp->p;
+    b.R = bp->max_retries;
+    b.seed = bp->seed;
+    b.step = step;
+    const int nb = int((n + 255) / 256);
+    DPS_CUDA(cudaMemsetAsync(kp.bd_flags, 0, DPSLAB_BD_MAX_RETRIES * sizeof(int), st));
+    k_bd_steric<<<nb, 256, 0, st>>>(kp, b);
+    for (int r = 0; r < b.R; ++r) {
+        k_bd_propose<<<nb, 256, 0, st>>>(kp, b, F, W, r);
+        k_bd_commit<<<nb, 256, 0, st>>>(kp, b, pos, W, r);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        trace("bd kernels", e, __LINE__);
+        return DPSLAB_ERR_CUDA;
+    }
+    plan->launches += 1 + 2 * b.R;
+    DPS_CUDA(cudaMemcpyAsync(plan->h_scal, kp.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DPS_CUDA(cudaMemcpyAsync(plan->h_status, kp.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DPS_CUDA(cudaEventRecord(plan->done, st));
+    plan->last_n = n;
+    plan->in_flight = true;
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_bd_last_retries(const dpslab_plan* plan) {
+    return plan ? int(plan->h_scal[9]) : 0;
+}
+
 extern "C" int dpslab_plan_footprint(const dpslab_params* p, int64_t max_n, int64_t* bytes) {
     if (!bytes) return DPSLAB_ERR_INVALID_ARG;
     *bytes = 0;
@@ -3168,6 +3401,7 @@ extern "C" const char* dpslab_strerror(int code) {
         case DPSLAB_ERR_GRID: return "grid too small for the Gaussian support or unsupported size";
         case DPSLAB_ERR_UNSUPPORTED: return "unsupported option";
         case DPSLAB_PENDING: return "the solve has not finished yet";
+        case DPSLAB_ERR_BD_REJECTED: return "every proposal of the Brownian-dynamics step left the slab";
         default: return "unknown error";
     }
 }
@@ -3319,6 +3553,7 @@ int collect(dpslab_plan* pl, double* U) {
     if (U) *U = pl->h_scal[4];
     if (*pl->h_status & kStatusCapacity) return DPSLAB_ERR_CAPACITY;
     if (*pl->h_status & kStatusTimeout) return DPSLAB_ERR_CUDA;
+    if (*pl->h_status & kStatusRejected) return DPSLAB_ERR_BD_REJECTED;
     if (*pl->h_status) return DPSLAB_ERR_OUT_OF_SLAB;
     double sq = pl->h_scal[5], saq = pl->h_scal[6];
     if (pl->kp.sigma_on) {   // Eq. (elecneu): charges and wall charges together

@@ -18,9 +18,10 @@ OK = 0
 ERRORS = {
     -1: "INVALID_ARG", -2: "NOT_NEUTRAL", -3: "OUT_OF_SLAB", -4: "CUTOFF_TOO_LARGE",
     -5: "SPLIT_CONSTRAINT", -6: "CAPACITY", -7: "CUDA", -8: "NO_DEVICE", -9: "GRID", -10: "UNSUPPORTED",
+    -11: "BD_REJECTED",
 }
 (ERR_INVALID_ARG, ERR_NOT_NEUTRAL, ERR_OUT_OF_SLAB, ERR_CUTOFF_TOO_LARGE, ERR_SPLIT_CONSTRAINT, ERR_CAPACITY,
- ERR_CUDA, ERR_NO_DEVICE, ERR_GRID, ERR_UNSUPPORTED) = range(-1, -11, -1)
+ ERR_CUDA, ERR_NO_DEVICE, ERR_GRID, ERR_UNSUPPORTED, ERR_BD_REJECTED) = range(-1, -12, -1)
 PENDING = 1                          # DPSLAB_PENDING
 FP64, MIXED, MIXED_SIMT = 0, 1, 2   # DPSLAB_FP64, DPSLAB_MIXED, DPSLAB_MIXED_SIMT
 NSTAGES = 12
@@ -79,6 +80,10 @@ def lib():
             "dpslab_plan_footprint": (ctypes.c_int, [P, i64, ctypes.POINTER(i64)]),
             "dpslab_plan_create_unbound": (ctypes.c_int, [P, i64, ctypes.POINTER(vp)]),
             "dpslab_plan_set_wall_charge": (ctypes.c_int, [vp, vp, vp, vp]),
+            "dpslab_bd_init_noise": (ctypes.c_int, [ctypes.c_uint64, i64, vp, vp]),
+            "dpslab_bd_step_enqueue": (ctypes.c_int, [vp, ctypes.POINTER(BdParams), i64, vp, vp, vp, ctypes.c_uint64,
+                                                      vp, vp]),
+            "dpslab_bd_last_retries": (ctypes.c_int, [vp]),
             "dpslab_plan_work_bytes": (i64, [vp]),
             "dpslab_plan_bind_work": (ctypes.c_int, [vp, vp, i64]),
             "dpslab_solve_enqueue": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, vp]),
@@ -148,6 +153,26 @@ def near_field_static(params, pos, q, out, stream=None, check=True):
     return rc
 
 
+class BdParams(ctypes.Structure):
+    """dpslab_bd_params (Brownian dynamics, Sec. 7.1)."""
+    _fields_ = [("dt", ctypes.c_double), ("mu", ctypes.c_double), ("kT", ctypes.c_double),
+                ("a", ctypes.c_double), ("U0", ctypes.c_double), ("r_m", ctypes.c_double),
+                ("p", ctypes.c_int), ("max_retries", ctypes.c_int), ("max_disp", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+def bd_params(dt, mu, kT, a, U0, r_m, p, max_retries=8, max_disp=0.0, seed=0):
+    return BdParams(float(dt), float(mu), float(kT), float(a), float(U0), float(r_m), int(p), int(max_retries),
+                    float(max_disp), int(seed))
+
+
+def bd_init_noise(seed, W, stream=None):
+    """dpslab_bd_init_noise: W^0 into the CUDA float64 tensor W [n, 3]."""
+    import torch
+    st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(lib().dpslab_bd_init_noise(int(seed), W.shape[0], W.data_ptr(), st))
+
+
 def plan_bytes(params, max_n):
     """dpslab_plan_footprint: device bytes a plan for (params, max_n) takes."""
     p = _as_params(params)
@@ -174,6 +199,26 @@ class Plan:
         self.device_bytes = lib().dpslab_plan_device_bytes(self._h)
         self.work_bytes = lib().dpslab_plan_work_bytes(self._h)
         self.work = None
+
+    def bd_enqueue(self, bp, pos, q, W, step, force=None, stream=None):
+        """dpslab_bd_step_enqueue: one Brownian-dynamics step on `stream`
+        (pos and W updated in place when accepted); finish with poll()."""
+        import torch
+        st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(lib().dpslab_bd_step_enqueue(self._h, ctypes.byref(bp), q.shape[0], pos.data_ptr(), q.data_ptr(),
+                                            W.data_ptr(), int(step),
+                                            force.data_ptr() if force is not None else None, st))
+
+    def bd_step(self, bp, pos, q, W, step, force=None, stream=None, check=True):
+        """One step, waited for: returns (code, retries used)."""
+        self.bd_enqueue(bp, pos, q, W, step, force, stream)
+        while True:
+            code, _ = self.poll()
+            if code != PENDING:
+                break
+        if check:
+            _check(code)
+        return code, lib().dpslab_bd_last_retries(self._h)
 
     def set_wall_charge(self, sigma_b=None, sigma_t=None, stream=None):
         """dpslab_plan_set_wall_charge: numpy arrays (ny, nx) of the wall
