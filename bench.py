@@ -301,7 +301,11 @@ def bench_batch(args):
 
 
 SERVE_WORKLOADS = {"c5_serve1000": dict(replicas=1000, seed=4, rate=20000.0, per_step=100, nstreams=8,
-                                         budget_frac=0.6)}
+                                         budget_frac=0.6, bd=True)}
+# Brownian dynamics of the served replicas (Sec. 7.1): ions of radius 1/2 in
+# units of the Gaussian width, soft cap at r_m = 2a, one hundredth of the
+# diffusive time per step
+SERVE_BD = dict(dt=0.01, mu=1.0, kT=1.0, a=0.5, U0=1.0, r_m=1.0, p=6, max_retries=8)
 
 
 def bench_serve(args):
@@ -310,7 +314,9 @@ def bench_serve(args):
     the 2^20-charge workload, 2 grid points per width, N_z from the paper's
     rule), requests for uniformly drawn replicas arriving as a Poisson stream
     of 20,000 per second (far above what one device serves: the run is in
-    overload and shows queueing and admission). Replica plans are registered
+    overload and shows queueing and admission). Each request is one
+    Brownian-dynamics step of its replica (Eq. (leimkuhler): the solve, the
+    steric forces, the update), so replicas move. Replica plans are registered
     up front; workspaces are admitted under a budget of 60% of the free
     device memory. `warmup` x 100 requests are served first (filling the
     resident set), then `steps` x 100 requests are timed. Reports charges/s,
@@ -326,13 +332,19 @@ def bench_serve(args):
     build.build()
     dev = torch.device("cuda:0")
     reps = synth.serve_replicas(cfg["replicas"], cfg["seed"])
-    # one input set per replica (a replica has one solve in flight at a time)
-    bufs = []
+    # one state per replica (a replica has one solve in flight at a time)
+    bufs, noise = [], []
     for i, r in enumerate(reps):
         pos, q = synth.electrolyte(r["n"], r["Lx"], r["Ly"], 1.0, r["H"] - 1.0, cfg["seed"] + 1 + i)
         bufs.append((torch.tensor(pos, dtype=torch.float64, device=dev), torch.tensor(q, dtype=torch.float64, device=dev),
                      torch.empty(r["n"], dtype=torch.float64, device=dev),
                      torch.empty((r["n"], 3), dtype=torch.float64, device=dev)))
+        if cfg["bd"]:
+            W = torch.empty((r["n"], 3), dtype=torch.float64, device=dev)
+            dpslab.bd_init_noise(cfg["seed"] * 100003 + i, W)
+            noise.append(W)
+    bdp = dpslab.bd_params(seed=cfg["seed"], **SERVE_BD) if cfg["bd"] else None
+    steps_of = [0] * len(reps)
     torch.cuda.synchronize()
     free, _ = torch.cuda.mem_get_info()
     budget = int(cfg["budget_frac"] * free)
@@ -347,7 +359,16 @@ def bench_serve(args):
 
     def requests(lo, hi):
         t_base = t_arr[lo]
-        return [Request(int(rep_ids[k]), *bufs[rep_ids[k]], t_arrival=float(t_arr[k] - t_base)) for k in range(lo, hi)]
+        out = []
+        for k in range(lo, hi):
+            i = int(rep_ids[k])
+            if cfg["bd"]:
+                out.append(Request(i, bufs[i][0], bufs[i][1], None, bufs[i][3], t_arrival=float(t_arr[k] - t_base),
+                                   bd=bdp, W=noise[i], step=steps_of[i]))
+                steps_of[i] += 1
+            else:
+                out.append(Request(i, *bufs[i], t_arrival=float(t_arr[k] - t_base)))
+        return out
 
     nw = warm * cfg["per_step"]
     srv.run(requests(0, nw))
@@ -376,7 +397,11 @@ def bench_serve(args):
     for r in subset:
         pl = srv.plans[r.replica]
         pl.bind_work(one)
-        pl.solve(r.pos, r.q, r.phi, r.force)
+        if r.bd is not None:
+            pl.bd_step(r.bd, r.pos, r.q, r.W, steps_of[r.replica], r.force)
+            steps_of[r.replica] += 1
+        else:
+            pl.solve(r.pos, r.q, r.phi, r.force)
         pl.bind_work(None)
         seq_charges += r.n
     torch.cuda.synchronize()
@@ -392,6 +417,8 @@ def bench_serve(args):
                 latency_ms=dict(p50=st["p50_ms"], p99=st["p99_ms"]),
                 service_ms=dict(p50=svc[len(svc) // 2], p99=svc[min(len(svc) - 1, int(0.99 * len(svc)))]),
                 requests=st["requests"], failed=st.get("failed", 0), charges=st["charges"],
+                request_kind="Brownian-dynamics step (solve + steric + update)" if cfg["bd"] else "solve",
+                bd_retries=int(sum(r.retries or 0 for r in done)) if cfg["bd"] else None,
                 admission=dict(counters, peak_workspace_gb=srv.peak_ws_bytes / 1e9,
                                resident_plans_gb=srv.plan_bytes() / 1e9, register_s=t_register),
                 sequential_value=seq_rate, served_over_sequential=(st["charges"] / wall) / seq_rate,

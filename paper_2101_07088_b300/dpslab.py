@@ -209,6 +209,9 @@ class Plan:
                                             W.data_ptr(), int(step),
                                             force.data_ptr() if force is not None else None, st))
 
+    def last_bd_retries(self):
+        return lib().dpslab_bd_last_retries(self._h)
+
     def bd_step(self, bp, pos, q, W, step, force=None, stream=None, check=True):
         """One step, waited for: returns (code, retries used)."""
         self.bd_enqueue(bp, pos, q, W, step, force, stream)

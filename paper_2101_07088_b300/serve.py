@@ -25,6 +25,10 @@ new workspaces too (no starvation of large systems); requests of replicas
 with a resident workspace pass it. A replica whose workspace alone exceeds
 the budget is rejected with DPSLAB_ERR_CAPACITY.
 
+Requests may be Brownian-dynamics steps of their replica (the solve, the
+steric forces and the update of Eq. (leimkuhler) in stream order): a
+replica's steps then run in order and its positions advance in place.
+
 Latency is arrival to completion on the host's clock; throughput is charges
 solved per second of the run.
 """
@@ -38,17 +42,24 @@ class Request:
     """One force/energy solve for `replica`: device tensors pos [n, 3] and
     q [n] (float64), outputs phi [n] and force [n, 3] (float64, device, or
     None). t_arrival is in seconds from the start of Server.run. The server
-    fills in U, code (DPSLAB_OK or an error), t_start and t_done."""
+    fills in U, code (DPSLAB_OK or an error), t_start and t_done.
 
-    def __init__(self, replica, pos, q, phi=None, force=None, t_arrival=0.0):
+    With bd (a dpslab.BdParams), W (device [n, 3]) and step, the request is
+    one Brownian-dynamics step (dpslab_bd_step_enqueue): the solve at pos,
+    then pos and W advanced in place; retries reports the discarded
+    proposals."""
+
+    def __init__(self, replica, pos, q, phi=None, force=None, t_arrival=0.0, bd=None, W=None, step=0):
         self.replica = replica
         self.pos, self.q, self.phi, self.force = pos, q, phi, force
+        self.bd, self.W, self.step = bd, W, step
         self.n = int(q.shape[0])
         self.t_arrival = t_arrival
         self.t_arrival_abs = None
         self.t_start = self.t_done = None
         self.U = None
         self.code = None
+        self.retries = None
 
 
 def _torch_backend(nstreams):
@@ -142,7 +153,10 @@ class Server:
         self.next_stream = (self.next_stream + 1) % len(self.streams)
         req.t_start = time.perf_counter()
         try:
-            plan.enqueue(req.pos, req.q, req.phi, req.force, stream=st)
+            if req.bd is not None:
+                plan.bd_enqueue(req.bd, req.pos, req.q, req.W, req.step, req.force, stream=st)
+            else:
+                plan.enqueue(req.pos, req.q, req.phi, req.force, stream=st)
         except dpslab.DpslabError as e:
             self._finish(req, e.code)
             return
@@ -156,7 +170,10 @@ class Server:
             code, U = self.plans[r].poll()
             if code == dpslab.PENDING:
                 continue
-            self._finish(self.busy.pop(r), code, U)
+            req = self.busy.pop(r)
+            if req.bd is not None:
+                req.retries = self.plans[r].last_bd_retries()
+            self._finish(req, code, U)
             finished += 1
         blocked = False
         keep = collections.deque()
