@@ -1264,7 +1264,9 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int CB = kColBlockM;
     const int N = kp.nz;
-    const int NP = N + 1;              // padded column stride (shared-memory banks)
+    // padded column stride, NP = 2 mod 16: eight modes x two rows of float2
+    // (the mode-major loads and stores) then fall in distinct banks
+    const int NP = N + ((2 - N) & 15);
     const int M = kp.ny * kp.nxh;
     float2* Vi = reinterpret_cast<float2*>(smraw);
     float2* Vo = Vi + CB * NP;
@@ -1368,17 +1370,24 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
         const int cmax = L - m;            // >= m: the longer sweep
         float qp = 0.f, xcp = 0.f;
         float2 fip = make_float2(0.f, 0.f), fop = fip;
+        int nn = ch + 2 * i0;
+        float jl = 0.f, jd = 0.f, ju = 0.f;
+        float2 Fin = make_float2(0.f, 0.f), Fon = Fin;
+        if (cnt > 0) { jl = kp.j2l32[nn]; jd = kp.j2d32[nn]; ju = kp.j2u32[nn]; Fin = Fi[nn]; Fon = Fo[nn]; }
         for (int k = 0; k < cmax; ++k) {
             if (k < cnt) {
-                const int i = i0 + di * k, n = ch + 2 * i;
-                const float an = n >= 2 ? -K2 * kp.j2l32[n] : 0.f;
-                const float bn = 1.f - K2 * kp.j2d32[n];
-                const float cn = n + 2 < N ? -K2 * kp.j2u32[n] : 0.f;
+                const int i = i0 + di * k, n = nn;
+                const float an = n >= 2 ? -K2 * jl : 0.f;
+                const float bn = 1.f - K2 * jd;
+                const float cn = n + 2 < N ? -K2 * ju : 0.f;
+                const float2 Fcur = Fin, Focur = Fon;
+                nn = n + 2 * di;
+                if (k + 1 < cnt) { jl = kp.j2l32[nn]; jd = kp.j2d32[nn]; ju = kp.j2u32[nn]; Fin = Fi[nn]; Fon = Fo[nn]; }
                 const float lo = side ? cn : an, up = side ? an : cn;   // toward / away from the sweep
-                const float inv = 1.f / (bn - lo * qp);
+                const float inv = __frcp_rn(bn - lo * qp);
                 const float rn = (i == 0) ? K2 : 0.f;
-                fip = cscale(csub(Fi[n], cscale(fip, lo)), inv);
-                fop = cscale(csub(Fo[n], cscale(fop, lo)), inv);
+                fip = cscale(csub(Fcur, cscale(fip, lo)), inv);
+                fop = cscale(csub(Focur, cscale(fop, lo)), inv);
                 xcp = (rn - lo * xcp) * inv;
                 qp = up * inv;
                 cq[n] = qp;
@@ -2936,7 +2945,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             }
         }
     }
-    pl->sm_col = size_t(col_block) * (nz + (mixed ? 1 : 0)) * (4 * csz + 2 * rsz);
+    pl->sm_col = size_t(col_block) * (nz + (mixed ? ((2 - nz) & 15) : 0)) * (4 * csz + 2 * rsz);
     pl->sm_interp = size_t(kInterpWarps) * (2 * kMaxSupport + kMaxNz) * rsz;
     pl->sm_spread = (2 * size_t(kp.slab) * kTile * kTile +
                      size_t(kSpreadBatch) * (((kp.supx + 31) & ~31) + ((kp.supy + 31) & ~31) + kp.slab)) * rsz;
