@@ -221,6 +221,26 @@ int dpslab_bd_step_enqueue(dpslab_plan* plan, const dpslab_bd_params* bp, int64_
 int dpslab_bd_last_retries(const dpslab_plan* plan);
 
 /*
+ * Launch-shape autotuning. Four knobs set how many sequences one thread
+ * block transforms in the xy FFT kernels:
+ *   knobs[0]  x forward (rows)     knobs[1]  y forward (columns)
+ *   knobs[2]  y inverse (columns)  knobs[3]  x inverse (rows)
+ * A value sets the block size and shared memory of its kernel; the results
+ * do not depend on it. dpslab_plan_autotune runs the solve on the caller's
+ * device inputs (as dpslab_solve, outputs discarded), and for each knob in
+ * turn times its stage with CUDA events (median of `reps` solves after one
+ * warm-up) at 1, 2, 4, ..., 32 within the kernel's thread and shared-memory
+ * limits, keeping a value only when it is at least 2% faster. Needs a bound
+ * workspace and no solve in flight. dpslab_plan_set_tuning applies knobs (for
+ * example cached from an earlier autotune of the same grid); it returns
+ * DPSLAB_ERR_INVALID_ARG and changes nothing if a value is outside its
+ * kernel's limits.
+ */
+int dpslab_plan_autotune(dpslab_plan* plan, int64_t n, const double* pos, const double* q, int reps, void* stream);
+int dpslab_plan_tuning(const dpslab_plan* plan, int* knobs, int n);
+int dpslab_plan_set_tuning(dpslab_plan* plan, const int* knobs, int n);
+
+/*
  * A plan without a workspace: tables and derived parameters only (a few MB);
  * the caller binds a workspace of at least dpslab_plan_work_bytes bytes with
  * dpslab_plan_bind_work before solving. Serving loops keep many such plans

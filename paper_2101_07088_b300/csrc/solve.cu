@@ -3390,6 +3390,140 @@ extern "C" int dpslab_stage_times(const dpslab_plan* plan, double* ms, int n) {
     return DPSLAB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// launch-shape autotuning (the xy transforms' sequences per block)
+// ---------------------------------------------------------------------------
+namespace {
+int finish(dpslab_plan* pl, cudaStream_t st, double* U);
+constexpr int kKnobs = 4;                 // x forward, y forward, y inverse, x inverse
+constexpr int kKnobStage[kKnobs] = {2, 3, 7, 8};
+
+int* shape_knob(dpslab_plan* pl, int which) {
+    switch (which) {
+        case 0: return &pl->px_fwd;
+        case 1: return &pl->tk_fwd;
+        case 2: return &pl->tk_inv;
+        default: return &pl->px_inv;
+    }
+}
+
+// set knob `which` to v sequences per block, with its block size and shared
+// memory; false (nothing changed) outside the kernel's thread and shared-memory limits
+template <class R>
+bool apply_shape_t(dpslab_plan* pl, int which, int v) {
+    if (v < 1 || v > 64) return false;
+    const size_t csz = 2 * sizeof(R), smax = 227 * 1024;
+    const int nx = pl->kp.nx, ny = pl->kp.ny;
+    auto maxthr = [](const void* f) {
+        cudaFuncAttributes fa{};
+        return cudaFuncGetAttributes(&fa, f) == cudaSuccess ? fa.maxThreadsPerBlock : 0;
+    };
+    const bool xk = which == 0 || which == 3;
+    const int n = xk ? nx : ny;
+    const bool p2 = xk ? pl->p2x : pl->p2y;
+    size_t sm;
+    int thr = 256;
+    const void* f;
+    if (p2) {
+        const int n16 = n / 16;
+        const size_t seq = size_t(n + n16) * csz, tw = size_t(n) * csz;
+        const int seqs = which == 3 ? 2 * v : v;         // the x inverse transforms two sequences per row
+        thr = seqs * n16;
+        sm = tw + seqs * seq;
+        f = which == 0 ? (const void*)k_fftx_fwd_p2<R> : which == 1 ? (const void*)k_ffty_fwd_p2<R>
+          : which == 2 ? (const void*)k_ffty_inv_p2<R> : (const void*)k_fftx_inv_p2<R>;
+        if (thr > maxthr(f)) return false;
+    } else {
+        const int mul = which == 0 || which == 1 ? 2 : which == 2 ? 6 : 4;
+        sm = (size_t(n) + size_t(mul) * v * n) * csz;
+        f = which == 0 ? (const void*)k_fftx_fwd<R> : which == 1 ? (const void*)k_ffty_fwd<R>
+          : which == 2 ? (const void*)k_ffty_inv<R> : (const void*)k_fftx_inv<R>;
+    }
+    if (sm > smax) return false;
+    raise_smem(f, sm);
+    *shape_knob(pl, which) = v;
+    switch (which) {
+        case 0: pl->sm_fftx_fwd = sm; pl->thr_x_fwd = thr; break;
+        case 1: pl->sm_ffty_fwd = sm; pl->thr_y_fwd = thr; break;
+        case 2: pl->sm_ffty_inv = sm; pl->thr_y_inv = thr; break;
+        default: pl->sm_fftx_inv = sm; pl->thr_x_inv = thr; break;
+    }
+    return true;
+}
+
+bool apply_shape(dpslab_plan* pl, int which, int v) {
+    return pl->kp.mixed ? apply_shape_t<float>(pl, which, v) : apply_shape_t<double>(pl, which, v);
+}
+}  // namespace
+
+extern "C" int dpslab_plan_tuning(const dpslab_plan* plan, int* knobs, int n) {
+    if (!plan || !knobs || n < kKnobs) return DPSLAB_ERR_INVALID_ARG;
+    knobs[0] = plan->px_fwd;
+    knobs[1] = plan->tk_fwd;
+    knobs[2] = plan->tk_inv;
+    knobs[3] = plan->px_inv;
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_plan_set_tuning(dpslab_plan* plan, const int* knobs, int n) {
+    if (!plan || !knobs || n < kKnobs || plan->in_flight) return DPSLAB_ERR_INVALID_ARG;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    int old[kKnobs];
+    dpslab_plan_tuning(plan, old, kKnobs);
+    for (int i = 0; i < kKnobs; ++i) {
+        if (!apply_shape(plan, i, knobs[i])) {
+            for (int j = 0; j < i; ++j) apply_shape(plan, j, old[j]);
+            return DPSLAB_ERR_INVALID_ARG;
+        }
+    }
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_plan_autotune(dpslab_plan* plan, int64_t n, const double* pos, const double* q, int reps,
+                                    void* stream) {
+    if (!plan || !pos || !q || n < 1 || reps < 1 || plan->in_flight || !plan->bound) return DPSLAB_ERR_INVALID_ARG;
+    if (n > plan->max_n) return DPSLAB_ERR_CAPACITY;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!plan->ev[0])
+        for (auto& e : plan->ev) DPS_CUDA(cudaEventCreate(&e));
+    const int prof = plan->profiling;
+    plan->profiling = 1;
+    // median stage time of `reps` solves after one warm-up
+    auto time_stage = [&](int stage, double& out) -> int {
+        std::vector<double> t;
+        for (int i = 0; i <= reps; ++i) {
+            int rc = enqueue(plan, n, pos, q, nullptr, nullptr, st);
+            if (!rc) rc = finish(plan, st, nullptr);
+            if (rc && rc != DPSLAB_ERR_NOT_NEUTRAL) return rc;
+            if (i) t.push_back(plan->stage_ms[stage]);
+        }
+        std::sort(t.begin(), t.end());
+        out = t[t.size() / 2];
+        return DPSLAB_OK;
+    };
+    int rc = DPSLAB_OK;
+    for (int which = 0; which < kKnobs && !rc; ++which) {
+        const int cur = *shape_knob(plan, which);
+        int best = cur;
+        double tbest = 0.0;
+        rc = time_stage(kKnobStage[which], tbest);
+        for (int v = 1; v <= 32 && !rc; v *= 2) {
+            if (v == cur || !apply_shape(plan, which, v)) continue;
+            double t = 0.0;
+            rc = time_stage(kKnobStage[which], t);
+            if (!rc && t < 0.98 * tbest) {
+                tbest = t;
+                best = v;
+            }
+        }
+        apply_shape(plan, which, best);
+    }
+    plan->profiling = prof;
+    plan->last_n = n;
+    return rc;
+}
+
 extern "C" const char* dpslab_stage_name(int stage) {
     static const char* names[DPSLAB_NSTAGES] = {"prepare", "spread", "fft_x_fwd", "fft_y_fwd", "z_fwd", "bvp",
                                                 "z_inv", "fft_y_inv", "fft_x_inv", "interp", "near", "finish"};

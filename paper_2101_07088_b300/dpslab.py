@@ -84,6 +84,9 @@ def lib():
             "dpslab_bd_step_enqueue": (ctypes.c_int, [vp, ctypes.POINTER(BdParams), i64, vp, vp, vp, ctypes.c_uint64,
                                                       vp, vp]),
             "dpslab_bd_last_retries": (ctypes.c_int, [vp]),
+            "dpslab_plan_autotune": (ctypes.c_int, [vp, i64, vp, vp, ctypes.c_int, vp]),
+            "dpslab_plan_tuning": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+            "dpslab_plan_set_tuning": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
             "dpslab_plan_work_bytes": (i64, [vp]),
             "dpslab_plan_bind_work": (ctypes.c_int, [vp, vp, i64]),
             "dpslab_solve_enqueue": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, vp]),
@@ -208,6 +211,22 @@ class Plan:
         _check(lib().dpslab_bd_step_enqueue(self._h, ctypes.byref(bp), q.shape[0], pos.data_ptr(), q.data_ptr(),
                                             W.data_ptr(), int(step),
                                             force.data_ptr() if force is not None else None, st))
+
+    def autotune(self, pos, q, reps=5, stream=None):
+        """dpslab_plan_autotune on device inputs; returns the chosen knobs."""
+        import torch
+        st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(lib().dpslab_plan_autotune(self._h, q.shape[0], pos.data_ptr(), q.data_ptr(), int(reps), st))
+        return self.tuning()
+
+    def tuning(self):
+        k = (ctypes.c_int * 4)()
+        _check(lib().dpslab_plan_tuning(self._h, k, 4))
+        return list(k)
+
+    def set_tuning(self, knobs):
+        k = (ctypes.c_int * 4)(*[int(v) for v in knobs])
+        _check(lib().dpslab_plan_set_tuning(self._h, k, 4))
 
     def last_bd_retries(self):
         return lib().dpslab_bd_last_retries(self._h)
