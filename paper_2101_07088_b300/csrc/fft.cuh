@@ -8,8 +8,9 @@
 // (autosort) form, so the result is in natural order with no bit reversal.
 // `tw` holds w^k = e^{-2 pi i k/n}, k < n; dir = -1 is the forward
 // transform sum_x f(x) e^{-2 pi i k x/n}, dir = +1 the unnormalised inverse.
-// Radices 2 and 4 have dedicated butterflies; any other radix uses the
-// direct R-point sum with table twiddles.
+// Radices 2 and 4 have dedicated butterflies, 3, 5 and 7 a paired one
+// (odd_butterfly); any other radix uses the direct R-point sum with table
+// twiddles.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -43,6 +44,52 @@ template <class C>
 __device__ __forceinline__ C twiddle(const C* tw, int k, int dir) {
     const C w = tw[k];
     return dir < 0 ? w : cconj(w);
+}
+
+// Odd radix R = 3, 5, 7: the inputs get their stage twiddle once, then the
+// R-point DFT pairs inputs r and R - r: with S = v_r + v_{R-r},
+// D = v_r - v_{R-r}, output r' gains S cos(2 pi k/R) + i dir D sin(2 pi k/R),
+// k = r r' mod R, the constants read from the twiddle table
+// (tw[k n/R] = e^{-2 pi i k/R}).
+template <int R, class C>
+__device__ __forceinline__ void odd_butterfly(const C* x, C* y, int j, int nR, int out0, int Ns, int jm, int step,
+                                              const C* tw, int dir) {
+    constexpr int h = (R - 1) / 2;
+    C v[R];
+    v[0] = x[j];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        v[r] = x[j + r * nR];
+        if (jm) v[r] = cmul(v[r], twiddle(tw, r * jm * step, dir));
+    }
+    C S[h], D[h];
+    C y0 = v[0];
+#pragma unroll
+    for (int m = 1; m <= h; ++m) {
+        S[m - 1] = cadd(v[m], v[R - m]);
+        D[m - 1] = csub(v[m], v[R - m]);
+        y0 = cadd(y0, S[m - 1]);
+    }
+    y[out0] = y0;
+    C cs[R];
+#pragma unroll
+    for (int k = 1; k < R; ++k) cs[k] = tw[k * nR];
+    const auto sd = decltype(v[0].x)(dir);
+#pragma unroll
+    for (int rp = 1; rp < R; ++rp) {
+        auto re = v[0].x, im = v[0].y;
+#pragma unroll
+        for (int m = 1; m <= h; ++m) {
+            const int k = (m * rp) % R;
+            const auto c = cs[k].x, sn = -cs[k].y * sd;   // cos(2 pi k/R), dir sin(2 pi k/R)
+            re += S[m - 1].x * c - sn * D[m - 1].y;
+            im += S[m - 1].y * c + sn * D[m - 1].x;
+        }
+        C o;
+        o.x = re;
+        o.y = im;
+        y[out0 + rp * Ns] = o;
+    }
 }
 
 // Returns the buffer holding the result (a or b). Ends with __syncthreads().
@@ -83,6 +130,12 @@ __device__ inline C* block_fft(C* a, C* b, const C* tw, int n, int nseq, const i
                 if (jm) v1 = cmul(v1, twiddle(tw, jm * step, dir));
                 y[out0] = cadd(v0, v1);
                 y[out0 + Ns] = csub(v0, v1);
+            } else if (R == 3) {
+                odd_butterfly<3>(x, y, j, nR, out0, Ns, jm, step, tw, dir);
+            } else if (R == 5) {
+                odd_butterfly<5>(x, y, j, nR, out0, Ns, jm, step, tw, dir);
+            } else if (R == 7) {
+                odd_butterfly<7>(x, y, j, nR, out0, Ns, jm, step, tw, dir);
             } else {
                 // y[out0 + r' Ns] = sum_r x[j + r nR] w^(r (jm step + r' nR))
                 for (int rp = 0; rp < R; ++rp) {

@@ -70,6 +70,7 @@ SMALL = [
     ("two-metal", (16.0, 16.0, 16.0), (30, 36, 41), math.inf, math.inf, 64, {}),
     ("no-split", (16.0, 16.0, 16.0), (32, 32, 48), 1 / 80, 1 / 20, 40, dict(xi=math.inf)),
     ("tol5e-4", (20.0, 20.0, 14.0), (40, 40, 33), 1 / 20, 1 / 50, 80, dict(tol=5e-4)),
+    ("radix-3-7", (21.0, 28.0, 16.0), (42, 56, 33), 1 / 80, 1 / 10, 90, {}),
 ]
 
 
