@@ -37,6 +37,8 @@ import time
 
 from . import dpslab
 
+CANCELLED = -100     # Request.code of a request withdrawn before it started
+
 
 class Request:
     """One force/energy solve for `replica`: device tensors pos [n, 3] and
@@ -140,9 +142,31 @@ class Server:
 
     # the loop ---------------------------------------------------------------
     def submit(self, req):
+        """Queue a request. A request for an unregistered replica, or one
+        whose charge count exceeds the replica's plan, finishes at once with
+        DPSLAB_ERR_INVALID_ARG / DPSLAB_ERR_CAPACITY (it never reaches the
+        device)."""
         if req.replica not in self.plans:
-            raise KeyError(f"replica {req.replica} is not registered")
+            self._finish(req, dpslab.ERR_INVALID_ARG)
+            self.stats["malformed"] += 1
+            return
+        if req.n > getattr(self.plans[req.replica], "max_n", req.n):
+            self._finish(req, dpslab.ERR_CAPACITY)
+            self.stats["malformed"] += 1
+            return
         self.waiting.append(req)
+
+    def cancel(self, req):
+        """Withdraw a waiting request (it finishes with code CANCELLED);
+        False if it is already on the device or done (a solve in flight runs
+        to completion: kernels are not interrupted)."""
+        try:
+            self.waiting.remove(req)
+        except ValueError:
+            return False
+        self._finish(req, CANCELLED)
+        self.stats["cancelled"] += 1
+        return True
 
     def _finish(self, req, code, U=None):
         req.code, req.U, req.t_done = code, U, time.perf_counter()
@@ -197,7 +221,26 @@ class Server:
                 blocked = True
                 keep.append(req)
                 continue
-            plan.bind_work(self.alloc(plan.work_bytes))
+            try:
+                work = self.alloc(plan.work_bytes)
+            except (MemoryError, RuntimeError):
+                # the device allocator refused (memory held outside the
+                # budget): give back every idle workspace and retry once; if
+                # that fails too, wait for solves in flight to free theirs,
+                # or fail the request when nothing is in flight
+                self.stats["alloc_failures"] += 1
+                for v in [k for k in self.ws if k not in self.busy]:
+                    self._evict(v)
+                try:
+                    work = self.alloc(plan.work_bytes)
+                except (MemoryError, RuntimeError):
+                    if self.busy:
+                        blocked = True
+                        keep.append(req)
+                    else:
+                        self._finish(req, dpslab.ERR_CUDA)
+                    continue
+            plan.bind_work(work)
             self.ws[r] = True
             self.ws_bytes += plan.work_bytes
             self.peak_ws_bytes = max(self.peak_ws_bytes, self.ws_bytes)
@@ -249,3 +292,28 @@ def latency_stats(done):
 
     return dict(requests=len(ok), failed=len(done) - len(ok), p50_ms=pick(0.5), p99_ms=pick(0.99),
                 charges=charges, wall_s=t_last - t_first, charges_per_s=charges / max(t_last - t_first, 1e-9))
+
+
+def snapshot(pos, q, W=None, step=0):
+    """Host copy of a replica's state (positions, charges, noise W^n and the
+    step index of a Brownian-dynamics replica): everything a plan needs to
+    resume it, since plans and workspaces are re-creatable from parameters."""
+    import numpy as np
+    out = dict(pos=np.asarray(pos.detach().cpu()), q=np.asarray(q.detach().cpu()), step=int(step))
+    if W is not None:
+        out["W"] = np.asarray(W.detach().cpu())
+    return out
+
+
+def save_snapshot(path, snap):
+    import numpy as np
+    np.savez(path, **snap)
+
+
+def load_snapshot(path, device="cuda"):
+    """The state saved by save_snapshot, as tensors on `device`."""
+    import numpy as np
+    import torch
+    with np.load(path) as z:
+        out = {k: (torch.tensor(z[k], device=device) if k != "step" else int(z[k])) for k in z.files}
+    return out

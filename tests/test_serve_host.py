@@ -151,3 +151,60 @@ def test_random_traffic_keeps_invariants():
         r.t_arrival_abs = r.t_start
     s = latency_stats(srv.done)
     assert s["requests"] == 150 and s["p50_ms"] <= s["p99_ms"]
+
+
+def test_injected_faults_malformed_cancel_and_allocator_refusal():
+    from paper_2101_07088_b300.serve import CANCELLED
+    srv, dev, allocs = _server(budget=100, sizes=[40, 40, 40], max_inflight=1)
+    srv.plans[0].max_n = 5
+    # malformed: unregistered replica, too many charges for the plan
+    srv.submit(Request(7, pos=0, q=FakeQ(1)))
+    srv.submit(Request(0, pos=0, q=FakeQ(9)))
+    assert [r.code for r in srv.done] == [dpslab.ERR_INVALID_ARG, dpslab.ERR_CAPACITY]
+    # cancellation: a waiting request can be withdrawn, one in flight cannot
+    a, b = Request(1, pos=1, q=FakeQ(1)), Request(2, pos=2, q=FakeQ(1))
+    srv.submit(a)
+    srv.submit(b)
+    srv.step()                                       # a starts (one slot), b waits
+    assert not srv.cancel(a) and srv.cancel(b)
+    assert b.code == CANCELLED and 2 not in srv.busy
+    _finish_all(srv, dev)
+    srv.step()
+    assert a.code == dpslab.OK
+    # the device allocator refuses once: idle workspaces are given back and
+    # the admission retried
+    fails = [1]
+
+    def flaky(nbytes):
+        if fails[0]:
+            fails[0] -= 1
+            raise RuntimeError("out of memory")
+        allocs.append(nbytes)
+        return bytearray(1)
+    srv.alloc = flaky
+    c = Request(0, pos=3, q=FakeQ(1))
+    srv.submit(c)
+    srv.step()
+    assert 0 in srv.busy and srv.stats["alloc_failures"] == 1 and list(srv.ws) == [0]
+    _finish_all(srv, dev)
+    srv.step()
+    assert c.code == dpslab.OK
+    # it refuses for good with nothing in flight: the request fails, the loop goes on
+    srv.alloc = lambda nbytes: (_ for _ in ()).throw(RuntimeError("out of memory"))
+    d = Request(2, pos=4, q=FakeQ(1))
+    srv.submit(d)
+    srv.step()
+    assert d.code == dpslab.ERR_CUDA and srv.idle()
+
+
+def test_snapshot_roundtrip(tmp_path):
+    torch = __import__("pytest").importorskip("torch")
+    from paper_2101_07088_b300.serve import load_snapshot, save_snapshot, snapshot
+    pos = torch.rand(10, 3, dtype=torch.float64)
+    q = torch.tensor([1.0, -1.0] * 5, dtype=torch.float64)
+    W = torch.randn(10, 3, dtype=torch.float64)
+    path = str(tmp_path / "rep.npz")
+    save_snapshot(path, snapshot(pos, q, W, step=17))
+    back = load_snapshot(path, device="cpu")
+    assert back["step"] == 17 and torch.equal(back["pos"], pos) and torch.equal(back["W"], W)
+    assert torch.equal(back["q"], q)
