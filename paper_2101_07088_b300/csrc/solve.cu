@@ -1327,25 +1327,32 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
         }
     }
     __syncthreads();
-    for (int t = tid; t < CB * N; t += bs) {
-        const int c = t / N, q = t - c * N;
+    // one thread per output row q for all CB modes: each table entry feeds
+    // 4 CB multiply-adds (the node values are shared-memory broadcasts)
+    for (int q = tid; q < N; q += bs) {
         const bool odd = q >= JE;
         const int na = odd ? JO : JE;
-        const float2* vi = Vi + c * NP;
-        const float2* vo = Vo + c * NP;
-        float ix = 0.f, iy = 0.f, ox = 0.f, oy = 0.f;
+        float acc[CB][4];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
         for (int a = 0; a < na; ++a) {
             const float w = kp.cft32[size_t(a) * N + q];
             const int ia = odd ? m - a : a;
-            const float2 u = vi[ia], v = vo[ia];
-            ix = fmaf(w, u.x, ix);
-            iy = fmaf(w, u.y, iy);
-            ox = fmaf(w, v.x, ox);
-            oy = fmaf(w, v.y, oy);
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                const float2 u = Vi[c * NP + ia], v = Vo[c * NP + ia];
+                acc[c][0] = fmaf(w, u.x, acc[c][0]);
+                acc[c][1] = fmaf(w, u.y, acc[c][1]);
+                acc[c][2] = fmaf(w, v.x, acc[c][2]);
+                acc[c][3] = fmaf(w, v.y, acc[c][3]);
+            }
         }
         const int n = odd ? 2 * (q - JE) + 1 : 2 * q;
-        Ci[c * NP + n] = make_float2(ix * scale, iy * scale);
-        Co[c * NP + n] = make_float2(ox * scale, oy * scale);
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            Ci[c * NP + n] = make_float2(acc[c][0] * scale, acc[c][1] * scale);
+            Co[c * NP + n] = make_float2(acc[c][2] * scale, acc[c][3] * scale);
+        }
     }
     __syncthreads();
     }
@@ -1617,26 +1624,44 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
     // node values (float), correction at the nodes (float)
     const float Ai = float(s_Ai);
     const float Gb = kp.f.Gb, Gt = kp.f.Gt, Hf = kp.f.H, HEf = kp.f.HE;
-    for (int t = tid; t < JE * CB; t += bs) {
-        const int c = t / JE, a = t - c * JE, col = col0 + c;
-        if (col >= M) continue;
-        const float2* yi = Ci + c * NP;
-        const float2* ypi = Vi + c * NP;
-        float ex = 0, ey = 0, dex = 0, dey = 0, ox = 0, oy = 0, dox = 0, doy = 0;
+    // one thread per node pair a for half the modes at a time: each table
+    // entry feeds 4 (CB/2) multiply-adds
+    constexpr int CH = CB / 2;
+    for (int t = tid; t < 2 * JE; t += bs) {
+        const int half = t / JE, a = t - half * JE;
+        float ev[CH][4], od[CH][4];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) ev[u][0] = ev[u][1] = ev[u][2] = ev[u][3] = od[u][0] = od[u][1] = od[u][2] = od[u][3] = 0.f;
         for (int r = 0; r < JE; ++r) {
             const float w = kp.tie32[size_t(r) * JE + a];
-            ex = fmaf(w, yi[2 * r].x, ex);
-            ey = fmaf(w, yi[2 * r].y, ey);
-            dex = fmaf(w, ypi[2 * r].x, dex);
-            dey = fmaf(w, ypi[2 * r].y, dey);
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int c = half * CH + u;
+                const float2 y = Ci[c * NP + 2 * r], yp = Vi[c * NP + 2 * r];
+                ev[u][0] = fmaf(w, y.x, ev[u][0]);
+                ev[u][1] = fmaf(w, y.y, ev[u][1]);
+                ev[u][2] = fmaf(w, yp.x, ev[u][2]);
+                ev[u][3] = fmaf(w, yp.y, ev[u][3]);
+            }
         }
         for (int r = 0; r < JO; ++r) {
             const float w = kp.tio32[size_t(r) * JE + a];
-            ox = fmaf(w, yi[2 * r + 1].x, ox);
-            oy = fmaf(w, yi[2 * r + 1].y, oy);
-            dox = fmaf(w, ypi[2 * r + 1].x, dox);
-            doy = fmaf(w, ypi[2 * r + 1].y, doy);
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int c = half * CH + u;
+                const float2 y = Ci[c * NP + 2 * r + 1], yp = Vi[c * NP + 2 * r + 1];
+                od[u][0] = fmaf(w, y.x, od[u][0]);
+                od[u][1] = fmaf(w, y.y, od[u][1]);
+                od[u][2] = fmaf(w, yp.x, od[u][2]);
+                od[u][3] = fmaf(w, yp.y, od[u][3]);
+            }
         }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+        const int c = half * CH + u, col = col0 + c;
+        if (col >= M) continue;
+        const float ex = ev[u][0], ey = ev[u][1], dex = ev[u][2], dey = ev[u][3];
+        const float ox = od[u][0], oy = od[u][1], dox = od[u][2], doy = od[u][3];
         const float sz = kp.f.sz;
         for (int side = 0; side < 2; ++side) {
             const int j = side ? m - a : a;
@@ -1661,6 +1686,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
             }
             sp[size_t(j) * M + col] = ps;
             sp[size_t(N + j) * M + col] = dps;
+        }
         }
     }
     if (tid == 0) {
