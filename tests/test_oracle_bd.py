@@ -145,3 +145,31 @@ def test_displacement_cap_and_retries():
     bp = dict(BP, a=1e-3, dt=10.0, max_retries=3)
     new, W, r, ok = bd.step(pos, np.zeros(n), zero, 3, P, bp, force=zero)
     assert not ok and r == 3 and np.array_equal(new, pos) and np.array_equal(W, zero)
+
+
+def test_harmonic_stationary_variance_is_exact():
+    # Eq. (leimkuhler) with F = -k z: z_{n+1} = c z_n + a (W_n + W_{n+1}),
+    # c = 1 - mu k dt, a^2 = kT mu dt / 2, whose stationary variance is
+    # a^2 (1 + (1 + c)^2 / (1 - c^2)) = kT / k for every dt; Euler-Maruyama
+    # (noise sqrt(2 kT mu dt) W_n) would give kT / (k (1 - mu k dt / 2)),
+    # 33% more at mu k dt = 0.5
+    P = params.derive(1e4, 1e4, 1e4, 0.2, 1e-4, 16, 16, r_cut=1.0)
+    n, steps, kspring = 1000, 100, 2.0
+    bp = dict(BP, a=1e-3, dt=0.25, kT=1.5, mu=1.0, seed=77)
+    rng = np.random.default_rng(10)
+    centre = rng.uniform(1e3, 9e3, (n, 3))             # ions far apart: no steric contact
+    pos, W = centre.copy(), bd.normals(n, 0, 0, bp["seed"])
+    samples = []
+    for k in range(steps):
+        force = -kspring * (pos - centre)
+        pos, W, r, ok = bd.step(pos, np.zeros(n), W, k, P, bp, force=force)
+        assert ok
+        if k >= 40:                                     # relaxation time 1/(mu k dt) = 2 steps
+            samples.append((pos - centre).ravel())
+    var = np.var(np.concatenate(samples))
+    want = bp["kT"] / kspring
+    # 60 x 3000 correlated samples (relaxation in two steps): about 1e5
+    # effective ones, a 0.5% standard error
+    assert abs(var / want - 1.0) < 0.02
+    em = want / (1.0 - bp["mu"] * kspring * bp["dt"] / 2.0)
+    assert abs(var / em - 1.0) > 0.2
