@@ -322,8 +322,9 @@ def bench_serve(args):
     device memory. `warmup` x 100 requests are served first (filling the
     resident set), then `steps` x 100 requests are timed. Reports charges/s,
     p50/p99 latency (arrival to completion) and service time (start to
-    completion), admission counters, and the first 100 timed requests solved
-    one after another on one stream for comparison."""
+    completion), admission counters, the first 100 timed requests solved
+    one after another on one stream for comparison, and 200 requests at half
+    the measured capacity (latency without the overload's queue)."""
     os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     import numpy as np
     import torch
@@ -407,6 +408,24 @@ def bench_serve(args):
         seq_charges += r.n
     torch.cuda.synchronize()
     seq_rate = seq_charges / (time.perf_counter() - t1)
+    del one
+    # the same replicas at half the measured capacity (Poisson arrivals at
+    # 0.5 x requests/s served above): latency without the overload's queue
+    half_rate = 0.5 * st["requests"] / wall
+    nh = 2 * cfg["per_step"]
+    h_ids, h_t = synth.serve_arrivals(nh, len(reps), half_rate, cfg["seed"] + 1)
+    h_reqs = []
+    for k in range(nh):
+        i = int(h_ids[k])
+        if cfg["bd"]:
+            h_reqs.append(Request(i, bufs[i][0], bufs[i][1], None, bufs[i][3], t_arrival=float(h_t[k] - h_t[0]),
+                                  bd=bdp, W=noise[i], step=steps_of[i]))
+            steps_of[i] += 1
+        else:
+            h_reqs.append(Request(i, *bufs[i], t_arrival=float(h_t[k] - h_t[0])))
+    h_done = srv.run(h_reqs)
+    torch.cuda.synchronize()
+    hs = latency_stats(h_done)
     line = dict(metric=METRIC, value=st["charges"] / wall, unit=UNIT, n_gpus=1, steps=steps, warmup=warm,
                 ms_per_step=wall * 1e3 / steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype={"fp64": "f64", "mixed": "f32+f64", "mixed_simt": "f32+f64"}[args.precision],
@@ -416,6 +435,9 @@ def bench_serve(args):
                             workspace_budget_gb=budget / 1e9,
                             l2="grids of 10 MB to 2 GB per request, requests interleaved; no flush"),
                 latency_ms=dict(p50=st["p50_ms"], p99=st["p99_ms"]),
+                half_load=dict(arrival_rate_per_s=half_rate, requests=hs.get("requests", 0),
+                               latency_ms=dict(p50=hs.get("p50_ms"), p99=hs.get("p99_ms")),
+                               charges_per_s=hs.get("charges_per_s")),
                 service_ms=dict(p50=svc[len(svc) // 2], p99=svc[min(len(svc) - 1, int(0.99 * len(svc)))]),
                 requests=st["requests"], failed=st.get("failed", 0), charges=st["charges"],
                 request_kind="Brownian-dynamics step (solve + steric + update)" if cfg["bd"] else "solve",
@@ -425,7 +447,6 @@ def bench_serve(args):
                 sequential_value=seq_rate, served_over_sequential=(st["charges"] / wall) / seq_rate,
                 clocks=ck)
     print(json.dumps(line))
-    del one
     srv.close()
     return 0
 
