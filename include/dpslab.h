@@ -55,7 +55,7 @@ extern "C" {
 #define DPSLAB_FP64   0   /* every stage in double precision */
 #define DPSLAB_MIXED  1   /* FP32 spreading, FFT, interpolation and near field; the z Chebyshev
                              transforms as tensor-core GEMMs on three-piece BF16 splits with FP32
-                             accumulation (Nz <= 128 and ny (nx/2+1) even; otherwise as
+                             accumulation (Nz <= 256 and ny (nx/2+1) even; otherwise as
                              DPSLAB_MIXED_SIMT); per-mode boundary-condition coefficients, the
                              k = 0 mode and the energy reduction accumulated in double */
 #define DPSLAB_MIXED_SIMT 2  /* DPSLAB_MIXED with the z transforms in FP32 on the CUDA cores */

@@ -14,7 +14,7 @@ constexpr int kMaxFft = 4096;      // xy grid size per direction
 constexpr int kMaxRadix = 64;      // largest prime factor of nx, ny
 constexpr int kMaxStages = 24;
 
-// Tensor-core z transforms (Nz <= 128): canonical K-major, no-swizzle
+// Tensor-core z transforms (Nz <= 256, blocks of 128): canonical K-major, no-swizzle
 // operand image of a rows x 128 bf16 operand, element (r, k) at
 // r/8 * 2048 B + k/8 * 128 B + (r%8) * 16 B + (k%8) * 2 B (8 x 16-byte core
 // matrices; K-direction stride 128 B, row-group stride 2048 B).
@@ -23,8 +23,14 @@ constexpr int kMaxStages = 24;
 #else
 #define DPS_HD
 #endif
-constexpr int kZMaxNz = 128;
+constexpr int kZBlock = 128;       // row and K block of the z-transform GEMM
+constexpr int kZMaxNz = 256;       // largest Nz on the tensor-core z transform (2 x 2 blocks)
 DPS_HD inline constexpr int zimg_index(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7); }
+// element offset of piece p of block (rb, kb) of an image with nb x nb
+// blocks: each block is three contiguous zimg_index pieces of 128 x 128
+DPS_HD inline constexpr size_t zimg_block(int rb, int kb, int nb, int p) {
+    return (size_t(rb * nb + kb) * 3 + size_t(p)) * size_t(kZBlock) * kZBlock;
+}
 
 struct Complex {
     double re, im;
@@ -54,7 +60,7 @@ struct Tables {
     std::vector<Complex> twx, twy;   // e^{-2 pi i k/n}
     std::vector<int> radx, rady;     // FFT radices (Stockham stages)
     // three bf16 pieces (x1 + x2 + x3) of the dense z transforms, 128 x 128
-    // padded, as zimg_index images (empty when Nz > 128): coefficients from
+    // padded to whole 128 blocks, as zimg_index blocks (see zimg_block; empty when Nz > 256): coefficients from
     // node values (DCT-I form) and node values from coefficients
     std::vector<unsigned short> zimg_fwd, zimg_inv;
 };

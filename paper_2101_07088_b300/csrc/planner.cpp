@@ -210,21 +210,23 @@ int build_tables(const dpslab_params& p, const dpslab_derived& d, Tables& t) {
         // 8 bits times a power of two, exact in bf16); pieces 2 and 3 the bf16
         // roundings of what remains
         auto image = [&](std::vector<unsigned short>& img, const std::function<double(int, int)>& A) {
-            img.assign(3 * size_t(kZMaxNz) * kZMaxNz, 0);
-            for (int r = 0; r < kZMaxNz; ++r) {
+            const int nb = (N + kZBlock - 1) / kZBlock, R = nb * kZBlock;
+            img.assign(size_t(nb) * nb * 3 * kZBlock * kZBlock, 0);
+            for (int r = 0; r < R; ++r) {
                 double amax = 0.0;
-                for (int k = 0; k < kZMaxNz; ++k) amax = std::max(amax, std::fabs(A(r, k)));
+                for (int k = 0; k < R; ++k) amax = std::max(amax, std::fabs(A(r, k)));
                 int e = 0;
                 if (amax > 0.0) std::frexp(amax, &e);
                 const double sc = std::ldexp(1.0, e);     // > amax
-                for (int k = 0; k < kZMaxNz; ++k) {
+                for (int k = 0; k < R; ++k) {
                     double x = A(r, k);
                     const double p1 = std::rint(x * 128.0 / sc) * (sc / 128.0);
-                    img[zimg_index(r, k)] = bf16(p1);
+                    const int rb = r / kZBlock, kb = k / kZBlock, ri = r % kZBlock, ki = k % kZBlock;
+                    img[zimg_block(rb, kb, nb, 0) + zimg_index(ri, ki)] = bf16(p1);
                     x -= p1;
                     for (int piece = 1; piece < 3; ++piece) {
                         const unsigned short h = bf16(x);
-                        img[size_t(piece) * kZMaxNz * kZMaxNz + zimg_index(r, k)] = h;
+                        img[zimg_block(rb, kb, nb, piece) + zimg_index(ri, ki)] = h;
                         x -= bf16v(h);
                     }
                 }

@@ -1697,7 +1697,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
 }
 
 // ---------------------------------------------------------------------------
-// z transforms on the tensor cores (zgemm.cuh), mixed precision, Nz <= 128:
+// z transforms on the tensor cores (zgemm.cuh), mixed precision, Nz <= 256:
 // k_zgemm_fwd turns the node values of both densities (planes 0, 1 of the
 // spectrum) into Chebyshev coefficients in place; k_column_mixed<true> solves
 // the BVPs on them; k_zgemm_inv turns the coefficients of psi_i and
@@ -1711,7 +1711,7 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_fwd(KP kp) {
     const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
     auto prep = [](int, int) {};
     auto epi = [](int, int, int, float*, int) {};
-    zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi);
+    zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock);
 }
 
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
@@ -1758,7 +1758,7 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
             v[i + 1] = im;
         }
     };
-    zgemm_run(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi);
+    zgemm_run(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock);
 }
 
 // ---------------------------------------------------------------------------
@@ -2773,7 +2773,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
     }
     const int M = ny * nxh;
     const bool mixed = p->precision == DPSLAB_MIXED || p->precision == DPSLAB_MIXED_SIMT;
-    // z transforms on the tensor cores: Nz <= 128, and rows of a spectrum
+    // z transforms on the tensor cores: Nz <= 256, and rows of a spectrum
     // plane (2 ny (nx/2+1) floats) a multiple of 16 bytes for the bulk copies
     pl->ztensor = p->precision == DPSLAB_MIXED && nz <= kZMaxNz && (M % 2) == 0 && !t.zimg_fwd.empty();
     kp.slab = mixed ? kSlabM : 16;

@@ -62,6 +62,7 @@ constexpr int kZRows = 8;                   // rows per thread and tile (4 colum
 constexpr int kZGroups = kZK / kZRows;      // row groups of a tile
 constexpr long kZSpinLimit = 1L << 26;      // polls of an mbarrier before giving up
 static_assert(kZThreads == (kZN / 4) * kZGroups, "one (column quad, row group) per thread");
+static_assert(kZMaxNz <= 2 * kZBlock, "at most two K blocks (held in registers)");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -97,6 +98,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (long i = 0; i < kZSpinLimit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// one-dimensional bulk copy global -> shared (both 16-byte aligned, bytes a
+// multiple of 16) that signals `bar` with its byte count
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -162,15 +175,26 @@ static_assert(size_t(kZK) * kZOStride * 4 <= kZSmemB, "staged outputs fit the B 
 // prep(plane, col0) runs on every thread once per tile while the MMAs are in
 // flight (before the barrier that precedes the epilogue): it may stage
 // per-tile data in shared memory for epi.
+// nblk = 1 (Nz <= 128): A stays in shared memory for all tiles and the next
+// tile's values load during the MMAs. nblk = 2 (128 < Nz <= 256): rows and K
+// come in two blocks of 128; each thread holds its 4 columns' 16 values of
+// the tile (8 per K block), so the column maxima over all K (one fixed-point
+// grid per column for the exact product) need no second read. For each K
+// block the values are split into B and, for each row block, that block of
+// A is staged by one bulk copy and its MMAs accumulate into the row block's
+// two accumulators (four in all, the whole 512 columns of tensor memory).
+// The outputs are written, in place, after every K row of the tile has been
+// read; the next tile's values load from the last split on.
 template <class Prep, class Epi>
 __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aimg, float* base, int nplanes,
                                           size_t pstride, int rows, int ncols, size_t ld, int* status, Prep prep,
-                                          Epi epi) {
+                                          Epi epi, int nblk = 1) {
     extern __shared__ __align__(1024) unsigned char zsm[];
     unsigned short* sA = reinterpret_cast<unsigned short*>(zsm);
     unsigned short* sB = reinterpret_cast<unsigned short*>(zsm + kZSmemA);
     uint64_t* bar = reinterpret_cast<uint64_t*>(zsm + kZSmemA + kZSmemB);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+    uint64_t* abar = bar + 1;                   // bulk copies of the A blocks (nblk > 1)
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
     __shared__ int s_abort;
     __shared__ float s_colmax[kZGroups][kZN];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -179,19 +203,22 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     // this thread's 4 columns (4 cq .. 4 cq + 3) and 8 rows (8 g .. 8 g + 7)
     const int cq = tid & (kZN / 4 - 1), g = tid / (kZN / 4), r0 = g * kZRows;
 
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(aimg);
+    auto stage_a = [&](int rb, int kb) {     // block (rb, kb) of the image into shared memory
+        const uint4* src = reinterpret_cast<const uint4*>(aimg + zimg_block(rb, kb, nblk, 0));
         uint4* dst = reinterpret_cast<uint4*>(sA);
         for (int i = tid; i < int(kZSmemA / 16); i += blockDim.x) dst[i] = src[i];
-    }
+    };
+    const uint32_t tcols = nblk > 1 ? 4u * kZN : uint32_t(kZTmemCols);
+    if (nblk == 1) stage_a(0, 0);
     if (tid == 0) {
         mbar_init(bar, 1);
+        mbar_init(abar, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
-                     "r"(kZTmemCols)
+                     "r"(tcols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -202,22 +229,160 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     const uint32_t tmem = *s_tmem;
 
     float4 rv[kZRows];
-    auto load = [&](int t) {
+    auto load = [&](int t, int kb) {         // K rows kb*128 + r0 .. + 7 of tile t
         const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
         const int c = c0 + 4 * cq;
         const float* src = base + size_t(plane) * pstride + c;
 #pragma unroll
         for (int i = 0; i < kZRows; ++i) {
-            const int r = r0 + i;
+            const int r = kb * kZBlock + r0 + i;
             rv[i] = (r < rows && c < ncols) ? __ldg(reinterpret_cast<const float4*>(src + size_t(r) * ld))
                                             : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
 
-    uint32_t ph = 0u;
-    bool pend = false;
-    if (int(blockIdx.x) < ntiles) load(blockIdx.x);
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint32_t ph = 0u, aph = 0u;
+    bool pend = false, apend = false;
+    if (nblk > 1) {
+        // both K blocks of the tile in registers: rv rows r0.., rw rows 128 + r0..
+        float4 rw[kZRows];
+        auto load2 = [&](int t) {
+            load(t, 0);
+            const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
+            const int c = c0 + 4 * cq;
+            const float* src = base + size_t(plane) * pstride + c;
+#pragma unroll
+            for (int i = 0; i < kZRows; ++i) {
+                const int r = kZBlock + r0 + i;
+                rw[i] = (r < rows && c < ncols) ? __ldg(reinterpret_cast<const float4*>(src + size_t(r) * ld))
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        if (int(blockIdx.x) < ntiles) load2(blockIdx.x);
+        for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x) {
+            const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
+            const int w = min(kZN, ncols - c0);
+            // each column's largest |entry| over all K: one fixed-point grid
+            // per column for the exact product
+            {
+                float cm[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < kZRows; ++i) {
+                    cm[0] = fmaxf(cm[0], fmaxf(fabsf(rv[i].x), fabsf(rw[i].x)));
+                    cm[1] = fmaxf(cm[1], fmaxf(fabsf(rv[i].y), fabsf(rw[i].y)));
+                    cm[2] = fmaxf(cm[2], fmaxf(fabsf(rv[i].z), fabsf(rw[i].z)));
+                    cm[3] = fmaxf(cm[3], fmaxf(fabsf(rv[i].w), fabsf(rw[i].w)));
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) s_colmax[g][4 * cq + j] = cm[j];
+            }
+            __syncthreads();
+            float qv[4], iqv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float amax = 0.f;
+#pragma unroll
+                for (int i = 0; i < kZGroups; ++i) amax = fmaxf(amax, s_colmax[i][4 * cq + j]);
+                int e = 0;
+                if (amax > 0.f) frexpf(amax, &e);
+                qv[j] = ldexpf(1.f, 7 - e);
+                iqv[j] = ldexpf(1.f, e - 7);
+            }
+            for (int kb = 0; kb < nblk && !s_abort; ++kb) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float x[kZRows];
+#pragma unroll
+                    for (int i = 0; i < kZRows; ++i) {
+                        const float4 a = kb == 0 ? rv[i] : rw[i];
+                        x[i] = j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : a.w;
+                    }
+                    put8(sB, 4 * cq + j, r0, x, qv[j], iqv[j]);
+                }
+                // the last K block is in B: the next tile's values load while
+                // the remaining copies, MMAs and the epilogue run
+                if (kb == nblk - 1 && t + int(gridDim.x) < ntiles) load2(t + gridDim.x);
+                for (int rb = 0; rb < nblk; ++rb) {
+                    // block (rb, kb) of A by one bulk copy (the previous MMAs,
+                    // which read sA, have completed)
+                    if (tid == 0) {
+                        mbar_expect_tx(abar, uint32_t(kZSmemA));
+                        bulk_g2s(sA, aimg + zimg_block(rb, kb, nblk, 0), uint32_t(kZSmemA), abar);
+                        apend = true;
+                        if (mbar_wait(abar, aph)) apend = false;
+                        else s_abort = 1;
+                    }
+                    fence_async_smem();
+                    __syncthreads();
+                    if (s_abort) break;
+                    aph ^= 1u;
+                    if (tid == 0) {
+                        tc_fence_after();
+                        constexpr uint32_t idesc = zidesc(kZK, kZN);
+                        const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+                        const uint32_t d0 = tmem + uint32_t(rb * 2 * kZN);
+                        const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+                        for (int qd = 0; qd < 6; ++qd)
+#pragma unroll
+                            for (int s8 = 0; s8 < kZK / 16; ++s8) {
+                                const uint64_t ad = zdesc(a0 + uint32_t(pa[qd]) * kZPieceA * 2 + uint32_t(s8) * 256u, 128u, 2048u);
+                                const uint64_t bd = zdesc(b0 + uint32_t(pb[qd]) * kZPieceB * 2 + uint32_t(s8) * 256u, 128u, kZSboB);
+                                const bool first = kb == 0 && s8 == 0 && qd <= 1;
+                                tc_mma(d0 + (qd == 0 ? 0u : uint32_t(kZN)), ad, bd, idesc, first ? 0u : 1u);
+                            }
+                        tc_commit(bar);
+                    }
+                    pend = true;
+                    if (tid == 0 && !mbar_wait(bar, ph)) s_abort = 1;
+                    __syncthreads();
+                    if (!s_abort) {
+                        ph ^= 1u;
+                        pend = false;
+                    }
+                    tc_fence_after();
+                    if (s_abort) break;
+                }
+            }
+            if (s_abort) break;
+            prep(plane, c0);
+            __syncthreads();
+            // epilogue per row block: warp = TMEM lane quarter x 32 columns
+            const int qtr = warp & 3, cc = (warp >> 2) * 32;
+            const int r = qtr * 32 + lane;
+            const int wv = min(32, w - cc);
+            float* O = reinterpret_cast<float*>(sB);
+            for (int rb = 0; rb < nblk; ++rb) {
+                const int rg = rb * kZBlock + r;
+                const uint32_t lb = tmem + (uint32_t(qtr * 32) << 16) + uint32_t(rb * 2 * kZN + cc);
+                float v[32], u[16];
+#pragma unroll
+                for (int h = 0; h < 32; h += 16) {
+                    tc_ld16(lb + uint32_t(h), v + h);
+                    tc_ld16(lb + uint32_t(kZN + h), u);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[h + i] += u[i];
+                }
+                if (rg < rows && wv > 0) epi(plane, rg, c0 + cc, v, wv);
+#pragma unroll
+                for (int i = 0; i < 32; i += 4)
+                    *reinterpret_cast<float4*>(O + r * kZOStride + cc + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                __syncthreads();
+                float* dst = base + size_t(plane) * pstride + c0 + 4 * lane;
+                if (4 * lane < w) {
+                    for (int rr = warp; rr < kZBlock && rb * kZBlock + rr < rows; rr += kZThreads / 32)
+                        __stcs(reinterpret_cast<float4*>(dst + size_t(rb * kZBlock + rr) * ld),
+                               *reinterpret_cast<const float4*>(O + rr * kZOStride + 4 * lane));
+                }
+                __syncthreads();
+            }
+            tc_fence_before();
+            fence_async_smem();
+            __syncthreads();
+        }
+    }
+    if (nblk == 1 && int(blockIdx.x) < ntiles) load(blockIdx.x, 0);
+    for (int t = blockIdx.x; nblk == 1 && t < ntiles; t += gridDim.x) {
         const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
         const int w = min(kZN, ncols - c0);
         // per column, the largest |entry| (fixed-point scale of piece 1), then
@@ -267,7 +432,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
         }
         pend = true;
         // the next tile's values, while the tensor cores work
-        if (t + int(gridDim.x) < ntiles) load(t + gridDim.x);
+        if (t + int(gridDim.x) < ntiles) load(t + gridDim.x, 0);
         prep(plane, c0);
         // one thread polls the MMA barrier (polls from every warp would
         // compete with the loads for the memory pipes); the rest wait here
@@ -315,12 +480,13 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     if (s_abort && tid == 0) {
         atomicOr(status, kStatusTimeout);
         if (pend) mbar_wait(bar, ph);
+        if (apend) mbar_wait(abar, aph);     // a bulk copy of A still in flight
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kZTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
 }
 
 }  // namespace dps

@@ -105,9 +105,9 @@ def test_mixed_against_fp64_gpu_at_one_million_charges():
     assert abs(np.sum(out["force"][:, 0])) < 1e-6 * s and abs(np.sum(out["force"][:, 1])) < 1e-6 * s
 
 
-@pytest.mark.parametrize("ny,nz", [(39, 37), (40, 136)], ids=["odd-columns", "nz-136"])
+@pytest.mark.parametrize("ny,nz", [(39, 37), (40, 272)], ids=["odd-columns", "nz-272"])
 def test_mixed_fallback_to_cuda_core_z_transform(ny, nz):
-    # ny (nx/2+1) odd, or Nz > 128: DPSLAB_MIXED runs the z transforms on the
+    # ny (nx/2+1) odd, or Nz > 256: DPSLAB_MIXED runs the z transforms on the
     # CUDA cores (same launch count as DPSLAB_MIXED_SIMT) and meets the same bar
     P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, ny, nz=nz, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
     pos, q = synth.electrolyte(102, 24.0, 20.0, 1.0, 19.0, seed=4)
@@ -119,3 +119,23 @@ def test_mixed_fallback_to_cuda_core_z_transform(ny, nz):
         counts[prec] = plan.last_launch_count()
         _check(ref, out, f"fallback ny={ny} nz={nz} prec={prec}", TOL_MIXED_ENERGY_SMALL)
     assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT], counts
+
+
+@pytest.mark.parametrize("nz", [136, 200, 256])
+def test_tensor_z_transform_in_two_blocks(nz):
+    # 128 < Nz <= 256: the z transforms run on the tensor cores in 2 x 2
+    # blocks of 128 (two launches more than the CUDA-core form), within the
+    # bar against the oracle and close to the CUDA-core form
+    # 800 charges: an energy that is not a handful of self terms (see
+    # TOL_MIXED_ENERGY_SMALL)
+    P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, 40, nz=nz, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
+    pos, q = synth.electrolyte(800, 24.0, 20.0, 1.0, 19.0, seed=8)
+    ref = osolver.solve(pos, q, P)
+    out, counts = {}, {}
+    for prec in (dpslab.MIXED, dpslab.MIXED_SIMT):
+        plan = plan_for(P, 800, precision=prec)
+        out[prec] = gpu_solve(plan, pos, q)
+        counts[prec] = plan.last_launch_count()
+        _check(ref, out[prec], f"two blocks nz={nz} prec={prec}", TOL_MIXED_ENERGY_SMALL)
+    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 2, counts
+    assert rel_l2(out[dpslab.MIXED]["force"], out[dpslab.MIXED_SIMT]["force"]) < TOL_MIXED_FORCE
