@@ -1298,19 +1298,31 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
     }
     if (tid == 0) s_Ai = 0.0;
     const float scale = kp.f.scale;
-    for (int t = tid; t < N * CB; t += bs) {
-        const int j = t / CB, c = t - j * CB, col = col0 + c;
-        float2 vi = make_float2(0.f, 0.f), vo = vi;
-        if (col < M) {
-            vi = sp[size_t(j) * M + col];
-            vo = sp[size_t(N + j) * M + col];
+    // every load of a batch is issued before the first store: one memory
+    // round trip per batch instead of one per row group
+    constexpr int kLd = 4;
+    for (int t0 = tid; t0 < N * CB; t0 += kLd * bs) {
+        float2 vi[kLd], vo[kLd];
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+            const int t = t0 + u * bs, j = t / CB, c = t - j * CB, col = col0 + c;
+            vi[u] = vo[u] = make_float2(0.f, 0.f);
+            if (t < N * CB && col < M) {
+                vi[u] = __ldcs(sp + size_t(j) * M + col);
+                vo[u] = __ldcs(sp + size_t(N + j) * M + col);
+            }
         }
-        if (kTensor) {                       // coefficients: right-hand sides of Eq. (blocksys)
-            Ci[c * NP + j] = cscale(vi, scale);
-            Co[c * NP + j] = cscale(vo, scale);
-        } else {
-            Vi[c * NP + j] = vi;
-            Vo[c * NP + j] = vo;
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+            const int t = t0 + u * bs, j = t / CB, c = t - j * CB;
+            if (t >= N * CB) break;
+            if (kTensor) {                   // coefficients: right-hand sides of Eq. (blocksys)
+                Ci[c * NP + j] = cscale(vi[u], scale);
+                Co[c * NP + j] = cscale(vo[u], scale);
+            } else {
+                Vi[c * NP + j] = vi[u];
+                Vo[c * NP + j] = vo[u];
+            }
         }
     }
     __syncthreads();
@@ -1482,16 +1494,17 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
             s_d[f][c] = dd;
         }
     }
-    __syncthreads();
-    // (field, column) pairs over the warps, n over the lanes; the three
-    // passes of a pair depend only on that pair's arrays, so a warp runs them
-    // back to back (warp barriers only): X += (c or d) xe gives y'', then
-    // y' = J y'' + d e0 and y = J y' + c e0 (Appendix A integration:
-    // entry n of J v is (v_{n-1} - v_{n+1})/(2n), entry 1 is v_0 - v_2/2)
+    // from here to the boundary values warp w works on mode w alone, so
+    // warp barriers suffice
+    static_assert(kColThreadsM == 32 * CB, "one warp per mode of the block");
+    __syncwarp();
+    // both fields of the warp's mode, n over the lanes: X += (c or d) xe
+    // gives y'', then y' = J y'' + d e0 and y = J y' + c e0 (Appendix A
+    // integration: entry n of J v is (v_{n-1} - v_{n+1})/(2n), entry 1 is
+    // v_0 - v_2/2)
     {
-        const int warp_id = tid >> 5, lane_id = tid & 31, nwarps = bs >> 5;
-        for (int fc = warp_id; fc < 2 * CB; fc += nwarps) {
-            const int f = fc / CB, c = fc % CB;
+        const int lane_id = tid & 31, c = tid >> 5;
+        for (int f = 0; f < 2; ++f) {
             float2* X = (f ? Co : Ci) + c * NP;
             float2* V = (f ? Vo : Vi) + c * NP;
             const float2 mc = s_c[f][c], md = s_d[f][c];
@@ -1515,7 +1528,6 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
             __syncwarp();
         }
     }
-    __syncthreads();
 
     // boundary values, mismatches, correction coefficients and the gauge
     // term in float; the k = 0 slope in double
