@@ -306,9 +306,13 @@ __device__ __forceinline__ void last_pass(C* v, const C* tw, int j, int n16, int
 // output i, after a barrier (it may write buf). All threads of the block
 // must call this function; it ends with the stores done by each thread.
 // kSyncLoad: a barrier between the first pass's loads and its writes, for
-// loads that read staged input from buf itself.
+// loads that read staged input from buf itself. twg: when given, the
+// twiddle table tw (n entries) is copied from it here, while the first
+// pass's loads are in flight (that pass needs no twiddles; the barrier
+// after its writes precedes the first use).
 template <bool QF, bool kSyncLoad = false, class C, class Load, class Store>
-__device__ __forceinline__ void fft_pow2(C* buf, const C* tw, int n, int logn, int nseq, int dir, Load load, Store store) {
+__device__ __forceinline__ void fft_pow2(C* buf, C* tw, int n, int logn, int nseq, int dir, Load load, Store store,
+                                         const C* twg = nullptr) {
     const int l16 = logn - 4, n16 = 1 << l16;
     const int s = threadIdx.x;
     const bool act = s < (nseq << l16);
@@ -322,6 +326,8 @@ __device__ __forceinline__ void fft_pow2(C* buf, const C* tw, int n, int logn, i
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = load(q, j + r * n16);
     }
+    if (twg)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
     if constexpr (kSyncLoad) __syncthreads();
     if (act) {
         dft16(v, dir);

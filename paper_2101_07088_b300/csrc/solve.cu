@@ -729,16 +729,14 @@ __global__ void k_ffty_fwd(KP kp, int TK) {
 // neighbouring kx columns per block (neighbouring threads on neighbouring
 // columns, so every row segment is read and written whole).
 // ---------------------------------------------------------------------------
-template <class R>
-__global__ void k_fftx_fwd_p2(KP kp, int P, int logn) {
+template <class R, int L>
+__global__ void k_fftx_fwd_p2(KP kp, int P, int) {
     using C = typename Prec<R>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int n = kp.nx, nxh = kp.nxh, np = n + (n >> 4);
+    constexpr int logn = L, n = 1 << L, nxh = n / 2 + 1, np = n + (n >> 4);
     C* tw = reinterpret_cast<C*>(smraw);
     C* buf = tw + n;
     const C* twg = twx_of<R>(kp);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
-    __syncthreads();
     const R* rho = static_cast<const R*>(kp.rho);
     C* spec = static_cast<C*>(kp.spec);
     const int npairs = kp.nz * kp.ny;
@@ -755,7 +753,7 @@ __global__ void k_fftx_fwd_p2(KP kp, int P, int logn) {
         return v;
     };
     auto store = [&](int q, int i, C v) { buf[q * np + pad16(i)] = v; };
-    fft_pow2<false>(buf, tw, n, logn, P, -1, load, store);
+    fft_pow2<false>(buf, tw, n, logn, P, -1, load, store, twg);
     __syncthreads();
     for (int t = threadIdx.x; t < P * nxh; t += blockDim.x) {
         const int p = t / nxh, k = t - p * nxh, pr = p0 + p;
@@ -772,16 +770,15 @@ __global__ void k_fftx_fwd_p2(KP kp, int P, int logn) {
     }
 }
 
-template <class R>
-__global__ void k_ffty_fwd_p2(KP kp, int TK, int logn) {
+template <class R, int L>
+__global__ void k_ffty_fwd_p2(KP kp, int TK, int) {
     using C = typename Prec<R>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int n = kp.ny, nxh = kp.nxh;
+    constexpr int logn = L, n = 1 << L;
+    const int nxh = kp.nxh;
     C* tw = reinterpret_cast<C*>(smraw);
     C* buf = tw + n;
     const C* twg = twy_of<R>(kp);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
-    __syncthreads();
     C* base = static_cast<C*>(kp.spec) + size_t(blockIdx.y) * n * nxh;
     const int k0 = blockIdx.x * TK;
     auto load = [&](int q, int i) {
@@ -794,16 +791,17 @@ __global__ void k_ffty_fwd_p2(KP kp, int TK, int logn) {
     auto store = [&](int q, int i, C v) {
         if (k0 + q < nxh) base[size_t(i) * nxh + k0 + q] = v;
     };
-    fft_pow2<true>(buf, tw, n, logn, TK, -1, load, store);
+    fft_pow2<true>(buf, tw, n, logn, TK, -1, load, store, twg);
 }
 
 // one of the three inverse column transforms: F = 0: -i k_y psi (psi -> specB),
 // F = 1: psi (in place), F = 2: dpsi/dz (in place)
-template <int F, class R>
-__device__ __forceinline__ void ffty_inv_field(const KP& kp, typename Prec<R>::C* buf, const typename Prec<R>::C* tw,
-                                               int TK, int logn) {
+template <int F, class R, int L>
+__device__ __forceinline__ void ffty_inv_field(const KP& kp, typename Prec<R>::C* buf, typename Prec<R>::C* tw,
+                                               int TK, const typename Prec<R>::C* twg = nullptr) {
     using C = typename Prec<R>::C;
-    const int n = kp.ny, nxh = kp.nxh;
+    constexpr int logn = L, n = 1 << L;
+    const int nxh = kp.nxh;
     const size_t plane = size_t(n) * nxh;
     C* src = static_cast<C*>(kp.spec) + size_t((F == 2 ? kp.nz : 0) + blockIdx.y) * plane;
     C* dst = F == 0 ? static_cast<C*>(kp.specB) + size_t(blockIdx.y) * plane : src;
@@ -825,37 +823,35 @@ __device__ __forceinline__ void ffty_inv_field(const KP& kp, typename Prec<R>::C
     auto store = [&](int c, int i, C v) {
         if (k0 + c < nxh) dst[size_t(i) * nxh + k0 + c] = v;
     };
-    fft_pow2<true>(buf, tw, n, logn, TK, +1, load, store);
+    fft_pow2<true>(buf, tw, n, logn, TK, +1, load, store, twg);
 }
 
-template <class R>
-__global__ void __launch_bounds__(512, sizeof(R) == sizeof(float) ? 2 : 1) k_ffty_inv_p2(KP kp, int TK, int logn) {
+template <class R, int L>
+__global__ void __launch_bounds__(512, sizeof(R) == sizeof(float) ? 2 : 1) k_ffty_inv_p2(KP kp, int TK, int) {
     using C = typename Prec<R>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int n = kp.ny;
+    constexpr int n = 1 << L;
     C* tw = reinterpret_cast<C*>(smraw);
     C* buf = tw + n;
     const C* twg = twy_of<R>(kp);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
-    __syncthreads();
     // -i k_y psi first: it reads psi before the psi transform overwrites it
-    ffty_inv_field<0, R>(kp, buf, tw, TK, logn);
+    // (the first transform also copies the twiddle table)
+    ffty_inv_field<0, R, L>(kp, buf, tw, TK, twg);
     __syncthreads();
-    ffty_inv_field<1, R>(kp, buf, tw, TK, logn);
+    ffty_inv_field<1, R, L>(kp, buf, tw, TK);
     __syncthreads();
-    ffty_inv_field<2, R>(kp, buf, tw, TK, logn);
+    ffty_inv_field<2, R, L>(kp, buf, tw, TK);
 }
 
-template <class R>
-__global__ void k_fftx_inv_p2(KP kp, int P, int logn) {
+template <class R, int L>
+__global__ void k_fftx_inv_p2(KP kp, int P, int) {
     using C = typename Prec<R>::C;
     using V4 = typename Prec<R>::V4;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int n = kp.nx, nxh = kp.nxh, np = n + (n >> 4);
+    constexpr int logn = L, n = 1 << L, nxh = n / 2 + 1, np = n + (n >> 4);
     C* tw = reinterpret_cast<C*>(smraw);
     C* buf = tw + n;
     const C* twg = twx_of<R>(kp);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
     const C* spec = static_cast<const C*>(kp.spec);
     const C* specB = static_cast<const C*>(kp.specB);
     V4* fields = static_cast<V4*>(kp.fields);
@@ -863,7 +859,6 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int logn) {
     const size_t S = size_t(nrows) * nxh;
     const R kxs = R(kTwoPi / kp.Lx);
     const int r0 = blockIdx.x * P;
-    __syncthreads();
     // sequence q = 2 p + w: row r0 + p; w = 0 packs (phi, E_x), w = 1 (E_y, E_z)
     auto load = [&](int q, int k) {
         const int p = q >> 1, w = q & 1, row = r0 + p;
@@ -899,7 +894,7 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int logn) {
         return z;
     };
     auto store = [&](int q, int i, C v) { buf[q * np + pad16(i)] = v; };
-    fft_pow2<false>(buf, tw, n, logn, 2 * P, +1, load, store);
+    fft_pow2<false>(buf, tw, n, logn, 2 * P, +1, load, store, twg);
     __syncthreads();
     const R s = R(kp.inv_nxny);
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
@@ -907,6 +902,30 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int logn) {
         if (row >= nrows) continue;
         const C u = buf[(2 * p) * np + pad16(x)], v = buf[(2 * p + 1) * np + pad16(x)];
         fields[size_t(row) * n + x] = Prec<R>::v4(u.x * s, u.y * s, v.x * s, v.y * s);
+    }
+}
+
+// The power-of-two kernels are compiled for each n = 2^L (32 <= n <= 4096),
+// so that their index arithmetic folds to constants. which: 0 x forward,
+// 1 y forward, 2 y inverse, 3 x inverse; nullptr for other sizes.
+using FftP2Kernel = void (*)(KP, int, int);
+template <class R, int L>
+FftP2Kernel fft_p2_at(int which) {
+    return which == 0 ? k_fftx_fwd_p2<R, L> : which == 1 ? k_ffty_fwd_p2<R, L>
+         : which == 2 ? k_ffty_inv_p2<R, L> : k_fftx_inv_p2<R, L>;
+}
+template <class R>
+FftP2Kernel fft_p2(int which, int logn) {
+    switch (logn) {
+        case 5: return fft_p2_at<R, 5>(which);
+        case 6: return fft_p2_at<R, 6>(which);
+        case 7: return fft_p2_at<R, 7>(which);
+        case 8: return fft_p2_at<R, 8>(which);
+        case 9: return fft_p2_at<R, 9>(which);
+        case 10: return fft_p2_at<R, 10>(which);
+        case 11: return fft_p2_at<R, 11>(which);
+        case 12: return fft_p2_at<R, 12>(which);
+        default: return nullptr;
     }
 }
 
@@ -2944,11 +2963,12 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             cudaFuncAttributes fa{};
             return cudaFuncGetAttributes(&fa, f) == cudaSuccess ? fa.maxThreadsPerBlock : 0;
         };
-        const int mxf = maxthr(mixed ? (const void*)k_fftx_fwd_p2<float> : (const void*)k_fftx_fwd_p2<double>);
-        const int mxi = maxthr(mixed ? (const void*)k_fftx_inv_p2<float> : (const void*)k_fftx_inv_p2<double>);
-        const int myf = maxthr(mixed ? (const void*)k_ffty_fwd_p2<float> : (const void*)k_ffty_fwd_p2<double>);
-        const int myi = maxthr(mixed ? (const void*)k_ffty_inv_p2<float> : (const void*)k_ffty_inv_p2<double>);
         auto lg = [](int v) { int l = 0; while ((1 << l) < v) ++l; return l; };
+        auto p2k = [&](int which, int n) {
+            return (const void*)(mixed ? fft_p2<float>(which, lg(n)) : fft_p2<double>(which, lg(n)));
+        };
+        const int mxf = pow2(nx) ? maxthr(p2k(0, nx)) : 0, mxi = pow2(nx) ? maxthr(p2k(3, nx)) : 0;
+        const int myf = pow2(ny) ? maxthr(p2k(1, ny)) : 0, myi = pow2(ny) ? maxthr(p2k(2, ny)) : 0;
         if (pow2(nx)) {
             const int n16 = nx / 16;
             const size_t seq = size_t(nx + n16) * csz;
@@ -2994,10 +3014,14 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         return DPSLAB_ERR_GRID;
     }
     if (mixed) {
-        raise_smem(reinterpret_cast<const void*>(k_fftx_fwd_p2<float>), size_t(pl->sm_fftx_fwd));
-        raise_smem(reinterpret_cast<const void*>(k_ffty_fwd_p2<float>), size_t(pl->sm_ffty_fwd));
-        raise_smem(reinterpret_cast<const void*>(k_ffty_inv_p2<float>), size_t(pl->sm_ffty_inv));
-        raise_smem(reinterpret_cast<const void*>(k_fftx_inv_p2<float>), size_t(pl->sm_fftx_inv));
+        if (pl->p2x) {
+            raise_smem(reinterpret_cast<const void*>(fft_p2<float>(0, pl->lognx)), size_t(pl->sm_fftx_fwd));
+            raise_smem(reinterpret_cast<const void*>(fft_p2<float>(3, pl->lognx)), size_t(pl->sm_fftx_inv));
+        }
+        if (pl->p2y) {
+            raise_smem(reinterpret_cast<const void*>(fft_p2<float>(1, pl->logny)), size_t(pl->sm_ffty_fwd));
+            raise_smem(reinterpret_cast<const void*>(fft_p2<float>(2, pl->logny)), size_t(pl->sm_ffty_inv));
+        }
         raise_smem(reinterpret_cast<const void*>(k_fftx_fwd<float>), size_t(pl->sm_fftx_fwd));
         raise_smem(reinterpret_cast<const void*>(k_ffty_fwd<float>), size_t(pl->sm_ffty_fwd));
         raise_smem(reinterpret_cast<const void*>(k_ffty_inv<float>), size_t(pl->sm_ffty_inv));
@@ -3014,10 +3038,14 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         raise_smem(reinterpret_cast<const void*>(k_column_mixed<true>), size_t(pl->sm_col));
         raise_smem(reinterpret_cast<const void*>(k_interp_f32), size_t(pl->sm_interp));
     } else {
-        raise_smem(reinterpret_cast<const void*>(k_fftx_fwd_p2<double>), size_t(pl->sm_fftx_fwd));
-        raise_smem(reinterpret_cast<const void*>(k_ffty_fwd_p2<double>), size_t(pl->sm_ffty_fwd));
-        raise_smem(reinterpret_cast<const void*>(k_ffty_inv_p2<double>), size_t(pl->sm_ffty_inv));
-        raise_smem(reinterpret_cast<const void*>(k_fftx_inv_p2<double>), size_t(pl->sm_fftx_inv));
+        if (pl->p2x) {
+            raise_smem(reinterpret_cast<const void*>(fft_p2<double>(0, pl->lognx)), size_t(pl->sm_fftx_fwd));
+            raise_smem(reinterpret_cast<const void*>(fft_p2<double>(3, pl->lognx)), size_t(pl->sm_fftx_inv));
+        }
+        if (pl->p2y) {
+            raise_smem(reinterpret_cast<const void*>(fft_p2<double>(1, pl->logny)), size_t(pl->sm_ffty_fwd));
+            raise_smem(reinterpret_cast<const void*>(fft_p2<double>(2, pl->logny)), size_t(pl->sm_ffty_inv));
+        }
         raise_smem(reinterpret_cast<const void*>(k_fftx_fwd<double>), size_t(pl->sm_fftx_fwd));
         raise_smem(reinterpret_cast<const void*>(k_ffty_fwd<double>), size_t(pl->sm_ffty_fwd));
         raise_smem(reinterpret_cast<const void*>(k_ffty_inv<double>), size_t(pl->sm_ffty_inv));
@@ -3066,16 +3094,16 @@ int xy_transforms(dpslab_plan* pl, const KP& kp, cudaStream_t st, bool inverse) 
     if (!inverse) {
         const dim3 gy((kp.nxh + pl->tk_fwd - 1) / pl->tk_fwd, 2 * kp.nz);
         const int gx = (npairs + pl->px_fwd - 1) / pl->px_fwd;
-        if (pl->p2x) k_fftx_fwd_p2<R><<<gx, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx);
+        if (pl->p2x) fft_p2<R>(0, pl->lognx)<<<gx, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx);
         else k_fftx_fwd<R><<<gx, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd);
-        if (pl->p2y) k_ffty_fwd_p2<R><<<gy, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny);
+        if (pl->p2y) fft_p2<R>(1, pl->logny)<<<gy, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny);
         else k_ffty_fwd<R><<<gy, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd);
     } else {
         const dim3 gy((kp.nxh + pl->tk_inv - 1) / pl->tk_inv, kp.nz);
         const int gx = (npairs + pl->px_inv - 1) / pl->px_inv;
-        if (pl->p2y) k_ffty_inv_p2<R><<<gy, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny);
+        if (pl->p2y) fft_p2<R>(2, pl->logny)<<<gy, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny);
         else k_ffty_inv<R><<<gy, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv);
-        if (pl->p2x) k_fftx_inv_p2<R><<<gx, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx);
+        if (pl->p2x) fft_p2<R>(3, pl->lognx)<<<gx, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx);
         else k_fftx_inv<R><<<gx, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv);
     }
     const cudaError_t e = cudaGetLastError();
@@ -3468,8 +3496,7 @@ bool apply_shape_t(dpslab_plan* pl, int which, int v) {
         const int seqs = which == 3 ? 2 * v : v;         // the x inverse transforms two sequences per row
         thr = seqs * n16;
         sm = tw + seqs * seq;
-        f = which == 0 ? (const void*)k_fftx_fwd_p2<R> : which == 1 ? (const void*)k_ffty_fwd_p2<R>
-          : which == 2 ? (const void*)k_ffty_inv_p2<R> : (const void*)k_fftx_inv_p2<R>;
+        f = (const void*)fft_p2<R>(which, which == 0 || which == 3 ? pl->lognx : pl->logny);
         if (thr > maxthr(f)) return false;
     } else {
         const int mul = which == 0 || which == 1 ? 2 : which == 2 ? 6 : 4;
@@ -3664,10 +3691,10 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     const int gx_inv = (kp.nz * kp.ny + pl->px_inv - 1) / pl->px_inv;
     const int gi = (n + kInterpWarps - 1) / kInterpWarps;
     if (kp.mixed) {
-        if (pl->p2x) LAUNCH(k_fftx_fwd_p2<float><<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
+        if (pl->p2x) LAUNCH(fft_p2<float>(0, pl->lognx)<<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
         else LAUNCH(k_fftx_fwd<float><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
         mark(3);
-        if (pl->p2y) LAUNCH(k_ffty_fwd_p2<float><<<gy_fwd, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny));
+        if (pl->p2y) LAUNCH(fft_p2<float>(1, pl->logny)<<<gy_fwd, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny));
         else LAUNCH(k_ffty_fwd<float><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
         mark(4);
         if (pl->ztensor) {
@@ -3682,29 +3709,29 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
             mark(6);
         }
         mark(7);
-        if (pl->p2y) LAUNCH(k_ffty_inv_p2<float><<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
+        if (pl->p2y) LAUNCH(fft_p2<float>(2, pl->logny)<<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
         else LAUNCH(k_ffty_inv<float><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
         mark(8);
-        if (pl->p2x) LAUNCH(k_fftx_inv_p2<float><<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
+        if (pl->p2x) LAUNCH(fft_p2<float>(3, pl->lognx)<<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
         else LAUNCH(k_fftx_inv<float><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(9);
         LAUNCH(k_interp_f32<<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
         if (kp.sigma_on) LAUNCH(k_wall_cross<float><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     } else {
-        if (pl->p2x) LAUNCH(k_fftx_fwd_p2<double><<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
+        if (pl->p2x) LAUNCH(fft_p2<double>(0, pl->lognx)<<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
         else LAUNCH(k_fftx_fwd<double><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
         mark(3);
-        if (pl->p2y) LAUNCH(k_ffty_fwd_p2<double><<<gy_fwd, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny));
+        if (pl->p2y) LAUNCH(fft_p2<double>(1, pl->logny)<<<gy_fwd, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny));
         else LAUNCH(k_ffty_fwd<double><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
         mark(4);
         mark(5);
         LAUNCH(k_column<<<kp.n_col_blocks, kColThreads, pl->sm_col, st>>>(kp));
         mark(6);
         mark(7);
-        if (pl->p2y) LAUNCH(k_ffty_inv_p2<double><<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
+        if (pl->p2y) LAUNCH(fft_p2<double>(2, pl->logny)<<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
         else LAUNCH(k_ffty_inv<double><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
         mark(8);
-        if (pl->p2x) LAUNCH(k_fftx_inv_p2<double><<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
+        if (pl->p2x) LAUNCH(fft_p2<double>(3, pl->lognx)<<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
         else LAUNCH(k_fftx_inv<double><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(9);
         LAUNCH(k_interp<double><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
