@@ -2256,8 +2256,13 @@ __global__ void k_origin(KP kp) {
         }
     }
     double v = 0.0;
-    if (k < kp.n && kp.near_on) {
-        const double4_32a p = kp.part[k];
+    const double4_32a p = k < kp.n ? kp.part[k] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    // x, y lie in [0, L]: the periodic distance to the origin is min(x, L - x),
+    // and a charge farther than r_cut in x or y reaches it with neither
+    // itself nor an image (the margin covers the rounding of min_image)
+    const double lim = kp.r_cut * (1.0 + 1e-9);
+    const bool cand = k < kp.n && fmin(p.x, kp.Lx - p.x) <= lim && fmin(p.y, kp.Ly - p.y) <= lim;
+    if (cand && kp.near_on) {
         const double dx = min_image(0.0 - p.x, kp.Lx), dy = min_image(0.0 - p.y, kp.Ly);
         const double rc = kp.r_cut;
         const double r = sqrt(dx * dx + dy * dy + p.z * p.z);
