@@ -17,14 +17,13 @@ enum : int {
     kStatusRejected = 16,     // every proposal of a Brownian-dynamics step left the slab
 };
 
-// One spreading source with its support precomputed: grid indices
-// xlo..xlo+sx-1, ylo..ylo+sy-1 (unwrapped) and nodes j0..j1, offsets of the
-// first x and y index from the source, strength, and whether it also feeds
-// rho_o (a charge of C_over).
+// The record types below are 16-byte aligned so that they move as 16-byte
+// vector loads and stores (one L2 sector per 32-byte record, not eight).
+
 // Interpolation window of one charge (mixed precision), Sec. 5.2.2 step 7:
 // the same index rule as the spreading, evaluated once per charge in double;
 // offsets of the first x and y points and z as a float pair.
-struct IRec {
+struct __align__(16) IRec {
     float d0x, d0y;           // x_lo h_x - x, y_lo h_y - y
     float zhi, zlo;           // z = zhi + zlo
     int xlo, ylo;
@@ -33,7 +32,7 @@ struct IRec {
 
 // A source of the mixed-precision spreading (float offsets and strength,
 // z as a float pair), stored once per (tile, slab) block it touches.
-struct SrcF {
+struct __align__(16) SrcF {
     float d0x, d0y;           // x_lo h_x - x, y_lo h_y - y
     float zhi, zlo;           // z = zhi + zlo
     float q;                  // strength (image strengths for images)
@@ -45,13 +44,17 @@ struct SrcF {
 // (mixed precision, normalised form of Eq. (inphisc)): the correction is
 // iden (P (-(e1 - Gt e2)) + Q (e3 - Gb e4)) with e1 = e^{-kz}, e3 = e^{k(z-H)},
 // e2 = e3 ekH, e4 = e1 ekH; corr = 0 for modes without one.
-struct ColP {
+struct __align__(16) ColP {
     float2 P, Q;
     float k, ekH, iden;
     int corr;
 };
 
-struct SrcRec {
+// One spreading source (FP64) with its support precomputed: grid indices
+// xlo..xlo+sx-1, ylo..ylo+sy-1 (unwrapped) and nodes j0..j1, offsets of the
+// first x and y index from the source, strength, and whether it also feeds
+// rho_o (a charge of C_over).
+struct __align__(16) SrcRec {
     double z, q, d0x, d0y;
     int xlo, ylo, j0, j1;
     int sx, sy, over, pad;

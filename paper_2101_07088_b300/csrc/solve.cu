@@ -534,13 +534,28 @@ __global__ void k_scatter_sources_f(KP kp) {
             nty = axis_tiles(r.ylo, (r.pack >> 6) & 63, kp.ny, ty);
         }
         const int j0 = (r.pack >> 12) & 511, j1 = (r.pack >> 21) & 511;
+        // per slab, up to 3 x 3 tiles at a time: every slot is claimed (the
+        // atomics are independent) before the first record is stored, so
+        // their round trips overlap
         for (int sl = j0 / kSlabM; sl <= j1 / kSlabM; ++sl)
-            for (int a = 0; a < nty; ++a)
-                for (int c = 0; c < ntx; ++c) {
-                    const int b = sl * kp.ntiles + ty[a] * kp.ntx + tx[c];
-                    const size_t at = size_t(kp.tile_start[b]) + atomicAdd(&kp.tile_fill[b], 1);
-                    if (at < kp.src_cap) kp.srcsf[at] = r;
-                    else atomicOr(kp.status, kStatusCapacity);
+            for (int a0 = 0; a0 < nty; a0 += 3)
+                for (int c0 = 0; c0 < ntx; c0 += 3) {
+                    int at[9];
+#pragma unroll
+                    for (int u = 0; u < 9; ++u) {
+                        const int a = a0 + u / 3, c = c0 + u % 3;
+                        at[u] = -1;
+                        if (a < nty && c < ntx) {
+                            const int b = sl * kp.ntiles + ty[a] * kp.ntx + tx[c];
+                            at[u] = kp.tile_start[b] + atomicAdd(&kp.tile_fill[b], 1);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 9; ++u) {
+                        if (at[u] < 0) continue;
+                        if (size_t(at[u]) < kp.src_cap) kp.srcsf[at[u]] = r;
+                        else atomicOr(kp.status, kStatusCapacity);
+                    }
                 }
     }
 }
