@@ -559,18 +559,20 @@ def main():
     # e2e: host buffers through dpslab_solve_host (H2D of pos, q; D2H of phi, force, U)
     pin_pos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
     pin_q = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    pin_phi = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    pin_force = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
     pin_pos.copy_(torch.from_numpy(pos))
     pin_q.copy_(torch.from_numpy(q))
-    hp, hq = pin_pos.numpy(), pin_q.numpy()
+    hp, hq, hphi, hforce = pin_pos.numpy(), pin_q.numpy(), pin_phi.numpy(), pin_force.numpy()
     for _ in range(2):
-        plan.solve_host(hp, hq, stream=stream)
+        plan.solve_host(hp, hq, stream=stream, phi=hphi, force=hforce)
     e2e_ms = []
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        plan.solve_host(hp, hq, stream=stream)
+        plan.solve_host(hp, hq, stream=stream, phi=hphi, force=hforce)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))

@@ -320,14 +320,26 @@ class Plan:
         rc = lib().dpslab_solve_poll(self._h, ctypes.byref(U))
         return (rc, None) if rc == PENDING else (rc, U.value)
 
-    def solve_host(self, pos, q, want_phi=True, want_force=True, stream=None, check=True):
+    def solve_host(self, pos, q, want_phi=True, want_force=True, stream=None, check=True, phi=None, force=None):
         """Host (numpy) buffers; copies happen inside the library call.
-        Returns (U, phi or None, force or None, return code)."""
+        phi [n] and force [n, 3] may be given as C-contiguous float64 arrays
+        (pinned memory, e.g. a pinned torch tensor's .numpy(), makes the
+        device-to-host copies asynchronous and fast); otherwise they are
+        allocated. Returns (U, phi or None, force or None, return code)."""
         pos = np.ascontiguousarray(pos, dtype=np.float64)
         q = np.ascontiguousarray(q, dtype=np.float64)
         n = q.shape[0]
-        phi = np.empty(n) if want_phi else None
-        force = np.empty((n, 3)) if want_force else None
+
+        def out(a, shape, want):
+            if not want:
+                return None
+            if a is None:
+                return np.empty(shape)
+            if a.shape != shape or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
+                raise ValueError(f"output must be a writeable C-contiguous float64 array of shape {shape}")
+            return a
+        phi = out(phi, (n,), want_phi)
+        force = out(force, (n, 3), want_force)
         U = ctypes.c_double(math.nan)
         st = None
         if stream is not None:

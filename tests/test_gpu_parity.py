@@ -182,3 +182,14 @@ def test_host_entry_point_matches_device_one():
     assert np.allclose(phi, a["phi"], rtol=0, atol=1e-13 * np.max(np.abs(a["phi"])))
     assert np.allclose(force, a["force"], rtol=0, atol=1e-13 * np.max(np.abs(a["force"])))
     assert plan.last_launch_count() >= 10
+    # caller-owned (pinned) output buffers give the same result; a wrongly
+    # shaped buffer is refused before any copy
+    pin_phi = torch.empty(len(q), dtype=torch.float64, pin_memory=True).numpy()
+    pin_force = torch.empty((len(q), 3), dtype=torch.float64, pin_memory=True).numpy()
+    U2, phi2, force2, rc = plan.solve_host(pos, q, phi=pin_phi, force=pin_force)
+    assert rc == 0 and phi2 is pin_phi and force2 is pin_force
+    assert abs(U2 - U) <= 1e-13 * abs(U)
+    assert np.allclose(phi2, phi, rtol=0, atol=1e-13 * np.max(np.abs(phi)))
+    assert np.allclose(force2, force, rtol=0, atol=1e-13 * np.max(np.abs(force)))
+    with pytest.raises(ValueError):
+        plan.solve_host(pos, q, force=np.empty((len(q), 2)))
