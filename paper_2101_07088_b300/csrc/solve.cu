@@ -31,6 +31,35 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
+// Warp sums of V = 2^k values at once (transposed butterfly): at each of the
+// first k steps a lane keeps half of its values and sends the other half to
+// its partner, which adds them to its own; the last 5 - k steps are plain.
+// That is V - 1 + 5 - k shuffles instead of 5 V. On return lane l holds the
+// sum of value (l >> (5 - k)) & (V - 1).
+template <int V, class T>
+__device__ __forceinline__ T warp_sum_multi(const T* in) {
+    static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V is a power of two up to 32");
+    T a[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) a[i] = in[i];
+    const int lane = threadIdx.x & 31;
+    int o = 16;
+#pragma unroll
+    for (int h = V / 2; h >= 1; h /= 2, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = up ? a[i] : a[i + h];
+            const T keep = up ? a[i + h] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    T r = a[0];
+#pragma unroll
+    for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -1092,7 +1121,13 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
             if (n & 1) { acc[9] = fma(gtn, xc[n], acc[9]); acc[11] = fma(gbn, xc[n], acc[11]); }
             else { acc[8] = fma(gtn, xc[n], acc[8]); acc[10] = fma(gbn, xc[n], acc[10]); }
         }
-        for (int i = 0; i < 12; ++i) acc[i] = warp_sum(acc[i]);
+        {   // the 12 sums (lane 4 v: value v < 8, lane 8 v: value 8 + v), gathered
+            const double r8 = warp_sum_multi<8>(acc), r4 = warp_sum_multi<4>(acc + 8);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = __shfl_sync(0xffffffffu, r8, 4 * i);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[8 + i] = __shfl_sync(0xffffffffu, r4, 8 * i);
+        }
         if (lane < 2) {
             const int f = lane;
             const double2 sFt = f ? make_double2(acc[4], acc[5]) : make_double2(acc[0], acc[1]);
@@ -1164,7 +1199,13 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
             acc[16] = fma(alt, ypo[n].x, acc[16]); acc[17] += ypo[n].x;                // psi_o*'(a), (b)
             acc[18] = fma(wg, yi[n].x, acc[18]); acc[19] = fma(wg, yi[n].y, acc[19]);   // gauge sum
         }
-        for (int i = 0; i < 20; ++i) acc[i] = warp_sum(acc[i]);
+        {   // the 20 sums (lane 2 v: value v < 16, lane 8 v: value 16 + v), gathered
+            const double r16 = warp_sum_multi<16>(acc), r4 = warp_sum_multi<4>(acc + 16);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = __shfl_sync(0xffffffffu, r16, 2 * i);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[16 + i] = __shfl_sync(0xffffffffu, r4, 8 * i);
+        }
         if (lane == 0 && s_valid[c]) {
             const double dz = 2.0 / Hbar;
             const double2 pi0 = make_double2(acc[0], acc[1]), dpi0 = make_double2(acc[2] * dz, acc[3] * dz);
@@ -1508,8 +1549,14 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
             if (n & 1) { acc[9] = fmaf(gtn, xc[n], acc[9]); acc[11] = fmaf(gbn, xc[n], acc[11]); }
             else { acc[8] = fmaf(gtn, xc[n], acc[8]); acc[10] = fmaf(gbn, xc[n], acc[10]); }
         }
+        // the 12 sums: values 0..7 (lane 4 v holds value v) and 8..11
+        // (lane 8 v holds value 8 + v), gathered where they are used
+        const float r8 = warp_sum_multi<8>(acc), r4 = warp_sum_multi<4>(acc + 8);
         float da[12];
-        for (int i = 0; i < 12; ++i) da[i] = warp_sum_f(acc[i]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) da[i] = __shfl_sync(0xffffffffu, r8, 4 * i);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) da[8 + i] = __shfl_sync(0xffffffffu, r4, 8 * i);
         if (lane < 2) {
             const int f = lane;
             const float2 sFt = f ? make_float2(da[4], da[5]) : make_float2(da[0], da[1]);
@@ -1583,8 +1630,14 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
             acc[16] = fmaf(alt, ypo[n].x, acc[16]); acc[17] += ypo[n].x;
             acc[18] = fmaf(wg, yi[n].x, acc[18]); acc[19] = fmaf(wg, yi[n].y, acc[19]);
         }
+        // the 20 sums: values 0..15 (lane 2 v holds value v) and 16..19
+        // (lane 8 v holds value 16 + v), gathered where they are used
+        const float r16 = warp_sum_multi<16>(acc), r4 = warp_sum_multi<4>(acc + 16);
         float da[20];
-        for (int i = 0; i < 20; ++i) da[i] = warp_sum_f(acc[i]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) da[i] = __shfl_sync(0xffffffffu, r16, 2 * i);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) da[16 + i] = __shfl_sync(0xffffffffu, r4, 8 * i);
         if (lane == 0 && s_valid[c]) {
             const float dz = kp.f.sz;
             const float2 pi0 = make_float2(da[0], da[1]), dpi0 = make_float2(da[2] * dz, da[3] * dz);
