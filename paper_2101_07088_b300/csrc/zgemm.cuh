@@ -56,8 +56,10 @@ constexpr int kZSboB = 2048 + 16;           // bytes between B row groups
 constexpr int kZPieceB = (kZN / 8) * (kZSboB / 2);   // bf16 elements per B piece
 constexpr size_t kZSmemA = 3 * size_t(kZPieceA) * 2;
 constexpr size_t kZSmemB = 3 * size_t(kZPieceB) * 2;
-constexpr size_t kZSmem = kZSmemA + kZSmemB + 64;
-constexpr int kZTmemCols = 2 * kZN;         // exact product 11 | the other five
+constexpr int kZOStride = kZN + 4;          // staged output row stride (16-byte rows, conflict-free)
+constexpr int kZORows = 32;                 // rows of the single-block path's staging area
+constexpr size_t kZSmemO = size_t(kZORows) * kZOStride * 4;
+constexpr size_t kZSmem = kZSmemA + kZSmemB + 64 + kZSmemO;
 constexpr int kZRows = 8;                   // rows per thread and tile (4 columns each)
 constexpr int kZGroups = kZK / kZRows;      // row groups of a tile
 constexpr long kZSpinLimit = 1L << 26;      // polls of an mbarrier before giving up
@@ -170,7 +172,6 @@ __device__ __forceinline__ void put8(unsigned short* sB, int n, int k0, const fl
 // epi(plane, row, col0, v[32], nvalid) may change the 32 outputs of row `row`
 // from column col0 before they are stored (the tile is staged in shared
 // memory so that each warp store writes 512 contiguous bytes of one row).
-constexpr int kZOStride = kZN + 4;          // staged output row stride (16-byte rows, conflict-free)
 static_assert(size_t(kZK) * kZOStride * 4 <= kZSmemB, "staged outputs fit the B pieces");
 // prep(plane, col0) runs on every thread once per tile while the MMAs are in
 // flight (before the barrier that precedes the epilogue): it may stage
@@ -196,19 +197,44 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     uint64_t* abar = bar + 1;                   // bulk copies of the A blocks (nblk > 1)
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
     __shared__ int s_abort;
-    __shared__ float s_colmax[kZGroups][kZN];
+    // column maxima: per (column offset j of a quad, row group, quad) and
+    // reduced over the row groups (transposed so that both passes are
+    // conflict-free)
+    __shared__ float s_cmT[4][kZGroups][kZN / 4];
+    __shared__ float s_amax[4][kZN / 4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_per_plane = (ncols + kZN - 1) / kZN;
     const int ntiles = nplanes * tiles_per_plane;
     // this thread's 4 columns (4 cq .. 4 cq + 3) and 8 rows (8 g .. 8 g + 7)
     const int cq = tid & (kZN / 4 - 1), g = tid / (kZN / 4), r0 = g * kZRows;
+    // the largest |entry| of this thread's four columns over all rows of the
+    // tile, from each thread's partial maxima cm
+    auto colmax = [&](const float* cm, float* amax) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s_cmT[j][g][cq] = cm[j];
+        __syncthreads();
+        if (tid < kZN) {
+            const int j = tid / (kZN / 4), c = tid & (kZN / 4 - 1);
+            float m = 0.f;
+#pragma unroll
+            for (int i = 0; i < kZGroups; ++i) m = fmaxf(m, s_cmT[j][i][c]);
+            s_amax[j][c] = m;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) amax[j] = s_amax[j][cq];
+    };
 
     auto stage_a = [&](int rb, int kb) {     // block (rb, kb) of the image into shared memory
         const uint4* src = reinterpret_cast<const uint4*>(aimg + zimg_block(rb, kb, nblk, 0));
         uint4* dst = reinterpret_cast<uint4*>(sA);
         for (int i = tid; i < int(kZSmemA / 16); i += blockDim.x) dst[i] = src[i];
     };
-    const uint32_t tcols = nblk > 1 ? 4u * kZN : uint32_t(kZTmemCols);
+    // tensor memory: nblk = 1 keeps two tiles' accumulators (the epilogue of
+    // one runs while the MMAs of the next are in flight); nblk = 2 the four
+    // accumulators of one tile
+    const uint32_t tcols = 4u * kZN;
+    float* sO = reinterpret_cast<float*>(zsm + kZSmemA + kZSmemB + 64);   // nblk = 1 staging
     if (nblk == 1) stage_a(0, 0);
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -264,6 +290,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
             const int w = min(kZN, ncols - c0);
             // each column's largest |entry| over all K: one fixed-point grid
             // per column for the exact product
+            float am[4];
             {
                 float cm[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -273,16 +300,12 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
                     cm[2] = fmaxf(cm[2], fmaxf(fabsf(rv[i].z), fabsf(rw[i].z)));
                     cm[3] = fmaxf(cm[3], fmaxf(fabsf(rv[i].w), fabsf(rw[i].w)));
                 }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) s_colmax[g][4 * cq + j] = cm[j];
+                colmax(cm, am);
             }
-            __syncthreads();
             float qv[4], iqv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float amax = 0.f;
-#pragma unroll
-                for (int i = 0; i < kZGroups; ++i) amax = fmaxf(amax, s_colmax[i][4 * cq + j]);
+                const float amax = am[j];
                 int e = 0;
                 if (amax > 0.f) frexpf(amax, &e);
                 qv[j] = ldexpf(1.f, 7 - e);
@@ -381,10 +404,53 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
             __syncthreads();
         }
     }
-    if (nblk == 1 && int(blockIdx.x) < ntiles) load(blockIdx.x, 0);
-    for (int t = blockIdx.x; nblk == 1 && t < ntiles; t += gridDim.x) {
+    // nblk = 1. Per tile t: split the values into B, issue the MMAs into
+    // accumulator buffer (i & 1), prefetch the next tile's values, then run
+    // the epilogue of tile t - 1 from the other buffer while those MMAs are
+    // in flight, and wait for them (B is then free for the next split).
+    auto epilogue = [&](int t, uint32_t tb) {
         const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
         const int w = min(kZN, ncols - c0);
+        // warp: TMEM lane quarter (warp % 4) = rows, 32 columns ((warp / 4) * 32)
+        const int qtr = warp & 3, cc = (warp >> 2) * 32;
+        const int r = qtr * 32 + lane;
+        const uint32_t lb = tb + (uint32_t(qtr * 32) << 16) + uint32_t(cc);
+        float v[32], u[16];
+#pragma unroll
+        for (int h = 0; h < 32; h += 16) {
+            tc_ld16(lb + uint32_t(h), v + h);
+            tc_ld16(lb + uint32_t(kZN + h), u);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[h + i] += u[i];
+        }
+        const int wv = min(32, w - cc);
+        if (r < rows && wv > 0) epi(plane, r, c0 + cc, v, wv);
+        // staged a quarter (32 rows) at a time, then stored whole rows: warp w
+        // stores rows w and w + 16 of the quarter, lane l columns 4l .. 4l + 3
+        float* dst = base + size_t(plane) * pstride + c0 + 4 * lane;
+        for (int q = 0; q < kZK / kZORows; ++q) {
+            if (qtr == q) {
+#pragma unroll
+                for (int i = 0; i < 32; i += 4)
+                    *reinterpret_cast<float4*>(sO + lane * kZOStride + cc + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
+            __syncthreads();
+            if (4 * lane < w) {
+                for (int rr = warp; rr < kZORows; rr += kZThreads / 32) {
+                    const int row = q * kZORows + rr;
+                    if (row < rows)
+                        __stcs(reinterpret_cast<float4*>(dst + size_t(row) * ld),
+                               *reinterpret_cast<const float4*>(sO + rr * kZOStride + 4 * lane));
+                }
+            }
+            __syncthreads();
+        }
+    };
+    int prev_t = -1;
+    uint32_t prev_buf = 0u;
+    if (nblk == 1 && int(blockIdx.x) < ntiles) load(blockIdx.x, 0);
+    for (int t = blockIdx.x, it = 0; nblk == 1 && t < ntiles; t += gridDim.x, ++it) {
+        const uint32_t buf = tmem + uint32_t((it & 1) * 2 * kZN);
         // per column, the largest |entry| (fixed-point scale of piece 1), then
         // the split into the three pieces at K entries r0 .. r0 + 7
         float cm[4] = {0.f, 0.f, 0.f, 0.f};
@@ -395,15 +461,12 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
             cm[2] = fmaxf(cm[2], fabsf(rv[i].z));
             cm[3] = fmaxf(cm[3], fabsf(rv[i].w));
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) s_colmax[g][4 * cq + j] = cm[j];
-        __syncthreads();
+        float am[4];
+        colmax(cm, am);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int n = 4 * cq + j;
-            float amax = 0.f;
-#pragma unroll
-            for (int i = 0; i < kZGroups; ++i) amax = fmaxf(amax, s_colmax[i][n]);
+            const float amax = am[j];
             int e = 0;
             if (amax > 0.f) frexpf(amax, &e);
             const float q = ldexpf(1.f, 7 - e), iq = ldexpf(1.f, e - 7);   // 128/s, s/128 with s = 2^e > amax
@@ -413,6 +476,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
             put8(sB, n, r0, x, q, iq);
         }
         fence_async_smem();
+        tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
@@ -422,60 +486,42 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
 #pragma unroll
             for (int qd = 0; qd < 6; ++qd)
 #pragma unroll
-                for (int s = 0; s < kZK / 16; ++s) {
-                    const uint64_t ad = zdesc(a0 + uint32_t(pa[qd]) * kZPieceA * 2 + uint32_t(s) * 256u, 128u, 2048u);
-                    const uint64_t bd = zdesc(b0 + uint32_t(pb[qd]) * kZPieceB * 2 + uint32_t(s) * 256u, 128u, kZSboB);
-                    const bool first = s == 0 && qd <= 1;      // first K step of either accumulator
-                    tc_mma(tmem + (qd == 0 ? 0u : uint32_t(kZN)), ad, bd, idesc, first ? 0u : 1u);
+                for (int s8 = 0; s8 < kZK / 16; ++s8) {
+                    const uint64_t ad = zdesc(a0 + uint32_t(pa[qd]) * kZPieceA * 2 + uint32_t(s8) * 256u, 128u, 2048u);
+                    const uint64_t bd = zdesc(b0 + uint32_t(pb[qd]) * kZPieceB * 2 + uint32_t(s8) * 256u, 128u, kZSboB);
+                    const bool first = s8 == 0 && qd <= 1;      // first K step of either accumulator
+                    tc_mma(buf + (qd == 0 ? 0u : uint32_t(kZN)), ad, bd, idesc, first ? 0u : 1u);
                 }
             tc_commit(bar);
         }
         pend = true;
         // the next tile's values, while the tensor cores work
         if (t + int(gridDim.x) < ntiles) load(t + gridDim.x, 0);
-        prep(plane, c0);
+        if (prev_t >= 0) {
+            const int pplane = prev_t / tiles_per_plane;
+            prep(pplane, (prev_t - pplane * tiles_per_plane) * kZN);
+            __syncthreads();
+            tc_fence_after();
+            epilogue(prev_t, prev_buf);
+        }
         // one thread polls the MMA barrier (polls from every warp would
         // compete with the loads for the memory pipes); the rest wait here
         if (tid == 0 && !mbar_wait(bar, ph)) s_abort = 1;
-        __syncthreads();
-        if (!s_abort) {
-            ph ^= 1u;
-            pend = false;
-        }
-        tc_fence_after();
-        if (s_abort) break;
-        {
-            // warp: TMEM lane quarter (warp % 4) = rows, 32 columns ((warp / 4) * 32)
-            const int qtr = warp & 3, cc = (warp >> 2) * 32;
-            const int r = qtr * 32 + lane;
-            const uint32_t lb = tmem + (uint32_t(qtr * 32) << 16) + uint32_t(cc);
-            float v[32], u[16];
-#pragma unroll
-            for (int h = 0; h < 32; h += 16) {
-                tc_ld16(lb + uint32_t(h), v + h);
-                tc_ld16(lb + uint32_t(kZN + h), u);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[h + i] += u[i];
-            }
-            const int wv = min(32, w - cc);
-            if (r < rows && wv > 0) epi(plane, r, c0 + cc, v, wv);
-            // stage (the B pieces are free once the MMAs completed)
-            float* O = reinterpret_cast<float*>(sB);
-#pragma unroll
-            for (int i = 0; i < 32; i += 4)
-                *reinterpret_cast<float4*>(O + r * kZOStride + cc + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-            __syncthreads();
-            // warp w stores rows w, w + 16, ...: lane l writes columns 4l .. 4l + 3
-            float* dst = base + size_t(plane) * pstride + c0 + 4 * lane;
-            if (4 * lane < w) {
-                for (int rr = warp; rr < rows; rr += kZThreads / 32)
-                    __stcs(reinterpret_cast<float4*>(dst + size_t(rr) * ld),
-                           *reinterpret_cast<const float4*>(O + rr * kZOStride + 4 * lane));
-            }
-        }
         tc_fence_before();
-        fence_async_smem();
         __syncthreads();
+        if (s_abort) break;
+        ph ^= 1u;
+        pend = false;
+        tc_fence_after();
+        prev_t = t;
+        prev_buf = buf;
+    }
+    if (nblk == 1 && prev_t >= 0 && !s_abort) {
+        const int pplane = prev_t / tiles_per_plane;
+        prep(pplane, (prev_t - pplane * tiles_per_plane) * kZN);
+        __syncthreads();
+        tc_fence_after();
+        epilogue(prev_t, prev_buf);
     }
     if (s_abort && tid == 0) {
         atomicOr(status, kStatusTimeout);
