@@ -2616,6 +2616,10 @@ struct dpslab_plan {
     void* sig_mem = nullptr;      // wall charges: transforms, correction grid, scratch
     size_t sig_bytes = 0;
     cudaEvent_t done = nullptr;   // end of an enqueued (asynchronous) solve
+    // the near field runs on its own stream, overlapping the far field: it
+    // forks after the cell list and joins before the assembly
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool in_flight = false;
     bool bound = false;           // a workspace is bound (owned, a batch's, or the caller's)
     int64_t last_n = 0;
@@ -2733,6 +2737,9 @@ size_t bind_work(dpslab_plan* pl, char* base) {
 void release(dpslab_plan* pl) {
     if (!pl) return;
     if (pl->done) cudaEventDestroy(pl->done);
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+    if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+    if (pl->side) cudaStreamDestroy(pl->side);
     for (auto& e : pl->ev)
         if (e) cudaEventDestroy(e);
     if (pl->tables) cudaFree(pl->tables);
@@ -3011,7 +3018,10 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         }
     }
     if (cudaMallocHost(&pl->h_scal, 16 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&pl->h_status, 16 * sizeof(int)) != cudaSuccess) {
+        cudaMallocHost(&pl->h_status, 16 * sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         release(pl);
         return DPSLAB_ERR_CUDA;
     }
@@ -3744,6 +3754,18 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         LAUNCH(k_scatter_cells<<<nb, kChargeThreads, 0, st>>>(kp));
     }
     mark(1);
+    // The near field needs only the cell list (and writes only nearv): it
+    // runs on the plan's second stream while the far field runs here, and
+    // this stream waits for it before the assembly. Profiled solves keep it
+    // in line so that every stage has its own time.
+    const bool fork = kp.near_on && !prof;
+    if (fork) {
+        DPS_CUDA(cudaEventRecord(pl->ev_fork, st));
+        DPS_CUDA(cudaStreamWaitEvent(pl->side, pl->ev_fork, 0));
+        if (kp.mixed) LAUNCH(k_near_f32<<<(n + 127) / 128, 128, 0, pl->side>>>(kp));
+        else LAUNCH(k_near<double><<<(n + 127) / 128, 128, 0, pl->side>>>(kp));
+        DPS_CUDA(cudaEventRecord(pl->ev_join, pl->side));
+    }
     const dim3 gs(kp.ntiles, kp.nslabs);
     if (kp.mixed) {
         LAUNCH(k_sources_f<<<nb, kChargeThreads, 0, st>>>(kp));
@@ -3811,10 +3833,11 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         if (kp.sigma_on) LAUNCH(k_wall_cross<double><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
     }
     mark(10);
-    if (kp.near_on) {
+    if (kp.near_on && !fork) {
         if (kp.mixed) LAUNCH(k_near_f32<<<(n + 127) / 128, 128, 0, st>>>(kp));
         else LAUNCH(k_near<double><<<(n + 127) / 128, 128, 0, st>>>(kp));
     }
+    if (fork) DPS_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
     mark(11);
     LAUNCH(k_origin<<<nb, kChargeThreads, 0, st>>>(kp));
     LAUNCH(k_final_gauge<<<1, 1024, 0, st>>>(kp));
