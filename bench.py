@@ -38,7 +38,7 @@ UNIT = "charges/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)   # p50/p99 from >= 50 timed solves
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="c3_jumps_n1048576")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_simt"])
