@@ -589,13 +589,18 @@ __global__ void k_scatter_sources_f(KP kp) {
     }
 }
 
-__global__ void __launch_bounds__(kTile * kTile) k_spread_f32(KP kp) {
+// Two neighbouring x columns per thread (128 threads for the 16 x 16
+// tile): the per-source work of a thread (the loop, the weight loads, the
+// zero test) is shared by 16 multiply-adds instead of 8.
+constexpr int kSpreadThreadsM = kTile * kTile / 2;
+
+__global__ void __launch_bounds__(kSpreadThreadsM) k_spread_f32(KP kp) {
     constexpr int B = kSpreadBatchM;
     __shared__ float s_wx[B][kTile + 1];
     __shared__ float s_wy[B][kTile + 1];
     __shared__ __align__(16) float s_wz[B][kWzStride];
     __shared__ int s_over[B];
-    const int tid = threadIdx.x, lx = tid % kTile, ly = tid / kTile;
+    const int tid = threadIdx.x, lx = 2 * (tid % (kTile / 2)), ly = tid / (kTile / 2);
     const int tile = blockIdx.x, txi = tile % kp.ntx, tyi = tile / kp.ntx;
     const int slab = blockIdx.y, js = slab * kSlabM;
     const int gx0 = txi * kTile, gy0 = tyi * kTile;
@@ -603,81 +608,94 @@ __global__ void __launch_bounds__(kTile * kTile) k_spread_f32(KP kp) {
     const int first = kp.tile_start[bk], total = kp.tile_start[bk + 1] - first;
     const SrcF* src = kp.srcsf + first;
     const float ig2 = kp.f.ig2, s1 = kp.f.s1norm;
-    float ai[kSlabM], ao[kSlabM];
+    float ai0[kSlabM], ai1[kSlabM], ao0[kSlabM], ao1[kSlabM];
 #pragma unroll
-    for (int j = 0; j < kSlabM; ++j) ai[j] = ao[j] = 0.f;
+    for (int j = 0; j < kSlabM; ++j) ai0[j] = ai1[j] = ao0[j] = ao1[j] = 0.f;
     for (int base = 0; base < total; base += B) {
         const int nb = min(B, total - base);
-        {
-            const int b = tid % B;
-            if (b < nb) {
-                const SrcF r = src[base + b];
-                if (tid < B) {
-                    // x weights of the tile's columns, then z weights times q
-                    const int sx = r.pack & 63;
-                    int i = wrap_index(gx0 - r.xlo, kp.nx);
-                    for (int l = 0; l < kTile; ++l) {
-                        float w = 0.f;
-                        if (i < sx) {
-                            const float d = r.d0x + float(i) * kp.f.hx;
-                            w = s1 * expf(-d * d * ig2);
-                        }
-                        s_wx[b][l] = w;
-                        if (++i >= kp.nx) i -= kp.nx;
+        // weight tables: thread b fills source b's x and z weights (times the
+        // strength), thread b + B/2 ... the y weights; B = 128 = 2 x 64
+        for (int b = tid; b < 2 * B; b += kSpreadThreadsM) {
+            const int rb = b % B;
+            if (rb >= nb) continue;
+            const SrcF r = src[base + rb];
+            if (b < B) {
+                const int sx = r.pack & 63;
+                int i = wrap_index(gx0 - r.xlo, kp.nx);
+                for (int l = 0; l < kTile; ++l) {
+                    float w = 0.f;
+                    if (i < sx) {
+                        const float d = r.d0x + float(i) * kp.f.hx;
+                        w = s1 * expf(-d * d * ig2);
                     }
-                    const int j0 = (r.pack >> 12) & 511, j1 = (r.pack >> 21) & 511;
-                    for (int jj = 0; jj < kSlabM; ++jj) {
-                        const int j = js + jj;
-                        float w = 0.f;
-                        if (j >= j0 && j <= j1) {
-                            const float d = (kp.zn32[j] - r.zhi) + (kp.znlo32[j] - r.zlo);
-                            w = r.q * (s1 * expf(-d * d * ig2));
-                        }
-                        s_wz[b][jj] = w;
+                    s_wx[rb][l] = w;
+                    if (++i >= kp.nx) i -= kp.nx;
+                }
+                const int j0 = (r.pack >> 12) & 511, j1 = (r.pack >> 21) & 511;
+                for (int jj = 0; jj < kSlabM; ++jj) {
+                    const int j = js + jj;
+                    float w = 0.f;
+                    if (j >= j0 && j <= j1) {
+                        const float d = (kp.zn32[j] - r.zhi) + (kp.znlo32[j] - r.zlo);
+                        w = r.q * (s1 * expf(-d * d * ig2));
                     }
-                    s_over[b] = int((r.pack >> 30) & 1u);
-                } else {
-                    const int sy = (r.pack >> 6) & 63;
-                    int i = wrap_index(gy0 - r.ylo, kp.ny);
-                    for (int l = 0; l < kTile; ++l) {
-                        float w = 0.f;
-                        if (i < sy) {
-                            const float d = r.d0y + float(i) * kp.f.hy;
-                            w = s1 * expf(-d * d * ig2);
-                        }
-                        s_wy[b][l] = w;
-                        if (++i >= kp.ny) i -= kp.ny;
+                    s_wz[rb][jj] = w;
+                }
+                s_over[rb] = int((r.pack >> 30) & 1u);
+            } else {
+                const int sy = (r.pack >> 6) & 63;
+                int i = wrap_index(gy0 - r.ylo, kp.ny);
+                for (int l = 0; l < kTile; ++l) {
+                    float w = 0.f;
+                    if (i < sy) {
+                        const float d = r.d0y + float(i) * kp.f.hy;
+                        w = s1 * expf(-d * d * ig2);
                     }
+                    s_wy[rb][l] = w;
+                    if (++i >= kp.ny) i -= kp.ny;
                 }
             }
         }
         __syncthreads();
         for (int b = 0; b < nb; ++b) {
-            const float w = s_wx[b][lx] * s_wy[b][ly];
-            if (w != 0.f) {
+            const float wy = s_wy[b][ly];
+            if (wy != 0.f) {
+                const float w0 = s_wx[b][lx] * wy, w1 = s_wx[b][lx + 1] * wy;
                 const float4 z0 = *reinterpret_cast<const float4*>(&s_wz[b][0]);
                 const float4 z1 = *reinterpret_cast<const float4*>(&s_wz[b][4]);
                 const float wz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
-                for (int j = 0; j < kSlabM; ++j) ai[j] = fmaf(w, wz[j], ai[j]);
+                for (int j = 0; j < kSlabM; ++j) {
+                    ai0[j] = fmaf(w0, wz[j], ai0[j]);
+                    ai1[j] = fmaf(w1, wz[j], ai1[j]);
+                }
                 if (s_over[b]) {
 #pragma unroll
-                    for (int j = 0; j < kSlabM; ++j) ao[j] = fmaf(w, wz[j], ao[j]);
+                    for (int j = 0; j < kSlabM; ++j) {
+                        ao0[j] = fmaf(w0, wz[j], ao0[j]);
+                        ao1[j] = fmaf(w1, wz[j], ao1[j]);
+                    }
                 }
             }
         }
         __syncthreads();
     }
     const int gx = gx0 + lx, gy = gy0 + ly;
-    if (gx < kp.nx && gy < kp.ny) {
+    if (gy < kp.ny) {
         float* rho = static_cast<float*>(kp.rho);
         const size_t G = size_t(kp.nz) * kp.ny * kp.nx;
 #pragma unroll
         for (int j = 0; j < kSlabM; ++j) {
             if (js + j < kp.nz) {
                 const size_t g = (size_t(js + j) * kp.ny + gy) * kp.nx + gx;
-                rho[g] = ai[j];
-                rho[G + g] = ao[j];
+                if (gx < kp.nx) {
+                    rho[g] = ai0[j];
+                    rho[G + g] = ao0[j];
+                }
+                if (gx + 1 < kp.nx) {
+                    rho[g + 1] = ai1[j];
+                    rho[G + g + 1] = ao1[j];
+                }
             }
         }
     }
@@ -3771,7 +3789,7 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         LAUNCH(k_sources_f<<<nb, kChargeThreads, 0, st>>>(kp));
         SCAN(kp.tile_count, kp.tile_start, kp.nbuckets);
         LAUNCH(k_scatter_sources_f<<<nb, kChargeThreads, 0, st>>>(kp));
-        LAUNCH(k_spread_f32<<<gs, kTile * kTile, 0, st>>>(kp));
+        LAUNCH(k_spread_f32<<<gs, kSpreadThreadsM, 0, st>>>(kp));
     } else {
         LAUNCH(k_count_sources<<<nb, kChargeThreads, 0, st>>>(kp));
         SCAN(kp.tile_count, kp.tile_start, kp.nbuckets);

@@ -193,3 +193,24 @@ def test_host_entry_point_matches_device_one():
     assert np.allclose(force2, force, rtol=0, atol=1e-13 * np.max(np.abs(force)))
     with pytest.raises(ValueError):
         plan.solve_host(pos, q, force=np.empty((len(q), 2)))
+
+
+@pytest.mark.parametrize("prec", [dpslab.FP64, dpslab.MIXED], ids=["fp64", "mixed"])
+def test_concurrent_near_field_matches_in_line(prec):
+    # unprofiled solves run the near field on the plan's second stream
+    # (forked after the cell list, joined before the assembly); profiled
+    # solves run it in line. Both give the oracle's result, and each other's
+    # to rounding (the spreading's summation order may differ between runs).
+    pos, q, p = synth.workload("c1_uniform_n128")
+    P = oracle_params(p["Lx"], p["Ly"], p["H"], p["gw"], p["tol"], p["nx"], p["ny"], nz=p["nz"],
+                      eps_b=p["eps_b"], eps_t=p["eps_t"], r_cut=p["r_cut"])
+    plan = plan_for(P, len(q), precision=prec)
+    plan.profile(True)
+    a = gpu_solve(plan, pos, q)
+    plan.profile(False)
+    b = gpu_solve(plan, pos, q)
+    tol = 1e-13 if prec == dpslab.FP64 else 1e-6
+    assert abs(a["U"] - b["U"]) <= tol * abs(a["U"])
+    assert rel_max(b["phi"], a["phi"]) < tol and rel_max(b["force"], a["force"]) < tol
+    if prec == dpslab.FP64:
+        compare(osolver.solve(pos, q, P), b, TOL_FP64)
