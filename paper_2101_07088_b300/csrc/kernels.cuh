@@ -195,7 +195,9 @@ __device__ __forceinline__ float derf(float x) { return erff(x); }
 __device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
 
 __device__ __forceinline__ double np_mod(double x, double L) {
-    // numpy float remainder: fmod, then shifted into the sign of L
+    // numpy float remainder: fmod, then shifted into the sign of L (a point
+    // already in [0, L) is its own remainder)
+    if (x >= 0.0 && x < L) return x;
     double r = fmod(x, L);
     if (r != 0.0 && r < 0.0) r += L;
     return r;
