@@ -306,13 +306,15 @@ __device__ __forceinline__ void last_pass(C* v, const C* tw, int j, int n16, int
 // output i, after a barrier (it may write buf). All threads of the block
 // must call this function; it ends with the stores done by each thread.
 // kSyncLoad: a barrier between the first pass's loads and its writes, for
-// loads that read staged input from buf itself. twg: when given, the
-// twiddle table tw (n entries) is copied from it here, while the first
-// pass's loads are in flight (that pass needs no twiddles; the barrier
-// after its writes precedes the first use).
+// loads that read staged input from buf itself. tw: the twiddle table (n
+// entries). Row transforms read the global table where it is (it stays in
+// L1). Column transforms pass tw_fill = tw in shared memory and tw_src, the
+// global table: it is copied here while the first pass's loads are in
+// flight (that pass needs no twiddles, and the barrier after its writes
+// precedes the first use).
 template <bool QF, bool kSyncLoad = false, class C, class Load, class Store>
-__device__ __forceinline__ void fft_pow2(C* buf, C* tw, int n, int logn, int nseq, int dir, Load load, Store store,
-                                         const C* twg = nullptr) {
+__device__ __forceinline__ void fft_pow2(C* buf, const C* tw, int n, int logn, int nseq, int dir, Load load,
+                                         Store store, C* tw_fill = nullptr, const C* tw_src = nullptr) {
     const int l16 = logn - 4, n16 = 1 << l16;
     const int s = threadIdx.x;
     const bool act = s < (nseq << l16);
@@ -326,8 +328,8 @@ __device__ __forceinline__ void fft_pow2(C* buf, C* tw, int n, int logn, int nse
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = load(q, j + r * n16);
     }
-    if (twg)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    if (tw_fill)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) tw_fill[i] = tw_src[i];
     if constexpr (kSyncLoad) __syncthreads();
     if (act) {
         dft16(v, dir);

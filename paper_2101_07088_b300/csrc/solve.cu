@@ -796,9 +796,8 @@ __global__ void k_fftx_fwd_p2(KP kp, int P, int) {
     using C = typename Prec<R>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int logn = L, n = 1 << L, nxh = n / 2 + 1, np = n + (n >> 4);
-    C* tw = reinterpret_cast<C*>(smraw);
-    C* buf = tw + n;
-    const C* twg = twx_of<R>(kp);
+    C* buf = reinterpret_cast<C*>(smraw);
+    const C* tw = twx_of<R>(kp);
     const R* rho = static_cast<const R*>(kp.rho);
     C* spec = static_cast<C*>(kp.spec);
     const int npairs = kp.nz * kp.ny;
@@ -815,7 +814,7 @@ __global__ void k_fftx_fwd_p2(KP kp, int P, int) {
         return v;
     };
     auto store = [&](int q, int i, C v) { buf[q * np + pad16(i)] = v; };
-    fft_pow2<false>(buf, tw, n, logn, P, -1, load, store, twg);
+    fft_pow2<false>(buf, tw, n, logn, P, -1, load, store);
     __syncthreads();
     for (int t = threadIdx.x; t < P * nxh; t += blockDim.x) {
         const int p = t / nxh, k = t - p * nxh, pr = p0 + p;
@@ -840,7 +839,6 @@ __global__ void k_ffty_fwd_p2(KP kp, int TK, int) {
     const int nxh = kp.nxh;
     C* tw = reinterpret_cast<C*>(smraw);
     C* buf = tw + n;
-    const C* twg = twy_of<R>(kp);
     C* base = static_cast<C*>(kp.spec) + size_t(blockIdx.y) * n * nxh;
     const int k0 = blockIdx.x * TK;
     auto load = [&](int q, int i) {
@@ -853,14 +851,14 @@ __global__ void k_ffty_fwd_p2(KP kp, int TK, int) {
     auto store = [&](int q, int i, C v) {
         if (k0 + q < nxh) base[size_t(i) * nxh + k0 + q] = v;
     };
-    fft_pow2<true>(buf, tw, n, logn, TK, -1, load, store, twg);
+    fft_pow2<true>(buf, tw, n, logn, TK, -1, load, store, tw, twy_of<R>(kp));
 }
 
 // one of the three inverse column transforms: F = 0: -i k_y psi (psi -> specB),
 // F = 1: psi (in place), F = 2: dpsi/dz (in place)
 template <int F, class R, int L>
 __device__ __forceinline__ void ffty_inv_field(const KP& kp, typename Prec<R>::C* buf, typename Prec<R>::C* tw,
-                                               int TK, const typename Prec<R>::C* twg = nullptr) {
+                                               int TK, bool fill) {
     using C = typename Prec<R>::C;
     constexpr int logn = L, n = 1 << L;
     const int nxh = kp.nxh;
@@ -885,24 +883,22 @@ __device__ __forceinline__ void ffty_inv_field(const KP& kp, typename Prec<R>::C
     auto store = [&](int c, int i, C v) {
         if (k0 + c < nxh) dst[size_t(i) * nxh + k0 + c] = v;
     };
-    fft_pow2<true>(buf, tw, n, logn, TK, +1, load, store, twg);
+    fft_pow2<true>(buf, tw, n, logn, TK, +1, load, store, fill ? tw : nullptr, twy_of<R>(kp));
 }
 
 template <class R, int L>
 __global__ void __launch_bounds__(512, sizeof(R) == sizeof(float) ? 2 : 1) k_ffty_inv_p2(KP kp, int TK, int) {
     using C = typename Prec<R>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
-    constexpr int n = 1 << L;
     C* tw = reinterpret_cast<C*>(smraw);
-    C* buf = tw + n;
-    const C* twg = twy_of<R>(kp);
+    C* buf = tw + (1 << L);
     // -i k_y psi first: it reads psi before the psi transform overwrites it
     // (the first transform also copies the twiddle table)
-    ffty_inv_field<0, R, L>(kp, buf, tw, TK, twg);
+    ffty_inv_field<0, R, L>(kp, buf, tw, TK, true);
     __syncthreads();
-    ffty_inv_field<1, R, L>(kp, buf, tw, TK);
+    ffty_inv_field<1, R, L>(kp, buf, tw, TK, false);
     __syncthreads();
-    ffty_inv_field<2, R, L>(kp, buf, tw, TK);
+    ffty_inv_field<2, R, L>(kp, buf, tw, TK, false);
 }
 
 template <class R, int L>
@@ -911,9 +907,8 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int) {
     using V4 = typename Prec<R>::V4;
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int logn = L, n = 1 << L, nxh = n / 2 + 1, np = n + (n >> 4);
-    C* tw = reinterpret_cast<C*>(smraw);
-    C* buf = tw + n;
-    const C* twg = twx_of<R>(kp);
+    C* buf = reinterpret_cast<C*>(smraw);
+    const C* tw = twx_of<R>(kp);
     const C* spec = static_cast<const C*>(kp.spec);
     const C* specB = static_cast<const C*>(kp.specB);
     V4* fields = static_cast<V4*>(kp.fields);
@@ -956,7 +951,7 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int) {
         return z;
     };
     auto store = [&](int q, int i, C v) { buf[q * np + pad16(i)] = v; };
-    fft_pow2<false>(buf, tw, n, logn, 2 * P, +1, load, store, twg);
+    fft_pow2<false>(buf, tw, n, logn, 2 * P, +1, load, store);
     __syncthreads();
     const R s = R(kp.inv_nxny);
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
@@ -3074,7 +3069,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             const int n16 = nx / 16;
             const size_t seq = size_t(nx + n16) * csz;
             const int P = std::max(1, std::min(256, mxf) / n16), Pi = std::max(1, std::min(128, mxi) / (2 * n16));
-            const size_t fwd = size_t(nx) * csz + P * seq, inv = size_t(nx) * csz + 2 * Pi * seq;
+            const size_t fwd = P * seq, inv = 2 * Pi * seq;   // the twiddle table is read from global memory
             if (fwd <= cap && inv <= cap && P * n16 <= mxf && 2 * Pi * n16 <= mxi) {
                 pl->p2x = 1;
                 pl->lognx = lg(nx);
@@ -3593,7 +3588,8 @@ bool apply_shape_t(dpslab_plan* pl, int which, int v) {
     const void* f;
     if (p2) {
         const int n16 = n / 16;
-        const size_t seq = size_t(n + n16) * csz, tw = size_t(n) * csz;
+        // x transforms read the global twiddle table, y transforms a shared copy
+        const size_t seq = size_t(n + n16) * csz, tw = which == 1 || which == 2 ? size_t(n) * csz : 0;
         const int seqs = which == 3 ? 2 * v : v;         // the x inverse transforms two sequences per row
         thr = seqs * n16;
         sm = tw + seqs * seq;

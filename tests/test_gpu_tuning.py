@@ -39,7 +39,10 @@ def test_autotune_keeps_results(prec, tmp_path):
     knobs = plan.autotune(pt, qt, reps=2)
     assert all(v >= 1 for v in knobs)
     U1, f1 = _solve(plan, pt, qt)
-    tol = 1e-12 if prec == dpslab.FP64 else 1e-6
+    # mixed: the sources are bucketed by atomics, so the spreading's FP32
+    # summation order (and the forces, by about 1e-6) differs between any two
+    # solves; the bar is half the mixed force bar
+    tol = 1e-12 if prec == dpslab.FP64 else 5e-6
     assert abs(U1 - U0) <= tol * abs(U0) and rel_l2(f1, f0) <= tol
     with pytest.raises(dpslab.DpslabError):
         plan.set_tuning([1 << 20, 1, 1, 1])
