@@ -24,7 +24,9 @@ def needs_build():
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(HERE, "csrc", "*.h*")) + [os.path.join(ROOT, "include", "dpslab.h")]
+    csrc = os.path.join(HERE, "csrc")
+    deps = (sources() + glob.glob(os.path.join(csrc, "*.h")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+            [os.path.join(ROOT, "include", "dpslab.h")])
     return any(os.path.getmtime(f) > t for f in deps)
 
 

@@ -119,3 +119,29 @@ def test_plan_create_without_gpu_reports_no_device():
     with pytest.raises(dpslab.DpslabError) as e:
         dpslab.Plan(dict(Lx=32.0, Ly=32.0, H=32.0, gw=1.0, tol=1e-4, nx=64, ny=64, nz=64, r_cut=4.0), 128)
     assert e.value.code in (-8, -7)
+
+
+def test_build_watches_every_source_and_header(monkeypatch):
+    # the library is rebuilt when any CUDA/C++ source or header under csrc/
+    # (including the .cuh kernel headers) is newer than it
+    import glob
+    import os
+
+    from paper_2101_07088_b300 import build
+    csrc = os.path.join(os.path.dirname(build.__file__), "csrc")
+    files = {os.path.abspath(f) for f in glob.glob(os.path.join(csrc, "*"))
+             if f.endswith((".cu", ".cpp", ".h", ".cuh"))}
+    assert any(f.endswith(".cuh") for f in files)
+    seen = set()
+    real = os.path.getmtime
+
+    def mtime(f):
+        f = os.path.abspath(f)
+        if f == os.path.abspath(build.LIB):
+            return float("inf")          # library newest: every dependency is examined
+        seen.add(f)
+        return real(f)
+    monkeypatch.setattr(os.path, "exists", lambda f: True)
+    monkeypatch.setattr(os.path, "getmtime", mtime)
+    assert build.needs_build() is False
+    assert files <= seen
