@@ -155,15 +155,29 @@ __device__ __forceinline__ void split3(float x, float q, float iq, __nv_bfloat16
 }
 
 // 8 values at K entries k0..k0+7 of column n, three pieces, one 16-byte
-// store each
+// store each. The same split as split3, two values at a time: x1 has at
+// most 8 significant bits, so its bf16 is the upper half of the float
+// (exact), and two halves pack with one byte permutation; the other two
+// pieces are rounded in pairs.
 __device__ __forceinline__ void put8(unsigned short* sB, int n, int k0, const float* x, float q, float iq) {
-    __align__(16) __nv_bfloat16 p1[8], p2[8], p3[8];
+    uint4 w1, w2, w3;
+    uint32_t* v1 = &w1.x;
+    uint32_t* v2 = &w2.x;
+    uint32_t* v3 = &w3.x;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) split3(x[i], q, iq, p1[i], p2[i], p3[i]);
+    for (int i = 0; i < 8; i += 2) {
+        const float x1a = rintf(x[i] * q) * iq, x1b = rintf(x[i + 1] * q) * iq;
+        v1[i / 2] = __byte_perm(__float_as_uint(x1a), __float_as_uint(x1b), 0x7632);
+        const float r1a = x[i] - x1a, r1b = x[i + 1] - x1b;
+        const __nv_bfloat162 b = __floats2bfloat162_rn(r1a, r1b);
+        const __nv_bfloat162 c = __floats2bfloat162_rn(r1a - __low2float(b), r1b - __high2float(b));
+        v2[i / 2] = *reinterpret_cast<const uint32_t*>(&b);
+        v3[i / 2] = *reinterpret_cast<const uint32_t*>(&c);
+    }
     const int e = (n >> 3) * (kZSboB / 2) + (k0 >> 3) * 64 + (n & 7) * 8;   // canonical layout, padded row groups
-    *reinterpret_cast<uint4*>(sB + e) = *reinterpret_cast<const uint4*>(p1);
-    *reinterpret_cast<uint4*>(sB + kZPieceB + e) = *reinterpret_cast<const uint4*>(p2);
-    *reinterpret_cast<uint4*>(sB + 2 * kZPieceB + e) = *reinterpret_cast<const uint4*>(p3);
+    *reinterpret_cast<uint4*>(sB + e) = w1;
+    *reinterpret_cast<uint4*>(sB + kZPieceB + e) = w2;
+    *reinterpret_cast<uint4*>(sB + 2 * kZPieceB + e) = w3;
 }
 
 // The GEMM over nplanes planes of rows (= Nz) x ncols floats (row stride ld,
