@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_helpers import TOL_FP64, compare, gpu_solve, oracle_params, plan_for, rel_max
+from gpu_helpers import TOL_FP64, compare, gpu_solve, oracle_params, plan_for, rel_l2, rel_max
 from oracle import solver as osolver
 from paper_2101_07088_b300 import build, dpslab, synth
 
@@ -214,3 +214,28 @@ def test_concurrent_near_field_matches_in_line(prec):
     assert rel_max(b["phi"], a["phi"]) < tol and rel_max(b["force"], a["force"]) < tol
     if prec == dpslab.FP64:
         compare(osolver.solve(pos, q, P), b, TOL_FP64)
+
+
+# The power-of-two FFT kernels are compiled once per size (n = 32 .. 4096):
+# thin boxes reach the sizes the other cases do not (128, 512, 2048, 4096 in
+# x and in y, with 32 at the other extreme), in both precisions.
+P2_SIZES = [
+    ("x4096-y32", (2048.0, 16.0, 12.0), (4096, 32, 33)),
+    ("x32-y4096", (16.0, 2048.0, 12.0), (32, 4096, 33)),
+    ("x2048-y128", (1024.0, 64.0, 12.0), (2048, 128, 33)),
+    ("x128-y512", (64.0, 256.0, 12.0), (128, 512, 33)),
+]
+
+
+@pytest.mark.parametrize("name,box,grid", P2_SIZES, ids=[c[0] for c in P2_SIZES])
+def test_fft_size_instances(name, box, grid):
+    from gpu_helpers import TOL_MIXED_FORCE
+    Lx, Ly, H = box
+    n = 64
+    pos, q = _charges(n, Lx, Ly, H, seed=sum(map(ord, name)))
+    P = oracle_params(Lx, Ly, H, 1.0, 1e-4, grid[0], grid[1], nz=grid[2], eps_b=1 / 80, eps_t=1 / 40, r_cut=4.0)
+    ref = osolver.solve(pos, q, P)
+    compare(ref, gpu_solve(plan_for(P, n), pos, q))
+    out = gpu_solve(plan_for(P, n, precision=dpslab.MIXED), pos, q)
+    assert rel_l2(out["force"], ref["force"]) < TOL_MIXED_FORCE
+    assert abs(out["U"] - ref["U"]) < 8 * 2.0 ** -24 * abs(ref["U"])
