@@ -1849,19 +1849,17 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
             float re = v[i], im = v[i + 1];
             if (plane == 1) { re *= sz; im *= sz; }
             const ColP cp = s_cp[col - s_c0 / 2];
-            // both exponentials below e^-80 (k z and k (H - z) large): the
-            // correction is below FP32 resolution of psi there
-            if (cp.corr && zin && (cp.k * z < 80.f || cp.k * (H - z) < 80.f)) {
-                const float e1 = expf(-cp.k * z), e3 = expf(cp.k * (z - H));
+            // without branches (the lanes are rows, which would diverge): the
+            // exponents are clamped at 88, where both terms are below 1e-38
+            // of the correction's amplitude, and modes without a correction
+            // or nodes outside [-H_E, H + H_E] are masked to exactly zero
+            {
+                const float m = (cp.corr && zin) ? cp.iden : 0.f;
+                const float e1 = expf(-fminf(cp.k * z, 88.f)), e3 = expf(-fminf(cp.k * (H - z), 88.f));
                 const float e2 = e3 * cp.ekH, e4 = e1 * cp.ekH;
-                float a, b;
-                if (plane == 0) {
-                    a = -(e1 - Gt * e2) * cp.iden;
-                    b = (e3 - Gb * e4) * cp.iden;
-                } else {
-                    a = (e1 + Gt * e2) * cp.k * cp.iden;
-                    b = (e3 + Gb * e4) * cp.k * cp.iden;
-                }
+                const float f = plane == 0 ? m : cp.k * m;
+                const float a = plane == 0 ? -(e1 - Gt * e2) * f : (e1 + Gt * e2) * f;
+                const float b = plane == 0 ? (e3 - Gb * e4) * f : (e3 + Gb * e4) * f;
                 re += cp.P.x * a + cp.Q.x * b;
                 im += cp.P.y * a + cp.Q.y * b;
             }
