@@ -1484,9 +1484,10 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
         for (int k = 0; k < cmax; ++k) {
             if (k < cnt) {
                 const int i = i0 + di * k, n = nn;
-                const float an = n >= 2 ? -K2 * jl : 0.f;
+                // the band tables are zero below row 2 and above row N - 3
+                const float an = -K2 * jl;
                 const float bn = 1.f - K2 * jd;
-                const float cn = n + 2 < N ? -K2 * ju : 0.f;
+                const float cn = -K2 * ju;
                 const float2 Fcur = Fin, Focur = Fon;
                 nn = n + 2 * di;
                 if (k + 1 < cnt) { jl = kp.j2l32[nn]; jd = kp.j2d32[nn]; ju = kp.j2u32[nn]; Fin = Fi[nn]; Fon = Fo[nn]; }
