@@ -112,3 +112,53 @@ def solve(pos, q, Lx, Ly, H, gw, eps=1.0, eps_b=1.0, eps_t=1.0, kcut_exp=40.0, t
                 E[t, 2] += -stc * np.sum(c * damp * mkz) / area
     U = 0.5 * float(np.sum(q * phi))
     return dict(U=U, phi=phi, force=q[:, None] * E)
+
+
+def pointwise_potential(points, pos, q, Lx, Ly, H, gw, eps=1.0, eps_b=1.0, eps_t=1.0,
+                        kcut_exp=40.0, tol=1e-18):
+    """The potential phi(x) of the Gaussian charges (Eq. (gcharge), std g_w per
+    direction) plus their full image series, at arbitrary points x with
+    0 <= z <= H. This is the field whose value at the origin the gauge
+    Eq. (phi00) sets to zero (Sec. 2).
+
+    Same sums as solve(), with the kernel of one Gaussian (variance g_w^2)
+    instead of the pair average (2 g_w^2): the k = 0 part is -|z|/2
+    convolved with that Gaussian, whose constant is the one solve() uses, so
+    differences phibar_k - phi(x) carry no undetermined constant for a neutral
+    system."""
+    points = np.atleast_2d(np.asarray(points, dtype=np.float64))
+    pos = np.asarray(pos, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    sigma = float(gw)
+    kcut = np.sqrt(2.0 * kcut_exp) / sigma
+    mx = int(np.ceil(kcut * Lx / (2 * np.pi)))
+    my = int(np.ceil(kcut * Ly / (2 * np.pi)))
+    KX, KY = np.meshgrid(2 * np.pi * np.arange(-mx, mx + 1) / Lx,
+                         2 * np.pi * np.arange(-my, my + 1) / Ly, indexing="ij")
+    KX, KY = KX.ravel(), KY.ravel()
+    K = np.sqrt(KX ** 2 + KY ** 2)
+    keep = (K > 0) & (K <= kcut)
+    KX, KY, K = KX[keep], KY[keep], K[keep]
+    damp = np.exp(-0.5 * sigma ** 2 * K ** 2)
+    kmin = K.min()
+
+    def gam(e):
+        return 1.0 if np.isinf(e) else (e - eps) / (e + eps)
+    Gb, Gt = gam(eps_b), gam(eps_t)
+    area = eps * Lx * Ly
+    a = sigma * np.sqrt(2.0)
+    out = np.zeros(len(points))
+    for s in range(len(q)):
+        zi, si = image_series(pos[s, 2], H, Gb, Gt, tol)
+        st = q[s] * si
+        for t, (px, py, pz) in enumerate(points):
+            dx, dy = px - pos[s, 0], py - pos[s, 1]
+            dz = pz - zi
+            out[t] += np.sum(st * (-0.5) * (dz * erf(dz / a) + sigma * np.sqrt(2 / np.pi)
+                                           * np.exp(-dz ** 2 / (2 * sigma ** 2)))) / area
+            close = kmin * np.abs(dz) < 60.0
+            c = np.cos(KX * dx + KY * dy) * damp
+            for dzc, stc in zip(dz[close], st[close]):
+                mk = (_h(K, dzc, sigma) + _h(K, -dzc, sigma)) / (4.0 * K)
+                out[t] += stc * np.sum(c * mk) / area
+    return out

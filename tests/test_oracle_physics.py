@@ -160,3 +160,71 @@ def test_near_field_tree_matches_pairs():
     b = solver.near_field(x, y, z, q, P, "tree")
     assert np.allclose(a[0], b[0], rtol=1e-13, atol=1e-16)
     assert np.allclose(a[1], b[1], rtol=1e-13, atol=1e-16)
+
+
+@pytest.mark.parametrize("name,eb,et,xi,rcut,tol", CASES, ids=[c[0] for c in CASES])
+def test_gauge_against_pointwise_image_series(charges, name, eb, et, xi, rcut, tol):
+    """The gauge phi(0) = 0 (Eq. (phi00); the gauge paragraph of Sec. 5.2.2)
+    without mean subtraction: the oracle's phibar_k must be the brute-force
+    averaged potential minus the brute-force pointwise potential of the
+    Gaussian charges and their image series at the origin. This fixes
+    B = -(phi^(n)(0) + phi^(f)(0)): the pointwise kernel Eq. (Gnear) at the
+    origin, the gamma^{1/2} average of the far series there (xy factor and z
+    weights), and the sign of B."""
+    pos, q = charges
+    ref = brute.solve(pos, q, L, L, H, GW, 1.0, eb, et)
+    phi0 = brute.pointwise_potential([[0.0, 0.0, 0.0]], pos, q, L, L, H, GW, 1.0, eb, et)[0]
+    out = solver.solve(pos, q, _params(eb, et, xi, rcut))
+    scale = np.max(np.abs(ref["phi"]))
+    assert np.max(np.abs(out["phi"] - (ref["phi"] - phi0))) < tol * scale
+    if np.isinf(eb):
+        # a metal bottom is grounded by its images: phi = 0 on all of it
+        assert abs(phi0) < tol * scale
+    else:
+        # the constant is not trivially small: a solve without the gauge fails
+        assert abs(phi0) > 100 * tol * scale
+
+
+def test_gauge_at_another_point():
+    """The same identity with the origin of the box moved: shifting every charge
+    by -c in x and y and wrapping puts the point c at the origin, so the
+    shifted solve's phibar_k equals the brute-force phibar_k minus phi(c).
+    Exercises the far-field gauge sum at nonzero phases of every mode."""
+    pos, q = _charges(6, seed=7)
+    c = np.array([7.3, 15.9])
+    sh = pos.copy()
+    sh[:, :2] = np.mod(pos[:, :2] - c, L)
+    eb, et = 1 / 80, 0.5
+    ref = brute.solve(pos, q, L, L, H, GW, 1.0, eb, et)
+    phic = brute.pointwise_potential([[c[0], c[1], 0.0]], pos, q, L, L, H, GW, 1.0, eb, et)[0]
+    out = solver.solve(sh, q, _params(eb, et, 1.2, 10.0))
+    assert np.max(np.abs(out["phi"] - (ref["phi"] - phic))) < 3e-7 * np.max(np.abs(ref["phi"]))
+
+
+@pytest.mark.parametrize("xi,nz", [(1.2, 60), (0.6, 90), (3.0, 41)])
+def test_gauge_weights_by_quadrature(xi, nz):
+    """gauge_weights: w_n = int G_sigma(z) T_n(s(z)) dz with sigma = 1/(2 xi)
+    (the z part of gamma^{1/2}, Eq. (gt)), against adaptive quadrature of the
+    same integral, with T_n(s) = cos(n arccos s) inside [-1, 1] and
+    cosh(n arccosh |s|) sgn(s)^n outside."""
+    from scipy.integrate import quad
+    P = params.derive(L, L, H, GW, 1e-4, 48, 48, nz=nz, xi=xi, r_cut=10.0,
+                      eps_b=1 / 80, eps_t=1 / 80, n_sigma=7.0)
+    w = solver.gauge_weights(P)
+    sigma = 1.0 / (2.0 * xi)
+    a, b = P["a"], P["b"]
+
+    def T(n, s):
+        if abs(s) <= 1.0:
+            return np.cos(n * np.arccos(s))
+        return np.cosh(n * np.arccosh(abs(s))) * (np.sign(s) ** n)
+
+    for n in (0, 1, 2, 5, nz // 2, nz - 1):
+        f = lambda z: np.exp(-z * z / (2 * sigma * sigma)) / np.sqrt(2 * np.pi * sigma * sigma) \
+            * T(n, 2.0 * (z - a) / (b - a) - 1.0)
+        ref, _ = quad(f, -12 * sigma, 12 * sigma, epsabs=1e-14, epsrel=1e-12, limit=200)
+        assert abs(w[n] - ref) < 1e-11 * max(1.0, abs(ref))
+    # without smearing (xi = inf) the weights are T_n at the origin
+    P2 = params.derive(L, L, H, GW, 1e-4, 48, 48, nz=nz, xi=np.inf, eps_b=1 / 80, eps_t=1 / 80)
+    s0 = 2.0 * (0.0 - P2["a"]) / (P2["b"] - P2["a"]) - 1.0
+    assert np.allclose(solver.gauge_weights(P2), np.cos(np.arange(nz) * np.arccos(s0)), atol=1e-14)
