@@ -7,7 +7,9 @@
  *   - the Gaussian-averaged potential phibar_k at every charge, Eq. (pbar),
  *     in the gauge phi(0) = 0, Eq. (phi00);
  *   - the force F_k = q_k Ebar(z_k), Eq. (fqE);
- *   - the energy U = 1/2 sum_k q_k phibar_k, Eq. (Ufinal) (no wall charge).
+ *   - the energy U = 1/2 sum_k q_k phibar_k of Eq. (Ufinal), plus, when wall
+ *     charge densities are set (dpslab_plan_set_wall_charge), their term
+ *     1/2 int (sigma_b phi(x, y, 0) + sigma_t phi(x, y, H)) dx dy.
  * It follows the far-field algorithm of Sec. 5.2.2 (steps 1-7, a Fourier
  * grid in x, y and a second-kind Chebyshev grid in z on [-3 H_E, H + 3 H_E],
  * one boundary value problem per transverse mode solved as in Appendix A,
@@ -49,6 +51,7 @@ extern "C" {
 #define DPSLAB_ERR_GRID              -9  /* grid too small for the Gaussian support, or a size the kernels do not support */
 #define DPSLAB_ERR_UNSUPPORTED      -10  /* option not built into this library */
 #define DPSLAB_ERR_BD_REJECTED      -11  /* every proposal of a Brownian-dynamics step left the slab */
+#define DPSLAB_ERR_TIMEOUT          -12  /* a bounded wait on the tensor-core pipeline gave up (dpslab_plan_set_wait_limit) */
 #define DPSLAB_PENDING                1  /* dpslab_solve_poll: the enqueued solve has not finished yet */
 
 /* ------------------------------------------------------------- precision */
@@ -56,8 +59,10 @@ extern "C" {
 #define DPSLAB_MIXED  1   /* FP32 spreading, FFT, interpolation and near field; the z Chebyshev
                              transforms as tensor-core GEMMs on three-piece BF16 splits with FP32
                              accumulation (Nz <= 256 and ny (nx/2+1) even; otherwise as
-                             DPSLAB_MIXED_SIMT); per-mode boundary-condition coefficients, the
-                             k = 0 mode and the energy reduction accumulated in double */
+                             DPSLAB_MIXED_SIMT); the banded BVP of k != 0 in FP32; in double:
+                             the whole k = 0 mode (z transform, BVP, slope A_i), every mode's
+                             boundary-condition correction (mismatches, coefficients of
+                             Eq. (inphisc)), the gauge and the energy reduction */
 #define DPSLAB_MIXED_SIMT 2  /* DPSLAB_MIXED with the z transforms in FP32 on the CUDA cores */
 
 /* Bits of dpslab_derived.violations (Sec. 5.3): */
@@ -89,7 +94,7 @@ typedef struct dpslab_params {
     double xi;                 /* splitting parameter; 0 = derive; INFINITY = none     */
     double r_cut;              /* near-field cutoff; 0 = derive                        */
     double n_sigma;            /* Gaussian truncation in standard deviations; 0 = table */
-    int    precision;          /* DPSLAB_FP64                                          */
+    int    precision;          /* DPSLAB_FP64, DPSLAB_MIXED or DPSLAB_MIXED_SIMT        */
     int    strict;             /* nonzero: constraint violations are errors            */
 } dpslab_params;
 
@@ -370,12 +375,30 @@ int dpslab_batch_destroy(dpslab_batch* batch);
  * stage durations in milliseconds (device time) to ms[0 .. DPSLAB_NSTAGES-1].
  * Stage i is named by dpslab_stage_name(i): prepare (validation, cell
  * list), spread (sources, buckets, spreading), fft_x_fwd, fft_y_fwd, z_fwd
- * (tensor-core z transform; 0 when the z transforms run inside the BVP
- * kernel), bvp (per-mode BVP, correction coefficients, k = 0 mode), z_inv
- * (tensor-core inverse z transform with the correction at the nodes; 0 as
- * z_fwd), fft_y_inv, fft_x_inv, interp, near (pairs), finish (gauge +
- * assembly + energy).
+ * (the k = 0 column in double, then the tensor-core z transform; only the
+ * former when the z transforms run inside the BVP kernel), bvp (per-mode
+ * BVP, correction coefficients), z_inv (tensor-core inverse z transform with
+ * the correction at the nodes; 0 as z_fwd), fft_y_inv, fft_x_inv, interp,
+ * near (pairs), finish (gauge + assembly + energy).
+ * on: 0 = off; 1 = on, the solve unchanged: the near field still runs on the
+ * plan's second stream beside the far field, and its stage time is taken by
+ * events on that stream (the stage times then add up to more than the
+ * solve); 2 = on, with the near field run in line on the solve's stream, so
+ * that the stages follow one another. Other values: DPSLAB_ERR_INVALID_ARG.
  */
+/*
+ * Watchdog of the tensor-core z transforms (DPSLAB_MIXED with Nz <= 256).
+ * Their kernels wait on the tensor cores and on bulk copies with bounded
+ * waits of at most `polls` polls each (default 2^26, seconds); a wait that
+ * runs out makes the kernel stop, wait for the work it has in flight, free
+ * its tensor memory and return, and the solve then reports
+ * DPSLAB_ERR_TIMEOUT (its outputs are not valid; the plan stays usable).
+ * polls = 0 makes every such wait give up at once, which is how that path is
+ * tested. Returns DPSLAB_ERR_INVALID_ARG for polls < 0 or a solve in flight.
+ * Not part of the paper's method.
+ */
+int dpslab_plan_set_wait_limit(dpslab_plan* plan, int64_t polls);
+
 #define DPSLAB_NSTAGES 12
 int dpslab_profile(dpslab_plan* plan, int on);
 int dpslab_stage_times(const dpslab_plan* plan, double* ms, int n);
@@ -395,7 +418,7 @@ const char* dpslab_stage_name(int stage);
  *   pos, q   device, [n][3] and [n], as for dpslab_solve;
  *   out      device, [n][4]: near-field phibar and Ebar (x, y, z) per charge;
  *   stream   cudaStream_t (NULL = legacy default stream).
- * The scratch space is one file-scope device array of about 8 MiB that every
+ * The scratch space is one file-scope device array of about 8.3 MiB that every
  * GPU loading this library holds until the process exits. All calls share
  * it: calls that overlap on the GPU (other streams, other threads) race and
  * must be serialised by the caller. The first call on a device looks up the

@@ -25,6 +25,7 @@ constexpr int kInterpWarps = 2;
 constexpr int kTile = 16;           // spreading tile: kTile x kTile xy grid points, one thread each
 constexpr int kSpreadBatch = 32;    // sources per batch in the tiled spreading
 constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kStageNear = 10;      // index of the near stage in the stage timings (dpslab_stage_name)
 
 __device__ __forceinline__ float warp_sum_f(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1333,12 +1334,236 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
 }
 
 // ---------------------------------------------------------------------------
+// The k = 0 column of the mixed-precision solve, in double, in one block:
+// the z transform of the two densities' plane sums (the xy transform's DC
+// bins), the Appendix-A BVP at k = 0 (A = I, so y'' = F, and the two
+// Dirichlet rows Eq. (BCs0) give y_0 and y'_0), the slope A_i of Sec. 4.3.4
+// (Eq. (CE), (ai1), (ai2)), this column's part of the gauge sum and, with
+// wall charges, the k = 0 far potential at the walls. It runs after the xy
+// transforms, before any z transform, and leaves the coefficients of psi_i
+// and dpsi_i/dz (before the factor 2/Hbar) in kp.zcol for k_column_mixed.
+// ---------------------------------------------------------------------------
+constexpr int kZeroThreads = 256;
+
+// Sums over the block of V values per thread, in a fixed order; every thread
+// must call it, and out (shared) holds the V sums on return.
+template <int V>
+__device__ void block_sums(const double (&v)[V], double* out) {
+    __shared__ double red[V][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const double s = warp_sum(v[i]);
+        if (lane == 0) red[i][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < V) {
+        double s = 0.0;
+        for (int k = 0; k < nw; ++k) s += red[threadIdx.x][k];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kZeroThreads) k_column_zero(KP kp) {
+    __shared__ double s_v[2][kMaxNz];   // node values, split into S_a / D_a
+    __shared__ double s_y[2][kMaxNz];   // F = y'' (k = 0), then y
+    __shared__ double s_p[2][kMaxNz];   // y'
+    __shared__ double s_sum[16];
+    const int N = kp.nz, M = kp.ny * kp.nxh, tid = threadIdx.x, bs = blockDim.x;
+    const float2* sp = static_cast<const float2*>(kp.spec);
+    // column 0 of both spectra: the plane sums of rho_i, rho_o (real)
+    for (int t = tid; t < 2 * N; t += bs) s_v[t / N][t % N] = double(sp[size_t(t) * M].x);
+    __syncthreads();
+    const int m = N - 1, JE = (N + 1) / 2, JO = N / 2;
+    for (int t = tid; t < 2 * JE; t += bs) {
+        const int f = t / JE, a = t - f * JE;
+        if (a < m - a) {
+            const double va = s_v[f][a], vb = s_v[f][m - a];
+            s_v[f][a] = va + vb;
+            s_v[f][m - a] = va - vb;
+        }
+    }
+    __syncthreads();
+    // coefficients (split forward transform, as in k_column), times
+    // -(Hbar/2)^2/eps: the right-hand side F of Eq. (blocksys)
+    const double scale = -(0.5 * kp.Hbar) * (0.5 * kp.Hbar) / kp.eps;
+    for (int t = tid; t < 2 * N; t += bs) {
+        const int f = t / N, q = t - f * N;
+        const bool odd = q >= JE;
+        const int na = odd ? JO : JE;
+        double acc = 0.0;
+        for (int a = 0; a < na; ++a) acc = fma(kp.cft[size_t(a) * N + q], s_v[f][odd ? m - a : a], acc);
+        s_y[f][odd ? 2 * (q - JE) + 1 : 2 * q] = acc * scale;
+    }
+    __syncthreads();
+    // k = 0 rows: sum y_n = c + d + u2.y'' = 0, sum (-1)^n y_n = c - d + v2.y'' = 0
+    {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int n = tid; n < N; n += bs) {
+            v[0] = fma(kp.u2[n], s_y[0][n], v[0]);
+            v[1] = fma(kp.v2[n], s_y[0][n], v[1]);
+            v[2] = fma(kp.u2[n], s_y[1][n], v[2]);
+            v[3] = fma(kp.v2[n], s_y[1][n], v[3]);
+        }
+        block_sums<4>(v, s_sum);
+    }
+    // y' = J y'' + d e0, then y = J y' + c e0 (entry n of J v is
+    // (v_{n-1} - v_{n+1})/(2n), entry 1 is v_0 - v_2/2)
+    for (int t = tid; t < 2 * N; t += bs) {
+        const int f = t / N, n = t - f * N;
+        const double* Y = s_y[f];
+        double v;
+        if (n == 0) v = -0.5 * (s_sum[2 * f] - s_sum[2 * f + 1]);
+        else if (n == 1) v = Y[0] - 0.5 * (N > 2 ? Y[2] : 0.0);
+        else v = (Y[n - 1] - (n + 1 < N ? Y[n + 1] : 0.0)) * (0.5 / n);
+        s_p[f][n] = v;
+    }
+    __syncthreads();
+    for (int t = tid; t < 2 * N; t += bs) {
+        const int f = t / N, n = t - f * N;
+        const double* Y = s_p[f];
+        double v;
+        if (n == 0) v = -0.5 * (s_sum[2 * f] + s_sum[2 * f + 1]);
+        else if (n == 1) v = Y[0] - 0.5 * (N > 2 ? Y[2] : 0.0);
+        else v = (Y[n - 1] - (n + 1 < N ? Y[n + 1] : 0.0)) * (0.5 / n);
+        s_y[f][n] = v;    // y'' of this n is no longer read: n - 1 and n + 1 of y' are
+    }
+    __syncthreads();
+    // boundary values (Sec. 4.3.4 needs psi_i*, d psi_i*/dz at z = 0, H and
+    // d psi_o*/dz at z = 0, H, a, b), the gauge sum, the wall potentials
+    {
+        double v[11];
+#pragma unroll
+        for (int i = 0; i < 11; ++i) v[i] = 0.0;
+        for (int n = tid; n < N; n += bs) {
+            const double a0 = kp.t0[n], aH = kp.tH[n], alt = (n & 1) ? -1.0 : 1.0;
+            const double yi = s_y[0][n], ypi = s_p[0][n], ypo = s_p[1][n];
+            v[0] = fma(a0, yi, v[0]);
+            v[1] = fma(aH, yi, v[1]);
+            v[2] = fma(a0, ypi, v[2]);
+            v[3] = fma(aH, ypi, v[3]);
+            v[4] = fma(a0, ypo, v[4]);
+            v[5] = fma(aH, ypo, v[5]);
+            v[6] = fma(alt, ypo, v[6]);
+            v[7] += ypo;
+            v[8] = fma(kp.wg[n], yi, v[8]);
+            if (kp.sigma_on) v[9] = fma(kp.wgH[n], yi, v[9]);
+        }
+        block_sums<11>(v, s_sum);
+    }
+    for (int t = tid; t < 2 * N; t += bs) kp.zcol[t] = t < N ? s_y[0][t] : s_p[0][t - N];
+    if (tid == 0) {
+        const double dz = 2.0 / kp.Hbar;
+        const double pi0 = s_sum[0], piH = s_sum[1];
+        const double dpi0 = s_sum[2] * dz, dpiH = s_sum[3] * dz;
+        const double dpo0 = s_sum[4] * dz, dpoH = s_sum[5] * dz, dpoa = s_sum[6] * dz, dpob = s_sum[7] * dz;
+        double ai1 = kp.rtb * (dpo0 - dpoa) - dpi0;
+        double ai2 = kp.rtt * (dpoH - dpob) - dpiH;
+        if (kp.sigma_on) {
+            ai1 -= kp.sig_hat[0].x / kp.eps;
+            ai2 += kp.sig_hat[M].x / kp.eps;
+        }
+        double Ai;
+        if (kp.metal_b && kp.metal_t) Ai = -(piH - pi0) / kp.H;
+        else if (kp.metal_b) Ai = ai2;
+        else if (kp.metal_t) Ai = ai1;
+        else Ai = 0.5 * (ai1 + ai2);
+        kp.scal[1] = Ai;
+        kp.zcol[2 * N] = s_sum[8];          // gauge term of k = 0: no damping, no correction
+        if (kp.sigma_on) {
+            kp.scal[7] = s_sum[8];
+            kp.scal[8] = s_sum[9] + Ai * kp.H;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The boundary-condition correction of one mode in double (Sec. 4.3.3): from
+// the wall values of psi_i*, psi_o* and their z derivatives (16 float sums
+// over the coefficients, the last factor 2/Hbar of the derivatives not yet
+// applied), the mismatches Eq. (mm1)-(mm4) (with wall charges, the sigma
+// terms), the coefficients P, Q of the normalised Eq. (inphisc) and its value
+// at z = 0. The factors of k (1/k, e^{-kH}, 1/den, the z = 0 factor of P) come
+// from the plan's extended-precision table kp.mtab.
+// ---------------------------------------------------------------------------
+struct BcCoef {
+    double2 P, Q;
+    double corr0;
+    double ekH, iden;
+};
+
+__device__ __forceinline__ BcCoef bc_correction(const KP& kp, int col, const float* v) {
+    const double4 t = kp.mtab[col];
+    const double dz = 2.0 / kp.Hbar;
+    double2 mpb = make_double2(fma(-kp.tb, double(v[8]), double(v[0])), fma(-kp.tb, double(v[9]), double(v[1])));
+    double2 meb = make_double2(fma(-kp.rtb, double(v[10]), double(v[2])) * dz,
+                               fma(-kp.rtb, double(v[11]), double(v[3])) * dz);
+    double2 mpt = make_double2(fma(-kp.tt, double(v[12]), double(v[4])), fma(-kp.tt, double(v[13]), double(v[5])));
+    double2 met = make_double2(fma(-kp.rtt, double(v[14]), double(v[6])) * dz,
+                               fma(-kp.rtt, double(v[15]), double(v[7])) * dz);
+    if (kp.sigma_on) {   // Eq. (mm2), (mm4): +sigma_b, -sigma_t (over eps)
+        const double ie = 1.0 / kp.eps;
+        meb = cadd(meb, cscale(kp.sig_hat[col], ie));
+        met = csub(met, cscale(kp.sig_hat[size_t(kp.ny) * kp.nxh + col], ie));
+    }
+    const double db = kp.db * t.x, dt = kp.dt * t.x;
+    BcCoef o;
+    o.P = csub(cscale(mpb, kp.cb), cscale(meb, db));
+    o.Q = csub(cscale(mpt, -kp.ct), cscale(met, dt));
+    o.ekH = t.y;
+    o.iden = t.z;
+    o.corr0 = t.w * o.P.x + (t.y * (1.0 - kp.Gb) * t.z) * o.Q.x;
+    return o;
+}
+
+// wave number of mode col (double) and its weight in the half spectrum
+__device__ __forceinline__ double mode_k(const KP& kp, int col, double& mult) {
+    const int iy = col / kp.nxh, ix = col - iy * kp.nxh;
+    const int my = iy < (kp.ny + 1) / 2 ? iy : iy - kp.ny;
+    const double kx = kTwoPi * ix / kp.Lx, ky = kTwoPi * my / kp.Ly;
+    mult = (ix == 0 || (kp.nx % 2 == 0 && ix == kp.nx / 2)) ? 1.0 : 2.0;
+    return sqrt(kx * kx + ky * ky);
+}
+
+// Tensor-core form: the correction of every mode, one thread per mode (the
+// FP64 pipe is then used by all lanes), between the column kernel (which
+// leaves the wall values in kp.bsum) and the inverse z transform (which
+// evaluates the correction at the nodes from kp.colp). Also this
+// correction's part of the gauge sum, per block.
+constexpr int kCorrThreads = 256;
+__global__ void __launch_bounds__(kCorrThreads) k_bc_correction(KP kp) {
+    const int M = kp.ny * kp.nxh;
+    const int col = blockIdx.x * kCorrThreads + threadIdx.x;
+    double g = 0.0;
+    if (col < M) {
+        double mult;
+        const double k = mode_k(kp, col, mult);
+        ColP cp{make_float2(0.f, 0.f), make_float2(0.f, 0.f), float(k), 0.f, 0.f, 0};
+        if (k > 0.0 && k <= kp.kmax) {
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = __ldcs(kp.bsum + size_t(i) * M + col);
+            const BcCoef b = bc_correction(kp, col, v);
+            cp = ColP{make_float2(float(b.P.x), float(b.P.y)), make_float2(float(b.Q.x), float(b.Q.y)), float(k),
+                      float(b.ekH), float(b.iden), 1};
+            g = mult * b.corr0;
+        }
+        kp.colp[col] = cp;
+    }
+    g = block_sum(g);
+    if (threadIdx.x == 0) kp.part_gauge_corr[blockIdx.x] = g;
+}
+
+// ---------------------------------------------------------------------------
 // Mixed-precision column kernel (DPSLAB_MIXED): the same steps as k_column
-// with the transforms, the banded solve and the node values in float; the
-// Schur 2x2 systems, the boundary values, the mismatches, the correction
-// coefficients, the k = 0 slope and the gauge sum in double. The correction
-// is evaluated at the nodes in float: its normalised form only multiplies
-// decaying factors bounded by e^{k_max H_E}, far inside float range.
+// with the transforms, the banded solve, the Schur 2x2 systems, the boundary
+// values and the node values in float; the mismatches, the correction
+// coefficients and the gauge sum in double; the k = 0 column (coefficients,
+// slope, gauge term) taken from k_column_zero, which solves it in double.
+// The correction is evaluated at the nodes in float: its normalised form
+// only multiplies decaying factors bounded by e^{k_max H_E}, far inside
+// float range.
 // ---------------------------------------------------------------------------
 constexpr int kColBlockM = 8;
 constexpr int kColThreadsM = 32 * kColBlockM;
@@ -1362,7 +1587,8 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
     float2* Co = Ci + CB * NP;
     float* cpv = reinterpret_cast<float*>(Co + CB * NP);
     float* xe = cpv + CB * NP;
-    __shared__ float s_k[CB], s_K[CB], s_mult[CB], s_den[CB], s_ekH[CB];
+    __shared__ float s_k[CB], s_K[CB], s_mult[CB], s_iden[CB], s_ekH[CB];
+    __shared__ float s_bs[CB][16];
     __shared__ double s_gauge[CB];
     __shared__ int s_valid[CB], s_corr[CB];
     __shared__ float2 s_c[2][CB], s_d[2][CB], s_P[CB], s_Q[CB];
@@ -1384,7 +1610,8 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
         s_corr[c] = (col < M) && k > 0.0 && k <= kp.kmax;
         s_gauge[c] = 0.0;
     }
-    if (tid == 0) s_Ai = 0.0;
+    // the k = 0 slope, from k_column_zero (block 0 holds column 0)
+    if (tid == 0) s_Ai = blockIdx.x == 0 ? kp.scal[1] : 0.0;
     const float scale = kp.f.scale;
     // every load of a batch is issued before the first store: one memory
     // round trip per batch instead of one per row group
@@ -1624,15 +1851,19 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
         }
     }
 
-    // boundary values, mismatches, correction coefficients and the gauge
-    // term in float; the k = 0 slope in double
+    // boundary values of psi_i*, psi_o* and their z derivatives at the walls
+    // (float sums over the coefficients); from them, in double
+    // (bc_correction), the mismatches Eq. (mm1)-(mm4) and the correction
+    // coefficients of Eq. (inphisc): here for the CUDA-core form, in
+    // k_bc_correction for the tensor-core form. The k = 0 column comes from
+    // k_column_zero.
     {
         const int c = tid >> 5, lane = tid & 31;
         const float2 *yi = Ci + c * NP, *ypi = Vi + c * NP, *yo = Co + c * NP, *ypo = Vo + c * NP;
-        float acc[20];
-        for (int i = 0; i < 20; ++i) acc[i] = 0.f;
+        float acc[18];
+        for (int i = 0; i < 18; ++i) acc[i] = 0.f;
         for (int n = lane; n < N; n += 32) {
-            const float a0 = kp.t032[n], aH = kp.tH32[n], alt = (n & 1) ? -1.f : 1.f, wg = kp.wg32[n];
+            const float a0 = kp.t032[n], aH = kp.tH32[n], wg = kp.wg32[n];
             acc[0] = fmaf(a0, yi[n].x, acc[0]);   acc[1] = fmaf(a0, yi[n].y, acc[1]);
             acc[2] = fmaf(a0, ypi[n].x, acc[2]);  acc[3] = fmaf(a0, ypi[n].y, acc[3]);
             acc[4] = fmaf(aH, yi[n].x, acc[4]);   acc[5] = fmaf(aH, yi[n].y, acc[5]);
@@ -1641,83 +1872,43 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
             acc[10] = fmaf(a0, ypo[n].x, acc[10]); acc[11] = fmaf(a0, ypo[n].y, acc[11]);
             acc[12] = fmaf(aH, yo[n].x, acc[12]); acc[13] = fmaf(aH, yo[n].y, acc[13]);
             acc[14] = fmaf(aH, ypo[n].x, acc[14]); acc[15] = fmaf(aH, ypo[n].y, acc[15]);
-            acc[16] = fmaf(alt, ypo[n].x, acc[16]); acc[17] += ypo[n].x;
-            acc[18] = fmaf(wg, yi[n].x, acc[18]); acc[19] = fmaf(wg, yi[n].y, acc[19]);
+            acc[16] = fmaf(wg, yi[n].x, acc[16]); acc[17] = fmaf(wg, yi[n].y, acc[17]);
         }
-        // the 20 sums: values 0..15 (lane 2 v holds value v) and 16..19
-        // (lane 8 v holds value 16 + v), gathered where they are used
-        const float r16 = warp_sum_multi<16>(acc), r4 = warp_sum_multi<4>(acc + 16);
-        float da[20];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) da[i] = __shfl_sync(0xffffffffu, r16, 2 * i);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) da[16 + i] = __shfl_sync(0xffffffffu, r4, 8 * i);
+        // the 18 sums: values 0..15 (lane 2 v holds value v) and 16, 17
+        // (lane 16 v holds value 16 + v)
+        const float r16 = warp_sum_multi<16>(acc), r2 = warp_sum_multi<2>(acc + 16);
+        const float wgs = __shfl_sync(0xffffffffu, r2, 0);
+        if (s_valid[c] && s_corr[c] && (lane & 1) == 0) {
+            if (kTensor) kp.bsum[size_t(lane >> 1) * M + col0 + c] = r16;   // to k_bc_correction
+            else s_bs[c][lane >> 1] = r16;
+        }
         if (lane == 0 && s_valid[c]) {
-            const float dz = kp.f.sz;
-            const float2 pi0 = make_float2(da[0], da[1]), dpi0 = make_float2(da[2] * dz, da[3] * dz);
-            const float2 piH = make_float2(da[4], da[5]), dpiH = make_float2(da[6] * dz, da[7] * dz);
-            const float2 po0 = make_float2(da[8], da[9]), dpo0 = make_float2(da[10] * dz, da[11] * dz);
-            const float2 poH = make_float2(da[12], da[13]), dpoH = make_float2(da[14] * dz, da[15] * dz);
-            const float k = s_k[c];
-            float corr0 = 0.f;
-            if (s_corr[c]) {
-                const float2 mpb = csub(pi0, cscale(po0, kp.f.tb));
-                float2 meb = csub(dpi0, cscale(dpo0, kp.f.rtb));
-                const float2 mpt = csub(piH, cscale(poH, kp.f.tt));
-                float2 met = csub(dpiH, cscale(dpoH, kp.f.rtt));
-                if (kp.sigma_on) {   // Eq. (mm2), (mm4): +sigma_b, -sigma_t (over eps)
-                    const double2 sb = kp.sig_hat[col0 + c], st = kp.sig_hat[M + col0 + c];
-                    const double ie = 1.0 / kp.eps;
-                    meb = cadd(meb, make_float2(float(sb.x * ie), float(sb.y * ie)));
-                    met = csub(met, make_float2(float(st.x * ie), float(st.y * ie)));
-                }
-                const float ik = 1.f / k;
-                const float2 P = csub(cscale(mpb, kp.f.cb), cscale(meb, kp.f.db * ik));
-                const float2 Q = csub(cscale(mpt, -kp.f.ct), cscale(met, kp.f.dt * ik));
-                const float ekH = expf(-k * kp.f.H);
-                const float den = 1.f - kp.f.Gb * kp.f.Gt * ekH * ekH;
-                s_P[c] = P;
-                s_Q[c] = Q;
-                s_ekH[c] = ekH;
-                s_den[c] = den;
-                corr0 = (-P.x * (1.f - kp.f.Gt * ekH * ekH) + Q.x * (ekH - kp.f.Gb * ekH)) / den;
-                if (kTensor) kp.colp[col0 + c] = ColP{P, Q, k, ekH, 1.f / den, 1};
-            } else if (kTensor) {
-                kp.colp[col0 + c] = ColP{make_float2(0.f, 0.f), make_float2(0.f, 0.f), k, 0.f, 0.f, 0};
-            }
-            if (col0 + c == 0) {
-                const double ddz = 2.0 / kp.Hbar;
-                const double dpi0x = double(da[2]) * ddz, dpiHx = double(da[6]) * ddz;
-                const double dpo0x = double(da[10]) * ddz, dpoHx = double(da[14]) * ddz;
-                const double dpoa = double(da[16]) * ddz, dpob = double(da[17]) * ddz;
-                double ai1 = kp.rtb * (dpo0x - dpoa) - dpi0x;
-                double ai2 = kp.rtt * (dpoHx - dpob) - dpiHx;
-                if (kp.sigma_on) {
-                    ai1 -= kp.sig_hat[0].x / kp.eps;
-                    ai2 += kp.sig_hat[M].x / kp.eps;
-                }
-                double Ai;
-                if (kp.metal_b && kp.metal_t) Ai = -(double(da[4]) - double(da[0])) / kp.H;
-                else if (kp.metal_b) Ai = ai2;
-                else if (kp.metal_t) Ai = ai1;
-                else Ai = 0.5 * (ai1 + ai2);
-                s_Ai = Ai;
-                kp.scal[1] = Ai;
-                if (kp.sigma_on) {   // k = 0 far potential at the walls, gamma^{1/2}-averaged in z
-                    double f0 = 0.0, fH = 0.0;
-                    for (int n = 0; n < N; ++n) {
-                        f0 = fma(kp.wg[n], double(yi[n].x), f0);
-                        fH = fma(kp.wgH[n], double(yi[n].x), fH);
-                    }
-                    kp.scal[7] = f0;
-                    kp.scal[8] = fH + Ai * kp.H;
-                }
-            }
-            const float damp = expf(-0.5f * kp.f.sigma2 * k * k);
-            s_gauge[c] = double(s_mult[c] * (damp * da[18] + corr0));
+            const double damp = double(expf(-0.5f * kp.f.sigma2 * s_k[c] * s_k[c]));
+            s_gauge[c] = (col0 + c == 0) ? kp.zcol[2 * N] : double(s_mult[c]) * damp * double(wgs);
+        }
+    }
+    if (!kTensor) {
+        // the correction of the block's modes in double, one lane each
+        __syncthreads();
+        if (tid < CB && s_valid[tid] && s_corr[tid]) {
+            const int c = tid;
+            const BcCoef b = bc_correction(kp, col0 + c, s_bs[c]);
+            s_P[c] = make_float2(float(b.P.x), float(b.P.y));
+            s_Q[c] = make_float2(float(b.Q.x), float(b.Q.y));
+            s_ekH[c] = float(b.ekH);
+            s_iden[c] = float(b.iden);
+            s_gauge[c] += double(s_mult[c]) * b.corr0;
         }
     }
     __syncthreads();
+    if (blockIdx.x == 0) {
+        // column 0: the coefficients of psi_i and dpsi_i/dz solved in double
+        for (int n = tid; n < N; n += bs) {
+            Ci[n] = make_float2(float(kp.zcol[n]), 0.f);
+            Vi[n] = make_float2(float(kp.zcol[N + n]), 0.f);
+        }
+        __syncthreads();
+    }
 
     if (kTensor) {
         // coefficients of psi_i (plane 0) and dpsi_i/dz (plane 1, before the
@@ -1784,7 +1975,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
             float2 dps = make_float2((dex + sg * dox) * sz, (dey + sg * doy) * sz);
             const float z = kp.zn32[j];
             if (s_corr[c] && z >= -HEf && z <= Hf + HEf) {
-                const float k = s_k[c], ekH = s_ekH[c], iden = 1.f / s_den[c];
+                const float k = s_k[c], ekH = s_ekH[c], iden = s_iden[c];
                 const float e1 = expf(-k * z), e3 = expf(k * (z - Hf));
                 const float e2 = e3 * ekH, e4 = e1 * ekH;
                 const float2 P = s_P[c], Q = s_Q[c];
@@ -1824,7 +2015,8 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_fwd(KP kp) {
     const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
     auto prep = [](int, int) {};
     auto epi = [](int, int, int, float*, int) {};
-    zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock);
+    zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock,
+              kp.zspin);
 }
 
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
@@ -1869,7 +2061,8 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
             v[i + 1] = im;
         }
     };
-    zgemm_run(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock);
+    zgemm_run(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock,
+              kp.zspin);
 }
 
 // ---------------------------------------------------------------------------
@@ -2369,6 +2562,7 @@ __global__ void k_origin(KP kp) {
 __global__ void k_final_gauge(KP kp) {
     double f = 0.0, nn = 0.0, q1 = 0.0, q2 = 0.0;
     for (int i = threadIdx.x; i < kp.n_col_blocks; i += blockDim.x) f += kp.part_gauge_far[i];
+    for (int i = threadIdx.x; i < kp.n_corr_blocks; i += blockDim.x) f += kp.part_gauge_corr[i];
     for (int i = threadIdx.x; i < kp.n_charge_blocks; i += blockDim.x) {
         nn += kp.part_gauge_near[i];
         q1 += kp.part_q[i];
@@ -2636,8 +2830,10 @@ struct dpslab_plan {
     bool bound = false;           // a workspace is bound (owned, a batch's, or the caller's)
     int64_t last_n = 0;
     int launches = 0;
-    int profiling = 0;
+    int profiling = 0;                 // 0 off, 1 stage events, 2 stage events with the near field in line
+    bool near_timed = false;           // the last profiled solve timed the near field on the second stream
     cudaEvent_t ev[DPSLAB_NSTAGES + 1] = {};
+    cudaEvent_t ev_near[2] = {};
     double stage_ms[DPSLAB_NSTAGES] = {};
 };
 
@@ -2716,6 +2912,9 @@ size_t bind_work(dpslab_plan* pl, char* base) {
     kp.irec = carve<IRec>(cur, n);
     kp.srcs_tmp = kp.mixed ? carve<SrcF>(cur, 3 * n) : nullptr;
     kp.colp = pl->ztensor ? carve<ColP>(cur, M) : nullptr;
+    kp.zcol = kp.mixed ? carve<double>(cur, 2 * size_t(kp.nz) + 1) : nullptr;
+    kp.bsum = pl->ztensor ? carve<float>(cur, 16 * M) : nullptr;
+    kp.part_gauge_corr = pl->ztensor ? carve<double>(cur, size_t(kp.n_corr_blocks)) : nullptr;
     kp.tile_count = carve<int>(cur, size_t(kp.nbuckets) + 1);
     kp.tile_start = carve<int>(cur, size_t(kp.nbuckets) + 1);
     kp.tile_fill = carve<int>(cur, size_t(kp.nbuckets) + 1);
@@ -2753,6 +2952,8 @@ void release(dpslab_plan* pl) {
     if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     if (pl->side) cudaStreamDestroy(pl->side);
     for (auto& e : pl->ev)
+        if (e) cudaEventDestroy(e);
+    for (auto& e : pl->ev_near)
         if (e) cudaEventDestroy(e);
     if (pl->tables) cudaFree(pl->tables);
     if (pl->work) cudaFree(pl->work);
@@ -2905,8 +3106,10 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
     kp.supx = d.support_x;
     kp.supy = d.support_y;
     kp.mixed = mixed ? 1 : 0;
+    kp.zspin = kZSpinLimit;
     const int col_block = mixed ? kColBlockM : kColBlock;
     kp.n_col_blocks = (M + col_block - 1) / col_block;
+    kp.n_corr_blocks = pl->ztensor ? int((M + kCorrThreads - 1) / kCorrThreads) : 0;
     const size_t rsz = mixed ? sizeof(float) : sizeof(double);   // grid element size
     kp.n_charge_blocks = int((max_n + kChargeThreads - 1) / kChargeThreads);
 
@@ -2921,6 +3124,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         bytes += 3 * align_up(N * N * sizeof(float)) + 14 * align_up(N * sizeof(float));
         if (pl->ztensor) bytes += 2 * align_up(t.zimg_fwd.size() * sizeof(unsigned short));   // bf16 images
         bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
+        if (mixed) bytes += align_up(size_t(M) * sizeof(double4));   // per-mode correction factors
         pl->device_bytes += int64_t(bytes);   // table bytes, taken up again below
     }
     if (!measure) {
@@ -2987,6 +3191,32 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         };
         upc(t.twx, kp.twx32);
         upc(t.twy, kp.twy32);
+        if (mixed) {
+            // per mode, in extended precision: 1/k, e^{-kH}, 1/den and
+            // -(1 - Gt e^{-2kH})/den, den = 1 - Gb Gt e^{-2kH}; both
+            // differences from 1 are formed as (1 - G) - G expm1(-2kH), which
+            // does not cancel as k -> 0 with G -> 1 (metal walls, small eps_w)
+            std::vector<double4> mt(static_cast<size_t>(M));
+            const long double Gb = kp.Gb, Gt = kp.Gt, H = p->H;
+            for (int col = 0; col < M; ++col) {
+                const int iy = col / kp.nxh, ix = col - iy * kp.nxh;
+                const int my = iy < (ny + 1) / 2 ? iy : iy - ny;
+                const long double kx = 2.0L * 3.141592653589793238462643383279503L * ix / p->Lx;
+                const long double ky = 2.0L * 3.141592653589793238462643383279503L * my / p->Ly;
+                const long double k = sqrtl(kx * kx + ky * ky);
+                if (k == 0.0L) {
+                    mt[col] = make_double4(0.0, 0.0, 0.0, 0.0);
+                    continue;
+                }
+                const long double e = expl(-k * H), em = expm1l(-2.0L * k * H);
+                const long double den = (1.0L - Gb * Gt) - Gb * Gt * em;
+                const long double ct = (1.0L - Gt) - Gt * em;
+                mt[col] = make_double4(double(1.0L / k), double(e), double(1.0L / den), double(-ct / den));
+            }
+            double4* dp = carve<double4>(cur, mt.size());
+            cudaMemcpy(dp, mt.data(), mt.size() * sizeof(double4), cudaMemcpyHostToDevice);
+            kp.mtab = dp;
+        }
         if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
     }
     // work space: sizes of the worst-case arrays, then one allocation (or,
@@ -3535,13 +3765,29 @@ extern "C" int dpslab_plan_destroy(dpslab_plan* plan) {
 
 extern "C" int dpslab_last_launch_count(const dpslab_plan* plan) { return plan ? plan->launches : 0; }
 
-extern "C" int dpslab_profile(dpslab_plan* plan, int on) {
-    if (!plan) return DPSLAB_ERR_INVALID_ARG;
-    DPS_CUDA(cudaSetDevice(plan->device));
-    if (on && !plan->ev[0]) {
+extern "C" int dpslab_plan_set_wait_limit(dpslab_plan* plan, int64_t polls) {
+    if (!plan || polls < 0 || plan->in_flight) return DPSLAB_ERR_INVALID_ARG;
+    plan->kp.zspin = polls;
+    return DPSLAB_OK;
+}
+
+// stage events (created on first use)
+int make_stage_events(dpslab_plan* plan) {
+    if (!plan->ev[0]) {
         for (auto& e : plan->ev) DPS_CUDA(cudaEventCreate(&e));
+        for (auto& e : plan->ev_near) DPS_CUDA(cudaEventCreate(&e));
     }
-    plan->profiling = on ? 1 : 0;
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_profile(dpslab_plan* plan, int on) {
+    if (!plan || on < 0 || on > 2) return DPSLAB_ERR_INVALID_ARG;
+    DPS_CUDA(cudaSetDevice(plan->device));
+    if (on) {
+        const int rc = make_stage_events(plan);
+        if (rc) return rc;
+    }
+    plan->profiling = on;
     return DPSLAB_OK;
 }
 
@@ -3646,10 +3892,9 @@ extern "C" int dpslab_plan_autotune(dpslab_plan* plan, int64_t n, const double* 
     if (n > plan->max_n) return DPSLAB_ERR_CAPACITY;
     DPS_CUDA(cudaSetDevice(plan->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (!plan->ev[0])
-        for (auto& e : plan->ev) DPS_CUDA(cudaEventCreate(&e));
+    if (const int erc = make_stage_events(plan)) return erc;
     const int prof = plan->profiling;
-    plan->profiling = 1;
+    plan->profiling = 2;   // stage times with nothing running beside them
     // median stage time of `reps` solves after one warm-up
     auto time_stage = [&](int stage, double& out) -> int {
         std::vector<double> t;
@@ -3706,6 +3951,7 @@ extern "C" const char* dpslab_strerror(int code) {
         case DPSLAB_ERR_UNSUPPORTED: return "unsupported option";
         case DPSLAB_PENDING: return "the solve has not finished yet";
         case DPSLAB_ERR_BD_REJECTED: return "every proposal of the Brownian-dynamics step left the slab";
+        case DPSLAB_ERR_TIMEOUT: return "a bounded wait on the tensor-core pipeline gave up";
         default: return "unknown error";
     }
 }
@@ -3769,14 +4015,18 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     mark(1);
     // The near field needs only the cell list (and writes only nearv): it
     // runs on the plan's second stream while the far field runs here, and
-    // this stream waits for it before the assembly. Profiled solves keep it
-    // in line so that every stage has its own time.
-    const bool fork = kp.near_on && !prof;
+    // this stream waits for it before the assembly. Profiling mode 1 keeps
+    // that and times the near field by its own events on the second stream;
+    // mode 2 runs it in line, so that the stage times add up to the solve.
+    const bool fork = kp.near_on && pl->profiling != 2;
+    pl->near_timed = fork && prof;
     if (fork) {
         DPS_CUDA(cudaEventRecord(pl->ev_fork, st));
         DPS_CUDA(cudaStreamWaitEvent(pl->side, pl->ev_fork, 0));
+        if (prof) DPS_CUDA(cudaEventRecord(pl->ev_near[0], pl->side));
         if (kp.mixed) LAUNCH(k_near_f32<<<(n + 127) / 128, 128, 0, pl->side>>>(kp));
         else LAUNCH(k_near<double><<<(n + 127) / 128, 128, 0, pl->side>>>(kp));
+        if (prof) DPS_CUDA(cudaEventRecord(pl->ev_near[1], pl->side));
         DPS_CUDA(cudaEventRecord(pl->ev_join, pl->side));
     }
     const dim3 gs(kp.ntiles, kp.nslabs);
@@ -3805,10 +4055,12 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         if (pl->p2y) LAUNCH(fft_p2<float>(1, pl->logny)<<<gy_fwd, pl->thr_y_fwd, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd, pl->logny));
         else LAUNCH(k_ffty_fwd<float><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
         mark(4);
+        LAUNCH(k_column_zero<<<1, kZeroThreads, 0, st>>>(kp));
         if (pl->ztensor) {
             LAUNCH(k_zgemm_fwd<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
             mark(5);
             LAUNCH(k_column_mixed<true><<<kp.n_col_blocks, kColThreadsM, pl->sm_col, st>>>(kp));
+            LAUNCH(k_bc_correction<<<kp.n_corr_blocks, kCorrThreads, 0, st>>>(kp));
             mark(6);
             LAUNCH(k_zgemm_inv<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
         } else {
@@ -3869,7 +4121,7 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
 int collect(dpslab_plan* pl, double* U) {
     if (U) *U = pl->h_scal[4];
     if (*pl->h_status & kStatusCapacity) return DPSLAB_ERR_CAPACITY;
-    if (*pl->h_status & kStatusTimeout) return DPSLAB_ERR_CUDA;
+    if (*pl->h_status & kStatusTimeout) return DPSLAB_ERR_TIMEOUT;
     if (*pl->h_status & kStatusRejected) return DPSLAB_ERR_BD_REJECTED;
     if (*pl->h_status) return DPSLAB_ERR_OUT_OF_SLAB;
     double sq = pl->h_scal[5], saq = pl->h_scal[6];
@@ -3888,6 +4140,11 @@ int finish(dpslab_plan* pl, cudaStream_t st, double* U) {
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, pl->ev[i], pl->ev[i + 1]);
             pl->stage_ms[i] = ms;
+        }
+        if (pl->near_timed) {   // the near stage ran beside the far field
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, pl->ev_near[0], pl->ev_near[1]);
+            pl->stage_ms[kStageNear] = ms;
         }
     }
     return collect(pl, U);
@@ -4010,10 +4267,12 @@ constexpr int kStaticMaxCells = 65536;     // near-field cells per call
 constexpr int kStaticMaxDevices = 64;
 constexpr size_t kStaticBlocks = (kStaticMaxN + kChargeThreads - 1) / kChargeThreads;
 constexpr size_t kStaticScratchBytes =
-    4 * align_up_c(kStaticMaxN * 32) +                        // part, sorted, near results, spare
+    3 * align_up_c(kStaticMaxN * 32) +                        // part, sorted, near results
+    align_up_c(kStaticMaxN * 16) +                            // sorted_rel
     2 * align_up_c(kStaticMaxN * 4) +                         // cell_of, sorted_idx
     3 * align_up_c((kStaticMaxCells + 1) * 4) +               // cell count, start, fill
     align_up_c(2 * kStaticBlocks * 8) + align_up_c(64);       // neutrality partials, status
+static_assert(kStaticScratchBytes < (8u << 20) + (512u << 10), "the documented size: about 8.3 MiB");
 
 static __device__ __align__(256) unsigned char g_near_scratch[kStaticScratchBytes];
 
@@ -4077,7 +4336,7 @@ extern "C" int dpslab_near_field_static(const dpslab_params* p, int64_t n, const
     kp.part = carve<double4_32a>(cur, kStaticMaxN);
     kp.sorted = carve<double4_32a>(cur, kStaticMaxN);
     kp.nearv = carve<double4_32a>(cur, kStaticMaxN);
-    kp.sorted_rel = reinterpret_cast<float4*>(carve<double4_32a>(cur, kStaticMaxN));   // 16 of the 32 bytes
+    kp.sorted_rel = carve<float4>(cur, kStaticMaxN);
     kp.cell_of = carve<int>(cur, kStaticMaxN);
     kp.sorted_idx = carve<int>(cur, kStaticMaxN);
     kp.cell_count = carve<int>(cur, size_t(kStaticMaxCells) + 1);

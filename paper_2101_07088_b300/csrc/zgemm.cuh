@@ -33,8 +33,10 @@
 //   3. each warp reads its quarter of the accumulator lanes, 32 columns, with
 //      tcgen05.ld, adds the two accumulators and stores the rows through an
 //      epilogue functor.
-// The wait on the MMAs is bounded; on a timeout the kernel records
-// kStatusTimeout, stops, waits (bounded) once more and frees its tensor memory.
+// The waits on the MMAs and on the bulk copies are bounded (`spin` polls);
+// on a timeout the kernel records kStatusTimeout, stops, waits for the work
+// still in flight (bounded by kZSpinLimit polls, whatever `spin` is) and
+// frees its tensor memory.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -95,9 +97,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long i = 0; i < kZSpinLimit; ++i)
+// bounded wait of at most `limit` polls; false on timeout (at once for limit 0)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kZSpinLimit) {
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -203,7 +205,7 @@ static_assert(size_t(kZK) * kZOStride * 4 <= kZSmemB, "staged outputs fit the B 
 template <class Prep, class Epi>
 __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aimg, float* base, int nplanes,
                                           size_t pstride, int rows, int ncols, size_t ld, int* status, Prep prep,
-                                          Epi epi, int nblk = 1) {
+                                          Epi epi, int nblk, long long spin) {
     extern __shared__ __align__(1024) unsigned char zsm[];
     unsigned short* sA = reinterpret_cast<unsigned short*>(zsm);
     unsigned short* sB = reinterpret_cast<unsigned short*>(zsm + kZSmemA);
@@ -346,7 +348,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
                         mbar_expect_tx(abar, uint32_t(kZSmemA));
                         bulk_g2s(sA, aimg + zimg_block(rb, kb, nblk, 0), uint32_t(kZSmemA), abar);
                         apend = true;
-                        if (mbar_wait(abar, aph)) apend = false;
+                        if (mbar_wait(abar, aph, spin)) apend = false;
                         else s_abort = 1;
                     }
                     fence_async_smem();
@@ -371,7 +373,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
                         tc_commit(bar);
                     }
                     pend = true;
-                    if (tid == 0 && !mbar_wait(bar, ph)) s_abort = 1;
+                    if (tid == 0 && !mbar_wait(bar, ph, spin)) s_abort = 1;
                     __syncthreads();
                     if (!s_abort) {
                         ph ^= 1u;
@@ -520,7 +522,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
         }
         // one thread polls the MMA barrier (polls from every warp would
         // compete with the loads for the memory pipes); the rest wait here
-        if (tid == 0 && !mbar_wait(bar, ph)) s_abort = 1;
+        if (tid == 0 && !mbar_wait(bar, ph, spin)) s_abort = 1;
         tc_fence_before();
         __syncthreads();
         if (s_abort) break;

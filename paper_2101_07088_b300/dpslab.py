@@ -18,10 +18,11 @@ OK = 0
 ERRORS = {
     -1: "INVALID_ARG", -2: "NOT_NEUTRAL", -3: "OUT_OF_SLAB", -4: "CUTOFF_TOO_LARGE",
     -5: "SPLIT_CONSTRAINT", -6: "CAPACITY", -7: "CUDA", -8: "NO_DEVICE", -9: "GRID", -10: "UNSUPPORTED",
-    -11: "BD_REJECTED",
+    -11: "BD_REJECTED", -12: "TIMEOUT",
 }
 (ERR_INVALID_ARG, ERR_NOT_NEUTRAL, ERR_OUT_OF_SLAB, ERR_CUTOFF_TOO_LARGE, ERR_SPLIT_CONSTRAINT, ERR_CAPACITY,
- ERR_CUDA, ERR_NO_DEVICE, ERR_GRID, ERR_UNSUPPORTED, ERR_BD_REJECTED) = range(-1, -12, -1)
+ ERR_CUDA, ERR_NO_DEVICE, ERR_GRID, ERR_UNSUPPORTED, ERR_BD_REJECTED, ERR_TIMEOUT) = range(-1, -13, -1)
+WAIT_LIMIT_DEFAULT = 1 << 26         # default polls of a bounded wait (dpslab_plan_set_wait_limit)
 PENDING = 1                          # DPSLAB_PENDING
 FP64, MIXED, MIXED_SIMT = 0, 1, 2   # DPSLAB_FP64, DPSLAB_MIXED, DPSLAB_MIXED_SIMT
 NSTAGES = 12
@@ -75,6 +76,7 @@ def lib():
             "dpslab_solve_host": (ctypes.c_int, [vp, i64, vp, vp, dp, vp, vp, vp]),
             "dpslab_debug_fetch": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_size_t]),
             "dpslab_last_launch_count": (ctypes.c_int, [vp]),
+            "dpslab_plan_set_wait_limit": (ctypes.c_int, [vp, i64]),
             "dpslab_plan_destroy": (ctypes.c_int, [vp]),
             "dpslab_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "dpslab_plan_footprint": (ctypes.c_int, [P, i64, ctypes.POINTER(i64)]),
@@ -362,8 +364,15 @@ class Plan:
     def last_launch_count(self):
         return lib().dpslab_last_launch_count(self._h)
 
-    def profile(self, on=True):
-        _check(lib().dpslab_profile(self._h, 1 if on else 0))
+    def set_wait_limit(self, polls=WAIT_LIMIT_DEFAULT):
+        """dpslab_plan_set_wait_limit: polls of each bounded wait of the
+        tensor-core z transforms before the solve reports ERR_TIMEOUT."""
+        _check(lib().dpslab_plan_set_wait_limit(self._h, int(polls)))
+
+    def profile(self, on=True, near_in_line=False):
+        """Stage timing on (the near field stays on the second stream and is
+        timed there) or off; near_in_line runs the near field in line."""
+        _check(lib().dpslab_profile(self._h, (2 if near_in_line else 1) if on else 0))
 
     def stage_times(self):
         """{stage name: device ms} of the last solve (profiling on)."""

@@ -8,8 +8,8 @@ import math
 import numpy as np
 import pytest
 
-from gpu_helpers import (TOL_MIXED_ENERGY, TOL_MIXED_FORCE, gpu_solve, oracle_params, plan_for, rel_l2,
-                         rel_max)
+from gpu_helpers import (TOL_MIXED_ENERGY, TOL_MIXED_FORCE, gpu_solve, mixed_energy_tol, oracle_params, plan_for,
+                         rel_l2, rel_max)
 from oracle import solver as osolver
 from paper_2101_07088_b300 import build, dpslab, synth
 
@@ -22,16 +22,6 @@ def gpu_ready():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     build.build()
-
-
-# For a handful of charges the energy is a short sum in which every FP32
-# rounding of the solve operator enters with the same sign through the
-# Gaussian self energies; there it sits at the FP32 noise level. On the
-# 102-charge ragged case it is 2.5e-7 to 3.3e-7 over 30 runs (the rounding of
-# that configuration, 1.5e-8 of it from the order of the spreading sums), so
-# the bar is 8 units of FP32 roundoff, 8 x 2^-24 = 4.8e-7. The benchmark
-# workloads (16384 and 2^20 charges) are held to the 1e-7 target.
-TOL_MIXED_ENERGY_SMALL = 8 * 2.0 ** -24
 
 
 def _check(ref, out, label, energy_tol=TOL_MIXED_ENERGY):
@@ -61,12 +51,14 @@ def test_mixed_against_oracle(name, _, prec, plabel):
                       eps_b=p["eps_b"], eps_t=p["eps_t"], r_cut=p["r_cut"])
     ref = osolver.solve(pos, q, P)
     out = gpu_solve(plan_for(P, len(q), precision=prec), pos, q)
-    _check(ref, out, f"{name} {plabel}", TOL_MIXED_ENERGY if len(q) >= 16384 else TOL_MIXED_ENERGY_SMALL)
+    _check(ref, out, f"{name} {plabel}", mixed_energy_tol(P, len(q)))
 
 
 def test_tensor_z_transform_runs():
     # Nz <= 128 with ny (nx/2+1) even: the z transforms run as two tensor-core
-    # GEMM launches around the BVP kernel (two launches more than the SIMT form)
+    # GEMM launches around the BVP kernel, and the correction coefficients of
+    # every mode in their own FP64 kernel (three launches more than the SIMT
+    # form)
     pos, q, p = synth.workload("c2_jumps_n16384")
     P = oracle_params(p["Lx"], p["Ly"], p["H"], p["gw"], p["tol"], p["nx"], p["ny"], nz=p["nz"],
                       eps_b=p["eps_b"], eps_t=p["eps_t"], r_cut=p["r_cut"])
@@ -75,18 +67,18 @@ def test_tensor_z_transform_runs():
         plan = plan_for(P, len(q), precision=prec)
         gpu_solve(plan, pos, q)
         counts[prec] = plan.last_launch_count()
-    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 2, counts
+    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 3, counts
 
 
 def test_mixed_small_ragged_and_paper_rule():
     P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, 40, nz=37, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
     pos, q = synth.electrolyte(102, 24.0, 20.0, 1.0, 19.0, seed=3)
     _check(osolver.solve(pos, q, P), gpu_solve(plan_for(P, 102, precision=dpslab.MIXED), pos, q), "ragged",
-           TOL_MIXED_ENERGY_SMALL)
+           mixed_energy_tol(P, 102))
     P = oracle_params(2.0, 2.0, 1.0, 0.01, 1e-4, 38, 38, eps_b=0.05, eps_t=0.02)
     pos, q = synth.electrolyte(40, 2.0, 2.0, 0.045, 0.955, seed=5)
     _check(osolver.solve(pos, q, P), gpu_solve(plan_for(P, 40, precision=dpslab.MIXED), pos, q), "paper-rule",
-           TOL_MIXED_ENERGY_SMALL)
+           mixed_energy_tol(P, 40))
 
 
 def test_mixed_against_fp64_gpu_at_one_million_charges():
@@ -119,17 +111,15 @@ def test_mixed_fallback_to_cuda_core_z_transform(ny, nz):
         plan = plan_for(P, 102, precision=prec)
         out = gpu_solve(plan, pos, q)
         counts[prec] = plan.last_launch_count()
-        _check(ref, out, f"fallback ny={ny} nz={nz} prec={prec}", TOL_MIXED_ENERGY_SMALL)
+        _check(ref, out, f"fallback ny={ny} nz={nz} prec={prec}", mixed_energy_tol(P, 102))
     assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT], counts
 
 
 @pytest.mark.parametrize("nz", [136, 200, 256])
 def test_tensor_z_transform_in_two_blocks(nz):
     # 128 < Nz <= 256: the z transforms run on the tensor cores in 2 x 2
-    # blocks of 128 (two launches more than the CUDA-core form), within the
+    # blocks of 128 (three launches more than the CUDA-core form), within the
     # bar against the oracle and close to the CUDA-core form
-    # 800 charges: an energy that is not a handful of self terms (see
-    # TOL_MIXED_ENERGY_SMALL)
     P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, 40, nz=nz, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
     pos, q = synth.electrolyte(800, 24.0, 20.0, 1.0, 19.0, seed=8)
     ref = osolver.solve(pos, q, P)
@@ -138,6 +128,28 @@ def test_tensor_z_transform_in_two_blocks(nz):
         plan = plan_for(P, 800, precision=prec)
         out[prec] = gpu_solve(plan, pos, q)
         counts[prec] = plan.last_launch_count()
-        _check(ref, out[prec], f"two blocks nz={nz} prec={prec}", TOL_MIXED_ENERGY_SMALL)
-    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 2, counts
+        _check(ref, out[prec], f"two blocks nz={nz} prec={prec}", mixed_energy_tol(P, 800))
+    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 3, counts
     assert rel_l2(out[dpslab.MIXED]["force"], out[dpslab.MIXED_SIMT]["force"]) < TOL_MIXED_FORCE
+
+
+@pytest.mark.parametrize("nz", [64, 200], ids=["one-block", "two-block"])
+def test_bounded_wait_reports_timeout(nz):
+    """The bounded waits of the tensor-core z transforms: with a limit of 0
+    polls every wait gives up at once; the kernels then wait for their work in
+    flight, free their tensor memory and return, and the solve reports
+    DPSLAB_ERR_TIMEOUT. With the default limit the same plan solves again and
+    matches a fresh plan."""
+    P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, 40, nz=nz, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
+    pos, q = synth.electrolyte(200, 24.0, 20.0, 1.0, 19.0, seed=12)
+    plan = plan_for(P, 200, precision=dpslab.MIXED)
+    ref = gpu_solve(plan, pos, q)
+    plan.set_wait_limit(0)
+    with pytest.raises(dpslab.DpslabError) as e:
+        gpu_solve(plan, pos, q)
+    assert e.value.code == dpslab.ERR_TIMEOUT
+    plan.set_wait_limit()
+    again = gpu_solve(plan, pos, q)
+    assert rel_l2(again["force"], ref["force"]) < 1e-6
+    with pytest.raises(dpslab.DpslabError):
+        plan.set_wait_limit(-1)
