@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=150.0)
+    ap.add_argument("--streams", type=int, default=0,
+                    help="batched workload: streams (systems per wave) of the mixed batch; 0 = the workload's")
     return ap.parse_args()
 
 
@@ -285,13 +287,25 @@ def bench_batch(args):
         return ms
 
     out = {}
+    streams = dict(mixed=args.streams or cfg["nstreams"], fp64=cfg["nstreams"])
+    args_ = ([b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs], [b[3] for b in bufs])
+    schedules = {}
     for name, prec in (("mixed", dpslab.MIXED), ("fp64", dpslab.FP64)):
         params = [dpslab.make_params(precision=prec, **p) for _, _, p in systems]
-        batch = dpslab.Batch(params, [len(q) for _, q, _ in systems], nstreams=cfg["nstreams"])
-        args_ = ([b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs], [b[3] for b in bufs])
+        batch = dpslab.Batch(params, [len(q) for _, q, _ in systems], nstreams=streams[name])
+        if name == "mixed":
+            # both schedules timed as the bench times steps, then the
+            # library's batch autotuner picks one (outside the timed region)
+            for sched, label in ((dpslab.BATCH_STREAMS, "streams"), (dpslab.BATCH_WAVES, "waves")):
+                batch.set_schedule(sched)
+                sms = timed(lambda: batch.solve(*args_), max(1, min(args.steps, 3)), 2)
+                schedules[label] = dict(ms_per_step=sum(sms) / len(sms), gpu_launches=batch.last_launch_count())
+            batch.set_schedule(dpslab.BATCH_STREAMS)
+            schedules["autotuned"] = "waves" if batch.autotune(args_[0], args_[1], reps=2) == dpslab.BATCH_WAVES \
+                else "streams"
         ms = timed(lambda: batch.solve(*args_), max(1, args.steps), max(3, args.warmup))
         U, _ = batch.solve(*args_)
-        out[name] = dict(ms=ms, U=U.copy(), bytes=batch.device_bytes)
+        out[name] = dict(ms=ms, U=U.copy(), bytes=batch.device_bytes, launches=batch.last_launch_count())
         batch.close()
     # the mixed plans one after another (no graph, no concurrency)
     plans = [dpslab.Plan(dpslab.make_params(precision=dpslab.MIXED, **p), len(q)) for _, q, p in systems]
@@ -306,9 +320,13 @@ def bench_batch(args):
                 warmup=max(3, args.warmup), ms_per_step=mean, p50_ms=ms[len(ms) // 2],
                 p99_ms=ms[min(len(ms) - 1, int(math.ceil(0.99 * len(ms))) - 1)], higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32+f64", data="synthetic (seeded +-1 electrolytes)",
-                config=dict(workload=args.workload, systems=cfg["count"], charges=total, streams=cfg["nstreams"],
-                            form="one dpslab_batch_solve call (CUDA graph replay)",
+                config=dict(workload=args.workload, systems=cfg["count"], charges=total, streams=streams,
+                            form="one dpslab_batch_solve call (CUDA graph replay); mixed schedule chosen by "
+                                 "dpslab_batch_autotune (per-system streams, or waves of `streams` systems with one "
+                                 "column-stage launch per kind over all their modes); FP64 per-system streams",
                             l2="512 MiB memset between timed steps"),
+                gpu_launches=dict(mixed=out["mixed"]["launches"], fp64=out["fp64"]["launches"]),
+                mixed_schedules=schedules,
                 fp64_value=total / (f64 * 1e-3), fp64_ms_per_step=f64,
                 mixed_over_fp64=f64 / mean, sequential_ms_per_step=sum(seq) / len(seq),
                 max_energy_rel_vs_fp64=uerr, device_bytes=dict(mixed=out["mixed"]["bytes"], fp64=out["fp64"]["bytes"]))

@@ -226,21 +226,30 @@ int dpslab_bd_step_enqueue(dpslab_plan* plan, const dpslab_bd_params* bp, int64_
 int dpslab_bd_last_retries(const dpslab_plan* plan);
 
 /*
- * Launch-shape autotuning. Four knobs set how many sequences one thread
- * block transforms in the xy FFT kernels:
- *   knobs[0]  x forward (rows)     knobs[1]  y forward (columns)
- *   knobs[2]  y inverse (columns)  knobs[3]  x inverse (rows)
+ * Launch-shape autotuning. DPSLAB_NKNOBS knobs set the launch shapes of the
+ * solve's kernels:
+ *   knobs[0]  x forward FFT: rows per block     knobs[1]  y forward FFT: columns per block
+ *   knobs[2]  y inverse FFT: columns per block  knobs[3]  x inverse FFT: rows per block
+ *   knobs[4]  interpolation: charges (warps) per block: 1, 2, 4 or 8
+ *   knobs[5]  column kernel (per-mode BVP): k modes per block: 4 or 8
+ *             (DPSLAB_MIXED), 2 or 4 (DPSLAB_FP64)
+ *   knobs[6]  spreading: x grid columns per thread: 1 or 2 (DPSLAB_MIXED),
+ *             1 (DPSLAB_FP64)
  * A value sets the block size and shared memory of its kernel; the results
- * do not depend on it. dpslab_plan_autotune runs the solve on the caller's
- * device inputs (as dpslab_solve, outputs discarded), and for each knob in
- * turn times its stage with CUDA events (median of `reps` solves after one
- * warm-up) at 1, 2, 4, ..., 32 within the kernel's thread and shared-memory
- * limits, keeping a value only when it is at least 2% faster. Needs a bound
- * workspace and no solve in flight. dpslab_plan_set_tuning applies knobs (for
- * example cached from an earlier autotune of the same grid); it returns
- * DPSLAB_ERR_INVALID_ARG and changes nothing if a value is outside its
- * kernel's limits.
+ * do not depend on it beyond the order of floating-point sums. The FFT knobs
+ * take 1, 2, 4, ..., 32 within the kernel's thread and shared-memory limits.
+ * dpslab_plan_autotune runs the solve on the caller's device inputs (as
+ * dpslab_solve, outputs discarded), and for each knob in turn times its
+ * stage with CUDA events (median of `reps` solves after one warm-up) at each
+ * allowed value, keeping a value only when it is at least 2% faster. Needs a
+ * bound workspace and no solve in flight. dpslab_plan_tuning writes the
+ * first n >= 4 knobs (n < DPSLAB_NKNOBS: the FFT knobs only);
+ * dpslab_plan_set_tuning applies the first n >= 4 knobs (for example cached
+ * from an earlier autotune of the same grid) and leaves the others; it
+ * returns DPSLAB_ERR_INVALID_ARG and changes nothing if a value is outside
+ * its kernel's limits.
  */
+#define DPSLAB_NKNOBS 7
 int dpslab_plan_autotune(dpslab_plan* plan, int64_t n, const double* pos, const double* q, int reps, void* stream);
 int dpslab_plan_tuning(const dpslab_plan* plan, int* knobs, int n);
 int dpslab_plan_set_tuning(dpslab_plan* plan, const int* knobs, int n);
@@ -348,9 +357,18 @@ int dpslab_solve_poll(dpslab_plan* plan, double* U);
  * left allocated then.
  *
  * dpslab_batch_solve solves every system. It forks the caller's stream into
- * the batch's streams, enqueues each system's solve there, and joins them
- * back. The first call with a given set of arguments (the n[i] and every
- * pointer) captures this into a CUDA graph; later calls with the same
+ * the batch's streams, enqueues the solves there and joins them back, in
+ * one of two schedules (dpslab_batch_set_schedule). DPSLAB_BATCH_STREAMS:
+ * system i's whole solve runs on stream i mod nstreams. DPSLAB_BATCH_WAVES:
+ * in waves of nstreams systems (systems w .. w + nstreams - 1, whose
+ * workspaces are distinct), each system's solve runs up to its column stage
+ * on its stream; then the column stage of the whole wave (the per-mode BVP,
+ * Appendix A, and the boundary-condition correction, Sec. 4.3.3, whose
+ * modes are independent, Sec. 5.2.2) runs as one launch per kind of column
+ * kernel over every k mode of every system of the wave; then the rest of
+ * each solve on its stream. With nstreams >= count the batch is one wave.
+ * The first call with a given set of arguments (the n[i], every pointer and
+ * the schedule) captures this into a CUDA graph; later calls with the same
  * arguments replay it (new values in the same buffers are fine). It returns
  * when the batch is done.
  *   n[count]; pos[count] ([n_i][3] device), q[count] ([n_i] device): the
@@ -367,6 +385,28 @@ int dpslab_batch_create(const dpslab_params* params, const int64_t* max_n, int c
 int dpslab_batch_solve(dpslab_batch* batch, const int64_t* n, const double* const* pos, const double* const* q,
                        double* U, double* const* phi, double* const* force, int* status, void* stream);
 int64_t dpslab_batch_device_bytes(const dpslab_batch* batch);
+/* Kernels the last dpslab_batch_solve launched, over all systems. */
+int dpslab_batch_last_launch_count(const dpslab_batch* batch);
+/*
+ * Schedule of a batch solve:
+ *   DPSLAB_BATCH_STREAMS (the default): each system's whole solve runs on
+ *     its stream, and the streams run freely beside one another;
+ *   DPSLAB_BATCH_WAVES: the waves described above, with the column stage of
+ *     each wave as one launch per kind of column kernel (and per 22 systems)
+ *     over all its systems' k modes.
+ * Both give the same results. dpslab_batch_set_schedule returns
+ * DPSLAB_ERR_INVALID_ARG for any other value; the next solve captures a new
+ * graph. dpslab_batch_autotune times both schedules on the caller's device
+ * inputs (as dpslab_batch_solve, outputs discarded; the median of `reps`
+ * solves after one warm-up each, CUDA events on `stream`) and keeps the
+ * other schedule only when it is at least 2% faster.
+ */
+#define DPSLAB_BATCH_STREAMS 0
+#define DPSLAB_BATCH_WAVES   1
+int dpslab_batch_set_schedule(dpslab_batch* batch, int schedule);
+int dpslab_batch_schedule(const dpslab_batch* batch);
+int dpslab_batch_autotune(dpslab_batch* batch, const int64_t* n, const double* const* pos, const double* const* q,
+                          int reps, void* stream);
 int dpslab_batch_destroy(dpslab_batch* batch);
 
 /*

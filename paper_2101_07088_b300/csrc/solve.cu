@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -21,7 +22,8 @@ namespace {
 constexpr int kColBlock = 4;        // k_par columns per block of the column kernel (one warp each)
 constexpr int kColThreads = 32 * kColBlock;
 constexpr int kChargeThreads = 256;
-constexpr int kInterpWarps = 2;
+constexpr int kInterpWarps = 2;     // default warps per block of the interpolation (one charge each)
+constexpr int kMaxInterpWarps = 8;
 constexpr int kTile = 16;           // spreading tile: kTile x kTile xy grid points, one thread each
 constexpr int kSpreadBatch = 32;    // sources per batch in the tiled spreading
 constexpr double kTwoPi = 6.283185307179586476925286766559;
@@ -78,6 +80,31 @@ __device__ double block_sum(double v) {
     v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
     if (w == 0) v = warp_sum(v);
     return v;
+}
+
+// The column stage of up to kBatchMaxSys systems in one launch: their
+// parameter blocks travel as the kernel's (read-only) parameter, 32 KB at
+// most, so that the kernels read them as they read a single system's.
+constexpr int kBatchMaxSys = 22;
+struct ColBatch {
+    int nsys;
+    int starts[kBatchMaxSys + 1];        // first column block of each system
+    int corr_starts[kBatchMaxSys + 1];   // first block of k_bc_correction
+    KP kp[kBatchMaxSys];
+};
+static_assert(sizeof(ColBatch) <= 32000, "kernel parameters are limited to 32 KB");
+
+// System of block b of a launch over several systems: starts[s] is the
+// first block of system s (ascending, starts[0] = 0); the largest s with
+// starts[s] <= b.
+__device__ __forceinline__ int batch_system(const int* starts, int nsys, int b) {
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // Cell list index, z fastest: the cell-sorted charge order then sweeps thin
@@ -590,18 +617,22 @@ __global__ void k_scatter_sources_f(KP kp) {
     }
 }
 
-// Two neighbouring x columns per thread (128 threads for the 16 x 16
+// CPT neighbouring x columns per thread (256 / CPT threads for the 16 x 16
 // tile): the per-source work of a thread (the loop, the weight loads, the
-// zero test) is shared by 16 multiply-adds instead of 8.
-constexpr int kSpreadThreadsM = kTile * kTile / 2;
+// zero test) is shared by 8 CPT multiply-adds. The default is 2; the
+// autotuner may choose 1.
+constexpr int kSpreadCptM = 2;
+constexpr int kSpreadThreadsM = kTile * kTile / kSpreadCptM;
 
-__global__ void __launch_bounds__(kSpreadThreadsM) k_spread_f32(KP kp) {
+template <int CPT>
+__global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
     constexpr int B = kSpreadBatchM;
+    constexpr int NT = kTile * kTile / CPT, XG = kTile / CPT;
     __shared__ float s_wx[B][kTile + 1];
     __shared__ float s_wy[B][kTile + 1];
     __shared__ __align__(16) float s_wz[B][kWzStride];
     __shared__ int s_over[B];
-    const int tid = threadIdx.x, lx = 2 * (tid % (kTile / 2)), ly = tid / (kTile / 2);
+    const int tid = threadIdx.x, lx = CPT * (tid % XG), ly = tid / XG;
     const int tile = blockIdx.x, txi = tile % kp.ntx, tyi = tile / kp.ntx;
     const int slab = blockIdx.y, js = slab * kSlabM;
     const int gx0 = txi * kTile, gy0 = tyi * kTile;
@@ -609,14 +640,16 @@ __global__ void __launch_bounds__(kSpreadThreadsM) k_spread_f32(KP kp) {
     const int first = kp.tile_start[bk], total = kp.tile_start[bk + 1] - first;
     const SrcF* src = kp.srcsf + first;
     const float ig2 = kp.f.ig2, s1 = kp.f.s1norm;
-    float ai0[kSlabM], ai1[kSlabM], ao0[kSlabM], ao1[kSlabM];
+    float ai[CPT][kSlabM], ao[CPT][kSlabM];
 #pragma unroll
-    for (int j = 0; j < kSlabM; ++j) ai0[j] = ai1[j] = ao0[j] = ao1[j] = 0.f;
+    for (int c = 0; c < CPT; ++c)
+#pragma unroll
+        for (int j = 0; j < kSlabM; ++j) ai[c][j] = ao[c][j] = 0.f;
     for (int base = 0; base < total; base += B) {
         const int nb = min(B, total - base);
-        // weight tables: thread b fills source b's x and z weights (times the
-        // strength), thread b + B/2 ... the y weights; B = 128 = 2 x 64
-        for (int b = tid; b < 2 * B; b += kSpreadThreadsM) {
+        // weight tables: entry b < B of the loop fills source b's x and z
+        // weights (times the strength), entry B + b its y weights
+        for (int b = tid; b < 2 * B; b += NT) {
             const int rb = b % B;
             if (rb >= nb) continue;
             const SrcF r = src[base + rb];
@@ -661,21 +694,21 @@ __global__ void __launch_bounds__(kSpreadThreadsM) k_spread_f32(KP kp) {
         for (int b = 0; b < nb; ++b) {
             const float wy = s_wy[b][ly];
             if (wy != 0.f) {
-                const float w0 = s_wx[b][lx] * wy, w1 = s_wx[b][lx + 1] * wy;
+                float w[CPT];
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) w[c] = s_wx[b][lx + c] * wy;
                 const float4 z0 = *reinterpret_cast<const float4*>(&s_wz[b][0]);
                 const float4 z1 = *reinterpret_cast<const float4*>(&s_wz[b][4]);
                 const float wz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
-                for (int j = 0; j < kSlabM; ++j) {
-                    ai0[j] = fmaf(w0, wz[j], ai0[j]);
-                    ai1[j] = fmaf(w1, wz[j], ai1[j]);
-                }
+                for (int j = 0; j < kSlabM; ++j)
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) ai[c][j] = fmaf(w[c], wz[j], ai[c][j]);
                 if (s_over[b]) {
 #pragma unroll
-                    for (int j = 0; j < kSlabM; ++j) {
-                        ao0[j] = fmaf(w0, wz[j], ao0[j]);
-                        ao1[j] = fmaf(w1, wz[j], ao1[j]);
-                    }
+                    for (int j = 0; j < kSlabM; ++j)
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c) ao[c][j] = fmaf(w[c], wz[j], ao[c][j]);
                 }
             }
         }
@@ -689,13 +722,12 @@ __global__ void __launch_bounds__(kSpreadThreadsM) k_spread_f32(KP kp) {
         for (int j = 0; j < kSlabM; ++j) {
             if (js + j < kp.nz) {
                 const size_t g = (size_t(js + j) * kp.ny + gy) * kp.nx + gx;
-                if (gx < kp.nx) {
-                    rho[g] = ai0[j];
-                    rho[G + g] = ao0[j];
-                }
-                if (gx + 1 < kp.nx) {
-                    rho[g + 1] = ai1[j];
-                    rho[G + g + 1] = ao1[j];
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    if (gx + c < kp.nx) {
+                        rho[g + c] = ai[c][j];
+                        rho[G + g + c] = ao[c][j];
+                    }
                 }
             }
         }
@@ -993,9 +1025,9 @@ FftP2Kernel fft_p2(int which, int logn) {
 // (step 5), the gauge partial sum, and the values of psi_i and dpsi_i/dz at
 // the nodes (step 6); written in place over the two spectra
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
+template <int CB>
+__device__ __forceinline__ void column_body(const KP& kp, const int bid) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    constexpr int CB = kColBlock;
     const int N = kp.nz;
     const int M = kp.ny * kp.nxh;
     double2* Vi = reinterpret_cast<double2*>(smraw);   // values, then y' (field i)
@@ -1009,7 +1041,7 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
     __shared__ double2 s_c[2][CB], s_d[2][CB], s_P[CB], s_Q[CB];
     __shared__ double s_Ai;
     const int tid = threadIdx.x, bs = blockDim.x;
-    const int col0 = blockIdx.x * CB;
+    const int col0 = bid * CB;
     const double Hbar = kp.Hbar;
     double2* const spd = static_cast<double2*>(kp.spec);
 
@@ -1330,7 +1362,13 @@ __global__ void __launch_bounds__(kColThreads) k_column(KP kp) {
         }
     }
     const double g = block_sum(tid < CB ? s_gauge[tid] : 0.0);
-    if (tid == 0) kp.part_gauge_far[blockIdx.x] = g;
+    if (tid == 0) kp.part_gauge_far[bid] = g;
+}
+template <int CB>
+__global__ void __launch_bounds__(32 * CB) k_column(KP kp) { column_body<CB>(kp, blockIdx.x); }
+__global__ void __launch_bounds__(kColThreads) k_column_batch(const __grid_constant__ ColBatch b) {
+    const int s = batch_system(b.starts, b.nsys, blockIdx.x);
+    column_body<kColBlock>(b.kp[s], blockIdx.x - b.starts[s]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1365,7 +1403,7 @@ __device__ void block_sums(const double (&v)[V], double* out) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kZeroThreads) k_column_zero(KP kp) {
+__device__ __forceinline__ void column_zero_body(const KP& kp) {
     __shared__ double s_v[2][kMaxNz];   // node values, split into S_a / D_a
     __shared__ double s_y[2][kMaxNz];   // F = y'' (k = 0), then y
     __shared__ double s_p[2][kMaxNz];   // y'
@@ -1477,6 +1515,7 @@ __global__ void __launch_bounds__(kZeroThreads) k_column_zero(KP kp) {
         }
     }
 }
+__global__ void __launch_bounds__(kZeroThreads) k_column_zero(KP kp) { column_zero_body(kp); }
 
 // ---------------------------------------------------------------------------
 // The boundary-condition correction of one mode in double (Sec. 4.3.3): from
@@ -1494,7 +1533,7 @@ struct BcCoef {
 };
 
 __device__ __forceinline__ BcCoef bc_correction(const KP& kp, int col, const float* v) {
-    const double4 t = kp.mtab[col];
+    const double4_32a t = kp.mtab[col];
     const double dz = 2.0 / kp.Hbar;
     double2 mpb = make_double2(fma(-kp.tb, double(v[8]), double(v[0])), fma(-kp.tb, double(v[9]), double(v[1])));
     double2 meb = make_double2(fma(-kp.rtb, double(v[10]), double(v[2])) * dz,
@@ -1532,9 +1571,9 @@ __device__ __forceinline__ double mode_k(const KP& kp, int col, double& mult) {
 // evaluates the correction at the nodes from kp.colp). Also this
 // correction's part of the gauge sum, per block.
 constexpr int kCorrThreads = 256;
-__global__ void __launch_bounds__(kCorrThreads) k_bc_correction(KP kp) {
+__device__ __forceinline__ void bc_correction_body(const KP& kp, const int bid) {
     const int M = kp.ny * kp.nxh;
-    const int col = blockIdx.x * kCorrThreads + threadIdx.x;
+    const int col = bid * kCorrThreads + threadIdx.x;
     double g = 0.0;
     if (col < M) {
         double mult;
@@ -1552,7 +1591,12 @@ __global__ void __launch_bounds__(kCorrThreads) k_bc_correction(KP kp) {
         kp.colp[col] = cp;
     }
     g = block_sum(g);
-    if (threadIdx.x == 0) kp.part_gauge_corr[blockIdx.x] = g;
+    if (threadIdx.x == 0) kp.part_gauge_corr[bid] = g;
+}
+__global__ void __launch_bounds__(kCorrThreads) k_bc_correction(KP kp) { bc_correction_body(kp, blockIdx.x); }
+__global__ void __launch_bounds__(kCorrThreads) k_bc_correction_batch(const __grid_constant__ ColBatch b) {
+    const int s = batch_system(b.corr_starts, b.nsys, blockIdx.x);
+    bc_correction_body(b.kp[s], blockIdx.x - b.corr_starts[s]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1572,10 +1616,9 @@ constexpr int kColThreadsM = 32 * kColBlockM;
 // (k_zgemm); it then reads the coefficients of both densities and writes
 // the coefficients of psi_i and dpsi_i/dz and each mode's correction
 // parameters, instead of transforming itself.
-template <bool kTensor>
-__global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(KP kp) {
+template <bool kTensor, int CB>
+__device__ __forceinline__ void column_mixed_body(const KP& kp, const int bid) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    constexpr int CB = kColBlockM;
     const int N = kp.nz;
     // padded column stride, NP = 2 mod 16: eight modes x two rows of float2
     // (the mode-major loads and stores) then fall in distinct banks
@@ -1594,7 +1637,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
     __shared__ float2 s_c[2][CB], s_d[2][CB], s_P[CB], s_Q[CB];
     __shared__ double s_Ai;
     const int tid = threadIdx.x, bs = blockDim.x;
-    const int col0 = blockIdx.x * CB;
+    const int col0 = bid * CB;
     float2* const sp = static_cast<float2*>(kp.spec);
 
     if (tid < CB) {
@@ -1611,7 +1654,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
         s_gauge[c] = 0.0;
     }
     // the k = 0 slope, from k_column_zero (block 0 holds column 0)
-    if (tid == 0) s_Ai = blockIdx.x == 0 ? kp.scal[1] : 0.0;
+    if (tid == 0) s_Ai = bid == 0 ? kp.scal[1] : 0.0;
     const float scale = kp.f.scale;
     // every load of a batch is issued before the first store: one memory
     // round trip per batch instead of one per row group
@@ -1692,6 +1735,8 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
     // both directions (per-lane start, step and coefficient roles). The
     // 4 CB lanes of warp 0: (mode c, chain ch, side).
     static_assert(4 * CB <= 32, "the two-way sweeps run in one warp");
+    // the lanes of warp 0 that take part (all of it for 8 modes per block)
+    constexpr unsigned kSweepLanes = 4 * CB == 32 ? 0xffffffffu : (1u << (4 * CB)) - 1u;
     if (tid < 4 * CB) {
         const int c = tid >> 2, ch = (tid >> 1) & 1, side = tid & 1;
         const float K2 = s_K[c] * s_K[c];
@@ -1731,7 +1776,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
                 xc[n] = xcp;
             }
         }
-        __syncwarp();
+        __syncwarp(kSweepLanes);
         if (side == 1 && m > 0) {
             // rows m-1 (y + c' y_m = f') and m (a'' y_{m-1} + y = f'')
             const int nA = ch + 2 * (m - 1), nB = ch + 2 * m;
@@ -1747,7 +1792,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
             Fo[nB] = yBo;
             xc[nB] = yBx;
         }
-        __syncwarp();
+        __syncwarp(kSweepLanes);
         // substitute outward from the interface: side 0 rows m-2 .. 0,
         // side 1 rows m+1 .. L-1
         const int bcnt = side ? L - m - 1 : m - 1, b0 = side ? m + 1 : m - 2, bdi = -di;
@@ -1818,7 +1863,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
     }
     // from here to the boundary values warp w works on mode w alone, so
     // warp barriers suffice
-    static_assert(kColThreadsM == 32 * CB, "one warp per mode of the block");
+    // (blocks of 32 CB threads: one warp per mode of the block)
     __syncwarp();
     // both fields of the warp's mode, n over the lanes: X += (c or d) xe
     // gives y'', then y' = J y'' + d e0 and y = J y' + c e0 (Appendix A
@@ -1901,7 +1946,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
         }
     }
     __syncthreads();
-    if (blockIdx.x == 0) {
+    if (bid == 0) {
         // column 0: the coefficients of psi_i and dpsi_i/dz solved in double
         for (int n = tid; n < N; n += bs) {
             Ci[n] = make_float2(float(kp.zcol[n]), 0.f);
@@ -1921,7 +1966,7 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
         if (tid == 0) {
             double g = 0.0;
             for (int c = 0; c < CB; ++c) g += s_gauge[c];
-            kp.part_gauge_far[blockIdx.x] = g;
+            kp.part_gauge_far[bid] = g;
         }
         return;
     }
@@ -1996,8 +2041,17 @@ __global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed(
     if (tid == 0) {
         double g = 0.0;
         for (int c = 0; c < CB; ++c) g += s_gauge[c];
-        kp.part_gauge_far[blockIdx.x] = g;
+        kp.part_gauge_far[bid] = g;
     }
+}
+template <bool kTensor, int CB>
+__global__ void __launch_bounds__(32 * CB, (kTensor ? 40 : 32) / CB) k_column_mixed(KP kp) {
+    column_mixed_body<kTensor, CB>(kp, blockIdx.x);
+}
+template <bool kTensor>
+__global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed_batch(const __grid_constant__ ColBatch b) {
+    const int s = batch_system(b.starts, b.nsys, blockIdx.x);
+    column_mixed_body<kTensor, kColBlockM>(b.kp[s], blockIdx.x - b.starts[s]);
 }
 
 // ---------------------------------------------------------------------------
@@ -2247,14 +2301,14 @@ __global__ void k_interp(KP kp) {
 // it (the support of the charge's own source). Each lane takes (x, y)
 // columns of the support and walks down z with one pointer step per node,
 // all in float; node distances use z and z_j as float pairs (~1e-7).
-__global__ void __launch_bounds__(32 * kInterpWarps) k_interp_f32(KP kp) {
+__global__ void __launch_bounds__(32 * kMaxInterpWarps) k_interp_f32(KP kp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float* smi = reinterpret_cast<float*>(smraw);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* wx = smi + w * (2 * kMaxSupport + kMaxNz);
     float* wy = wx + kMaxSupport;
     float* wzz = wy + kMaxSupport;
-    const int slot = blockIdx.x * kInterpWarps + w;
+    const int slot = blockIdx.x * (blockDim.x >> 5) + w;
     if (slot >= kp.n) return;
     const int k = kp.near_on ? kp.sorted_idx[slot] : slot;
     const IRec r = kp.irec[k];
@@ -2800,6 +2854,9 @@ struct dpslab_plan {
     int nxh = 0;
     size_t G = 0, S = 0;
     int px_fwd = 1, tk_fwd = 1, tk_inv = 1, px_inv = 1;
+    int interp_warps = kInterpWarps;   // warps (charges) per block of the interpolation
+    int col_cb = 0;                    // modes per block of the column kernel
+    int spread_cpt = 1;                // x columns per thread of the mixed spreading
     int p2x = 0, p2y = 0, lognx = 0, logny = 0;        // power-of-two FFT kernels in x, y
     bool ztensor = false;                              // z transforms as tensor-core GEMMs
     int zgrid = 0;                                     // persistent CTAs of the z GEMMs
@@ -2890,6 +2947,24 @@ int floor_pow2(int v) {
     return p;
 }
 
+// Column kernels by modes per block (launch-shape knob): FP64 2 or 4, mixed 4 or 8.
+constexpr int kMinColBlock = 4;         // smallest mixed block; the FP64 one is half of it
+using ColKernel = void (*)(KP);
+ColKernel column_mixed_kernel(bool tensor, int cb) {
+    if (cb == 4) return tensor ? k_column_mixed<true, 4> : k_column_mixed<false, 4>;
+    return tensor ? k_column_mixed<true, 8> : k_column_mixed<false, 8>;
+}
+ColKernel column_kernel(int cb) { return cb == 2 ? k_column<2> : k_column<4>; }
+// dynamic shared memory of the column kernel with cb modes per block
+size_t col_smem(const dpslab_plan* pl, int cb) {
+    const int nz = pl->kp.nz;
+    const bool mixed = pl->kp.mixed != 0;
+    const size_t rsz = mixed ? sizeof(float) : sizeof(double), csz = 2 * rsz;
+    return size_t(cb) * (nz + (mixed ? ((2 - nz) & 15) : 0)) * (4 * csz + 2 * rsz);
+}
+using SpreadKernel = void (*)(KP);
+SpreadKernel spread_mixed_kernel(int cpt) { return cpt == 1 ? k_spread_f32<1> : k_spread_f32<2>; }
+
 // Carve the plan's workspace from base (every per-solve device array: grids,
 // charge arrays, buckets, cell list, partial sums); with base == nullptr it
 // only measures. Returns the bytes used.
@@ -2924,7 +2999,9 @@ size_t bind_work(dpslab_plan* pl, char* base) {
     kp.cell_start = carve<int>(cur, size_t(kp.ncells) + 1);
     kp.cell_fill = carve<int>(cur, size_t(kp.ncells) + 1);
     carve<int>(cur, size_t(kp.ncells));
-    kp.part_gauge_far = carve<double>(cur, kp.n_col_blocks);
+    // one per column block, for the smallest block the autotuner may choose
+    // (kMinColBlock / 2 modes: the FP64 kernel's smaller shape)
+    kp.part_gauge_far = carve<double>(cur, (M + kMinColBlock / 2 - 1) / (kMinColBlock / 2));
     kp.part_gauge_near = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
     kp.part_u = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
     kp.part_q = carve<double>(cur, 2 * size_t(kp.n_charge_blocks));
@@ -3124,7 +3201,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         bytes += 3 * align_up(N * N * sizeof(float)) + 14 * align_up(N * sizeof(float));
         if (pl->ztensor) bytes += 2 * align_up(t.zimg_fwd.size() * sizeof(unsigned short));   // bf16 images
         bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
-        if (mixed) bytes += align_up(size_t(M) * sizeof(double4));   // per-mode correction factors
+        if (mixed) bytes += align_up(size_t(M) * sizeof(double4_32a));   // per-mode correction factors
         pl->device_bytes += int64_t(bytes);   // table bytes, taken up again below
     }
     if (!measure) {
@@ -3196,7 +3273,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             // -(1 - Gt e^{-2kH})/den, den = 1 - Gb Gt e^{-2kH}; both
             // differences from 1 are formed as (1 - G) - G expm1(-2kH), which
             // does not cancel as k -> 0 with G -> 1 (metal walls, small eps_w)
-            std::vector<double4> mt(static_cast<size_t>(M));
+            std::vector<double4_32a> mt(static_cast<size_t>(M));
             const long double Gb = kp.Gb, Gt = kp.Gt, H = p->H;
             for (int col = 0; col < M; ++col) {
                 const int iy = col / kp.nxh, ix = col - iy * kp.nxh;
@@ -3205,16 +3282,16 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
                 const long double ky = 2.0L * 3.141592653589793238462643383279503L * my / p->Ly;
                 const long double k = sqrtl(kx * kx + ky * ky);
                 if (k == 0.0L) {
-                    mt[col] = make_double4(0.0, 0.0, 0.0, 0.0);
+                    mt[col] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
                     continue;
                 }
                 const long double e = expl(-k * H), em = expm1l(-2.0L * k * H);
                 const long double den = (1.0L - Gb * Gt) - Gb * Gt * em;
                 const long double ct = (1.0L - Gt) - Gt * em;
-                mt[col] = make_double4(double(1.0L / k), double(e), double(1.0L / den), double(-ct / den));
+                mt[col] = make_double4_32a(double(1.0L / k), double(e), double(1.0L / den), double(-ct / den));
             }
-            double4* dp = carve<double4>(cur, mt.size());
-            cudaMemcpy(dp, mt.data(), mt.size() * sizeof(double4), cudaMemcpyHostToDevice);
+            double4_32a* dp = carve<double4_32a>(cur, mt.size());
+            cudaMemcpy(dp, mt.data(), mt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice);
             kp.mtab = dp;
         }
         if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
@@ -3328,8 +3405,10 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             }
         }
     }
-    pl->sm_col = size_t(col_block) * (nz + (mixed ? ((2 - nz) & 15) : 0)) * (4 * csz + 2 * rsz);
-    pl->sm_interp = size_t(kInterpWarps) * (2 * kMaxSupport + kMaxNz) * rsz;
+    pl->col_cb = col_block;
+    pl->spread_cpt = mixed ? kSpreadCptM : 1;
+    pl->sm_col = col_smem(pl, col_block);
+    pl->sm_interp = size_t(pl->interp_warps) * (2 * kMaxSupport + kMaxNz) * rsz;
     pl->sm_spread = (2 * size_t(kp.slab) * kTile * kTile +
                      size_t(kSpreadBatch) * (((kp.supx + 31) & ~31) + ((kp.supy + 31) & ~31) + kp.slab)) * rsz;
     const size_t smax = 227 * 1024;
@@ -3359,9 +3438,12 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             const int ntiles = 2 * int((2 * size_t(M) + kZN - 1) / kZN);   // both planes
             pl->zgrid = std::max(1, std::min(ntiles, nsm));
         }
-        raise_smem(reinterpret_cast<const void*>(k_column_mixed<false>), size_t(pl->sm_col));
-        raise_smem(reinterpret_cast<const void*>(k_column_mixed<true>), size_t(pl->sm_col));
-        raise_smem(reinterpret_cast<const void*>(k_interp_f32), size_t(pl->sm_interp));
+        for (int cb = kMinColBlock; cb <= kColBlockM; cb *= 2) {
+            raise_smem(reinterpret_cast<const void*>(column_mixed_kernel(false, cb)), col_smem(pl, cb));
+            raise_smem(reinterpret_cast<const void*>(column_mixed_kernel(true, cb)), col_smem(pl, cb));
+        }
+        raise_smem(reinterpret_cast<const void*>(k_interp_f32),
+                   size_t(kMaxInterpWarps) * (2 * kMaxSupport + kMaxNz) * sizeof(float));
     } else {
         if (pl->p2x) {
             raise_smem(reinterpret_cast<const void*>(fft_p2<double>(0, pl->lognx)), size_t(pl->sm_fftx_fwd));
@@ -3375,7 +3457,8 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         raise_smem(reinterpret_cast<const void*>(k_ffty_fwd<double>), size_t(pl->sm_ffty_fwd));
         raise_smem(reinterpret_cast<const void*>(k_ffty_inv<double>), size_t(pl->sm_ffty_inv));
         raise_smem(reinterpret_cast<const void*>(k_fftx_inv<double>), size_t(pl->sm_fftx_inv));
-        raise_smem(reinterpret_cast<const void*>(k_column), size_t(pl->sm_col));
+        for (int cb = kMinColBlock / 2; cb <= kColBlock; cb *= 2)
+            raise_smem(reinterpret_cast<const void*>(column_kernel(cb)), col_smem(pl, cb));
         raise_smem(reinterpret_cast<const void*>(k_interp<double>), size_t(pl->sm_interp));
         raise_smem(reinterpret_cast<const void*>(k_spread_tiled<double>), size_t(pl->sm_spread));
     }
@@ -3520,8 +3603,12 @@ extern "C" int dpslab_plan_set_wall_charge(dpslab_plan* plan, const double* sigm
 // Brownian dynamics, Sec. 7.1: Eq. (leimkuhler), (steric), (lj)
 // ---------------------------------------------------------------------------
 namespace {
+// Which part of a solve enqueue() issues: all of it, or (for batches, whose
+// column stage is one launch over several systems) the part before the
+// column stage or the part after it.
+enum SolvePart { kSolveAll = 0, kSolveFront = 1, kSolveBack = 2 };
 int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, double* phi, double* force,
-            cudaStream_t st);
+            cudaStream_t st, SolvePart part = kSolveAll);
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;   // Philox4x32 multipliers
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;   // key increments
 
@@ -3802,16 +3889,56 @@ extern "C" int dpslab_stage_times(const dpslab_plan* plan, double* ms, int n) {
 // ---------------------------------------------------------------------------
 namespace {
 int finish(dpslab_plan* pl, cudaStream_t st, double* U);
-constexpr int kKnobs = 4;                 // x forward, y forward, y inverse, x inverse
-constexpr int kKnobStage[kKnobs] = {2, 3, 7, 8};
+// x forward, y forward, y inverse, x inverse transforms; interpolation;
+// column kernel; spreading (DPSLAB_NKNOBS)
+constexpr int kKnobs = DPSLAB_NKNOBS;
+constexpr int kKnobStage[kKnobs] = {2, 3, 7, 8, 9, 5, 1};
 
 int* shape_knob(dpslab_plan* pl, int which) {
     switch (which) {
         case 0: return &pl->px_fwd;
         case 1: return &pl->tk_fwd;
         case 2: return &pl->tk_inv;
-        default: return &pl->px_inv;
+        case 3: return &pl->px_inv;
+        case 4: return &pl->interp_warps;
+        case 5: return &pl->col_cb;
+        default: return &pl->spread_cpt;
     }
+}
+
+// knobs 4-6: warps per block of the interpolation (1, 2, 4, 8), modes per
+// block of the column kernel (mixed 4 or 8, FP64 2 or 4), x columns per
+// thread of the mixed spreading (1 or 2; FP64 1)
+bool apply_kernel_knob(dpslab_plan* pl, int which, int v) {
+    const bool mixed = pl->kp.mixed != 0;
+    const size_t rsz = mixed ? sizeof(float) : sizeof(double);
+    if (which == 4) {
+        if (v != 1 && v != 2 && v != 4 && v != kMaxInterpWarps) return false;
+        const size_t sm = size_t(v) * (2 * kMaxSupport + kMaxNz) * rsz;
+        if (!mixed) {
+            raise_smem(reinterpret_cast<const void*>(k_interp<double>), sm);
+            raise_smem(reinterpret_cast<const void*>(k_wall_cross<double>), sm);
+        } else {
+            raise_smem(reinterpret_cast<const void*>(k_wall_cross<float>), sm);
+        }
+        pl->interp_warps = v;
+        pl->sm_interp = sm;
+        return true;
+    }
+    if (which == 5) {
+        const int lo = mixed ? kMinColBlock : kMinColBlock / 2, hi = mixed ? kColBlockM : kColBlock;
+        if (v != lo && v != hi) return false;
+        const size_t sm = col_smem(pl, v);
+        if (sm > 227 * 1024) return false;
+        const int M = pl->kp.ny * pl->kp.nxh;
+        pl->col_cb = v;
+        pl->sm_col = sm;
+        pl->kp.n_col_blocks = (M + v - 1) / v;
+        return true;
+    }
+    if (v != 1 && !(mixed && v == 2)) return false;
+    pl->spread_cpt = v;
+    return true;
 }
 
 // set knob `which` to v sequences per block, with its block size and shared
@@ -3859,25 +3986,23 @@ bool apply_shape_t(dpslab_plan* pl, int which, int v) {
 }
 
 bool apply_shape(dpslab_plan* pl, int which, int v) {
+    if (which >= 4) return apply_kernel_knob(pl, which, v);
     return pl->kp.mixed ? apply_shape_t<float>(pl, which, v) : apply_shape_t<double>(pl, which, v);
 }
 }  // namespace
 
 extern "C" int dpslab_plan_tuning(const dpslab_plan* plan, int* knobs, int n) {
-    if (!plan || !knobs || n < kKnobs) return DPSLAB_ERR_INVALID_ARG;
-    knobs[0] = plan->px_fwd;
-    knobs[1] = plan->tk_fwd;
-    knobs[2] = plan->tk_inv;
-    knobs[3] = plan->px_inv;
+    if (!plan || !knobs || n < 4) return DPSLAB_ERR_INVALID_ARG;
+    for (int i = 0; i < std::min(n, kKnobs); ++i) knobs[i] = *shape_knob(const_cast<dpslab_plan*>(plan), i);
     return DPSLAB_OK;
 }
 
 extern "C" int dpslab_plan_set_tuning(dpslab_plan* plan, const int* knobs, int n) {
-    if (!plan || !knobs || n < kKnobs || plan->in_flight) return DPSLAB_ERR_INVALID_ARG;
+    if (!plan || !knobs || n < 4 || plan->in_flight) return DPSLAB_ERR_INVALID_ARG;
     DPS_CUDA(cudaSetDevice(plan->device));
     int old[kKnobs];
     dpslab_plan_tuning(plan, old, kKnobs);
-    for (int i = 0; i < kKnobs; ++i) {
+    for (int i = 0; i < std::min(n, kKnobs); ++i) {
         if (!apply_shape(plan, i, knobs[i])) {
             for (int j = 0; j < i; ++j) apply_shape(plan, j, old[j]);
             return DPSLAB_ERR_INVALID_ARG;
@@ -3959,7 +4084,7 @@ extern "C" const char* dpslab_strerror(int code) {
 namespace {
 
 int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, double* phi, double* force,
-            cudaStream_t st) {
+            cudaStream_t st, SolvePart part) {
     KP kp = pl->kp;
     const int n = int(n64);
     kp.n = n;
@@ -3969,8 +4094,9 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     kp.out_force = force;
     const int nb = (n + kChargeThreads - 1) / kChargeThreads;
     kp.n_charge_blocks = nb;
-    int launches = 0;
+    int launches = part == kSolveBack ? pl->launches : 0;
     const bool prof = pl->profiling != 0;
+    const bool front = part != kSolveBack, back = part != kSolveFront, column = part == kSolveAll;
     auto mark = [&](int i) {
         if (prof) cudaEventRecord(pl->ev[i], st);
     };
@@ -3999,6 +4125,8 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         if (const int e_ = scan(c, s_, m)) return e_; \
     } while (0)
 
+    const bool fork = kp.near_on && pl->profiling != 2;
+    if (front) {
     DPS_CUDA(cudaMemsetAsync(kp.status, 0, sizeof(int), st));
     DPS_CUDA(cudaMemsetAsync(kp.tile_count, 0, (size_t(kp.nbuckets) + 1) * sizeof(int), st));
     DPS_CUDA(cudaMemsetAsync(kp.tile_fill, 0, (size_t(kp.nbuckets) + 1) * sizeof(int), st));
@@ -4018,7 +4146,6 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     // this stream waits for it before the assembly. Profiling mode 1 keeps
     // that and times the near field by its own events on the second stream;
     // mode 2 runs it in line, so that the stage times add up to the solve.
-    const bool fork = kp.near_on && pl->profiling != 2;
     pl->near_timed = fork && prof;
     if (fork) {
         DPS_CUDA(cudaEventRecord(pl->ev_fork, st));
@@ -4034,7 +4161,7 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         LAUNCH(k_sources_f<<<nb, kChargeThreads, 0, st>>>(kp));
         SCAN(kp.tile_count, kp.tile_start, kp.nbuckets);
         LAUNCH(k_scatter_sources_f<<<nb, kChargeThreads, 0, st>>>(kp));
-        LAUNCH(k_spread_f32<<<gs, kSpreadThreadsM, 0, st>>>(kp));
+        LAUNCH(spread_mixed_kernel(pl->spread_cpt)<<<gs, kTile * kTile / pl->spread_cpt, 0, st>>>(kp));
     } else {
         LAUNCH(k_count_sources<<<nb, kChargeThreads, 0, st>>>(kp));
         SCAN(kp.tile_count, kp.tile_start, kp.nbuckets);
@@ -4042,13 +4169,15 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         LAUNCH(k_spread_tiled<double><<<gs, kTile * kTile, pl->sm_spread, st>>>(kp));
     }
     mark(2);
+    }
     const int npairs = kp.nz * kp.ny;
     const dim3 gy_fwd((kp.nxh + pl->tk_fwd - 1) / pl->tk_fwd, 2 * kp.nz);
     const dim3 gy_inv((kp.nxh + pl->tk_inv - 1) / pl->tk_inv, kp.nz);
     const int gx_fwd = (npairs + pl->px_fwd - 1) / pl->px_fwd;
     const int gx_inv = (kp.nz * kp.ny + pl->px_inv - 1) / pl->px_inv;
-    const int gi = (n + kInterpWarps - 1) / kInterpWarps;
+    const int iw = pl->interp_warps, gi = (n + iw - 1) / iw;
     if (kp.mixed) {
+        if (front) {
         if (pl->p2x) LAUNCH(fft_p2<float>(0, pl->lognx)<<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
         else LAUNCH(k_fftx_fwd<float><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
         mark(3);
@@ -4056,18 +4185,16 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         else LAUNCH(k_ffty_fwd<float><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
         mark(4);
         LAUNCH(k_column_zero<<<1, kZeroThreads, 0, st>>>(kp));
-        if (pl->ztensor) {
-            LAUNCH(k_zgemm_fwd<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
-            mark(5);
-            LAUNCH(k_column_mixed<true><<<kp.n_col_blocks, kColThreadsM, pl->sm_col, st>>>(kp));
-            LAUNCH(k_bc_correction<<<kp.n_corr_blocks, kCorrThreads, 0, st>>>(kp));
-            mark(6);
-            LAUNCH(k_zgemm_inv<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
-        } else {
-            mark(5);
-            LAUNCH(k_column_mixed<false><<<kp.n_col_blocks, kColThreadsM, pl->sm_col, st>>>(kp));
-            mark(6);
+        if (pl->ztensor) LAUNCH(k_zgemm_fwd<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
+        mark(5);
         }
+        if (column) {
+        LAUNCH(column_mixed_kernel(pl->ztensor, pl->col_cb)<<<kp.n_col_blocks, 32 * pl->col_cb, pl->sm_col, st>>>(kp));
+        if (pl->ztensor) LAUNCH(k_bc_correction<<<kp.n_corr_blocks, kCorrThreads, 0, st>>>(kp));
+        }
+        if (back) {
+        mark(6);
+        if (pl->ztensor) LAUNCH(k_zgemm_inv<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
         mark(7);
         if (pl->p2y) LAUNCH(fft_p2<float>(2, pl->logny)<<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
         else LAUNCH(k_ffty_inv<float><<<gy_inv, 256, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv));
@@ -4075,9 +4202,11 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         if (pl->p2x) LAUNCH(fft_p2<float>(3, pl->lognx)<<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
         else LAUNCH(k_fftx_inv<float><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(9);
-        LAUNCH(k_interp_f32<<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
-        if (kp.sigma_on) LAUNCH(k_wall_cross<float><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
+        LAUNCH(k_interp_f32<<<gi, 32 * iw, pl->sm_interp, st>>>(kp));
+        if (kp.sigma_on) LAUNCH(k_wall_cross<float><<<gi, 32 * iw, pl->sm_interp, st>>>(kp));
+        }
     } else {
+        if (front) {
         if (pl->p2x) LAUNCH(fft_p2<double>(0, pl->lognx)<<<gx_fwd, pl->thr_x_fwd, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd, pl->lognx));
         else LAUNCH(k_fftx_fwd<double><<<gx_fwd, 256, pl->sm_fftx_fwd, st>>>(kp, pl->px_fwd));
         mark(3);
@@ -4085,7 +4214,9 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         else LAUNCH(k_ffty_fwd<double><<<gy_fwd, 256, pl->sm_ffty_fwd, st>>>(kp, pl->tk_fwd));
         mark(4);
         mark(5);
-        LAUNCH(k_column<<<kp.n_col_blocks, kColThreads, pl->sm_col, st>>>(kp));
+        }
+        if (column) LAUNCH(column_kernel(pl->col_cb)<<<kp.n_col_blocks, 32 * pl->col_cb, pl->sm_col, st>>>(kp));
+        if (back) {
         mark(6);
         mark(7);
         if (pl->p2y) LAUNCH(fft_p2<double>(2, pl->logny)<<<gy_inv, pl->thr_y_inv, pl->sm_ffty_inv, st>>>(kp, pl->tk_inv, pl->logny));
@@ -4094,8 +4225,13 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         if (pl->p2x) LAUNCH(fft_p2<double>(3, pl->lognx)<<<gx_inv, pl->thr_x_inv, pl->sm_fftx_inv, st>>>(kp, pl->px_inv, pl->lognx));
         else LAUNCH(k_fftx_inv<double><<<gx_inv, 256, pl->sm_fftx_inv, st>>>(kp, pl->px_inv));
         mark(9);
-        LAUNCH(k_interp<double><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
-        if (kp.sigma_on) LAUNCH(k_wall_cross<double><<<gi, 32 * kInterpWarps, pl->sm_interp, st>>>(kp));
+        LAUNCH(k_interp<double><<<gi, 32 * iw, pl->sm_interp, st>>>(kp));
+        if (kp.sigma_on) LAUNCH(k_wall_cross<double><<<gi, 32 * iw, pl->sm_interp, st>>>(kp));
+        }
+    }
+    if (!back) {
+        pl->launches = launches;
+        return DPSLAB_OK;
     }
     mark(10);
     if (kp.near_on && !fork) {
@@ -4381,7 +4517,20 @@ struct dpslab_batch {
     cudaGraphExec_t exec = nullptr;
     std::vector<int64_t> g_n;              // arguments the graph was captured with
     std::vector<const void*> g_ptr;
+    int g_schedule = -1;
     int64_t device_bytes = 0;
+    // The column stage (per-mode BVP and correction) of the systems of one
+    // wave (the systems that have workspaces of their own: one per stream)
+    // runs as one launch per kind of column kernel over all their k modes.
+    struct ColGroup {
+        int kind = 0;                      // 0 FP64, 1 mixed CUDA-core z transforms, 2 mixed tensor-core
+        int blocks = 0, corr_blocks = 0;
+        size_t smem = 0;
+        std::shared_ptr<ColBatch> arg;     // the launch's parameter: up to kBatchMaxSys systems
+    };
+    std::vector<std::vector<ColGroup>> waves;
+    int launches = 0;                      // kernels of the last batch solve
+    int schedule = DPSLAB_BATCH_STREAMS;   // DPSLAB_BATCH_STREAMS or DPSLAB_BATCH_WAVES
 };
 
 namespace {
@@ -4433,6 +4582,39 @@ extern "C" int dpslab_batch_create(const dpslab_params* params, const int64_t* m
         if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { batch_release(b); return DPSLAB_ERR_CUDA; }
         b->joins.push_back(ev);
     }
+    // column groups: per wave of S systems, per kind of column kernel, one
+    // launch per kBatchMaxSys systems
+    b->waves.assign((count + S - 1) / S, {});
+    for (int w0 = 0; w0 < count; w0 += S) {
+        std::vector<int> sys[3];
+        for (int i = w0; i < std::min(count, w0 + S); ++i) {
+            const dpslab_plan* pl = b->plans[i];
+            sys[!pl->kp.mixed ? 0 : (pl->ztensor ? 2 : 1)].push_back(i);
+        }
+        for (int kind = 0; kind < 3; ++kind) {
+            for (size_t c0 = 0; c0 < sys[kind].size(); c0 += kBatchMaxSys) {
+                dpslab_batch::ColGroup cg;
+                cg.kind = kind;
+                cg.arg = std::make_shared<ColBatch>();
+                ColBatch& a = *cg.arg;
+                std::memset(static_cast<void*>(&a), 0, sizeof(ColBatch));
+                a.nsys = int(std::min<size_t>(kBatchMaxSys, sys[kind].size() - c0));
+                for (int j = 0; j < a.nsys; ++j) {
+                    const dpslab_plan* pl = b->plans[sys[kind][c0 + j]];
+                    std::memcpy(static_cast<void*>(&a.kp[j]), &pl->kp, sizeof(KP));
+                    a.starts[j + 1] = a.starts[j] + pl->kp.n_col_blocks;
+                    a.corr_starts[j + 1] = a.corr_starts[j] + pl->kp.n_corr_blocks;
+                    cg.smem = std::max(cg.smem, pl->sm_col);
+                }
+                cg.blocks = a.starts[a.nsys];
+                cg.corr_blocks = a.corr_starts[a.nsys];
+                if (kind == 0) raise_smem(reinterpret_cast<const void*>(k_column_batch), cg.smem);
+                if (kind == 1) raise_smem(reinterpret_cast<const void*>(k_column_mixed_batch<false>), cg.smem);
+                if (kind == 2) raise_smem(reinterpret_cast<const void*>(k_column_mixed_batch<true>), cg.smem);
+                b->waves[w0 / S].push_back(std::move(cg));
+            }
+        }
+    }
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->out, cudaEventDisableTiming) != cudaSuccess ||
@@ -4464,7 +4646,7 @@ extern "C" int dpslab_batch_solve(dpslab_batch* b, const int64_t* n, const doubl
     DPS_CUDA(cudaEventRecord(b->in, caller));
     DPS_CUDA(cudaStreamWaitEvent(st, b->in, 0));
     const bool same = b->exec && b->g_ptr == ptr && int(b->g_n.size()) == count &&
-                      std::equal(b->g_n.begin(), b->g_n.end(), n);
+                      std::equal(b->g_n.begin(), b->g_n.end(), n) && b->g_schedule == b->schedule;
     if (!same) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);
@@ -4472,20 +4654,70 @@ extern "C" int dpslab_batch_solve(dpslab_batch* b, const int64_t* n, const doubl
         b->graph = nullptr;
         DPS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         int rc = DPSLAB_OK;
-        if (cudaEventRecord(b->fork, st) != cudaSuccess) rc = DPSLAB_ERR_CUDA;
-        for (int s = 0; s < S && !rc; ++s)
-            if (cudaStreamWaitEvent(b->streams[s], b->fork, 0) != cudaSuccess) rc = DPSLAB_ERR_CUDA;
-        for (int i = 0; i < count && !rc; ++i) {
-            dpslab_plan* pl = b->plans[i];
-            pl->profiling = 0;
-            rc = enqueue(pl, n[i], pos[i], q[i], phi ? phi[i] : nullptr, force ? force[i] : nullptr, b->streams[i % S]);
-            pl->last_n = n[i];
+        int launches = 0;
+        // the streams of systems w0 .. w0 + S - 1 wait for `st`, or `st` for them
+        auto fork = [&](int w0) {
+            if (!rc && cudaEventRecord(b->fork, st) != cudaSuccess) rc = DPSLAB_ERR_CUDA;
+            for (int s = 0; s < S && !rc && w0 + s < count; ++s)
+                if (cudaStreamWaitEvent(b->streams[s], b->fork, 0) != cudaSuccess) rc = DPSLAB_ERR_CUDA;
+        };
+        auto join = [&](int w0) {
+            for (int s = 0; s < S && !rc && w0 + s < count; ++s)
+                if (cudaEventRecord(b->joins[s], b->streams[s]) != cudaSuccess ||
+                    cudaStreamWaitEvent(st, b->joins[s], 0) != cudaSuccess)
+                    rc = DPSLAB_ERR_CUDA;
+        };
+        if (b->schedule == DPSLAB_BATCH_STREAMS) {
+            // every system's whole solve on its stream; the streams run freely
+            fork(0);
+            for (int i = 0; i < count && !rc; ++i) {
+                dpslab_plan* pl = b->plans[i];
+                pl->profiling = 0;
+                rc = enqueue(pl, n[i], pos[i], q[i], phi ? phi[i] : nullptr, force ? force[i] : nullptr,
+                             b->streams[i % S], kSolveAll);
+                pl->last_n = n[i];
+                launches += pl->launches;
+            }
+            join(0);
         }
-        for (int s = 0; s < S && !rc; ++s) {
-            if (cudaEventRecord(b->joins[s], b->streams[s]) != cudaSuccess ||
-                cudaStreamWaitEvent(st, b->joins[s], 0) != cudaSuccess)
-                rc = DPSLAB_ERR_CUDA;
+        for (int w0 = 0, wave = 0; b->schedule == DPSLAB_BATCH_WAVES && w0 < count && !rc; w0 += S, ++wave) {
+            const int w1 = std::min(count, w0 + S);
+            fork(w0);
+            for (int i = w0; i < w1 && !rc; ++i) {
+                dpslab_plan* pl = b->plans[i];
+                pl->profiling = 0;
+                rc = enqueue(pl, n[i], pos[i], q[i], phi ? phi[i] : nullptr, force ? force[i] : nullptr,
+                             b->streams[i % S], kSolveFront);
+            }
+            join(w0);
+            // the wave's column stage: one launch per kind over all its systems' modes
+            for (const auto& g : b->waves[wave]) {
+                if (rc) break;
+                if (g.kind == 0) k_column_batch<<<g.blocks, kColThreads, g.smem, st>>>(*g.arg);
+                if (g.kind == 1) k_column_mixed_batch<false><<<g.blocks, kColThreadsM, g.smem, st>>>(*g.arg);
+                if (g.kind == 2) {
+                    k_column_mixed_batch<true><<<g.blocks, kColThreadsM, g.smem, st>>>(*g.arg);
+                    k_bc_correction_batch<<<g.corr_blocks, kCorrThreads, 0, st>>>(*g.arg);
+                    ++launches;
+                }
+                ++launches;
+                const cudaError_t le = cudaGetLastError();
+                if (le != cudaSuccess) {
+                    trace("batched column stage", le, __LINE__);
+                    rc = DPSLAB_ERR_CUDA;
+                }
+            }
+            fork(w0);
+            for (int i = w0; i < w1 && !rc; ++i) {
+                dpslab_plan* pl = b->plans[i];
+                rc = enqueue(pl, n[i], pos[i], q[i], phi ? phi[i] : nullptr, force ? force[i] : nullptr,
+                             b->streams[i % S], kSolveBack);
+                pl->last_n = n[i];
+                launches += pl->launches;
+            }
+            join(w0);
         }
+        b->launches = launches;
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(st, &g);
         if (e != cudaSuccess) trace("cudaStreamEndCapture", e, __LINE__);
@@ -4504,6 +4736,7 @@ extern "C" int dpslab_batch_solve(dpslab_batch* b, const int64_t* n, const doubl
         b->graph = g;
         b->g_ptr = ptr;
         b->g_n.assign(n, n + count);
+        b->g_schedule = b->schedule;
     }
     DPS_CUDA(cudaGraphLaunch(b->exec, st));
     DPS_CUDA(cudaEventRecord(b->out, st));
@@ -4520,6 +4753,55 @@ extern "C" int dpslab_batch_solve(dpslab_batch* b, const int64_t* n, const doubl
 }
 
 extern "C" int64_t dpslab_batch_device_bytes(const dpslab_batch* b) { return b ? b->device_bytes : 0; }
+
+extern "C" int dpslab_batch_last_launch_count(const dpslab_batch* b) { return b ? b->launches : 0; }
+
+extern "C" int dpslab_batch_set_schedule(dpslab_batch* b, int schedule) {
+    if (!b || (schedule != DPSLAB_BATCH_STREAMS && schedule != DPSLAB_BATCH_WAVES)) return DPSLAB_ERR_INVALID_ARG;
+    b->schedule = schedule;
+    return DPSLAB_OK;
+}
+
+extern "C" int dpslab_batch_schedule(const dpslab_batch* b) { return b ? b->schedule : DPSLAB_ERR_INVALID_ARG; }
+
+extern "C" int dpslab_batch_autotune(dpslab_batch* b, const int64_t* n, const double* const* pos,
+                                     const double* const* q, int reps, void* stream) {
+    if (!b || !n || !pos || !q || reps < 1) return DPSLAB_ERR_INVALID_ARG;
+    DPS_CUDA(cudaSetDevice(b->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DPS_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return DPSLAB_ERR_CUDA;
+    }
+    // median time of `reps` batch solves after one warm-up (which captures the graph)
+    auto time_schedule = [&](int sched, double& out) -> int {
+        b->schedule = sched;
+        std::vector<double> t;
+        for (int i = 0; i <= reps; ++i) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) return DPSLAB_ERR_CUDA;
+            const int rc = dpslab_batch_solve(b, n, pos, q, nullptr, nullptr, nullptr, nullptr, stream);
+            if (rc && rc != DPSLAB_ERR_NOT_NEUTRAL) return rc;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return DPSLAB_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (i) t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        out = t[t.size() / 2];
+        return DPSLAB_OK;
+    };
+    const int cur = b->schedule;
+    double t_cur = 0.0, t_other = 0.0;
+    const int other = cur == DPSLAB_BATCH_STREAMS ? DPSLAB_BATCH_WAVES : DPSLAB_BATCH_STREAMS;
+    int rc = time_schedule(cur, t_cur);
+    if (!rc) rc = time_schedule(other, t_other);
+    b->schedule = (!rc && t_other < 0.98 * t_cur) ? other : cur;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
 
 extern "C" int dpslab_batch_destroy(dpslab_batch* b) {
     if (!b) return DPSLAB_ERR_INVALID_ARG;

@@ -26,6 +26,8 @@ WAIT_LIMIT_DEFAULT = 1 << 26         # default polls of a bounded wait (dpslab_p
 PENDING = 1                          # DPSLAB_PENDING
 FP64, MIXED, MIXED_SIMT = 0, 1, 2   # DPSLAB_FP64, DPSLAB_MIXED, DPSLAB_MIXED_SIMT
 NSTAGES = 12
+NKNOBS = 7                           # DPSLAB_NKNOBS
+BATCH_STREAMS, BATCH_WAVES = 0, 1    # DPSLAB_BATCH_STREAMS, DPSLAB_BATCH_WAVES
 
 
 class DpslabError(RuntimeError):
@@ -99,6 +101,11 @@ def lib():
                                                   ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                   ctypes.POINTER(ctypes.c_int), vp]),
             "dpslab_batch_device_bytes": (i64, [vp]),
+            "dpslab_batch_last_launch_count": (ctypes.c_int, [vp]),
+            "dpslab_batch_set_schedule": (ctypes.c_int, [vp, ctypes.c_int]),
+            "dpslab_batch_schedule": (ctypes.c_int, [vp]),
+            "dpslab_batch_autotune": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                     ctypes.c_int, vp]),
             "dpslab_batch_destroy": (ctypes.c_int, [vp]),
             "dpslab_profile": (ctypes.c_int, [vp, ctypes.c_int]),
             "dpslab_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
@@ -222,13 +229,15 @@ class Plan:
         return self.tuning()
 
     def tuning(self):
-        k = (ctypes.c_int * 4)()
-        _check(lib().dpslab_plan_tuning(self._h, k, 4))
+        """The NKNOBS launch-shape knobs (dpslab_plan_tuning)."""
+        k = (ctypes.c_int * NKNOBS)()
+        _check(lib().dpslab_plan_tuning(self._h, k, NKNOBS))
         return list(k)
 
     def set_tuning(self, knobs):
-        k = (ctypes.c_int * 4)(*[int(v) for v in knobs])
-        _check(lib().dpslab_plan_set_tuning(self._h, k, 4))
+        """Apply 4 (FFT shapes only) or NKNOBS knobs (dpslab_plan_set_tuning)."""
+        k = (ctypes.c_int * len(knobs))(*[int(v) for v in knobs])
+        _check(lib().dpslab_plan_set_tuning(self._h, k, len(knobs)))
 
     def last_bd_retries(self):
         return lib().dpslab_bd_last_retries(self._h)
@@ -429,3 +438,26 @@ class Batch:
         if check:
             _check(rc)
         return U, status
+
+    def last_launch_count(self):
+        """Kernels launched by the last solve, over all systems."""
+        return lib().dpslab_batch_last_launch_count(self._h)
+
+    def set_schedule(self, schedule):
+        """BATCH_STREAMS or BATCH_WAVES (dpslab_batch_set_schedule)."""
+        _check(lib().dpslab_batch_set_schedule(self._h, int(schedule)))
+
+    def schedule(self):
+        return lib().dpslab_batch_schedule(self._h)
+
+    def autotune(self, pos, q, reps=3, stream=None):
+        """dpslab_batch_autotune on device inputs; returns the schedule kept."""
+        import torch
+        c = self.count
+        vp = ctypes.c_void_p
+        n = (ctypes.c_int64 * c)(*[int(t.shape[0]) for t in q])
+        P = (vp * c)(*[t.data_ptr() for t in pos])
+        Q = (vp * c)(*[t.data_ptr() for t in q])
+        st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(lib().dpslab_batch_autotune(self._h, n, P, Q, int(reps), st))
+        return self.schedule()

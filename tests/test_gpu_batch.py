@@ -40,12 +40,14 @@ def _alone(pos, q, p, prec):
     return U, phi.cpu().numpy(), f.cpu().numpy()
 
 
+@pytest.mark.parametrize("schedule", [dpslab.BATCH_STREAMS, dpslab.BATCH_WAVES], ids=["streams", "waves"])
 @pytest.mark.parametrize("prec,ftol,utol", [(dpslab.FP64, 1e-12, 1e-12), (dpslab.MIXED, TOL_MIXED_FORCE, TOL_MIXED_ENERGY)],
                          ids=["fp64", "mixed"])
-def test_batch_equals_alone_and_replays(prec, ftol, utol):
+def test_batch_equals_alone_and_replays(prec, ftol, utol, schedule):
     systems = _systems(7, 11)
     params = [dpslab.make_params(precision=prec, **p) for _, _, p in systems]
     batch = dpslab.Batch(params, [len(q) for _, q, _ in systems], nstreams=3)
+    batch.set_schedule(schedule)
     bufs = [_tensors(pos, q) for pos, q, _ in systems]
     for rnd in range(2):
         if rnd == 1:
@@ -91,3 +93,71 @@ def test_batch_shares_workspaces_by_stream():
     assert b2.device_bytes < b8.device_bytes <= one * 1.01 + 1
     b2.close()
     b8.close()
+
+
+def _column_launches(plan_params, prec):
+    """Column-stage launches of one system solved alone: the FP64 column
+    kernel; the mixed BVP kernel, plus the correction kernel when the z
+    transforms run on the tensor cores (Nz <= 256 and ny (nx/2 + 1) even)."""
+    if prec == dpslab.FP64:
+        return 1, 0
+    d = dpslab.derive(plan_params)
+    tensor = d["nz"] <= 256 and (d["ny"] * (d["nx"] // 2 + 1)) % 2 == 0
+    return (2, 2) if tensor else (1, 1)
+
+
+@pytest.mark.parametrize("prec,ftol,utol", [(dpslab.FP64, 1e-12, 1e-12), (dpslab.MIXED, TOL_MIXED_FORCE, TOL_MIXED_ENERGY)],
+                         ids=["fp64", "mixed"])
+@pytest.mark.parametrize("nstreams", [2, 9])
+def test_batch_column_stage_is_one_launch_per_wave(prec, ftol, utol, nstreams):
+    """The per-mode column stage (BVP and correction) of every system of a
+    wave runs as one launch per kind of column kernel: the batch launches
+    the per-system kernels of the systems solved alone, less their column
+    launches, plus one column launch per kind and wave. Results equal the
+    systems solved alone."""
+    systems = _systems(9, 21)
+    params = [dpslab.make_params(precision=prec, **p) for _, _, p in systems]
+    batch = dpslab.Batch(params, [len(q) for _, q, _ in systems], nstreams=nstreams)
+    batch.set_schedule(dpslab.BATCH_WAVES)
+    bufs = [_tensors(pos, q) for pos, q, _ in systems]
+    U, status = batch.solve([b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs], [b[3] for b in bufs])
+    assert (status == 0).all(), status
+    alone_launches, col_alone, kinds = 0, 0, []
+    for i, (pos, q, p) in enumerate(systems):
+        plan = dpslab.Plan(params[i], len(q))
+        pt, qt, phi, f = _tensors(pos, q)
+        U1, _ = plan.solve(pt, qt, phi, f)
+        alone_launches += plan.last_launch_count()
+        plan.close()
+        launches, kind = _column_launches(params[i], prec)
+        col_alone += launches
+        kinds.append((i // nstreams, kind, launches))
+        assert abs(U[i] - U1) <= utol * abs(U1), (i, U[i], U1)
+        assert rel_l2(bufs[i][3].cpu().numpy(), f.cpu().numpy()) <= ftol, i
+    per_wave = sum(launches for _, _, launches in set(kinds))
+    assert batch.last_launch_count() == alone_launches - col_alone + per_wave, \
+        (batch.last_launch_count(), alone_launches, col_alone, per_wave)
+    batch.close()
+
+
+def test_batch_autotune_picks_a_schedule():
+    """dpslab_batch_autotune times both schedules and keeps one; the batch
+    then still equals its systems solved alone. Unknown schedules are
+    refused."""
+    systems = _systems(5, 17)
+    params = [dpslab.make_params(precision=dpslab.MIXED, **p) for _, _, p in systems]
+    batch = dpslab.Batch(params, [len(q) for _, q, _ in systems], nstreams=5)
+    bufs = [_tensors(pos, q) for pos, q, _ in systems]
+    assert batch.schedule() == dpslab.BATCH_STREAMS
+    kept = batch.autotune([b[0] for b in bufs], [b[1] for b in bufs], reps=2)
+    assert kept in (dpslab.BATCH_STREAMS, dpslab.BATCH_WAVES) and batch.schedule() == kept
+    U, status = batch.solve([b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs], [b[3] for b in bufs])
+    assert (status == 0).all()
+    for i, (pos, q, p) in enumerate(systems):
+        U1, _, f1 = _alone(pos, q, p, dpslab.MIXED)
+        assert abs(U[i] - U1) <= TOL_MIXED_ENERGY * abs(U1)
+        assert rel_l2(bufs[i][3].cpu().numpy(), f1) <= TOL_MIXED_FORCE
+    with pytest.raises(dpslab.DpslabError):
+        batch.set_schedule(7)
+    assert batch.schedule() == kept
+    batch.close()

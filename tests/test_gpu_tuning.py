@@ -56,3 +56,39 @@ def test_autotune_keeps_results(prec, tmp_path):
     plan2 = dpslab.Plan(dpslab.make_params(precision=prec, **p), len(q))
     kn2, cached2 = tuning.tuned(plan2, pt, qt, path)
     assert cached2 and kn2 == kn and plan2.tuning() == kn
+
+
+@pytest.mark.parametrize("prec", [dpslab.FP64, dpslab.MIXED], ids=["fp64", "mixed"])
+def test_kernel_knobs_keep_results(prec):
+    """Knobs 4-6 (interpolation warps per block, column-kernel modes per
+    block, spreading columns per thread): every allowed value gives the same
+    solve; values outside the kernels' shapes are refused with nothing
+    changed."""
+    pos, q = synth.electrolyte(600, 24.0, 20.0, 1.0, 19.0, seed=31)
+    p = dict(Lx=24.0, Ly=20.0, H=20.0, gw=1.0, tol=1e-4, nx=48, ny=40, nz=37, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
+    plan = dpslab.Plan(dpslab.make_params(precision=prec, **p), len(q))
+    pt = torch.tensor(pos, dtype=torch.float64, device="cuda")
+    qt = torch.tensor(q, dtype=torch.float64, device="cuda")
+    k0 = plan.tuning()
+    assert len(k0) == dpslab.NKNOBS
+    U0, f0 = _solve(plan, pt, qt)
+    tol = 1e-12 if prec == dpslab.FP64 else 5e-6
+    cols = (4, 8) if prec == dpslab.MIXED else (2, 4)
+    cpts = (1, 2) if prec == dpslab.MIXED else (1,)
+    for w in (1, 2, 4, 8):
+        for cb in cols:
+            for cpt in cpts:
+                plan.set_tuning(k0[:4] + [w, cb, cpt])
+                assert plan.tuning()[4:] == [w, cb, cpt]
+                U1, f1 = _solve(plan, pt, qt)
+                assert abs(U1 - U0) <= tol * abs(U0) and rel_l2(f1, f0) <= tol, (w, cb, cpt)
+    plan.set_tuning(k0)
+    for bad in ([3, k0[5], k0[6]], [k0[4], 16, k0[6]], [k0[4], k0[5], 4]) + (
+            ([k0[4], k0[5], 2],) if prec == dpslab.FP64 else ()):
+        with pytest.raises(dpslab.DpslabError):
+            plan.set_tuning(k0[:4] + bad)
+        assert plan.tuning() == k0
+    # four knobs (the FFT shapes) are still accepted and leave the others
+    plan.set_tuning(k0[:4])
+    assert plan.tuning() == k0
+    plan.close()
