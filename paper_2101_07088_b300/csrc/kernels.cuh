@@ -148,10 +148,10 @@ struct KP {
     SrcF* srcs_tmp;           // [3n] sources of each charge before bucketing (mixed)
     ColP* colp;               // [ny nxh] correction parameters per mode (tensor-core z transforms)
     double* zcol;             // [2 nz + 1] mixed: the k = 0 column from k_column_zero (y, y', gauge term)
+    // J^T t0, J^T J^T t0, J^T tH, J^T J^T tH (J: Appendix-A integration,
+    // y' = J y'' + d e0, y = J y' + c e0), float: wall values from y'' directly
+    const float *jt0_32, *jjt0_32, *jtH_32, *jjtH_32;
     const double4_32a* mtab;  // [ny nxh] mixed: per mode 1/k, e^{-kH}, 1/den, -(1 - Gt e^{-2kH})/den (0 at k = 0)
-    float* bsum;              // [16][ny nxh] mixed, tensor-core form: wall values of psi_i*, psi_o* per mode
-    double* part_gauge_corr;  // [n_corr_blocks]: gauge terms of the correction (tensor-core form)
-    int n_corr_blocks;        // blocks of k_bc_correction (0 when the column kernel adds these terms itself)
     const unsigned short* zimg_fwd;   // split bf16 images of the z transforms (tensor cores)
     const unsigned short* zimg_inv;
     int* sorted_idx;

@@ -89,7 +89,6 @@ constexpr int kBatchMaxSys = 22;
 struct ColBatch {
     int nsys;
     int starts[kBatchMaxSys + 1];        // first column block of each system
-    int corr_starts[kBatchMaxSys + 1];   // first block of k_bc_correction
     KP kp[kBatchMaxSys];
 };
 static_assert(sizeof(ColBatch) <= 32000, "kernel parameters are limited to 32 KB");
@@ -622,7 +621,6 @@ __global__ void k_scatter_sources_f(KP kp) {
 // zero test) is shared by 8 CPT multiply-adds. The default is 2; the
 // autotuner may choose 1.
 constexpr int kSpreadCptM = 2;
-constexpr int kSpreadThreadsM = kTile * kTile / kSpreadCptM;
 
 template <int CPT>
 __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
@@ -1565,38 +1563,356 @@ __device__ __forceinline__ double mode_k(const KP& kp, int col, double& mult) {
     return sqrt(kx * kx + ky * ky);
 }
 
-// Tensor-core form: the correction of every mode, one thread per mode (the
-// FP64 pipe is then used by all lanes), between the column kernel (which
-// leaves the wall values in kp.bsum) and the inverse z transform (which
-// evaluates the correction at the nodes from kp.colp). Also this
-// correction's part of the gauge sum, per block.
-constexpr int kCorrThreads = 256;
-__device__ __forceinline__ void bc_correction_body(const KP& kp, const int bid) {
+
+// ---------------------------------------------------------------------------
+// Column stage of the tensor-core form (DPSLAB_MIXED with the z transforms as
+// GEMMs around it): the per-mode BVP of Appendix A on 8 W modes per block of
+// 2 W warps, the boundary-condition correction in double (Sec. 4.3.3)
+// inside the block.
+//  1. The Chebyshev coefficients of both densities come in as whole rows of
+//     the block's modes, scaled to the right-hand side of Eq. (blocksys):
+//     F[mode][n] = (f_i, f_o).
+//  2. Warp w < W runs the two-way banded sweeps of 8 modes, one lane per
+//     (mode, chain, side): A y'' = F and A x = K^2 e0 (e1), A = I - K^2 J^2.
+//  3. Every warp then takes modes one at a time, lanes over n = lane + 32 r:
+//     the 2 x 2 Schur system for (c, d) of each field, y'' += (c or d) x,
+//     then y' = J y'' + d e0 and y = J y' + c e0 for field i (neighbours by
+//     shuffles), and the wall values: psi_i*, d psi_i*/dz from y, y'; psi_o*,
+//     d psi_o*/dz from y''_o through J^T t and J^T J^T t (t = T_n at the
+//     wall), since sum t y = (J^T J^T t).y'' + d (J^T t)_0 + c t_0 and
+//     sum t y' = (J^T t).y'' + d t_0.
+//  4. One thread per mode: the correction coefficients in double
+//     (bc_correction) -> colp, and its gauge term.
+//  5. y and y' of field i leave as whole rows, for the node-value GEMM.
+// R = ceil(N / 32) values of n per lane (4 for N <= 128, 8 for N <= 256).
+// ---------------------------------------------------------------------------
+constexpr int kTcTables = 15;   // j2l j2d j2u u1 u2 v1 v2 t0 tH wg hinv jt0 jjt0 jtH jjtH
+
+__host__ __device__ inline int tc_stride(int N) { return N | 1; }   // odd: rows of modes fall in distinct banks
+
+template <int W, int R>
+__device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
+    constexpr int MB = 8 * W;                 // modes per block
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = kp.nz, NP = tc_stride(N);
     const int M = kp.ny * kp.nxh;
-    const int col = bid * kCorrThreads + threadIdx.x;
-    double g = 0.0;
-    if (col < M) {
+    float4* F = reinterpret_cast<float4*>(smraw);                  // [MB][NP]
+    float2* Q = reinterpret_cast<float2*>(F + MB * NP);            // [MB][NP]: c' or a'', x
+    float* tb = reinterpret_cast<float*>(Q + MB * NP);             // [kTcTables][N]
+    const float *j2l = tb, *j2d = tb + N, *j2u = tb + 2 * N, *u1 = tb + 3 * N, *u2 = tb + 4 * N, *v1 = tb + 5 * N,
+                *v2 = tb + 6 * N, *t0 = tb + 7 * N, *tH = tb + 8 * N, *wgt = tb + 9 * N, *hinv = tb + 10 * N,
+                *jt0 = tb + 11 * N, *jjt0 = tb + 12 * N, *jtH = tb + 13 * N, *jjtH = tb + 14 * N;
+    __shared__ float s_K[MB], s_mult[MB], s_damp[MB];
+    __shared__ double s_k[MB];
+    __shared__ float s_bs[MB][16];
+    __shared__ double s_gauge[MB];
+    __shared__ int s_valid[MB], s_corr[MB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = 2 * W, bs = 32 * NW;   // the first W warps sweep; all take part in the rest
+    const int col0 = bid * MB;
+    float2* const sp = static_cast<float2*>(kp.spec);
+
+    if (tid < MB) {
+        const int c = tid, col = col0 + c;
         double mult;
         const double k = mode_k(kp, col, mult);
-        ColP cp{make_float2(0.f, 0.f), make_float2(0.f, 0.f), float(k), 0.f, 0.f, 0};
-        if (k > 0.0 && k <= kp.kmax) {
-            float v[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = __ldcs(kp.bsum + size_t(i) * M + col);
-            const BcCoef b = bc_correction(kp, col, v);
-            cp = ColP{make_float2(float(b.P.x), float(b.P.y)), make_float2(float(b.Q.x), float(b.Q.y)), float(k),
-                      float(b.ekH), float(b.iden), 1};
-            g = mult * b.corr0;
-        }
-        kp.colp[col] = cp;
+        s_valid[c] = col < M;
+        s_k[c] = k;
+        s_K[c] = float(0.5 * k * kp.Hbar);
+        s_mult[c] = float(mult);
+        s_damp[c] = expf(-0.5f * kp.f.sigma2 * float(k) * float(k));
+        s_corr[c] = (col < M) && k > 0.0 && k <= kp.kmax;
+        s_gauge[c] = 0.0;
     }
-    g = block_sum(g);
-    if (threadIdx.x == 0) kp.part_gauge_corr[bid] = g;
+    {
+        const float* src[kTcTables] = {kp.j2l32, kp.j2d32, kp.j2u32, kp.u132, kp.u232, kp.v132, kp.v232, kp.t032,
+                                       kp.tH32, kp.wg32, kp.hinv32, kp.jt0_32, kp.jjt0_32, kp.jtH_32, kp.jjtH_32};
+        for (int t = tid; t < kTcTables * N; t += bs) tb[t] = __ldg(src[t / N] + t % N);
+    }
+    // 1. coefficients of both densities, whole rows of the block's modes;
+    //    every load of a batch is issued before the first store
+    const float scale = kp.f.scale;
+    constexpr int kLd = 4;
+    for (int t0 = tid; t0 < N * MB; t0 += kLd * bs) {
+        float2 vi[kLd], vo[kLd];
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+            const int t = t0 + u * bs, n = t / MB, c = t - n * MB, col = col0 + c;
+            vi[u] = vo[u] = make_float2(0.f, 0.f);
+            if (t < N * MB && col < M) {
+                vi[u] = __ldcs(sp + size_t(n) * M + col);
+                vo[u] = __ldcs(sp + size_t(N + n) * M + col);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+            const int t = t0 + u * bs, n = t / MB, c = t - n * MB;
+            if (t < N * MB) F[c * NP + n] = make_float4(vi[u].x * scale, vi[u].y * scale, vo[u].x * scale, vo[u].y * scale);
+        }
+    }
+    __syncthreads();
+
+    // 2. two-way banded sweeps: lane (mode c, chain ch, side) of warp w < W. Side
+    //    0 sweeps rows 0 .. m-1 downward (row i becomes y_i + c'_i y_{i+1} =
+    //    f'_i), side 1 rows L-1 .. m upward (a''_i y_{i-1} + y_i = f''_i);
+    //    they meet in a 2 x 2 system at rows m-1, m, then substitute outward.
+    if (warp < W) {
+        const int c = 8 * warp + (lane >> 2), ch = (lane >> 1) & 1, side = lane & 1;
+        const float K2 = s_K[c] * s_K[c];
+        float4* Fc = F + c * NP;
+        float2* Qc = Q + c * NP;
+        const int L = (N - ch + 1) / 2, m = L / 2;
+        const int cnt = side ? L - m : m, i0 = side ? L - 1 : 0, di = side ? -1 : 1;
+        const int cmax = L - m;
+        float qp = 0.f, xcp = 0.f;
+        float4 fp = make_float4(0.f, 0.f, 0.f, 0.f);
+        int nn = ch + 2 * i0;
+        float jl = 0.f, jd = 0.f, ju = 0.f;
+        float4 Fn = fp;
+        if (cnt > 0) { jl = j2l[nn]; jd = j2d[nn]; ju = j2u[nn]; Fn = Fc[nn]; }
+        for (int k = 0; k < cmax; ++k) {
+            if (k < cnt) {
+                const int i = i0 + di * k, n = nn;
+                const float an = -K2 * jl, bn = 1.f - K2 * jd, cn = -K2 * ju;
+                const float4 Fcur = Fn;
+                nn = n + 2 * di;
+                if (k + 1 < cnt) { jl = j2l[nn]; jd = j2d[nn]; ju = j2u[nn]; Fn = Fc[nn]; }
+                const float lo = side ? cn : an, up = side ? an : cn;   // toward / away from the sweep
+                const float inv = __frcp_rn(bn - lo * qp);
+                const float rn = (i == 0) ? K2 : 0.f;
+                fp = make_float4((Fcur.x - fp.x * lo) * inv, (Fcur.y - fp.y * lo) * inv, (Fcur.z - fp.z * lo) * inv,
+                                 (Fcur.w - fp.w * lo) * inv);
+                xcp = (rn - lo * xcp) * inv;
+                qp = up * inv;
+                Qc[n] = make_float2(qp, xcp);
+                Fc[n] = fp;
+            }
+        }
+        __syncwarp();
+        if (side == 1 && m > 0) {
+            const int nA = ch + 2 * (m - 1), nB = ch + 2 * m;
+            const float2 qA = Qc[nA], qB = Qc[nB];
+            const float cA = qA.x, aB = qB.x;
+            const float den = 1.f / (1.f - aB * cA);
+            const float4 FA = Fc[nA], FB = Fc[nB];
+            const float4 yB = make_float4((FB.x - aB * FA.x) * den, (FB.y - aB * FA.y) * den, (FB.z - aB * FA.z) * den,
+                                          (FB.w - aB * FA.w) * den);
+            const float yBx = (qB.y - aB * qA.y) * den;
+            Fc[nA] = make_float4(FA.x - cA * yB.x, FA.y - cA * yB.y, FA.z - cA * yB.z, FA.w - cA * yB.w);
+            Qc[nA] = make_float2(cA, qA.y - cA * yBx);
+            Fc[nB] = yB;
+            Qc[nB] = make_float2(aB, yBx);
+        }
+        __syncwarp();
+        const int bcnt = side ? L - m - 1 : m - 1, b0 = side ? m + 1 : m - 2, bdi = -di;
+        if (bcnt > 0) {
+            const int nprev = ch + 2 * (b0 - bdi);
+            fp = Fc[nprev];
+            xcp = Qc[nprev].y;
+        }
+        for (int k = 0; k < cmax; ++k) {
+            if (k < bcnt) {
+                const int i = b0 + bdi * k, n = ch + 2 * i;
+                const float2 qn = Qc[n];
+                const float4 Fv = Fc[n];
+                fp = make_float4(Fv.x - qn.x * fp.x, Fv.y - qn.x * fp.y, Fv.z - qn.x * fp.z, Fv.w - qn.x * fp.w);
+                xcp = qn.y - qn.x * xcp;
+                Fc[n] = fp;
+                Qc[n] = make_float2(qn.x, xcp);
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3. per mode, lanes over n = lane + 32 r
+    for (int c = warp; c < MB; c += NW) {
+        const float K = s_K[c];
+        float2 yi[R], yo[R];
+        float x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int n = lane + 32 * r;
+            yi[r] = yo[r] = make_float2(0.f, 0.f);
+            x[r] = 0.f;
+            if (n < N) {
+                const float4 f = F[c * NP + n];
+                yi[r] = make_float2(f.x, f.y);
+                yo[r] = make_float2(f.z, f.w);
+                x[r] = Q[c * NP + n].y;
+            }
+        }
+        // Schur rows (Eq. (BCs); Eq. (BCs0) for K = 0): sums of g_t, g_b times
+        // y'' of both fields and times x (by the parity of n = that of lane)
+        float da[12];
+        {
+            float acc[12];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) acc[i] = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int n = lane + 32 * r;
+                if (n < N) {
+                    const float gtn = K > 0.f ? u1[n] + K * u2[n] : u2[n];
+                    const float gbn = K > 0.f ? v1[n] - K * v2[n] : v2[n];
+                    acc[0] = fmaf(gtn, yi[r].x, acc[0]); acc[1] = fmaf(gtn, yi[r].y, acc[1]);
+                    acc[2] = fmaf(gbn, yi[r].x, acc[2]); acc[3] = fmaf(gbn, yi[r].y, acc[3]);
+                    acc[4] = fmaf(gtn, yo[r].x, acc[4]); acc[5] = fmaf(gtn, yo[r].y, acc[5]);
+                    acc[6] = fmaf(gbn, yo[r].x, acc[6]); acc[7] = fmaf(gbn, yo[r].y, acc[7]);
+                    if (lane & 1) { acc[9] = fmaf(gtn, x[r], acc[9]); acc[11] = fmaf(gbn, x[r], acc[11]); }
+                    else { acc[8] = fmaf(gtn, x[r], acc[8]); acc[10] = fmaf(gbn, x[r], acc[10]); }
+                }
+            }
+            const float r8 = warp_sum_multi<8>(acc), r4 = warp_sum_multi<4>(acc + 8);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) da[i] = __shfl_sync(0xffffffffu, r8, 4 * i);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) da[8 + i] = __shfl_sync(0xffffffffu, r4, 8 * i);
+        }
+        float2 cc[2], dd[2];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const float2 sFt = f ? make_float2(da[4], da[5]) : make_float2(da[0], da[1]);
+            const float2 sFb = f ? make_float2(da[6], da[7]) : make_float2(da[2], da[3]);
+            if (K > 0.f) {
+                const float m11 = K + da[8], m12 = 1.f + K + da[9], m21 = -K + da[10], m22 = 1.f + K + da[11];
+                const float idet = 1.f / (m11 * m22 - m12 * m21);
+                cc[f] = cscale(csub(cscale(sFt, m22), cscale(sFb, m12)), -idet);
+                dd[f] = cscale(csub(cscale(sFb, m11), cscale(sFt, m21)), -idet);
+            } else {
+                cc[f] = cscale(cadd(sFt, sFb), -0.5f);
+                dd[f] = cscale(csub(sFt, sFb), -0.5f);
+            }
+        }
+        // y'' = x_F + c x_c + d x_d (c on even n, d on odd n)
+        {
+            const float2 mi = (lane & 1) ? dd[0] : cc[0], mo = (lane & 1) ? dd[1] : cc[1];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                yi[r] = cadd(yi[r], cscale(mi, x[r]));
+                yo[r] = cadd(yo[r], cscale(mo, x[r]));
+            }
+        }
+        // y' = J y'' + d e0 and y = J y' + c e0 for field i: entry n of J v is
+        // (v_{n-1} - v_{n+1}) / (2n) for n >= 2 and v_0 - v_2 / 2 for n = 1;
+        // v_{n-1} and v_{n+1} from the neighbouring lanes (lane 0 takes lane
+        // 31's value of row r - 1, lane 31 lane 0's of row r + 1)
+        auto integrate = [&](const float2* v, float2* out, float2 e0) {
+            // rotations by one lane: lane 0 takes lane 31's value of the row
+            // before (the previous row's rotation), lane 31 lane 0's of the
+            // row after (the next row's)
+            float2 pr[R], nr[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                pr[r].x = __shfl_sync(0xffffffffu, v[r].x, (lane + 31) & 31);
+                pr[r].y = __shfl_sync(0xffffffffu, v[r].y, (lane + 31) & 31);
+                nr[r].x = __shfl_sync(0xffffffffu, v[r].x, (lane + 1) & 31);
+                nr[r].y = __shfl_sync(0xffffffffu, v[r].y, (lane + 1) & 31);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int n = lane + 32 * r;
+                const float2 prev = lane != 0 ? pr[r] : (r > 0 ? pr[r - 1] : make_float2(0.f, 0.f));
+                float2 next = lane != 31 ? nr[r] : (r + 1 < R ? nr[r + 1] : make_float2(0.f, 0.f));
+                if (n + 1 >= N) next = make_float2(0.f, 0.f);
+                float2 o;
+                if (n == 0) o = e0;
+                else if (n == 1) o = csub(prev, cscale(next, 0.5f));
+                else o = cscale(csub(prev, next), hinv[n < N ? n : 0]);
+                out[r] = n < N ? o : make_float2(0.f, 0.f);
+            }
+        };
+        float2 ypi[R], yyi[R];
+        integrate(yi, ypi, dd[0]);
+        integrate(ypi, yyi, cc[0]);
+        // wall values: values 0..15 in the order of bc_correction, 16-17 the
+        // gauge sum of psi_i*
+        float acc[18];
+#pragma unroll
+        for (int i = 0; i < 18; ++i) acc[i] = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int n = lane + 32 * r;
+            if (n < N) {
+                const float a0 = t0[n], aH = tH[n];
+                acc[0] = fmaf(a0, yyi[r].x, acc[0]);   acc[1] = fmaf(a0, yyi[r].y, acc[1]);
+                acc[2] = fmaf(a0, ypi[r].x, acc[2]);   acc[3] = fmaf(a0, ypi[r].y, acc[3]);
+                acc[4] = fmaf(aH, yyi[r].x, acc[4]);   acc[5] = fmaf(aH, yyi[r].y, acc[5]);
+                acc[6] = fmaf(aH, ypi[r].x, acc[6]);   acc[7] = fmaf(aH, ypi[r].y, acc[7]);
+                acc[8] = fmaf(jjt0[n], yo[r].x, acc[8]);  acc[9] = fmaf(jjt0[n], yo[r].y, acc[9]);
+                acc[10] = fmaf(jt0[n], yo[r].x, acc[10]); acc[11] = fmaf(jt0[n], yo[r].y, acc[11]);
+                acc[12] = fmaf(jjtH[n], yo[r].x, acc[12]); acc[13] = fmaf(jjtH[n], yo[r].y, acc[13]);
+                acc[14] = fmaf(jtH[n], yo[r].x, acc[14]); acc[15] = fmaf(jtH[n], yo[r].y, acc[15]);
+                acc[16] = fmaf(wgt[n], yyi[r].x, acc[16]); acc[17] = fmaf(wgt[n], yyi[r].y, acc[17]);
+            }
+        }
+        // lane 2 v holds value v (0..15); lane 16 v holds value 16 + v
+        float r16 = warp_sum_multi<16>(acc);
+        const float r2 = warp_sum_multi<2>(acc + 16);
+        {
+            // the (c, d) terms of field o's wall values
+            const int v = lane >> 1, comp = v & 1;
+            const float co = comp ? cc[1].y : cc[1].x, dv = comp ? dd[1].y : dd[1].x;
+            if (v == 8 || v == 9) r16 += dv * jt0[0] + co * t0[0];
+            else if (v == 10 || v == 11) r16 += dv * t0[0];
+            else if (v == 12 || v == 13) r16 += dv * jtH[0] + co * tH[0];
+            else if (v == 14 || v == 15) r16 += dv * tH[0];
+        }
+        const float wgs = __shfl_sync(0xffffffffu, r2, 0);
+        if (s_corr[c] && (lane & 1) == 0) s_bs[c][lane >> 1] = r16;
+        if (lane == 0 && s_valid[c]) s_gauge[c] = double(s_mult[c]) * double(s_damp[c]) * double(wgs);
+        // y and y' of field i, for the node-value GEMM
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int n = lane + 32 * r;
+            if (n < N) F[c * NP + n] = make_float4(yyi[r].x, yyi[r].y, ypi[r].x, ypi[r].y);
+        }
+    }
+    __syncthreads();
+
+    // 4. the correction coefficients in double, one thread per mode
+    if (tid < MB) {
+        const int c = tid, col = col0 + c;
+        if (s_valid[c]) {
+            const double k = s_k[c], mult = s_mult[c];
+            ColP cp{make_float2(0.f, 0.f), make_float2(0.f, 0.f), float(k), 0.f, 0.f, 0};
+            if (s_corr[c]) {
+                const BcCoef b = bc_correction(kp, col, s_bs[c]);
+                cp = ColP{make_float2(float(b.P.x), float(b.P.y)), make_float2(float(b.Q.x), float(b.Q.y)), float(k),
+                          float(b.ekH), float(b.iden), 1};
+                s_gauge[c] += mult * b.corr0;
+            }
+            kp.colp[col] = cp;
+        }
+    }
+    // column 0 (block 0): the coefficients and gauge term of k_column_zero
+    if (bid == 0) {
+        for (int n = tid; n < N; n += bs) F[n] = make_float4(float(kp.zcol[n]), 0.f, float(kp.zcol[N + n]), 0.f);
+        if (tid == 0) s_gauge[0] = kp.zcol[2 * N];
+    }
+    __syncthreads();
+    // 5. coefficients of psi_i (plane 0) and dpsi_i/dz (plane 1, before the
+    //    factor 2/Hbar), whole rows
+    for (int t = tid; t < 2 * N * MB; t += bs) {
+        const int c = t % MB, fn = t / MB, col = col0 + c;
+        const int f = fn >= N, n = fn - f * N;
+        if (col < M) {
+            const float4 v = F[c * NP + n];
+            __stcs(sp + size_t(fn) * M + col, f ? make_float2(v.z, v.w) : make_float2(v.x, v.y));
+        }
+    }
+    if (tid == 0) {
+        double g = 0.0;
+        for (int c = 0; c < MB; ++c) g += s_gauge[c];
+        kp.part_gauge_far[bid] = g;
+    }
 }
-__global__ void __launch_bounds__(kCorrThreads) k_bc_correction(KP kp) { bc_correction_body(kp, blockIdx.x); }
-__global__ void __launch_bounds__(kCorrThreads) k_bc_correction_batch(const __grid_constant__ ColBatch b) {
-    const int s = batch_system(b.corr_starts, b.nsys, blockIdx.x);
-    bc_correction_body(b.kp[s], blockIdx.x - b.corr_starts[s]);
+
+template <int W, int R>
+__global__ void __launch_bounds__(64 * W) k_column_tc(KP kp) { column_tc_body<W, R>(kp, blockIdx.x); }
+template <int W, int R>
+__global__ void __launch_bounds__(64 * W) k_column_tc_batch(const __grid_constant__ ColBatch b) {
+    const int s = batch_system(b.starts, b.nsys, blockIdx.x);
+    column_tc_body<W, R>(b.kp[s], blockIdx.x - b.starts[s]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1616,7 +1932,7 @@ constexpr int kColThreadsM = 32 * kColBlockM;
 // (k_zgemm); it then reads the coefficients of both densities and writes
 // the coefficients of psi_i and dpsi_i/dz and each mode's correction
 // parameters, instead of transforming itself.
-template <bool kTensor, int CB>
+template <int CB>
 __device__ __forceinline__ void column_mixed_body(const KP& kp, const int bid) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = kp.nz;
@@ -1674,19 +1990,14 @@ __device__ __forceinline__ void column_mixed_body(const KP& kp, const int bid) {
         for (int u = 0; u < kLd; ++u) {
             const int t = t0 + u * bs, j = t / CB, c = t - j * CB;
             if (t >= N * CB) break;
-            if (kTensor) {                   // coefficients: right-hand sides of Eq. (blocksys)
-                Ci[c * NP + j] = cscale(vi[u], scale);
-                Co[c * NP + j] = cscale(vo[u], scale);
-            } else {
-                Vi[c * NP + j] = vi[u];
-                Vo[c * NP + j] = vo[u];
-            }
+            Vi[c * NP + j] = vi[u];
+            Vo[c * NP + j] = vo[u];
         }
     }
     __syncthreads();
 
     const int m = N - 1, JE = (N + 1) / 2, JO = N / 2;
-    if (!kTensor) {
+    {
     for (int t = tid; t < 2 * CB * JE; t += bs) {
         const int f = t / (CB * JE), r = t - f * CB * JE, c = r / JE, a = r - c * JE;
         if (a < m - a) {
@@ -1924,15 +2235,14 @@ __device__ __forceinline__ void column_mixed_body(const KP& kp, const int bid) {
         const float r16 = warp_sum_multi<16>(acc), r2 = warp_sum_multi<2>(acc + 16);
         const float wgs = __shfl_sync(0xffffffffu, r2, 0);
         if (s_valid[c] && s_corr[c] && (lane & 1) == 0) {
-            if (kTensor) kp.bsum[size_t(lane >> 1) * M + col0 + c] = r16;   // to k_bc_correction
-            else s_bs[c][lane >> 1] = r16;
+            s_bs[c][lane >> 1] = r16;
         }
         if (lane == 0 && s_valid[c]) {
             const double damp = double(expf(-0.5f * kp.f.sigma2 * s_k[c] * s_k[c]));
             s_gauge[c] = (col0 + c == 0) ? kp.zcol[2 * N] : double(s_mult[c]) * damp * double(wgs);
         }
     }
-    if (!kTensor) {
+    {
         // the correction of the block's modes in double, one lane each
         __syncthreads();
         if (tid < CB && s_valid[tid] && s_corr[tid]) {
@@ -1955,21 +2265,6 @@ __device__ __forceinline__ void column_mixed_body(const KP& kp, const int bid) {
         __syncthreads();
     }
 
-    if (kTensor) {
-        // coefficients of psi_i (plane 0) and dpsi_i/dz (plane 1, before the
-        // factor 2/Hbar), for the node-value GEMM
-        for (int t = tid; t < 2 * CB * N; t += bs) {
-            const int c = t % CB, fn = t / CB, col = col0 + c;       // fn = f N + n (CB a power of two)
-            const int f = fn >= N, n = fn - f * N;
-            if (col < M) sp[size_t(fn) * M + col] = (f ? Vi : Ci)[c * NP + n];
-        }
-        if (tid == 0) {
-            double g = 0.0;
-            for (int c = 0; c < CB; ++c) g += s_gauge[c];
-            kp.part_gauge_far[bid] = g;
-        }
-        return;
-    }
     // node values (float), correction at the nodes (float)
     const float Ai = float(s_Ai);
     const float Gb = kp.f.Gb, Gt = kp.f.Gt, Hf = kp.f.H, HEf = kp.f.HE;
@@ -2044,14 +2339,11 @@ __device__ __forceinline__ void column_mixed_body(const KP& kp, const int bid) {
         kp.part_gauge_far[bid] = g;
     }
 }
-template <bool kTensor, int CB>
-__global__ void __launch_bounds__(32 * CB, (kTensor ? 40 : 32) / CB) k_column_mixed(KP kp) {
-    column_mixed_body<kTensor, CB>(kp, blockIdx.x);
-}
-template <bool kTensor>
-__global__ void __launch_bounds__(kColThreadsM, kTensor ? 5 : 4) k_column_mixed_batch(const __grid_constant__ ColBatch b) {
+template <int CB>
+__global__ void __launch_bounds__(32 * CB, 32 / CB) k_column_mixed(KP kp) { column_mixed_body<CB>(kp, blockIdx.x); }
+__global__ void __launch_bounds__(kColThreadsM, 4) k_column_mixed_batch(const __grid_constant__ ColBatch b) {
     const int s = batch_system(b.starts, b.nsys, blockIdx.x);
-    column_mixed_body<kTensor, kColBlockM>(b.kp[s], blockIdx.x - b.starts[s]);
+    column_mixed_body<kColBlockM>(b.kp[s], blockIdx.x - b.starts[s]);
 }
 
 // ---------------------------------------------------------------------------
@@ -2616,7 +2908,6 @@ __global__ void k_origin(KP kp) {
 __global__ void k_final_gauge(KP kp) {
     double f = 0.0, nn = 0.0, q1 = 0.0, q2 = 0.0;
     for (int i = threadIdx.x; i < kp.n_col_blocks; i += blockDim.x) f += kp.part_gauge_far[i];
-    for (int i = threadIdx.x; i < kp.n_corr_blocks; i += blockDim.x) f += kp.part_gauge_corr[i];
     for (int i = threadIdx.x; i < kp.n_charge_blocks; i += blockDim.x) {
         nn += kp.part_gauge_near[i];
         q1 += kp.part_q[i];
@@ -2855,7 +3146,8 @@ struct dpslab_plan {
     size_t G = 0, S = 0;
     int px_fwd = 1, tk_fwd = 1, tk_inv = 1, px_inv = 1;
     int interp_warps = kInterpWarps;   // warps (charges) per block of the interpolation
-    int col_cb = 0;                    // modes per block of the column kernel
+    int col_cb = 0;                    // modes per block of the column kernel (tensor-core form: 8 W)
+    int tc_r = 4;                      // tensor-core form: rows of n per lane, ceil(nz / 32)
     int spread_cpt = 1;                // x columns per thread of the mixed spreading
     int p2x = 0, p2y = 0, lognx = 0, logny = 0;        // power-of-two FFT kernels in x, y
     bool ztensor = false;                              // z transforms as tensor-core GEMMs
@@ -2950,15 +3242,26 @@ int floor_pow2(int v) {
 // Column kernels by modes per block (launch-shape knob): FP64 2 or 4, mixed 4 or 8.
 constexpr int kMinColBlock = 4;         // smallest mixed block; the FP64 one is half of it
 using ColKernel = void (*)(KP);
-ColKernel column_mixed_kernel(bool tensor, int cb) {
-    if (cb == 4) return tensor ? k_column_mixed<true, 4> : k_column_mixed<false, 4>;
-    return tensor ? k_column_mixed<true, 8> : k_column_mixed<false, 8>;
+ColKernel column_mixed_kernel(int cb) { return cb == 4 ? k_column_mixed<4> : k_column_mixed<8>; }
+// tensor-core form: 8 W modes per block, R = ceil(N / 32) rows per lane
+ColKernel column_tc_kernel(int W, int R) {
+    if (R == 4) return W == 1 ? k_column_tc<1, 4> : W == 2 ? k_column_tc<2, 4> : k_column_tc<4, 4>;
+    return W == 1 ? k_column_tc<1, 8> : W == 2 ? k_column_tc<2, 8> : k_column_tc<4, 8>;
+}
+using ColBatchKernel = void (*)(ColBatch);
+ColBatchKernel column_tc_batch_kernel(int W, int R) {
+    if (R == 4) return W == 1 ? k_column_tc_batch<1, 4> : W == 2 ? k_column_tc_batch<2, 4> : k_column_tc_batch<4, 4>;
+    return W == 1 ? k_column_tc_batch<1, 8> : W == 2 ? k_column_tc_batch<2, 8> : k_column_tc_batch<4, 8>;
+}
+size_t tc_smem(int nz, int W) {
+    return size_t(8 * W) * size_t(tc_stride(nz)) * (sizeof(float4) + sizeof(float2)) + size_t(kTcTables) * nz * sizeof(float);
 }
 ColKernel column_kernel(int cb) { return cb == 2 ? k_column<2> : k_column<4>; }
 // dynamic shared memory of the column kernel with cb modes per block
 size_t col_smem(const dpslab_plan* pl, int cb) {
     const int nz = pl->kp.nz;
     const bool mixed = pl->kp.mixed != 0;
+    if (pl->ztensor) return tc_smem(nz, cb / 8);
     const size_t rsz = mixed ? sizeof(float) : sizeof(double), csz = 2 * rsz;
     return size_t(cb) * (nz + (mixed ? ((2 - nz) & 15) : 0)) * (4 * csz + 2 * rsz);
 }
@@ -2988,8 +3291,6 @@ size_t bind_work(dpslab_plan* pl, char* base) {
     kp.srcs_tmp = kp.mixed ? carve<SrcF>(cur, 3 * n) : nullptr;
     kp.colp = pl->ztensor ? carve<ColP>(cur, M) : nullptr;
     kp.zcol = kp.mixed ? carve<double>(cur, 2 * size_t(kp.nz) + 1) : nullptr;
-    kp.bsum = pl->ztensor ? carve<float>(cur, 16 * M) : nullptr;
-    kp.part_gauge_corr = pl->ztensor ? carve<double>(cur, size_t(kp.n_corr_blocks)) : nullptr;
     kp.tile_count = carve<int>(cur, size_t(kp.nbuckets) + 1);
     kp.tile_start = carve<int>(cur, size_t(kp.nbuckets) + 1);
     kp.tile_fill = carve<int>(cur, size_t(kp.nbuckets) + 1);
@@ -3184,9 +3485,16 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
     kp.supy = d.support_y;
     kp.mixed = mixed ? 1 : 0;
     kp.zspin = kZSpinLimit;
-    const int col_block = mixed ? kColBlockM : kColBlock;
+    int col_block = mixed ? kColBlockM : kColBlock;
+    if (pl->ztensor) {
+        // the tensor-core form's column kernel: the most modes per block whose
+        // shared memory lets two blocks share an SM
+        pl->tc_r = nz <= 128 ? 4 : 8;
+        col_block = 8;
+        for (int W = 4; W >= 1; W /= 2)
+            if (2 * (tc_smem(nz, W) + 1024) <= 228 * 1024) { col_block = 8 * W; break; }
+    }
     kp.n_col_blocks = (M + col_block - 1) / col_block;
-    kp.n_corr_blocks = pl->ztensor ? int((M + kCorrThreads - 1) / kCorrThreads) : 0;
     const size_t rsz = mixed ? sizeof(float) : sizeof(double);   // grid element size
     kp.n_charge_blocks = int((max_n + kChargeThreads - 1) / kChargeThreads);
 
@@ -3197,8 +3505,8 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         const size_t vec = align_up(N * sizeof(double));
         bytes += 2 * vec + 4 * align_up(N * N * sizeof(double)) + 12 * vec;
         bytes += align_up(nx * sizeof(double2)) + align_up(ny * sizeof(double2));
-        // float copies: cft, tie, tio (together <= 2 N^2) and 14 vectors
-        bytes += 3 * align_up(N * N * sizeof(float)) + 14 * align_up(N * sizeof(float));
+        // float copies: cft, tie, tio (together <= 2 N^2) and 18 vectors
+        bytes += 3 * align_up(N * N * sizeof(float)) + 18 * align_up(N * sizeof(float));
         if (pl->ztensor) bytes += 2 * align_up(t.zimg_fwd.size() * sizeof(unsigned short));   // bf16 images
         bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
         if (mixed) bytes += align_up(size_t(M) * sizeof(double4_32a));   // per-mode correction factors
@@ -3259,6 +3567,22 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         upf(t.j2l, kp.j2l32); upf(t.j2d, kp.j2d32); upf(t.j2u, kp.j2u32);
         upf(t.u1, kp.u132); upf(t.u2, kp.u232); upf(t.v1, kp.v132); upf(t.v2, kp.v232);
         upf(t.t0, kp.t032); upf(t.tH, kp.tH32); upf(t.wg, kp.wg32);
+        {
+            // (J^T v)_m = a(m+1) v_{m+1} + b(m-1) v_{m-1}: row n of J has
+            // 1/(2n) at n-1 and -1/(2n) at n+1 for n >= 2, 1 at 0 and -1/2 at
+            // 2 for n = 1, and nothing for n = 0; columns stop at N-1
+            const int nn = int(t.t0.size());
+            auto jt = [&](const std::vector<double>& v) {
+                std::vector<double> o(nn, 0.0);
+                for (int m = 0; m < nn; ++m) {
+                    if (m + 1 < nn) o[m] += (m + 1 == 1 ? 1.0 : 0.5 / (m + 1)) * v[m + 1];
+                    if (m - 1 >= 1) o[m] += (m - 1 == 1 ? -0.5 : -0.5 / (m - 1)) * v[m - 1];
+                }
+                return o;
+            };
+            const std::vector<double> j0 = jt(t.t0), jj0 = jt(j0), jH = jt(t.tH), jjH = jt(jH);
+            upf(j0, kp.jt0_32); upf(jj0, kp.jjt0_32); upf(jH, kp.jtH_32); upf(jjH, kp.jjtH_32);
+        }
         auto upc = [&](const std::vector<dps::Complex>& v, const float2*& dst) {
             std::vector<float2> f(v.size());
             for (size_t i = 0; i < v.size(); ++i) f[i] = make_float2(float(v[i].re), float(v[i].im));
@@ -3438,9 +3762,13 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             const int ntiles = 2 * int((2 * size_t(M) + kZN - 1) / kZN);   // both planes
             pl->zgrid = std::max(1, std::min(ntiles, nsm));
         }
-        for (int cb = kMinColBlock; cb <= kColBlockM; cb *= 2) {
-            raise_smem(reinterpret_cast<const void*>(column_mixed_kernel(false, cb)), col_smem(pl, cb));
-            raise_smem(reinterpret_cast<const void*>(column_mixed_kernel(true, cb)), col_smem(pl, cb));
+        if (pl->ztensor) {
+            for (int W = 1; W <= 4; W *= 2)
+                if (tc_smem(nz, W) <= 227 * 1024)
+                    raise_smem(reinterpret_cast<const void*>(column_tc_kernel(W, pl->tc_r)), tc_smem(nz, W));
+        } else {
+            for (int cb = kMinColBlock; cb <= kColBlockM; cb *= 2)
+                raise_smem(reinterpret_cast<const void*>(column_mixed_kernel(cb)), col_smem(pl, cb));
         }
         raise_smem(reinterpret_cast<const void*>(k_interp_f32),
                    size_t(kMaxInterpWarps) * (2 * kMaxSupport + kMaxNz) * sizeof(float));
@@ -3926,8 +4254,12 @@ bool apply_kernel_knob(dpslab_plan* pl, int which, int v) {
         return true;
     }
     if (which == 5) {
-        const int lo = mixed ? kMinColBlock : kMinColBlock / 2, hi = mixed ? kColBlockM : kColBlock;
-        if (v != lo && v != hi) return false;
+        if (pl->ztensor) {
+            if (v != 8 && v != 16 && v != 32) return false;
+        } else {
+            const int lo = mixed ? kMinColBlock : kMinColBlock / 2, hi = mixed ? kColBlockM : kColBlock;
+            if (v != lo && v != hi) return false;
+        }
         const size_t sm = col_smem(pl, v);
         if (sm > 227 * 1024) return false;
         const int M = pl->kp.ny * pl->kp.nxh;
@@ -4189,8 +4521,10 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         mark(5);
         }
         if (column) {
-        LAUNCH(column_mixed_kernel(pl->ztensor, pl->col_cb)<<<kp.n_col_blocks, 32 * pl->col_cb, pl->sm_col, st>>>(kp));
-        if (pl->ztensor) LAUNCH(k_bc_correction<<<kp.n_corr_blocks, kCorrThreads, 0, st>>>(kp));
+        if (pl->ztensor)
+            LAUNCH(column_tc_kernel(pl->col_cb / 8, pl->tc_r)<<<kp.n_col_blocks, 8 * pl->col_cb, pl->sm_col, st>>>(kp));
+        else
+            LAUNCH(column_mixed_kernel(pl->col_cb)<<<kp.n_col_blocks, 32 * pl->col_cb, pl->sm_col, st>>>(kp));
         }
         if (back) {
         mark(6);
@@ -4524,7 +4858,8 @@ struct dpslab_batch {
     // runs as one launch per kind of column kernel over all their k modes.
     struct ColGroup {
         int kind = 0;                      // 0 FP64, 1 mixed CUDA-core z transforms, 2 mixed tensor-core
-        int blocks = 0, corr_blocks = 0;
+        int tc_w = 0, tc_r = 0;            // kind 2: the column kernel's shape (8 W modes per block, R)
+        int blocks = 0;
         size_t smem = 0;
         std::shared_ptr<ColBatch> arg;     // the launch's parameter: up to kBatchMaxSys systems
     };
@@ -4582,35 +4917,42 @@ extern "C" int dpslab_batch_create(const dpslab_params* params, const int64_t* m
         if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { batch_release(b); return DPSLAB_ERR_CUDA; }
         b->joins.push_back(ev);
     }
-    // column groups: per wave of S systems, per kind of column kernel, one
-    // launch per kBatchMaxSys systems
+    // column groups: per wave of S systems, per kind (and shape) of column
+    // kernel, one launch per kBatchMaxSys systems
     b->waves.assign((count + S - 1) / S, {});
     for (int w0 = 0; w0 < count; w0 += S) {
-        std::vector<int> sys[3];
+        std::vector<std::pair<int, std::vector<int>>> keyed;   // (kind, W, R) code, systems
         for (int i = w0; i < std::min(count, w0 + S); ++i) {
             const dpslab_plan* pl = b->plans[i];
-            sys[!pl->kp.mixed ? 0 : (pl->ztensor ? 2 : 1)].push_back(i);
+            const int kind = !pl->kp.mixed ? 0 : (pl->ztensor ? 2 : 1);
+            const int key = kind == 2 ? 200 + 10 * (pl->col_cb / 8) + pl->tc_r : 100 * kind;
+            auto it = std::find_if(keyed.begin(), keyed.end(), [&](const auto& e) { return e.first == key; });
+            if (it == keyed.end()) keyed.push_back({key, {i}});
+            else it->second.push_back(i);
         }
-        for (int kind = 0; kind < 3; ++kind) {
-            for (size_t c0 = 0; c0 < sys[kind].size(); c0 += kBatchMaxSys) {
+        for (const auto& e : keyed) {
+            const std::vector<int>& sys = e.second;
+            for (size_t c0 = 0; c0 < sys.size(); c0 += kBatchMaxSys) {
                 dpslab_batch::ColGroup cg;
-                cg.kind = kind;
+                cg.kind = e.first / 100;
+                if (cg.kind == 2) {
+                    cg.tc_w = (e.first % 100) / 10;
+                    cg.tc_r = e.first % 10;
+                }
                 cg.arg = std::make_shared<ColBatch>();
                 ColBatch& a = *cg.arg;
                 std::memset(static_cast<void*>(&a), 0, sizeof(ColBatch));
-                a.nsys = int(std::min<size_t>(kBatchMaxSys, sys[kind].size() - c0));
+                a.nsys = int(std::min<size_t>(kBatchMaxSys, sys.size() - c0));
                 for (int j = 0; j < a.nsys; ++j) {
-                    const dpslab_plan* pl = b->plans[sys[kind][c0 + j]];
+                    const dpslab_plan* pl = b->plans[sys[c0 + j]];
                     std::memcpy(static_cast<void*>(&a.kp[j]), &pl->kp, sizeof(KP));
                     a.starts[j + 1] = a.starts[j] + pl->kp.n_col_blocks;
-                    a.corr_starts[j + 1] = a.corr_starts[j] + pl->kp.n_corr_blocks;
                     cg.smem = std::max(cg.smem, pl->sm_col);
                 }
                 cg.blocks = a.starts[a.nsys];
-                cg.corr_blocks = a.corr_starts[a.nsys];
-                if (kind == 0) raise_smem(reinterpret_cast<const void*>(k_column_batch), cg.smem);
-                if (kind == 1) raise_smem(reinterpret_cast<const void*>(k_column_mixed_batch<false>), cg.smem);
-                if (kind == 2) raise_smem(reinterpret_cast<const void*>(k_column_mixed_batch<true>), cg.smem);
+                if (cg.kind == 0) raise_smem(reinterpret_cast<const void*>(k_column_batch), cg.smem);
+                if (cg.kind == 1) raise_smem(reinterpret_cast<const void*>(k_column_mixed_batch), cg.smem);
+                if (cg.kind == 2) raise_smem(reinterpret_cast<const void*>(column_tc_batch_kernel(cg.tc_w, cg.tc_r)), cg.smem);
                 b->waves[w0 / S].push_back(std::move(cg));
             }
         }
@@ -4694,12 +5036,8 @@ extern "C" int dpslab_batch_solve(dpslab_batch* b, const int64_t* n, const doubl
             for (const auto& g : b->waves[wave]) {
                 if (rc) break;
                 if (g.kind == 0) k_column_batch<<<g.blocks, kColThreads, g.smem, st>>>(*g.arg);
-                if (g.kind == 1) k_column_mixed_batch<false><<<g.blocks, kColThreadsM, g.smem, st>>>(*g.arg);
-                if (g.kind == 2) {
-                    k_column_mixed_batch<true><<<g.blocks, kColThreadsM, g.smem, st>>>(*g.arg);
-                    k_bc_correction_batch<<<g.corr_blocks, kCorrThreads, 0, st>>>(*g.arg);
-                    ++launches;
-                }
+                if (g.kind == 1) k_column_mixed_batch<<<g.blocks, kColThreadsM, g.smem, st>>>(*g.arg);
+                if (g.kind == 2) column_tc_batch_kernel(g.tc_w, g.tc_r)<<<g.blocks, 64 * g.tc_w, g.smem, st>>>(*g.arg);
                 ++launches;
                 const cudaError_t le = cudaGetLastError();
                 if (le != cudaSuccess) {

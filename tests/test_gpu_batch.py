@@ -95,15 +95,21 @@ def test_batch_shares_workspaces_by_stream():
     b8.close()
 
 
-def _column_launches(plan_params, prec):
-    """Column-stage launches of one system solved alone: the FP64 column
-    kernel; the mixed BVP kernel, plus the correction kernel when the z
-    transforms run on the tensor cores (Nz <= 256 and ny (nx/2 + 1) even)."""
+def _column_kind(plan_params, prec):
+    """The column kernel of one system solved alone (one launch): FP64; mixed
+    with CUDA-core z transforms; or mixed with tensor-core z transforms
+    (Nz <= 256 and ny (nx/2 + 1) even), whose kernel shape is 8 W modes per
+    block and R rows per lane, W the largest of 4, 2, 1 whose shared memory
+    lets two blocks share an SM. A wave launches once per distinct kind."""
     if prec == dpslab.FP64:
-        return 1, 0
+        return ("fp64",)
     d = dpslab.derive(plan_params)
-    tensor = d["nz"] <= 256 and (d["ny"] * (d["nx"] // 2 + 1)) % 2 == 0
-    return (2, 2) if tensor else (1, 1)
+    nz = d["nz"]
+    if not (nz <= 256 and (d["ny"] * (d["nx"] // 2 + 1)) % 2 == 0):
+        return ("simt",)
+    smem = lambda w: 8 * w * (nz | 1) * 24 + 15 * nz * 4
+    w = next((w for w in (4, 2, 1) if 2 * (smem(w) + 1024) <= 228 * 1024), 1)
+    return ("tensor", w, 4 if nz <= 128 else 8)
 
 
 @pytest.mark.parametrize("prec,ftol,utol", [(dpslab.FP64, 1e-12, 1e-12), (dpslab.MIXED, TOL_MIXED_FORCE, TOL_MIXED_ENERGY)],
@@ -122,19 +128,17 @@ def test_batch_column_stage_is_one_launch_per_wave(prec, ftol, utol, nstreams):
     bufs = [_tensors(pos, q) for pos, q, _ in systems]
     U, status = batch.solve([b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs], [b[3] for b in bufs])
     assert (status == 0).all(), status
-    alone_launches, col_alone, kinds = 0, 0, []
+    alone_launches, kinds = 0, []
     for i, (pos, q, p) in enumerate(systems):
         plan = dpslab.Plan(params[i], len(q))
         pt, qt, phi, f = _tensors(pos, q)
         U1, _ = plan.solve(pt, qt, phi, f)
         alone_launches += plan.last_launch_count()
         plan.close()
-        launches, kind = _column_launches(params[i], prec)
-        col_alone += launches
-        kinds.append((i // nstreams, kind, launches))
+        kinds.append((i // nstreams,) + _column_kind(params[i], prec))
         assert abs(U[i] - U1) <= utol * abs(U1), (i, U[i], U1)
         assert rel_l2(bufs[i][3].cpu().numpy(), f.cpu().numpy()) <= ftol, i
-    per_wave = sum(launches for _, _, launches in set(kinds))
+    col_alone, per_wave = len(systems), len(set(kinds))
     assert batch.last_launch_count() == alone_launches - col_alone + per_wave, \
         (batch.last_launch_count(), alone_launches, col_alone, per_wave)
     batch.close()
