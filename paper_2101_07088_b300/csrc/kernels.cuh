@@ -151,7 +151,7 @@ struct KP {
     // J^T t0, J^T J^T t0, J^T tH, J^T J^T tH (J: Appendix-A integration,
     // y' = J y'' + d e0, y = J y' + c e0), float: wall values from y'' directly
     const float *jt0_32, *jjt0_32, *jtH_32, *jjtH_32;
-    const double4_32a* mtab;  // [ny nxh] mixed: per mode 1/k, e^{-kH}, 1/den, -(1 - Gt e^{-2kH})/den (0 at k = 0)
+    const double4_32a* mtab;  // [ny nxh] mixed: per mode k, e^{-kH}, 1/den, -(1 - Gt e^{-2kH})/den (k only: no correction)
     const unsigned short* zimg_fwd;   // split bf16 images of the z transforms (tensor cores)
     const unsigned short* zimg_inv;
     int* sorted_idx;

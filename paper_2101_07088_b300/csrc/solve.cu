@@ -1521,7 +1521,7 @@ __global__ void __launch_bounds__(kZeroThreads) k_column_zero(KP kp) { column_ze
 // over the coefficients, the last factor 2/Hbar of the derivatives not yet
 // applied), the mismatches Eq. (mm1)-(mm4) (with wall charges, the sigma
 // terms), the coefficients P, Q of the normalised Eq. (inphisc) and its value
-// at z = 0. The factors of k (1/k, e^{-kH}, 1/den, the z = 0 factor of P) come
+// at z = 0. The factors of k (k, e^{-kH}, 1/den, the z = 0 factor of P) come
 // from the plan's extended-precision table kp.mtab.
 // ---------------------------------------------------------------------------
 struct BcCoef {
@@ -1544,7 +1544,8 @@ __device__ __forceinline__ BcCoef bc_correction(const KP& kp, int col, const flo
         meb = cadd(meb, cscale(kp.sig_hat[col], ie));
         met = csub(met, cscale(kp.sig_hat[size_t(kp.ny) * kp.nxh + col], ie));
     }
-    const double db = kp.db * t.x, dt = kp.dt * t.x;
+    const double ik = 1.0 / t.x;
+    const double db = kp.db * ik, dt = kp.dt * ik;
     BcCoef o;
     o.P = csub(cscale(mpb, kp.cb), cscale(meb, db));
     o.Q = csub(cscale(mpt, -kp.ct), cscale(met, dt));
@@ -1563,6 +1564,18 @@ __device__ __forceinline__ double mode_k(const KP& kp, int col, double& mult) {
     return sqrt(kx * kx + ky * ky);
 }
 
+
+// Once per plan: the correction factors of the modes without a correction
+// (k = 0 or k > k_max, decided with the wave number in double exactly as the
+// FP64 column kernel decides it) are set to zero, keeping k, so that the
+// per-solve kernels read the decision from the table (1/den != 0).
+__global__ void k_mode_flags(KP kp, double4_32a* mtab) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= kp.ny * kp.nxh) return;
+    double mult;
+    const double k = mode_k(kp, col, mult);
+    if (!(k > 0.0 && k <= kp.kmax)) mtab[col] = make_double4_32a(mtab[col].x, 0.0, 0.0, 0.0);
+}
 
 // ---------------------------------------------------------------------------
 // Column stage of the tensor-core form (DPSLAB_MIXED with the z transforms as
@@ -1602,8 +1615,7 @@ __device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
     const float *j2l = tb, *j2d = tb + N, *j2u = tb + 2 * N, *u1 = tb + 3 * N, *u2 = tb + 4 * N, *v1 = tb + 5 * N,
                 *v2 = tb + 6 * N, *t0 = tb + 7 * N, *tH = tb + 8 * N, *wgt = tb + 9 * N, *hinv = tb + 10 * N,
                 *jt0 = tb + 11 * N, *jjt0 = tb + 12 * N, *jtH = tb + 13 * N, *jjtH = tb + 14 * N;
-    __shared__ float s_K[MB], s_mult[MB], s_damp[MB];
-    __shared__ double s_k[MB];
+    __shared__ float s_K[MB], s_mult[MB], s_damp[MB], s_kf[MB];
     __shared__ float s_bs[MB][16];
     __shared__ double s_gauge[MB];
     __shared__ int s_valid[MB], s_corr[MB];
@@ -1613,21 +1625,38 @@ __device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
     float2* const sp = static_cast<float2*>(kp.spec);
 
     if (tid < MB) {
+        // wave number from the plan's factor table (whose zero factors mark
+        // the modes without a correction: k = 0 or k > k_max)
         const int c = tid, col = col0 + c;
-        double mult;
-        const double k = mode_k(kp, col, mult);
+        const int iy = col / kp.nxh, ix = col - iy * kp.nxh;
+        const double4_32a t = col < M ? kp.mtab[col] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        const float k = float(t.x);
         s_valid[c] = col < M;
-        s_k[c] = k;
-        s_K[c] = float(0.5 * k * kp.Hbar);
-        s_mult[c] = float(mult);
-        s_damp[c] = expf(-0.5f * kp.f.sigma2 * float(k) * float(k));
-        s_corr[c] = (col < M) && k > 0.0 && k <= kp.kmax;
+        s_kf[c] = k;
+        s_K[c] = float(0.5 * t.x * kp.Hbar);
+        s_mult[c] = (ix == 0 || (kp.nx % 2 == 0 && ix == kp.nx / 2)) ? 1.f : 2.f;
+        s_damp[c] = expf(-0.5f * kp.f.sigma2 * k * k);
+        s_corr[c] = t.z != 0.0;
         s_gauge[c] = 0.0;
     }
     {
+        // the tables into shared memory: every load of a batch of 8 is issued
+        // before the first store (one round trip per batch)
         const float* src[kTcTables] = {kp.j2l32, kp.j2d32, kp.j2u32, kp.u132, kp.u232, kp.v132, kp.v232, kp.t032,
                                        kp.tH32, kp.wg32, kp.hinv32, kp.jt0_32, kp.jjt0_32, kp.jtH_32, kp.jjtH_32};
-        for (int t = tid; t < kTcTables * N; t += bs) tb[t] = __ldg(src[t / N] + t % N);
+        for (int t0b = tid; t0b < kTcTables * N; t0b += 8 * bs) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0b + u * bs;
+                v[u] = t < kTcTables * N ? __ldg(src[t / N] + t % N) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0b + u * bs;
+                if (t < kTcTables * N) tb[t] = v[u];
+            }
+        }
     }
     // 1. coefficients of both densities, whole rows of the block's modes;
     //    every load of a batch is issued before the first store
@@ -1869,27 +1898,29 @@ __device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
     }
     __syncthreads();
 
-    // 4. the correction coefficients in double, one thread per mode
+    // column 0 (block 0): the coefficients and gauge term of k_column_zero
+    if (bid == 0) {
+        for (int n = tid; n < N; n += bs) F[n] = make_float4(float(kp.zcol[n]), 0.f, float(kp.zcol[N + n]), 0.f);
+        if (tid == 0) s_gauge[0] = kp.zcol[2 * N];
+        __syncthreads();
+    }
+    // 4. the correction coefficients in double, one thread per mode (while
+    //    the other warps store)
     if (tid < MB) {
         const int c = tid, col = col0 + c;
         if (s_valid[c]) {
-            const double k = s_k[c], mult = s_mult[c];
-            ColP cp{make_float2(0.f, 0.f), make_float2(0.f, 0.f), float(k), 0.f, 0.f, 0};
+            const float k = s_kf[c];
+            const double mult = s_mult[c];
+            ColP cp{make_float2(0.f, 0.f), make_float2(0.f, 0.f), k, 0.f, 0.f, 0};
             if (s_corr[c]) {
                 const BcCoef b = bc_correction(kp, col, s_bs[c]);
-                cp = ColP{make_float2(float(b.P.x), float(b.P.y)), make_float2(float(b.Q.x), float(b.Q.y)), float(k),
+                cp = ColP{make_float2(float(b.P.x), float(b.P.y)), make_float2(float(b.Q.x), float(b.Q.y)), k,
                           float(b.ekH), float(b.iden), 1};
                 s_gauge[c] += mult * b.corr0;
             }
             kp.colp[col] = cp;
         }
     }
-    // column 0 (block 0): the coefficients and gauge term of k_column_zero
-    if (bid == 0) {
-        for (int n = tid; n < N; n += bs) F[n] = make_float4(float(kp.zcol[n]), 0.f, float(kp.zcol[N + n]), 0.f);
-        if (tid == 0) s_gauge[0] = kp.zcol[2 * N];
-    }
-    __syncthreads();
     // 5. coefficients of psi_i (plane 0) and dpsi_i/dz (plane 1, before the
     //    factor 2/Hbar), whole rows
     for (int t = tid; t < 2 * N * MB; t += bs) {
@@ -1900,6 +1931,7 @@ __device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
             __stcs(sp + size_t(fn) * M + col, f ? make_float2(v.z, v.w) : make_float2(v.x, v.y));
         }
     }
+    __syncthreads();
     if (tid == 0) {
         double g = 0.0;
         for (int c = 0; c < MB; ++c) g += s_gauge[c];
@@ -1908,9 +1940,9 @@ __device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
 }
 
 template <int W, int R>
-__global__ void __launch_bounds__(64 * W) k_column_tc(KP kp) { column_tc_body<W, R>(kp, blockIdx.x); }
+__global__ void __launch_bounds__(64 * W, 2) k_column_tc(KP kp) { column_tc_body<W, R>(kp, blockIdx.x); }
 template <int W, int R>
-__global__ void __launch_bounds__(64 * W) k_column_tc_batch(const __grid_constant__ ColBatch b) {
+__global__ void __launch_bounds__(64 * W, 2) k_column_tc_batch(const __grid_constant__ ColBatch b) {
     const int s = batch_system(b.starts, b.nsys, blockIdx.x);
     column_tc_body<W, R>(b.kp[s], blockIdx.x - b.starts[s]);
 }
@@ -3593,7 +3625,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         upc(t.twx, kp.twx32);
         upc(t.twy, kp.twy32);
         if (mixed) {
-            // per mode, in extended precision: 1/k, e^{-kH}, 1/den and
+            // per mode, in extended precision: k, e^{-kH}, 1/den and
             // -(1 - Gt e^{-2kH})/den, den = 1 - Gb Gt e^{-2kH}; both
             // differences from 1 are formed as (1 - G) - G expm1(-2kH), which
             // does not cancel as k -> 0 with G -> 1 (metal walls, small eps_w)
@@ -3612,11 +3644,13 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
                 const long double e = expl(-k * H), em = expm1l(-2.0L * k * H);
                 const long double den = (1.0L - Gb * Gt) - Gb * Gt * em;
                 const long double ct = (1.0L - Gt) - Gt * em;
-                mt[col] = make_double4_32a(double(1.0L / k), double(e), double(1.0L / den), double(-ct / den));
+                mt[col] = make_double4_32a(double(k), double(e), double(1.0L / den), double(-ct / den));
             }
             double4_32a* dp = carve<double4_32a>(cur, mt.size());
             cudaMemcpy(dp, mt.data(), mt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice);
             kp.mtab = dp;
+            k_mode_flags<<<(M + 255) / 256, 256>>>(kp, dp);
+            if (cudaStreamSynchronize(0) != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
         }
         if (cudaGetLastError() != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
     }
