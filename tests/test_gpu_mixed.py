@@ -10,6 +10,7 @@ import pytest
 
 from gpu_helpers import (TOL_MIXED_ENERGY, TOL_MIXED_FORCE, gpu_solve, mixed_energy_tol, oracle_params, plan_for,
                          rel_l2, rel_max)
+from oracle import chebyshev as cheb
 from oracle import solver as osolver
 from paper_2101_07088_b300 import build, dpslab, synth
 
@@ -78,6 +79,45 @@ def test_mixed_small_ragged_and_paper_rule():
     pos, q = synth.electrolyte(40, 2.0, 2.0, 0.045, 0.955, seed=5)
     _check(osolver.solve(pos, q, P), gpu_solve(plan_for(P, 40, precision=dpslab.MIXED), pos, q), "paper-rule",
            mixed_energy_tol(P, 40))
+
+
+@pytest.mark.parametrize("case", ["ragged", "c2"])
+def test_interpolation_stage_against_oracle_quadrature(case):
+    """The interpolation stage of the mixed form on its own (Sec. 5.2.2
+    step 7): the far parts a solve returns (the warp-per-charge gather, with
+    one and with eight warps per block) against the oracle's quadrature of
+    the very grid fields that solve produced, widened to FP64. The ragged
+    grid (48 x 40 x 37) has supports that wrap around the period; two
+    charges of each sign get zero strength, whose potential still needs the
+    far part."""
+    if case == "ragged":
+        P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, 40, nz=37, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
+        pos, q = synth.electrolyte(102, 24.0, 20.0, 1.0, 19.0, seed=3)
+    else:
+        pos, q, p = synth.workload("c2_jumps_n16384")
+        P = oracle_params(p["Lx"], p["Ly"], p["H"], p["gw"], p["tol"], p["nx"], p["ny"], nz=p["nz"],
+                          eps_b=p["eps_b"], eps_t=p["eps_t"], r_cut=p["r_cut"])
+    q = np.array(q, dtype=float)
+    zero = np.concatenate([np.nonzero(q > 0)[0][:2], np.nonzero(q < 0)[0][:2]])
+    q[zero] = 0.0
+    n = len(q)
+    zn = cheb.nodes(P["nz"], P["a"], P["b"])
+    wz = cheb.quadrature_weights(P["nz"], P["a"], P["b"])
+    plan = plan_for(P, n, precision=dpslab.MIXED)
+    k0 = plan.tuning()
+    for knob in (1, 8):
+        plan.set_tuning(k0[:4] + [knob] + k0[5:])
+        out = gpu_solve(plan, pos, q)
+        far = plan.debug_fetch(2, n)
+        fields = np.moveaxis(plan.debug_fetch(1, n), -1, 0)
+        ref = osolver.interpolate(fields, pos[:, 0], pos[:, 1], pos[:, 2], P, zn, wz)
+        errs = [rel_max(far[:, c], ref[:, c]) for c in range(4)]
+        print(case, "knob", knob, "far-part errors (phi, E):", [f"{e:.1e}" for e in errs])
+        # FP32 fields and an FP32 quadrature: a few FP32 roundoff units of
+        # the largest value
+        assert max(errs) < 1e-6, (knob, errs)
+        assert np.all(out["force"][zero] == 0.0)
+    plan.close()
 
 
 def test_mixed_against_fp64_gpu_at_one_million_charges():
