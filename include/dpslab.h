@@ -234,7 +234,7 @@ int dpslab_bd_last_retries(const dpslab_plan* plan);
  *   knobs[5]  column kernel (per-mode BVP): k modes per block: 8, 16 or 32
  *             (DPSLAB_MIXED with tensor-core z transforms), 4 or 8 (with
  *             CUDA-core z transforms), 2 or 4 (DPSLAB_FP64)
- *   knobs[6]  spreading: x grid columns per thread: 1 or 2 (DPSLAB_MIXED),
+ *   knobs[6]  spreading: x grid columns per thread: 1, 2 or 4 (DPSLAB_MIXED),
  *             1 (DPSLAB_FP64)
  * A value sets the block size and shared memory of its kernel; the results
  * do not depend on it beyond the order of floating-point sums. The FFT knobs

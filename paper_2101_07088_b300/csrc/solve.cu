@@ -618,8 +618,8 @@ __global__ void k_scatter_sources_f(KP kp) {
 
 // CPT neighbouring x columns per thread (256 / CPT threads for the 16 x 16
 // tile): the per-source work of a thread (the loop, the weight loads, the
-// zero test) is shared by 8 CPT multiply-adds. The default is 2; the
-// autotuner may choose 1.
+// zero test) is shared by 8 CPT multiply-adds, issued as 4 CPT packed FP32x2
+// FMAs over node pairs. The default is 2; the autotuner may choose 1 or 4.
 constexpr int kSpreadCptM = 2;
 
 template <int CPT>
@@ -638,11 +638,12 @@ __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
     const int first = kp.tile_start[bk], total = kp.tile_start[bk + 1] - first;
     const SrcF* src = kp.srcsf + first;
     const float ig2 = kp.f.ig2, s1 = kp.f.s1norm;
-    float ai[CPT][kSlabM], ao[CPT][kSlabM];
+    // accumulators as node pairs (j, j + 1): one packed FP32x2 FMA per pair
+    float2 ai[CPT][kSlabM / 2], ao[CPT][kSlabM / 2];
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
 #pragma unroll
-        for (int j = 0; j < kSlabM; ++j) ai[c][j] = ao[c][j] = 0.f;
+        for (int j = 0; j < kSlabM / 2; ++j) ai[c][j] = ao[c][j] = make_float2(0.f, 0.f);
     for (int base = 0; base < total; base += B) {
         const int nb = min(B, total - base);
         // weight tables: entry b < B of the loop fills source b's x and z
@@ -692,21 +693,25 @@ __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
         for (int b = 0; b < nb; ++b) {
             const float wy = s_wy[b][ly];
             if (wy != 0.f) {
-                float w[CPT];
+                float2 w[CPT];
 #pragma unroll
-                for (int c = 0; c < CPT; ++c) w[c] = s_wx[b][lx + c] * wy;
+                for (int c = 0; c < CPT; ++c) {
+                    const float v = s_wx[b][lx + c] * wy;
+                    w[c] = make_float2(v, v);
+                }
                 const float4 z0 = *reinterpret_cast<const float4*>(&s_wz[b][0]);
                 const float4 z1 = *reinterpret_cast<const float4*>(&s_wz[b][4]);
-                const float wz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+                const float2 wz[4] = {make_float2(z0.x, z0.y), make_float2(z0.z, z0.w), make_float2(z1.x, z1.y),
+                                      make_float2(z1.z, z1.w)};
 #pragma unroll
-                for (int j = 0; j < kSlabM; ++j)
+                for (int j = 0; j < kSlabM / 2; ++j)
 #pragma unroll
-                    for (int c = 0; c < CPT; ++c) ai[c][j] = fmaf(w[c], wz[j], ai[c][j]);
+                    for (int c = 0; c < CPT; ++c) ai[c][j] = __ffma2_rn(w[c], wz[j], ai[c][j]);
                 if (s_over[b]) {
 #pragma unroll
-                    for (int j = 0; j < kSlabM; ++j)
+                    for (int j = 0; j < kSlabM / 2; ++j)
 #pragma unroll
-                        for (int c = 0; c < CPT; ++c) ao[c][j] = fmaf(w[c], wz[j], ao[c][j]);
+                        for (int c = 0; c < CPT; ++c) ao[c][j] = __ffma2_rn(w[c], wz[j], ao[c][j]);
                 }
             }
         }
@@ -723,8 +728,8 @@ __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
 #pragma unroll
                 for (int c = 0; c < CPT; ++c) {
                     if (gx + c < kp.nx) {
-                        rho[g + c] = ai[c][j];
-                        rho[G + g + c] = ao[c][j];
+                        rho[g + c] = j & 1 ? ai[c][j / 2].y : ai[c][j / 2].x;
+                        rho[G + g + c] = j & 1 ? ao[c][j / 2].y : ao[c][j / 2].x;
                     }
                 }
             }
@@ -3298,7 +3303,9 @@ size_t col_smem(const dpslab_plan* pl, int cb) {
     return size_t(cb) * (nz + (mixed ? ((2 - nz) & 15) : 0)) * (4 * csz + 2 * rsz);
 }
 using SpreadKernel = void (*)(KP);
-SpreadKernel spread_mixed_kernel(int cpt) { return cpt == 1 ? k_spread_f32<1> : k_spread_f32<2>; }
+SpreadKernel spread_mixed_kernel(int cpt) {
+    return cpt == 1 ? k_spread_f32<1> : cpt == 2 ? k_spread_f32<2> : k_spread_f32<4>;
+}
 
 // Carve the plan's workspace from base (every per-solve device array: grids,
 // charge arrays, buckets, cell list, partial sums); with base == nullptr it
@@ -4302,7 +4309,7 @@ bool apply_kernel_knob(dpslab_plan* pl, int which, int v) {
         pl->kp.n_col_blocks = (M + v - 1) / v;
         return true;
     }
-    if (v != 1 && !(mixed && v == 2)) return false;
+    if (v != 1 && !(mixed && (v == 2 || v == 4))) return false;
     pl->spread_cpt = v;
     return true;
 }

@@ -76,7 +76,7 @@ def test_kernel_knobs_keep_results(prec):
     # column kernel modes per block: the tensor-core form (this grid: Nz 37,
     # ny (nx/2+1) = 1000 even) 8, 16, 32; FP64 2, 4
     cols = (8, 16, 32) if prec == dpslab.MIXED else (2, 4)
-    cpts = (1, 2) if prec == dpslab.MIXED else (1,)
+    cpts = (1, 2, 4) if prec == dpslab.MIXED else (1,)
     for w in (1, 2, 4, 8):
         for cb in cols:
             for cpt in cpts:
@@ -85,7 +85,7 @@ def test_kernel_knobs_keep_results(prec):
                 U1, f1 = _solve(plan, pt, qt)
                 assert abs(U1 - U0) <= tol * abs(U0) and rel_l2(f1, f0) <= tol, (w, cb, cpt)
     plan.set_tuning(k0)
-    for bad in ([3, k0[5], k0[6]], [k0[4], 64, k0[6]], [k0[4], k0[5], 4]) + (
+    for bad in ([3, k0[5], k0[6]], [k0[4], 64, k0[6]], [k0[4], k0[5], 3], [k0[4], k0[5], 8]) + (
             ([k0[4], k0[5], 2],) if prec == dpslab.FP64 else ()):
         with pytest.raises(dpslab.DpslabError):
             plan.set_tuning(k0[:4] + bad)

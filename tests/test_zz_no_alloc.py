@@ -4,14 +4,16 @@ dpslab_near_field_static serves callers that cannot call cudaMalloc (code
 running inside an allocator, under a memory pool that must not grow, or in
 a loop that reserves everything at start-up): its scratch space is a
 file-scope device array. Here its output is checked against the near-field
-part that the planned entry point dpslab_solve computes, on two calls in a
-row (the array keeps the previous call's contents, so the second call also
-checks that the library clears what it must). This file is collected last.
+part that the planned entry point dpslab_solve computes, and directly
+against the oracle's near field, each on two calls in a row (the array keeps
+the previous call's contents, so the second call also checks that the
+library clears what it must). This file is collected last.
 """
 import numpy as np
 import pytest
 
 from gpu_helpers import TOL_FP64, gpu_solve, oracle_params, plan_for, rel_max
+from oracle import solver as osolver
 from paper_2101_07088_b300 import build, dpslab, synth
 
 pytestmark = pytest.mark.gpu
@@ -57,6 +59,20 @@ def test_static_near_field_matches_planned_solve_twice():
         assert rc == 0
         assert rel_max(got[:, 0], ref[:, 0]) < TOL_FP64
         assert rel_max(got[:, 1:], ref[:, 1:]) < TOL_FP64
+
+
+def test_static_near_field_matches_oracle():
+    """The same entry point held directly to the oracle's near field (the
+    plain double loop over all pairs and one image per wall), on a small
+    box with unequal walls: two calls in a row with different charges."""
+    P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, 40, nz=37, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
+    for n, seed in ((300, 41), (517, 42)):
+        pos, q = synth.electrolyte(n, 24.0, 20.0, 1.0, 19.0, seed=seed)
+        phin, En = osolver.near_field(pos[:, 0], pos[:, 1], pos[:, 2], q, P, method="pairs")
+        rc, got = _static(_params(P), pos, q)
+        assert rc == 0
+        assert rel_max(got[:, 0], phin) < TOL_FP64
+        assert rel_max(got[:, 1:], En) < TOL_FP64
 
 
 def test_static_near_field_rejects_oversize_inputs():
