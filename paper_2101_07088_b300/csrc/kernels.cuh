@@ -153,6 +153,11 @@ struct KP {
     const float *jt0_32, *jjt0_32, *jtH_32, *jjtH_32;
     const double4_32a* mtab;  // [ny nxh] mixed: per mode k, e^{-kH}, 1/den, -(1 - Gt e^{-2kH})/den (k only: no correction)
     const unsigned short* zimg_fwd;   // split bf16 images of the z transforms (tensor cores)
+    // mixed, tensor-core form: 1 at the nodes rho_o can reach (within H_E of
+    // a charge of C_over, so z_j in [-H_E, 3 H_E] or [H - 3 H_E, H + H_E]),
+    // 0 elsewhere; null: every node. rho_o is neither stored, transformed in
+    // x and y, nor read by the z transform at the other nodes (it is zero there).
+    const unsigned char* o_node;
     const unsigned short* zimg_inv;
     int* sorted_idx;
     // reductions
@@ -182,6 +187,12 @@ struct KP {
     double* out_phi;
     double* out_force;
 };
+
+// row (of the 2 nz ny rows of both densities) of rho_o at a node it cannot reach
+__device__ __forceinline__ bool o_row_zero(const KP& kp, int row) {
+    const int nzy = kp.nz * kp.ny;
+    return kp.o_node && row >= nzy && !kp.o_node[(row - nzy) / kp.ny];
+}
 
 template <class R> struct Prec;
 template <> struct Prec<double> {

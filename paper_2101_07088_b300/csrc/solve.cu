@@ -638,6 +638,13 @@ __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
     const int first = kp.tile_start[bk], total = kp.tile_start[bk + 1] - first;
     const SrcF* src = kp.srcsf + first;
     const float ig2 = kp.f.ig2, s1 = kp.f.s1norm;
+    // the slab's nodes where rho_o is stored (it is zero, and never read, at
+    // the nodes it cannot reach)
+    unsigned onm = 0xffu;
+    if (kp.o_node) {
+        onm = 0u;
+        for (int j = 0; j < kSlabM && js + j < kp.nz; ++j) onm |= unsigned(kp.o_node[js + j] != 0) << j;
+    }
     // accumulators as node pairs (j, j + 1): one packed FP32x2 FMA per pair
     float2 ai[CPT][kSlabM / 2], ao[CPT][kSlabM / 2];
 #pragma unroll
@@ -725,11 +732,12 @@ __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
         for (int j = 0; j < kSlabM; ++j) {
             if (js + j < kp.nz) {
                 const size_t g = (size_t(js + j) * kp.ny + gy) * kp.nx + gx;
+                const bool on = (onm >> j) & 1u;   // rho_o is zero (and unread) elsewhere
 #pragma unroll
                 for (int c = 0; c < CPT; ++c) {
                     if (gx + c < kp.nx) {
                         rho[g + c] = j & 1 ? ai[c][j / 2].y : ai[c][j / 2].x;
-                        rho[G + g + c] = j & 1 ? ao[c][j / 2].y : ao[c][j / 2].x;
+                        if (on) rho[G + g + c] = j & 1 ? ao[c][j / 2].y : ao[c][j / 2].x;
                     }
                 }
             }
@@ -748,6 +756,35 @@ template <> __device__ __forceinline__ const float2* twy_of<float>(const KP& kp)
 // xy FFT, forward: rows along x (two real rows packed into one complex FFT),
 // then columns along y, for both densities
 // ---------------------------------------------------------------------------
+// Rows of the pairs p0 .. p0 + P - 1 of a forward x transform (two rows
+// each, P <= 64) that are rho_o at nodes it cannot reach: bit q of a (b)
+// for the first (second) row of pair q. Those rows are never written, so
+// they are read as zero (a pair can straddle two planes when ny is odd);
+// all is set when no pair of the block needs a transform.
+struct FftxZero {
+    unsigned long long a, b;
+    bool all;
+};
+__device__ __forceinline__ FftxZero fftx_zero_rows(const KP& kp, int p0, int P, int npairs) {
+    FftxZero z{0ull, 0ull, false};
+    if (!kp.o_node) return z;
+    bool all = true;
+    for (int q = 0; q < P; ++q) {
+        const int pr = p0 + q;
+        if (pr >= npairs) continue;
+        const bool za = o_row_zero(kp, 2 * pr), zb = o_row_zero(kp, 2 * pr + 1);
+        if (za) z.a |= 1ull << q;
+        if (zb) z.b |= 1ull << q;
+        all = all && za && zb;
+    }
+    z.all = all;
+    return z;
+}
+// plane (of the 2 nz planes of both densities) of rho_o at a node it cannot reach
+__device__ __forceinline__ bool fft_plane_skip(const KP& kp, int plane) {
+    return kp.o_node && plane >= kp.nz && !kp.o_node[plane - kp.nz];
+}
+
 template <class R>
 __global__ void k_fftx_fwd(KP kp, int P) {
     using C = typename Prec<R>::C;
@@ -763,6 +800,9 @@ __global__ void k_fftx_fwd(KP kp, int P) {
     C* spec = static_cast<C*>(kp.spec);
     const int npairs = kp.nz * kp.ny;           // 2 nz ny rows
     const int p0 = blockIdx.x * P;
+    const FftxZero zr = fftx_zero_rows(kp, p0, P, npairs);
+    if (zr.all) return;
+    const unsigned long long skip = zr.a & zr.b;
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t / n, x = t - p * n, pr = p0 + p;
         C v;
@@ -770,8 +810,8 @@ __global__ void k_fftx_fwd(KP kp, int P) {
         v.y = R(0);
         if (pr < npairs) {
             const size_t r0 = 2 * size_t(pr);
-            v.x = rho[r0 * n + x];
-            v.y = rho[(r0 + 1) * n + x];
+            if (!((zr.a >> p) & 1ull)) v.x = rho[r0 * n + x];
+            if (!((zr.b >> p) & 1ull)) v.y = rho[(r0 + 1) * n + x];
         }
         A[p * n + x] = v;
     }
@@ -779,7 +819,7 @@ __global__ void k_fftx_fwd(KP kp, int P) {
     const C* Rr = block_fft(A, B, tw, n, P, kp.radx, kp.nradx, -1);
     for (int t = threadIdx.x; t < P * nxh; t += blockDim.x) {
         const int p = t / nxh, k = t - p * nxh, pr = p0 + p;
-        if (pr >= npairs) continue;
+        if (pr >= npairs || ((skip >> p) & 1ull)) continue;
         const C Z = Rr[p * n + k];
         const C Zm = cconj(Rr[p * n + (n - k) % n]);
         const C sum = cadd(Z, Zm), d = csub(Z, Zm);
@@ -796,6 +836,7 @@ template <class R>
 __global__ void k_ffty_fwd(KP kp, int TK) {
     using C = typename Prec<R>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
+    if (fft_plane_skip(kp, blockIdx.y)) return;
     C* sm = reinterpret_cast<C*>(smraw);
     const int n = kp.ny, nxh = kp.nxh;
     C* tw = sm;
@@ -838,14 +879,17 @@ __global__ void k_fftx_fwd_p2(KP kp, int P, int) {
     C* spec = static_cast<C*>(kp.spec);
     const int npairs = kp.nz * kp.ny;
     const int p0 = blockIdx.x * P;
+    const FftxZero zr = fftx_zero_rows(kp, p0, P, npairs);
+    if (zr.all) return;
+    const unsigned long long skip = zr.a & zr.b;
     auto load = [&](int q, int i) {
         C v;
         v.x = R(0);
         v.y = R(0);
         if (p0 + q < npairs) {
             const size_t r0 = 2 * size_t(p0 + q);
-            v.x = rho[r0 * n + i];
-            v.y = rho[(r0 + 1) * n + i];
+            if (!((zr.a >> q) & 1ull)) v.x = rho[r0 * n + i];
+            if (!((zr.b >> q) & 1ull)) v.y = rho[(r0 + 1) * n + i];
         }
         return v;
     };
@@ -854,7 +898,7 @@ __global__ void k_fftx_fwd_p2(KP kp, int P, int) {
     __syncthreads();
     for (int t = threadIdx.x; t < P * nxh; t += blockDim.x) {
         const int p = t / nxh, k = t - p * nxh, pr = p0 + p;
-        if (pr >= npairs) continue;
+        if (pr >= npairs || ((skip >> p) & 1ull)) continue;
         const C Z = buf[p * np + pad16(k)];
         const C Zm = cconj(buf[p * np + pad16((n - k) & (n - 1))]);
         const C sum = cadd(Z, Zm), d = csub(Z, Zm);
@@ -873,6 +917,7 @@ __global__ void k_ffty_fwd_p2(KP kp, int TK, int) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int logn = L, n = 1 << L;
     const int nxh = kp.nxh;
+    if (fft_plane_skip(kp, blockIdx.y)) return;
     C* tw = reinterpret_cast<C*>(smraw);
     C* buf = tw + n;
     C* base = static_cast<C*>(kp.spec) + size_t(blockIdx.y) * n * nxh;
@@ -1414,7 +1459,8 @@ __device__ __forceinline__ void column_zero_body(const KP& kp) {
     const int N = kp.nz, M = kp.ny * kp.nxh, tid = threadIdx.x, bs = blockDim.x;
     const float2* sp = static_cast<const float2*>(kp.spec);
     // column 0 of both spectra: the plane sums of rho_i, rho_o (real)
-    for (int t = tid; t < 2 * N; t += bs) s_v[t / N][t % N] = double(sp[size_t(t) * M].x);
+    for (int t = tid; t < 2 * N; t += bs)
+        s_v[t / N][t % N] = (t >= N && kp.o_node && !kp.o_node[t - N]) ? 0.0 : double(sp[size_t(t) * M].x);
     __syncthreads();
     const int m = N - 1, JE = (N + 1) / 2, JO = N / 2;
     for (int t = tid; t < 2 * JE; t += bs) {
@@ -2399,7 +2445,7 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_fwd(KP kp) {
     auto prep = [](int, int) {};
     auto epi = [](int, int, int, float*, int) {};
     zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock,
-              kp.zspin);
+              kp.zspin, kp.o_node);
 }
 
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
@@ -3549,6 +3595,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         if (pl->ztensor) bytes += 2 * align_up(t.zimg_fwd.size() * sizeof(unsigned short));   // bf16 images
         bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
         if (mixed) bytes += align_up(size_t(M) * sizeof(double4_32a));   // per-mode correction factors
+        bytes += align_up(N);                                              // rho_o node mask
         pl->device_bytes += int64_t(bytes);   // table bytes, taken up again below
     }
     if (!measure) {
@@ -3581,6 +3628,22 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             dst = dp;
         };
         upf(t.zn, kp.zn32);
+        kp.o_node = nullptr;
+        if (pl->ztensor) {
+            // the nodes rho_o can reach: a charge of C_over lies in (0, 2 H_E]
+            // or [H - 2 H_E, H), its support within H_E of it (a relative
+            // margin of 1e-6 keeps every node the spreading's test admits)
+            const double he = d.HE * (1.0 + 1e-6), H = p->H;
+            const size_t N = size_t(nz);
+            std::vector<unsigned char> on(N);
+            for (size_t j = 0; j < N; ++j) {
+                const double z = t.zn[j];
+                on[j] = ((z >= -he && z <= 3.0 * he) || (z >= H - 3.0 * he && z <= H + he)) ? 1 : 0;
+            }
+            unsigned char* dp = carve<unsigned char>(cur, N);
+            cudaMemcpy(dp, on.data(), N, cudaMemcpyHostToDevice);
+            kp.o_node = dp;
+        }
         {
             std::vector<double> hinv(t.zn.size(), 0.0);
             for (size_t j = 1; j < hinv.size(); ++j) hinv[j] = 0.5 / double(j);
@@ -3699,6 +3762,9 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             if (e != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
             pl->device_bytes += int64_t(pl->work_bytes);
             bind_work(pl, static_cast<char*>(pl->work));
+            // rho_o at the nodes it cannot reach is never written: zero once
+            // (nothing reads it; this keeps the grid clean for inspection)
+            if (cudaMemset(kp.rho, 0, 2 * pl->G * rsz) != cudaSuccess) { release(pl); return DPSLAB_ERR_CUDA; }
         }
     }
     if (cudaMallocHost(&pl->h_scal, 16 * sizeof(double)) != cudaSuccess ||

@@ -182,6 +182,8 @@ __device__ __forceinline__ void put8(unsigned short* sB, int n, int k0, const fl
     *reinterpret_cast<uint4*>(sB + 2 * kZPieceB + e) = w3;
 }
 
+// mask1 (optional, Nz bytes): rows of plane 1 to read; the others are zero
+// (rho_o at the nodes it cannot reach) and are not loaded.
 // The GEMM over nplanes planes of rows (= Nz) x ncols floats (row stride ld,
 // plane stride pstride floats; ld and the plane base multiples of 4 floats),
 // written back in place. A image: three pieces, zimg_index layout.
@@ -205,7 +207,7 @@ static_assert(size_t(kZK) * kZOStride * 4 <= kZSmemB, "staged outputs fit the B 
 template <class Prep, class Epi>
 __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aimg, float* base, int nplanes,
                                           size_t pstride, int rows, int ncols, size_t ld, int* status, Prep prep,
-                                          Epi epi, int nblk, long long spin) {
+                                          Epi epi, int nblk, long long spin, const unsigned char* mask1 = nullptr) {
     extern __shared__ __align__(1024) unsigned char zsm[];
     unsigned short* sA = reinterpret_cast<unsigned short*>(zsm);
     unsigned short* sB = reinterpret_cast<unsigned short*>(zsm + kZSmemA);
@@ -223,6 +225,16 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     const int ntiles = nplanes * tiles_per_plane;
     // this thread's 4 columns (4 cq .. 4 cq + 3) and 8 rows (8 g .. 8 g + 7)
     const int cq = tid & (kZN / 4 - 1), g = tid / (kZN / 4), r0 = g * kZRows;
+    // which of this thread's rows (bit kb 8 + i: row kb 128 + r0 + i) plane 1 reads
+    unsigned rows1 = 0xffffu;
+    if (mask1) {
+        rows1 = 0u;
+        for (int kb = 0; kb < 2; ++kb)
+            for (int i = 0; i < kZRows; ++i) {
+                const int r = kb * kZBlock + r0 + i;
+                if (r < rows && mask1[r]) rows1 |= 1u << (kb * kZRows + i);
+            }
+    }
     // the largest |entry| of this thread's four columns over all rows of the
     // tile, from each thread's partial maxima cm
     auto colmax = [&](const float* cm, float* amax) {
@@ -275,11 +287,12 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
         const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
         const int c = c0 + 4 * cq;
         const float* src = base + size_t(plane) * pstride + c;
+        const unsigned rm = plane == 1 ? rows1 >> (kb * kZRows) : 0xffu;
 #pragma unroll
         for (int i = 0; i < kZRows; ++i) {
             const int r = kb * kZBlock + r0 + i;
-            rv[i] = (r < rows && c < ncols) ? __ldg(reinterpret_cast<const float4*>(src + size_t(r) * ld))
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            rv[i] = (r < rows && c < ncols && ((rm >> i) & 1u)) ? __ldg(reinterpret_cast<const float4*>(src + size_t(r) * ld))
+                                                                : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
 
@@ -293,11 +306,12 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
             const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
             const int c = c0 + 4 * cq;
             const float* src = base + size_t(plane) * pstride + c;
+            const unsigned rm = plane == 1 ? rows1 >> kZRows : 0xffu;
 #pragma unroll
             for (int i = 0; i < kZRows; ++i) {
                 const int r = kZBlock + r0 + i;
-                rw[i] = (r < rows && c < ncols) ? __ldg(reinterpret_cast<const float4*>(src + size_t(r) * ld))
-                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                rw[i] = (r < rows && c < ncols && ((rm >> i) & 1u)) ? __ldg(reinterpret_cast<const float4*>(src + size_t(r) * ld))
+                                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         };
         if (int(blockIdx.x) < ntiles) load2(blockIdx.x);
