@@ -153,11 +153,14 @@ struct KP {
     const float *jt0_32, *jjt0_32, *jtH_32, *jjtH_32;
     const double4_32a* mtab;  // [ny nxh] mixed: per mode k, e^{-kH}, 1/den, -(1 - Gt e^{-2kH})/den (k only: no correction)
     const unsigned short* zimg_fwd;   // split bf16 images of the z transforms (tensor cores)
-    // mixed, tensor-core form: 1 at the nodes rho_o can reach (within H_E of
-    // a charge of C_over, so z_j in [-H_E, 3 H_E] or [H - 3 H_E, H + H_E]),
-    // 0 elsewhere; null: every node. rho_o is neither stored, transformed in
-    // x and y, nor read by the z transform at the other nodes (it is zero there).
-    const unsigned char* o_node;
+    // mixed, tensor-core form, per node: bit 0 where rho_o can be non-zero
+    // (within H_E of a charge of C_over: z_j in [-H_E, 3 H_E] or
+    // [H - 3 H_E, H + H_E]), bit 1 where the interpolation reads the fields
+    // (z_j in [-H_E, H + H_E]); null: every node has both. rho_o is neither
+    // stored, transformed in x and y, nor read by the forward z transform
+    // without bit 0; the inverse transforms neither form nor store the
+    // fields without bit 1.
+    const unsigned char* node_mask;
     const unsigned short* zimg_inv;
     int* sorted_idx;
     // reductions
@@ -191,7 +194,26 @@ struct KP {
 // row (of the 2 nz ny rows of both densities) of rho_o at a node it cannot reach
 __device__ __forceinline__ bool o_row_zero(const KP& kp, int row) {
     const int nzy = kp.nz * kp.ny;
-    return kp.o_node && row >= nzy && !kp.o_node[(row - nzy) / kp.ny];
+    return kp.node_mask && row >= nzy && !(kp.node_mask[(row - nzy) / kp.ny] & 1);
+}
+
+// row (of the nz ny rows of a field grid) at a node the interpolation never reads
+__device__ __forceinline__ bool f_row_skip(const KP& kp, int row) {
+    return kp.node_mask && !(kp.node_mask[row / kp.ny] & 2);
+}
+// rows r0 .. r0 + P - 1 (P <= 64) skipped by f_row_skip: bit p for row r0 + p
+// (rows past nrows count as skipped)
+__device__ __forceinline__ unsigned long long f_rows_skip(const KP& kp, int r0, int P, int nrows) {
+    if (!kp.node_mask) {
+        unsigned long long m = 0ull;
+        for (int p = 0; p < P; ++p)
+            if (r0 + p >= nrows) m |= 1ull << p;
+        return m;
+    }
+    unsigned long long m = 0ull;
+    for (int p = 0; p < P; ++p)
+        if (r0 + p >= nrows || f_row_skip(kp, r0 + p)) m |= 1ull << p;
+    return m;
 }
 
 template <class R> struct Prec;

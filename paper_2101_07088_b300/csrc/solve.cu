@@ -641,9 +641,9 @@ __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
     // the slab's nodes where rho_o is stored (it is zero, and never read, at
     // the nodes it cannot reach)
     unsigned onm = 0xffu;
-    if (kp.o_node) {
+    if (kp.node_mask) {
         onm = 0u;
-        for (int j = 0; j < kSlabM && js + j < kp.nz; ++j) onm |= unsigned(kp.o_node[js + j] != 0) << j;
+        for (int j = 0; j < kSlabM && js + j < kp.nz; ++j) onm |= unsigned(kp.node_mask[js + j] & 1) << j;
     }
     // accumulators as node pairs (j, j + 1): one packed FP32x2 FMA per pair
     float2 ai[CPT][kSlabM / 2], ao[CPT][kSlabM / 2];
@@ -767,7 +767,7 @@ struct FftxZero {
 };
 __device__ __forceinline__ FftxZero fftx_zero_rows(const KP& kp, int p0, int P, int npairs) {
     FftxZero z{0ull, 0ull, false};
-    if (!kp.o_node) return z;
+    if (!kp.node_mask) return z;
     bool all = true;
     for (int q = 0; q < P; ++q) {
         const int pr = p0 + q;
@@ -782,7 +782,7 @@ __device__ __forceinline__ FftxZero fftx_zero_rows(const KP& kp, int p0, int P, 
 }
 // plane (of the 2 nz planes of both densities) of rho_o at a node it cannot reach
 __device__ __forceinline__ bool fft_plane_skip(const KP& kp, int plane) {
-    return kp.o_node && plane >= kp.nz && !kp.o_node[plane - kp.nz];
+    return kp.node_mask && plane >= kp.nz && !(kp.node_mask[plane - kp.nz] & 1);
 }
 
 template <class R>
@@ -971,6 +971,7 @@ template <class R, int L>
 __global__ void __launch_bounds__(512, sizeof(R) == sizeof(float) ? 2 : 1) k_ffty_inv_p2(KP kp, int TK, int) {
     using C = typename Prec<R>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
+    if (kp.node_mask && !(kp.node_mask[blockIdx.y] & 2)) return;   // a plane the interpolation never reads
     C* tw = reinterpret_cast<C*>(smraw);
     C* buf = tw + (1 << L);
     // -i k_y psi first: it reads psi before the psi transform overwrites it
@@ -997,13 +998,16 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int) {
     const size_t S = size_t(nrows) * nxh;
     const R kxs = R(kTwoPi / kp.Lx);
     const int r0 = blockIdx.x * P;
+    // rows past the grid or at nodes the interpolation never reads
+    const unsigned long long skip = f_rows_skip(kp, r0, P, nrows);
+    if (skip == (P >= 64 ? ~0ull : (1ull << P) - 1ull)) return;
     // sequence q = 2 p + w: row r0 + p; w = 0 packs (phi, E_x), w = 1 (E_y, E_z)
     auto load = [&](int q, int k) {
         const int p = q >> 1, w = q & 1, row = r0 + p;
         C z;
         z.x = R(0);
         z.y = R(0);
-        if (row >= nrows) return z;
+        if ((skip >> p) & 1ull) return z;
         const bool hi = k >= nxh;
         const int kk = hi ? n - k : k;
         const bool edge = kk == 0 || kk == n / 2;
@@ -1037,7 +1041,7 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int) {
     const R s = R(kp.inv_nxny);
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t / n, x = t - p * n, row = r0 + p;
-        if (row >= nrows) continue;
+        if ((skip >> p) & 1ull) continue;
         const C u = buf[(2 * p) * np + pad16(x)], v = buf[(2 * p + 1) * np + pad16(x)];
         fields[size_t(row) * n + x] = Prec<R>::v4(u.x * s, u.y * s, v.x * s, v.y * s);
     }
@@ -1460,7 +1464,7 @@ __device__ __forceinline__ void column_zero_body(const KP& kp) {
     const float2* sp = static_cast<const float2*>(kp.spec);
     // column 0 of both spectra: the plane sums of rho_i, rho_o (real)
     for (int t = tid; t < 2 * N; t += bs)
-        s_v[t / N][t % N] = (t >= N && kp.o_node && !kp.o_node[t - N]) ? 0.0 : double(sp[size_t(t) * M].x);
+        s_v[t / N][t % N] = (t >= N && kp.node_mask && !(kp.node_mask[t - N] & 1)) ? 0.0 : double(sp[size_t(t) * M].x);
     __syncthreads();
     const int m = N - 1, JE = (N + 1) / 2, JO = N / 2;
     for (int t = tid; t < 2 * JE; t += bs) {
@@ -2444,8 +2448,8 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_fwd(KP kp) {
     const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
     auto prep = [](int, int) {};
     auto epi = [](int, int, int, float*, int) {};
-    zgemm_run(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock,
-              kp.zspin, kp.o_node);
+    zgemm_run<true>(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock,
+              kp.zspin, kp.node_mask);
 }
 
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
@@ -2490,8 +2494,8 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
             v[i + 1] = im;
         }
     };
-    zgemm_run(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock,
-              kp.zspin);
+    zgemm_run<false>(kp.zimg_inv, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock,
+              kp.zspin, nullptr, kp.node_mask);
 }
 
 // ---------------------------------------------------------------------------
@@ -2502,6 +2506,7 @@ template <class R>
 __global__ void k_ffty_inv(KP kp, int TK) {
     using C = typename Prec<R>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
+    if (kp.node_mask && !(kp.node_mask[blockIdx.y] & 2)) return;   // a plane the interpolation never reads
     C* sm = reinterpret_cast<C*>(smraw);
     const int n = kp.ny, nxh = kp.nxh;
     C* tw = sm;
@@ -2562,11 +2567,14 @@ __global__ void k_fftx_inv(KP kp, int P) {
     const size_t S = size_t(nrows) * nxh;
     const R kxs = R(kTwoPi / kp.Lx);
     const int r0 = blockIdx.x * P;
+    // rows past the grid or at nodes the interpolation never reads
+    const unsigned long long skip = f_rows_skip(kp, r0, P, nrows);
+    if (skip == (P >= 64 ? ~0ull : (1ull << P) - 1ull)) return;
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t / n, k = t - p * n, row = r0 + p;
         C z1, z2;
         z1.x = z1.y = z2.x = z2.y = R(0);
-        if (row < nrows) {
+        if (!((skip >> p) & 1ull)) {
             const bool hi = k >= nxh;
             const int kk = hi ? n - k : k;
             C a = spec[size_t(row) * nxh + kk];
@@ -2594,7 +2602,7 @@ __global__ void k_fftx_inv(KP kp, int P) {
     const R s = R(kp.inv_nxny);
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t / n, x = t - p * n, row = r0 + p;
-        if (row >= nrows) continue;
+        if ((skip >> p) & 1ull) continue;
         const C u = Rr[(2 * p) * n + x], v = Rr[(2 * p + 1) * n + x];
         fields[size_t(row) * n + x] = Prec<R>::v4(u.x * s, u.y * s, v.x * s, v.y * s);
     }
@@ -3595,7 +3603,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         if (pl->ztensor) bytes += 2 * align_up(t.zimg_fwd.size() * sizeof(unsigned short));   // bf16 images
         bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
         if (mixed) bytes += align_up(size_t(M) * sizeof(double4_32a));   // per-mode correction factors
-        bytes += align_up(N);                                              // rho_o node mask
+        bytes += align_up(N);                                              // node masks
         pl->device_bytes += int64_t(bytes);   // table bytes, taken up again below
     }
     if (!measure) {
@@ -3628,21 +3636,25 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             dst = dp;
         };
         upf(t.zn, kp.zn32);
-        kp.o_node = nullptr;
+        kp.node_mask = nullptr;
         if (pl->ztensor) {
-            // the nodes rho_o can reach: a charge of C_over lies in (0, 2 H_E]
-            // or [H - 2 H_E, H), its support within H_E of it (a relative
-            // margin of 1e-6 keeps every node the spreading's test admits)
+            // bit 0, the nodes rho_o can reach: a charge of C_over lies in
+            // (0, 2 H_E] or [H - 2 H_E, H), its support within H_E of it; bit
+            // 1, the nodes the interpolation reads: within H_E of a charge in
+            // (0, H) (a relative margin of 1e-6 keeps every node the
+            // spreading's and the interpolation's test admits)
             const double he = d.HE * (1.0 + 1e-6), H = p->H;
             const size_t N = size_t(nz);
             std::vector<unsigned char> on(N);
             for (size_t j = 0; j < N; ++j) {
                 const double z = t.zn[j];
-                on[j] = ((z >= -he && z <= 3.0 * he) || (z >= H - 3.0 * he && z <= H + he)) ? 1 : 0;
+                const bool o = (z >= -he && z <= 3.0 * he) || (z >= H - 3.0 * he && z <= H + he);
+                const bool f = z >= -he && z <= H + he;
+                on[j] = (o ? 1 : 0) | (f ? 2 : 0);
             }
             unsigned char* dp = carve<unsigned char>(cur, N);
             cudaMemcpy(dp, on.data(), N, cudaMemcpyHostToDevice);
-            kp.o_node = dp;
+            kp.node_mask = dp;
         }
         {
             std::vector<double> hinv(t.zn.size(), 0.0);
@@ -3962,6 +3974,7 @@ int xy_transforms(dpslab_plan* pl, const KP& kp, cudaStream_t st, bool inverse) 
 template <class R>
 int wall_setup(dpslab_plan* pl, const double* planes, cudaStream_t st) {
     KP kp = pl->kp;
+    kp.node_mask = nullptr;   // the set-up transforms every plane
     const int M = kp.ny * kp.nxh;
     const size_t G = size_t(kp.nz) * kp.ny * kp.nx, P2 = 2 * size_t(kp.ny) * kp.nx;
     char* base = static_cast<char*>(pl->sig_mem);

@@ -182,8 +182,11 @@ __device__ __forceinline__ void put8(unsigned short* sB, int n, int k0, const fl
     *reinterpret_cast<uint4*>(sB + 2 * kZPieceB + e) = w3;
 }
 
-// mask1 (optional, Nz bytes): rows of plane 1 to read; the others are zero
-// (rho_o at the nodes it cannot reach) and are not loaded.
+// mask1 (optional, Nz bytes): rows of plane 1 to read where bit 0 is set;
+// the others are zero (rho_o at the nodes it cannot reach) and are not
+// loaded. smask (optional, Nz bytes): output rows to form and store where
+// bit 1 is set (the nodes the interpolation reads); the others are left as
+// they are.
 // The GEMM over nplanes planes of rows (= Nz) x ncols floats (row stride ld,
 // plane stride pstride floats; ld and the plane base multiples of 4 floats),
 // written back in place. A image: three pieces, zimg_index layout.
@@ -204,10 +207,11 @@ static_assert(size_t(kZK) * kZOStride * 4 <= kZSmemB, "staged outputs fit the B 
 // two accumulators (four in all, the whole 512 columns of tensor memory).
 // The outputs are written, in place, after every K row of the tile has been
 // read; the next tile's values load from the last split on.
-template <class Prep, class Epi>
+template <bool kRead1, class Prep, class Epi>
 __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aimg, float* base, int nplanes,
                                           size_t pstride, int rows, int ncols, size_t ld, int* status, Prep prep,
-                                          Epi epi, int nblk, long long spin, const unsigned char* mask1 = nullptr) {
+                                          Epi epi, int nblk, long long spin, const unsigned char* mask1 = nullptr,
+                                          const unsigned char* smask = nullptr) {
     extern __shared__ __align__(1024) unsigned char zsm[];
     unsigned short* sA = reinterpret_cast<unsigned short*>(zsm);
     unsigned short* sB = reinterpret_cast<unsigned short*>(zsm + kZSmemA);
@@ -225,16 +229,21 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     const int ntiles = nplanes * tiles_per_plane;
     // this thread's 4 columns (4 cq .. 4 cq + 3) and 8 rows (8 g .. 8 g + 7)
     const int cq = tid & (kZN / 4 - 1), g = tid / (kZN / 4), r0 = g * kZRows;
-    // which of this thread's rows (bit kb 8 + i: row kb 128 + r0 + i) plane 1 reads
-    unsigned rows1 = 0xffffu;
-    if (mask1) {
-        rows1 = 0u;
-        for (int kb = 0; kb < 2; ++kb)
-            for (int i = 0; i < kZRows; ++i) {
-                const int r = kb * kZBlock + r0 + i;
-                if (r < rows && mask1[r]) rows1 |= 1u << (kb * kZRows + i);
+    // rows plane 1 reads (mask1 bit 0) and output rows formed and stored
+    // (smask bit 1): bit r % 32 of word r / 32 (filled by warp 0 below)
+    __shared__ unsigned s_read1[2 * kZBlock / 32], s_store[2 * kZBlock / 32];
+    if (warp == 0) {
+        for (int i = 0; i < 2 * kZBlock / 32; ++i) {
+            const int r = 32 * i + lane;
+            const unsigned rd = __ballot_sync(0xffffffffu, !mask1 || (r < rows && (mask1[r] & 1)));
+            const unsigned sv = __ballot_sync(0xffffffffu, !smask || (r < rows && (smask[r] & 2)));
+            if (lane == 0) {
+                s_read1[i] = rd;
+                s_store[i] = sv;
             }
+        }
     }
+    auto stored = [&](int r) { return (s_store[r >> 5] >> (r & 31)) & 1u; };
     // the largest |entry| of this thread's four columns over all rows of the
     // tile, from each thread's partial maxima cm
     auto colmax = [&](const float* cm, float* amax) {
@@ -281,16 +290,23 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
+    // kRead1: which of this thread's rows plane 1 reads (bit kb 8 + i: row
+    // kb 128 + r0 + i; r0 is a multiple of 8, so each block's 8 rows lie in
+    // one mask word)
+    unsigned rows1 = 0xffffu;
+    if (kRead1)
+        rows1 = ((s_read1[r0 >> 5] >> (r0 & 31)) & 0xffu) | (((s_read1[(kZBlock + r0) >> 5] >> (r0 & 31)) & 0xffu) << 8);
 
     float4 rv[kZRows];
     auto load = [&](int t, int kb) {         // K rows kb*128 + r0 .. + 7 of tile t
         const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
         const int c = c0 + 4 * cq;
         const float* src = base + size_t(plane) * pstride + c;
-        const unsigned rm = plane == 1 ? rows1 >> (kb * kZRows) : 0xffu;
+        const int rb0 = kb * kZBlock + r0;
+        const unsigned rm = (kRead1 && plane == 1) ? rows1 >> (kb * kZRows) : 0xffu;
 #pragma unroll
         for (int i = 0; i < kZRows; ++i) {
-            const int r = kb * kZBlock + r0 + i;
+            const int r = rb0 + i;
             rv[i] = (r < rows && c < ncols && ((rm >> i) & 1u)) ? __ldg(reinterpret_cast<const float4*>(src + size_t(r) * ld))
                                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -306,10 +322,11 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
             const int plane = t / tiles_per_plane, c0 = (t - plane * tiles_per_plane) * kZN;
             const int c = c0 + 4 * cq;
             const float* src = base + size_t(plane) * pstride + c;
-            const unsigned rm = plane == 1 ? rows1 >> kZRows : 0xffu;
+            const int rb1 = kZBlock + r0;
+            const unsigned rm = (kRead1 && plane == 1) ? rows1 >> kZRows : 0xffu;
 #pragma unroll
             for (int i = 0; i < kZRows; ++i) {
-                const int r = kZBlock + r0 + i;
+                const int r = rb1 + i;
                 rw[i] = (r < rows && c < ncols && ((rm >> i) & 1u)) ? __ldg(reinterpret_cast<const float4*>(src + size_t(r) * ld))
                                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
             }
@@ -416,7 +433,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[h + i] += u[i];
                 }
-                if (rg < rows && wv > 0) epi(plane, rg, c0 + cc, v, wv);
+                if (rg < rows && wv > 0 && stored(rg)) epi(plane, rg, c0 + cc, v, wv);
 #pragma unroll
                 for (int i = 0; i < 32; i += 4)
                     *reinterpret_cast<float4*>(O + r * kZOStride + cc + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
@@ -424,8 +441,9 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
                 float* dst = base + size_t(plane) * pstride + c0 + 4 * lane;
                 if (4 * lane < w) {
                     for (int rr = warp; rr < kZBlock && rb * kZBlock + rr < rows; rr += kZThreads / 32)
-                        __stcs(reinterpret_cast<float4*>(dst + size_t(rb * kZBlock + rr) * ld),
-                               *reinterpret_cast<const float4*>(O + rr * kZOStride + 4 * lane));
+                        if (stored(rb * kZBlock + rr))
+                            __stcs(reinterpret_cast<float4*>(dst + size_t(rb * kZBlock + rr) * ld),
+                                   *reinterpret_cast<const float4*>(O + rr * kZOStride + 4 * lane));
                 }
                 __syncthreads();
             }
@@ -454,7 +472,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
             for (int i = 0; i < 16; ++i) v[h + i] += u[i];
         }
         const int wv = min(32, w - cc);
-        if (r < rows && wv > 0) epi(plane, r, c0 + cc, v, wv);
+        if (r < rows && wv > 0 && stored(r)) epi(plane, r, c0 + cc, v, wv);
         // staged a quarter (32 rows) at a time, then stored whole rows: warp w
         // stores rows w and w + 16 of the quarter, lane l columns 4l .. 4l + 3
         float* dst = base + size_t(plane) * pstride + c0 + 4 * lane;
@@ -468,7 +486,7 @@ __device__ __forceinline__ void zgemm_run(const unsigned short* __restrict__ aim
             if (4 * lane < w) {
                 for (int rr = warp; rr < kZORows; rr += kZThreads / 32) {
                     const int row = q * kZORows + rr;
-                    if (row < rows)
+                    if (row < rows && stored(row))
                         __stcs(reinterpret_cast<float4*>(dst + size_t(row) * ld),
                                *reinterpret_cast<const float4*>(sO + rr * kZOStride + 4 * lane));
                 }
