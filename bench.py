@@ -54,32 +54,51 @@ def parse():
 # ---------------------------------------------------------------------------
 # roofline bookkeeping: algorithmic work per launch of each stage
 # ---------------------------------------------------------------------------
-def stage_work(d, n, n_over, wbytes=8):
+def node_fractions(params, d):
+    """Fractions of the z nodes where rho_o can be non-zero (within H_E of a
+    charge within 2 H_E of a wall: z_j in [-H_E, 3 H_E] or [H - 3 H_E, H + H_E])
+    and where the interpolation reads the fields (z_j in [-H_E, H + H_E]):
+    the mixed form's tensor-core path moves those planes only."""
+    import numpy as np
+    from paper_2101_07088_b300 import dpslab
+    zn = dpslab.table(params, 0)
+    he, H = d["HE"], params.H
+    fo = np.mean(((zn >= -he) & (zn <= 3 * he)) | ((zn >= H - 3 * he) & (zn <= H + he)))
+    ff = np.mean((zn >= -he) & (zn <= H + he))
+    return float(fo), float(ff)
+
+
+def stage_work(d, n, n_over, wbytes=8, fo=1.0, ff=1.0):
     """Algorithmic bytes (HBM-bound stages) or flops (ALU-bound stages) of
     one launch of each stage, for the grid and charge counts of the solve.
     G = nx ny nz grid points, S = nz ny (nx/2+1) complex modes, M = ny (nx/2+1)
-    columns. Bytes count every grid array read or written once; flops count
-    the operations the stage's algorithm cannot avoid."""
+    columns; fo, ff the fractions of the nodes where rho_o can be non-zero
+    and where the interpolation reads the fields (1 when every plane moves).
+    Bytes count every grid array read or written once where the path needs
+    it; flops count the operations the stage's algorithm cannot avoid."""
     nx, ny, nz = d["nx"], d["ny"], d["nz"]
     G, S = nx * ny * nz, nz * ny * (nx // 2 + 1)
     M = ny * (nx // 2 + 1)
     c = 2 * wbytes                     # complex
     lg = lambda v: math.log2(v)
     out = {
-        # rho_i over the whole grid, rho_o over its share, charges read once
-        "spread": ("hbm", (G + G * n_over / max(n, 1)) * wbytes + n * 4 * wbytes),
-        "fft_x_fwd": ("hbm", 2 * G * wbytes + 2 * S * c),
-        "fft_y_fwd": ("hbm", 2 * 2 * S * c),
-        # z transforms: both spectra in and out (tensor cores; FP32 storage)
-        "z_fwd": ("hbm", 4 * S * c),
-        "z_inv": ("hbm", 4 * S * c),
+        # rho_i over the whole grid, rho_o over its planes, charges read once
+        "spread": ("hbm", (G + G * fo) * wbytes + n * 4 * wbytes),
+        "fft_x_fwd": ("hbm", (1 + fo) * (G * wbytes + S * c)),
+        "fft_y_fwd": ("hbm", 2 * (1 + fo) * S * c),
+        # z transforms (tensor cores; FP32 storage): node values of both
+        # densities in, coefficients out; coefficients in, psi and dpsi/dz
+        # out at the planes the interpolation reads
+        "z_fwd": ("hbm", (1 + fo) * S * c + 2 * S * c),
+        "z_inv": ("hbm", 2 * S * c + 2 * ff * S * c),
         # per-mode BVP: coefficients of both densities in, psi and dpsi/dz
         # coefficients out (mixed); the FP64 form also transforms in z, dense
         # N/2 x N/2 blocks, even/odd, real x complex = 4 flops per entry
         "bvp": ("hbm", 4 * S * c) if wbytes == 4 else ("alu", M * 4 * (2 * (nz // 2 + 1) ** 2) * 4.0),
-        "fft_y_inv": ("hbm", 2 * S * c + 3 * S * c),
-        "fft_x_inv": ("hbm", 3 * S * c + 4 * G * wbytes),
-        "interp": ("hbm", 4 * G * wbytes + n * 8 * wbytes),
+        "fft_y_inv": ("hbm", ff * (2 * S * c + 3 * S * c)),
+        "fft_x_inv": ("hbm", ff * (3 * S * c + 4 * G * wbytes)),
+        # the fields once over the planes the supports reach, the charges' windows
+        "interp": ("hbm", ff * 4 * G * wbytes + n * 8 * wbytes),
         "near": ("hbm", n * 12 * wbytes),
         "prepare": ("hbm", n * 8 * wbytes),
         "finish": ("hbm", n * 12 * wbytes),
@@ -101,7 +120,7 @@ SINGLE_KERNEL_STAGES = ("fft_x_fwd", "fft_y_fwd", "z_fwd", "bvp", "z_inv", "fft_
 # from one ncu capture of the mixed path on the 262144-charge quarter box
 # (512 x 512 x 128 grid, 131584 columns); scaled to another grid by its column
 # count. Only kernels unchanged since their capture are listed.
-NCU_TRAFFIC_C3Q = {"interp": 393214976 + 10461184, "fft_x_inv": 404299520 + 485086464}
+NCU_TRAFFIC_C3Q = {"interp": 393214976 + 10461184}
 NCU_TRAFFIC_COLUMNS = 512 * 257
 
 
@@ -653,7 +672,8 @@ def main():
 
     # roofline of the dominant stage
     over = int(np.sum((pos[:, 2] <= 2 * d["HE"]) | (pos[:, 2] >= p["H"] - 2 * d["HE"])))
-    work, fft_flops = stage_work(d, n, over, wbytes=4 if args.precision != "fp64" else 8)
+    fo, ff = node_fractions(dpslab.make_params(precision=prec, **p), d) if args.precision == "mixed" else (1.0, 1.0)
+    work, fft_flops = stage_work(d, n, over, wbytes=4 if args.precision != "fp64" else 8, fo=fo, ff=ff)
     stage_ms = {k: v / prof_steps for k, v in stage_sum.items()}
     top = max(SINGLE_KERNEL_STAGES, key=lambda k: stage_ms.get(k, 0.0))
     pk = peaks()
