@@ -626,7 +626,10 @@ template <int CPT>
 __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
     constexpr int B = kSpreadBatchM;
     constexpr int NT = kTile * kTile / CPT, XG = kTile / CPT;
-    __shared__ float s_wx[B][kTile + 1];
+    // x-weight rows padded to a multiple of CPT, so that a thread's CPT
+    // weights are one vector load
+    constexpr int WXS = CPT == 1 ? kTile + 1 : kTile + CPT;
+    __shared__ __align__(16) float s_wx[B][WXS];
     __shared__ float s_wy[B][kTile + 1];
     __shared__ __align__(16) float s_wz[B][kWzStride];
     __shared__ int s_over[B];
@@ -697,13 +700,24 @@ __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
             }
         }
         __syncthreads();
+#pragma unroll 2
         for (int b = 0; b < nb; ++b) {
             const float wy = s_wy[b][ly];
             if (wy != 0.f) {
+                float wxv[CPT];
+                if constexpr (CPT == 4) {
+                    const float4 t = *reinterpret_cast<const float4*>(&s_wx[b][lx]);
+                    wxv[0] = t.x; wxv[1] = t.y; wxv[2] = t.z; wxv[3] = t.w;
+                } else if constexpr (CPT == 2) {
+                    const float2 t = *reinterpret_cast<const float2*>(&s_wx[b][lx]);
+                    wxv[0] = t.x; wxv[1] = t.y;
+                } else {
+                    wxv[0] = s_wx[b][lx];
+                }
                 float2 w[CPT];
 #pragma unroll
                 for (int c = 0; c < CPT; ++c) {
-                    const float v = s_wx[b][lx + c] * wy;
+                    const float v = wxv[c] * wy;
                     w[c] = make_float2(v, v);
                 }
                 const float4 z0 = *reinterpret_cast<const float4*>(&s_wz[b][0]);
