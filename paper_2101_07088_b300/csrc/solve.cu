@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(kTile * kTile / CPT) k_spread_f32(KP kp) {
             }
         }
         __syncthreads();
-#pragma unroll 2
+#pragma unroll 4
         for (int b = 0; b < nb; ++b) {
             const float wy = s_wy[b][ly];
             if (wy != 0.f) {
