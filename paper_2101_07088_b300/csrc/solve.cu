@@ -2495,7 +2495,10 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
             // or nodes outside [-H_E, H + H_E] are masked to exactly zero
             {
                 const float m = (cp.corr && zin) ? cp.iden : 0.f;
-                const float e1 = expf(-fminf(cp.k * z, 88.f)), e3 = expf(-fminf(cp.k * (H - z), 88.f));
+                // the fast exponential: its error grows as |x| 2^-24 of the
+                // result, and amplitude x e^{-x} <= 0.37 amplitude, so each
+                // term is within 2e-8 of its amplitude (below FP32 rounding)
+                const float e1 = __expf(-fminf(cp.k * z, 88.f)), e3 = __expf(-fminf(cp.k * (H - z), 88.f));
                 const float e2 = e3 * cp.ekH, e4 = e1 * cp.ekH;
                 const float f = plane == 0 ? m : cp.k * m;
                 const float a = plane == 0 ? -(e1 - Gt * e2) * f : (e1 + Gt * e2) * f;
