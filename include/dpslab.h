@@ -393,7 +393,7 @@ int dpslab_batch_last_launch_count(const dpslab_batch* batch);
  *   DPSLAB_BATCH_STREAMS (the default): each system's whole solve runs on
  *     its stream, and the streams run freely beside one another;
  *   DPSLAB_BATCH_WAVES: the waves described above, with the column stage of
- *     each wave as one launch per kind of column kernel (and per 22 systems)
+ *     each wave as one launch per kind of column kernel (and per 21 systems)
  *     over all its systems' k modes.
  * Both give the same results. dpslab_batch_set_schedule returns
  * DPSLAB_ERR_INVALID_ARG for any other value; the next solve captures a new

@@ -161,6 +161,15 @@ struct KP {
     // without bit 0; the inverse transforms neither form nor store the
     // fields without bit 1.
     const unsigned char* node_mask;
+    // mixed, tensor-core form: rho_o's Chebyshev coefficients come from its
+    // node values at the o_pairs node pairs (a, m - a) it can reach, formed
+    // in the column kernel instead of the tensor-core transform: o_pair[p] =
+    // a (a <= m - a), o_fwd[p][n] = the forward transform's entry for node a
+    // and coefficient n, applied to v_a + v_{m-a} for even n and
+    // v_a - v_{m-a} for odd n. o_pairs = 0: the z transform handles rho_o.
+    int o_pairs;
+    const int* o_pair;
+    const float* o_fwd;
     const unsigned short* zimg_inv;
     int* sorted_idx;
     // reductions

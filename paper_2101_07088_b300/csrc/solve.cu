@@ -85,7 +85,8 @@ __device__ double block_sum(double v) {
 // The column stage of up to kBatchMaxSys systems in one launch: their
 // parameter blocks travel as the kernel's (read-only) parameter, 32 KB at
 // most, so that the kernels read them as they read a single system's.
-constexpr int kBatchMaxSys = 22;
+constexpr int kBatchMaxSys = 21;
+constexpr int kMaxOPairs = 32;      // node pairs of rho_o transformed in the column kernel (else by the z GEMM)
 struct ColBatch {
     int nsys;
     int starts[kBatchMaxSys + 1];        // first column block of each system
@@ -1748,6 +1749,11 @@ __device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
             if (t < N * MB) F[c * NP + n] = make_float4(vi[u].x * scale, vi[u].y * scale, vo[u].x * scale, vo[u].y * scale);
         }
     }
+    // 1b. rho_o's coefficients from its node values at the pairs (a, m - a)
+    //     it can reach (Sec. 5.2.2 step 3, the DCT-I form): S = v_a + v_{m-a}
+    //     and D = v_a - v_{m-a} per mode and pair (staged where the sweeps'
+    //     Q goes), then coefficient n = sum_p o_fwd[p][n] (S_p or D_p by the
+    //     parity of n), threads over consecutive n
     __syncthreads();
 
     // 2. two-way banded sweeps: lane (mode c, chain ch, side) of warp w < W. Side
@@ -2462,8 +2468,61 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_fwd(KP kp) {
     const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
     auto prep = [](int, int) {};
     auto epi = [](int, int, int, float*, int) {};
-    zgemm_run<true>(kp.zimg_fwd, base, 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock,
+    // plane 1 (rho_o) only when the column kernel does not form its
+    // coefficients from its node pairs
+    zgemm_run<true>(kp.zimg_fwd, base, kp.o_pairs > 0 ? 1 : 2, pstride, kp.nz, int(ld), ld, kp.status, prep, epi, (kp.nz + kZBlock - 1) / kZBlock,
               kp.zspin, kp.node_mask);
+}
+
+// rho_o's Chebyshev coefficients (Sec. 5.2.2 step 3, the DCT-I form of the
+// extrema grid) from its node values at the o_pairs node pairs (a, m - a) it
+// can reach, in place in plane 1 of the spectra: the other nodes are zero,
+// so each coefficient is a sum over those pairs only, S = v_a + v_{m-a} for
+// even n and D = v_a - v_{m-a} for odd n (cos(pi n (m - a)/m) = (-1)^n
+// cos(pi n a/m)). One block per kOcCols columns: the pairs' values of its
+// columns are read first, then every coefficient row of its columns written.
+constexpr int kOcCols = 64;
+__global__ void __launch_bounds__(256) k_o_coeffs(KP kp) {
+    __shared__ float4 sSD[kMaxOPairs][kOcCols];
+    const int N = kp.nz, M = kp.ny * kp.nxh, P = kp.o_pairs, m = N - 1;
+    const int col0 = blockIdx.x * kOcCols, tid = threadIdx.x;
+    float2* const sp = static_cast<float2*>(kp.spec) + size_t(N) * M;   // plane 1
+    for (int t = tid; t < P * kOcCols; t += blockDim.x) {
+        const int q = t / kOcCols, c = t - q * kOcCols, col = col0 + c, a = kp.o_pair[q];
+        float2 va = make_float2(0.f, 0.f), vb = va;
+        if (col < M) {
+            va = sp[size_t(a) * M + col];
+            if (m - a != a) vb = sp[size_t(m - a) * M + col];
+        }
+        sSD[q][c] = make_float4(va.x + vb.x, va.y + vb.y, va.x - vb.x, va.y - vb.y);
+    }
+    __syncthreads();
+    // thread: column c, coefficients n0 .. n0 + 7 for n0 = 8 (g + 4 k); the
+    // warp's lanes are 32 columns sharing n0, so the transform entries are
+    // one broadcast load per 4 and each column's S, D one load per pair
+    const int c = tid % kOcCols, g = tid / kOcCols, col = col0 + c;
+    if (col < M) {
+        for (int n0 = 8 * g; n0 < N; n0 += 8 * (256 / kOcCols)) {
+            float2 acc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = make_float2(0.f, 0.f);
+            for (int q = 0; q < P; ++q) {
+                const float4 wa = __ldg(reinterpret_cast<const float4*>(kp.o_fwd + size_t(q) * N + n0));
+                const float4 wb = __ldg(reinterpret_cast<const float4*>(kp.o_fwd + size_t(q) * N + n0 + 4));
+                const float4 v = sSD[q][c];
+                const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int i = 0; i < 8; i += 2) {   // even n: S, odd n: D
+                    acc[i].x = fmaf(w[i], v.x, acc[i].x);
+                    acc[i].y = fmaf(w[i], v.y, acc[i].y);
+                    acc[i + 1].x = fmaf(w[i + 1], v.z, acc[i + 1].x);
+                    acc[i + 1].y = fmaf(w[i + 1], v.w, acc[i + 1].y);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sp[size_t(n0 + i) * M + col] = acc[i];
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
@@ -3621,6 +3680,8 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         bytes += align_up(nx * sizeof(float2)) + align_up(ny * sizeof(float2));
         if (mixed) bytes += align_up(size_t(M) * sizeof(double4_32a));   // per-mode correction factors
         bytes += align_up(N);                                              // node masks
+        if (pl->ztensor)                                                   // rho_o's pair transform
+            bytes += align_up(kMaxOPairs * sizeof(int)) + align_up(size_t(kMaxOPairs) * N * sizeof(float));
         pl->device_bytes += int64_t(bytes);   // table bytes, taken up again below
     }
     if (!measure) {
@@ -3654,6 +3715,9 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         };
         upf(t.zn, kp.zn32);
         kp.node_mask = nullptr;
+        kp.o_pairs = 0;
+        kp.o_pair = nullptr;
+        kp.o_fwd = nullptr;
         if (pl->ztensor) {
             // bit 0, the nodes rho_o can reach: a charge of C_over lies in
             // (0, 2 H_E] or [H - 2 H_E, H), its support within H_E of it; bit
@@ -3672,6 +3736,36 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             unsigned char* dp = carve<unsigned char>(cur, N);
             cudaMemcpy(dp, on.data(), N, cudaMemcpyHostToDevice);
             kp.node_mask = dp;
+            // rho_o's coefficients from its node pairs (a, m - a), a <= m - a,
+            // either node reachable: the forward transform of the extrema
+            // grid (DCT-I form), fhat_n = (2/m) w_n sum_j w_j v_j cos(pi n j/m),
+            // w = 1/2 at the ends, by the symmetry cos(pi n (m - a)/m) =
+            // (-1)^n cos(pi n a/m); with more than kMaxOPairs pairs (or N not
+            // a multiple of 8) the z transform keeps rho_o
+            const int m = int(N) - 1;
+            std::vector<int> pairs;
+            for (int a = 0; 2 * a <= m; ++a)
+                if ((on[a] | on[m - a]) & 1) pairs.push_back(a);
+            int* pp = carve<int>(cur, kMaxOPairs);
+            float* fw = carve<float>(cur, size_t(kMaxOPairs) * N);
+            kp.o_pairs = 0;
+            if (!pairs.empty() && int(pairs.size()) <= kMaxOPairs && m > 0 && N % 8 == 0) {
+                std::vector<float> tab(pairs.size() * N);
+                for (size_t q = 0; q < pairs.size(); ++q) {
+                    const int a = pairs[q];
+                    const double wa = (a == 0 || a == m) ? 0.5 : 1.0;
+                    for (int n = 0; n < int(N); ++n) {
+                        const double wn = (n == 0 || n == m) ? 0.5 : 1.0;
+                        const double ang = 3.14159265358979323846 * double((size_t(n) * a) % (2 * size_t(m))) / m;
+                        tab[q * N + n] = float(2.0 / m * wa * wn * std::cos(ang));
+                    }
+                }
+                cudaMemcpy(pp, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice);
+                cudaMemcpy(fw, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
+                kp.o_pairs = int(pairs.size());
+            }
+            kp.o_pair = pp;
+            kp.o_fwd = fw;
         }
         {
             std::vector<double> hinv(t.zn.size(), 0.0);
@@ -4655,6 +4749,8 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         mark(4);
         LAUNCH(k_column_zero<<<1, kZeroThreads, 0, st>>>(kp));
         if (pl->ztensor) LAUNCH(k_zgemm_fwd<<<pl->zgrid, kZThreads, kZSmem, st>>>(kp));
+        if (pl->ztensor && kp.o_pairs > 0)
+            LAUNCH(k_o_coeffs<<<(kp.ny * kp.nxh + kOcCols - 1) / kOcCols, 256, 0, st>>>(kp));
         mark(5);
         }
         if (column) {

@@ -80,3 +80,18 @@ def compare(ref, out, tol=TOL_FP64):
     print("parity errors:", {k: f"{v:.2e}" for k, v in errs.items()})
     assert all(v < tol for v in errs.values()), errs
     return errs
+
+
+def rho_o_pair_launch(P):
+    """1 when the tensor-core form forms rho_o's coefficients by its own
+    launch (rho_o reaches at most 32 node pairs (a, m - a) and N_z is a
+    multiple of 8), else 0 (the z transform keeps it): nodes within H_E of a
+    charge within 2 H_E of a wall, z_j in [-H_E, 3 H_E] or [H - 3 H_E, H + H_E]."""
+    from oracle import chebyshev as cheb
+    nz = P["nz"]
+    zn = cheb.nodes(nz, P["a"], P["b"])
+    he, H, m = P["HE"] * (1 + 1e-6), P["H"], nz - 1
+    on = ((zn >= -he) & (zn <= 3 * he)) | ((zn >= H - 3 * he) & (zn <= H + he))
+    pairs = sum(1 for a in range(m // 2 + 1) if on[a] or on[m - a])
+    return int(0 < pairs <= 32 and nz % 8 == 0)
+

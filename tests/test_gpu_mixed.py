@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from gpu_helpers import (TOL_MIXED_ENERGY, TOL_MIXED_FORCE, gpu_solve, mixed_energy_tol, oracle_params, plan_for,
-                         rel_l2, rel_max)
+                         rel_l2, rel_max, rho_o_pair_launch)
 from oracle import chebyshev as cheb
 from oracle import solver as osolver
 from paper_2101_07088_b300 import build, dpslab, synth
@@ -57,8 +57,9 @@ def test_mixed_against_oracle(name, _, prec, plabel):
 
 def test_tensor_z_transform_runs():
     # Nz <= 128 with ny (nx/2+1) even: the z transforms run as two tensor-core
-    # GEMM launches around the BVP kernel (two launches more than the SIMT
-    # form)
+    # GEMM launches around the BVP kernel, and rho_o's coefficients (20 node
+    # pairs here) as one CUDA-core launch: three launches more than the SIMT
+    # form
     pos, q, p = synth.workload("c2_jumps_n16384")
     P = oracle_params(p["Lx"], p["Ly"], p["H"], p["gw"], p["tol"], p["nx"], p["ny"], nz=p["nz"],
                       eps_b=p["eps_b"], eps_t=p["eps_t"], r_cut=p["r_cut"])
@@ -67,7 +68,7 @@ def test_tensor_z_transform_runs():
         plan = plan_for(P, len(q), precision=prec)
         gpu_solve(plan, pos, q)
         counts[prec] = plan.last_launch_count()
-    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 2, counts
+    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 3, counts
 
 
 def test_mixed_small_ragged_and_paper_rule():
@@ -157,7 +158,7 @@ def test_mixed_fallback_to_cuda_core_z_transform(ny, nz):
 @pytest.mark.parametrize("nz", [136, 200, 256])
 def test_tensor_z_transform_in_two_blocks(nz):
     # 128 < Nz <= 256: the z transforms run on the tensor cores in 2 x 2
-    # blocks of 128 (two launches more than the CUDA-core form), within the
+    # blocks of 128 (two or three launches more than the CUDA-core form), within the
     # bar against the oracle and close to the CUDA-core form
     P = oracle_params(24.0, 20.0, 20.0, 1.0, 1e-4, 48, 40, nz=nz, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
     pos, q = synth.electrolyte(800, 24.0, 20.0, 1.0, 19.0, seed=8)
@@ -168,7 +169,8 @@ def test_tensor_z_transform_in_two_blocks(nz):
         out[prec] = gpu_solve(plan, pos, q)
         counts[prec] = plan.last_launch_count()
         _check(ref, out[prec], f"two blocks nz={nz} prec={prec}", mixed_energy_tol(P, 800))
-    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 2, counts
+    # plus rho_o's coefficients by their own launch when it reaches few nodes
+    assert counts[dpslab.MIXED] == counts[dpslab.MIXED_SIMT] + 2 + rho_o_pair_launch(P), counts
     assert rel_l2(out[dpslab.MIXED]["force"], out[dpslab.MIXED_SIMT]["force"]) < TOL_MIXED_FORCE
 
 
