@@ -4717,6 +4717,10 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         if (kp.mixed) LAUNCH(k_near_f32<<<(n + 127) / 128, 128, 0, pl->side>>>(kp));
         else LAUNCH(k_near<double><<<(n + 127) / 128, 128, 0, pl->side>>>(kp));
         if (prof) DPS_CUDA(cudaEventRecord(pl->ev_near[1], pl->side));
+        // the near potential at the origin (the gauge) needs only the
+        // charges: beside the far field too (with wall charges it also
+        // needs their interpolation, so it stays on the solve's stream)
+        if (!kp.sigma_on) LAUNCH(k_origin<<<nb, kChargeThreads, 0, pl->side>>>(kp));
         DPS_CUDA(cudaEventRecord(pl->ev_join, pl->side));
     }
     const dim3 gs(kp.ntiles, kp.nslabs);
@@ -4807,7 +4811,7 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
     }
     if (fork) DPS_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
     mark(11);
-    LAUNCH(k_origin<<<nb, kChargeThreads, 0, st>>>(kp));
+    if (!fork || kp.sigma_on) LAUNCH(k_origin<<<nb, kChargeThreads, 0, st>>>(kp));
     LAUNCH(k_final_gauge<<<1, 1024, 0, st>>>(kp));
     LAUNCH(k_assemble<<<nb, kChargeThreads, 0, st>>>(kp));
     LAUNCH(k_final_energy<<<1, 1024, 0, st>>>(kp));
