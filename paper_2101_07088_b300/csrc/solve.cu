@@ -2948,6 +2948,18 @@ __global__ void k_near_f32(KP kp) {
     const float rc2 = float(kp.r_cut * kp.r_cut);
     const bool wrap3x = kp.ncx >= 3, wrap3y = kp.ncy >= 3;
     const int nxc = wrap3x ? 3 : kp.ncx, nyc = wrap3y ? 3 : kp.ncy;
+    // the neighbour columns and rows (wrapped once: the unwrapped index lies
+    // in [-1, n]) and the shifts of their cell-relative offsets, once
+    int xcs[3], ycs[3];
+    float sxhs[3], syhs[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        const int xu = wrap3x ? cx - 1 + o : o, yu = wrap3y ? cy - 1 + o : o;
+        xcs[o] = xu < 0 ? xu + kp.ncx : (xu >= kp.ncx ? xu - kp.ncx : xu);
+        ycs[o] = yu < 0 ? yu + kp.ncy : (yu >= kp.ncy ? yu - kp.ncy : yu);
+        sxhs[o] = float(cx - xu) * cwx;
+        syhs[o] = float(cy - yu) * cwy;
+    }
     float phi = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
     auto pair = [&](float dx, float dy, float dz, float qs) {
         const float r2 = dx * dx + dy * dy + dz * dz;
@@ -2974,13 +2986,12 @@ __global__ void k_near_f32(KP kp) {
         }
         for (int zc = zl; zc <= zh; ++zc) {
             for (int oy = 0; oy < nyc; ++oy) {
-                const int yu = wrap3y ? cy - 1 + oy : oy;            // unwrapped neighbour row
-                const int yc = wrap3y ? wrap_index(yu, kp.ncy) : oy;
+                const int yc = ycs[oy];
+                const float syh = syhs[oy];
                 for (int ox = 0; ox < nxc; ++ox) {
-                    const int xu = wrap3x ? cx - 1 + ox : ox;
-                    const int xc = wrap3x ? wrap_index(xu, kp.ncx) : ox;
+                    const int xc = xcs[ox];
                     const int cell = cell_index(kp, xc, yc, zc);
-                    const float sxh = float(cx - xu) * cwx, syh = float(cy - yu) * cwy;
+                    const float sxh = sxhs[ox];
                     for (int q = kp.cell_start[cell]; q < kp.cell_start[cell + 1]; ++q) {
                         const float4 src = kp.sorted_rel[q];
                         float dx = t.x - src.x + sxh, dy = t.y - src.y + syh;
