@@ -312,15 +312,24 @@ __device__ __forceinline__ void last_pass(C* v, const C* tw, int j, int n16, int
 // global table: it is copied here while the first pass's loads are in
 // flight (that pass needs no twiddles, and the barrier after its writes
 // precedes the first use).
-template <bool QF, bool kSyncLoad = false, class C, class Load, class Store>
+// kPaired (row transforms, nseq even): the sequences come in pairs
+// (2 m, 2 m + 1) on neighbouring lanes, thread s taking
+// (q, j) = (2 (s div 2 n16) + s mod 2, (s div 2) mod n16), with sequences
+// n + n16 + 8 elements apart so that the two lanes of a pair use opposite
+// halves of the banks; the outputs stay in registers: store(q, j, act, v)
+// receives all 16 of a thread (output j + g n16 in v[g]), with no barrier
+// before it, and every thread calls it, so that it may exchange values
+// between the two lanes of a pair.
+template <bool QF, bool kSyncLoad = false, bool kPaired = false, class C, class Load, class Store>
 __device__ __forceinline__ void fft_pow2(C* buf, const C* tw, int n, int logn, int nseq, int dir, Load load,
                                          Store store, C* tw_fill = nullptr, const C* tw_src = nullptr) {
     const int l16 = logn - 4, n16 = 1 << l16;
     const int s = threadIdx.x;
     const bool act = s < (nseq << l16);
-    const int q = QF ? s % nseq : s >> l16;
-    const int j = QF ? s / nseq : s & (n16 - 1);
-    auto at = [&](int i) { return QF ? pad16(i * nseq + q) : q * (n + n16) + pad16(i); };
+    const int q = QF ? s % nseq : kPaired ? 2 * (s >> (l16 + 1)) + (s & 1) : s >> l16;
+    const int j = QF ? s / nseq : kPaired ? (s >> 1) & (n16 - 1) : s & (n16 - 1);
+    const int sstr = n + n16 + (kPaired ? 8 : 0);
+    auto at = [&](int i) { return QF ? pad16(i * nseq + q) : q * sstr + pad16(i); };
     const int a = (logn - 1) >> 2;            // radix-16 passes
     const int lrl = logn - 4 * a;             // log2 of the last radix
     C v[16];
@@ -361,10 +370,14 @@ __device__ __forceinline__ void fft_pow2(C* buf, const C* tw, int n, int logn, i
         else if (lrl == 3) last_pass<8>(v, tw, j, n16, dir);
         else last_pass<16>(v, tw, j, n16, dir);
     }
-    __syncthreads();
-    if (act) {
+    if constexpr (kPaired) {
+        store(q, j, act, v);
+    } else {
+        __syncthreads();
+        if (act) {
 #pragma unroll
-        for (int g = 0; g < 16; ++g) store(q, j + g * n16, v[g]);
+            for (int g = 0; g < 16; ++g) store(q, j + g * n16, v[g]);
+        }
     }
 }
 

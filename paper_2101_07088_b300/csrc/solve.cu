@@ -1003,7 +1003,7 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int) {
     using C = typename Prec<R>::C;
     using V4 = typename Prec<R>::V4;
     extern __shared__ __align__(16) unsigned char smraw[];
-    constexpr int logn = L, n = 1 << L, nxh = n / 2 + 1, np = n + (n >> 4);
+    constexpr int logn = L, n = 1 << L, nxh = n / 2 + 1, n16 = n >> 4;
     C* buf = reinterpret_cast<C*>(smraw);
     const C* tw = twx_of<R>(kp);
     const C* spec = static_cast<const C*>(kp.spec);
@@ -1050,16 +1050,29 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int) {
         }
         return z;
     };
-    auto store = [&](int q, int i, C v) { buf[q * np + pad16(i)] = v; };
-    fft_pow2<false>(buf, tw, n, logn, 2 * P, +1, load, store);
-    __syncthreads();
+    // the two sequences of a row sit on neighbouring lanes (w = lane parity)
+    // and hold the same outputs x = j + g n16: the w = 0 lane stores the even
+    // g, the w = 1 lane the odd g, each taking the other half from its
+    // partner by a shuffle, so the outputs need no second pass through
+    // shared memory
     const R s = R(kp.inv_nxny);
-    for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
-        const int p = t / n, x = t - p * n, row = r0 + p;
-        if ((skip >> p) & 1ull) continue;
-        const C u = buf[(2 * p) * np + pad16(x)], v = buf[(2 * p + 1) * np + pad16(x)];
-        fields[size_t(row) * n + x] = Prec<R>::v4(u.x * s, u.y * s, v.x * s, v.y * s);
-    }
+    const int wlanes = min(32, int(blockDim.x) - (int(threadIdx.x) & ~31));
+    const unsigned wmask = wlanes == 32 ? 0xffffffffu : (1u << wlanes) - 1u;
+    auto store = [&](int q, int j, bool act, C(&v)[16]) {
+        const int p = q >> 1, w = q & 1;
+        const bool keep = act && !((skip >> p) & 1ull);
+        V4* out = fields + size_t(r0 + p) * n + j;
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const C send = w ? v[2 * h] : v[2 * h + 1];
+            C recv;
+            recv.x = __shfl_xor_sync(wmask, send.x, 1);
+            recv.y = __shfl_xor_sync(wmask, send.y, 1);
+            const C u = w ? recv : v[2 * h], e = w ? v[2 * h + 1] : recv;
+            if (keep) out[(2 * h + w) * n16] = Prec<R>::v4(u.x * s, u.y * s, e.x * s, e.y * s);
+        }
+    };
+    fft_pow2<false, false, true>(buf, tw, n, logn, 2 * P, +1, load, store);
 }
 
 // The power-of-two kernels are compiled for each n = 2^L (32 <= n <= 4096),
@@ -3938,9 +3951,10 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
         const int myf = pow2(ny) ? maxthr(p2k(1, ny)) : 0, myi = pow2(ny) ? maxthr(p2k(2, ny)) : 0;
         if (pow2(nx)) {
             const int n16 = nx / 16;
-            const size_t seq = size_t(nx + n16) * csz;
+            // the inverse pairs its two sequences per row across lanes (8 elements more each)
+            const size_t seq = size_t(nx + n16) * csz, seq_inv = size_t(nx + n16 + 8) * csz;
             const int P = std::max(1, std::min(256, mxf) / n16), Pi = std::max(1, std::min(128, mxi) / (2 * n16));
-            const size_t fwd = P * seq, inv = 2 * Pi * seq;   // the twiddle table is read from global memory
+            const size_t fwd = P * seq, inv = 2 * Pi * seq_inv;   // the twiddle table is read from global memory
             if (fwd <= cap && inv <= cap && P * n16 <= mxf && 2 * Pi * n16 <= mxi) {
                 pl->p2x = 1;
                 pl->lognx = lg(nx);
@@ -4535,7 +4549,8 @@ bool apply_shape_t(dpslab_plan* pl, int which, int v) {
     if (p2) {
         const int n16 = n / 16;
         // x transforms read the global twiddle table, y transforms a shared copy
-        const size_t seq = size_t(n + n16) * csz, tw = which == 1 || which == 2 ? size_t(n) * csz : 0;
+        const size_t seq = size_t(n + n16 + (which == 3 ? 8 : 0)) * csz,
+                     tw = which == 1 || which == 2 ? size_t(n) * csz : 0;
         const int seqs = which == 3 ? 2 * v : v;         // the x inverse transforms two sequences per row
         thr = seqs * n16;
         sm = tw + seqs * seq;
