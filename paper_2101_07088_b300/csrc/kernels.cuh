@@ -144,8 +144,8 @@ struct KP {
     int* cell_fill;
     double4_32a* sorted;
     float4* sorted_rel;       // float offsets from the cell corner, and q (mixed near field)
-    IRec* irec;               // [n] interpolation windows by charge (mixed)
-    SrcF* srcs_tmp;           // [3n] sources of each charge before bucketing (mixed)
+    IRec* irec;               // [n] interpolation windows in cell-list order (mixed)
+    SrcF* srcs_tmp;           // [3n] sources of each charge before bucketing, same order (mixed)
     ColP* colp;               // [ny nxh] correction parameters per mode (tensor-core z transforms)
     double* zcol;             // [2 nz + 1] mixed: the k = 0 column from k_column_zero (y, y', gauge term)
     // J^T t0, J^T J^T t0, J^T tH, J^T J^T tH (J: Appendix-A integration,

@@ -530,14 +530,32 @@ __device__ __forceinline__ void axis_window(double x, double HE, double h, int& 
     d0 = float(double(lo) * h - x);
 }
 
-// One thread per charge: the interpolation window of the charge (irec[k]),
-// its spreading sources (the charge and its images, Eq. (ims)) as records
-// srcs_tmp[3k + s], and the bucket counts of every (tile, slab) block each
-// source touches.
+// Bucket counters shared by the lanes that call together: one atomic per
+// distinct bucket b among them, adding the number of lanes with that b.
+// agg_claim returns the lane's own slot (the counter's old value plus the
+// lane's rank among those lanes).
+__device__ __forceinline__ void agg_count(int* count, int b) {
+    const unsigned peers = __match_any_sync(__activemask(), b);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(count + b, __popc(peers));
+}
+__device__ __forceinline__ int agg_claim(int* fill, int b) {
+    const unsigned peers = __match_any_sync(__activemask(), b);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int old = 0;
+    if (lane == leader) old = atomicAdd(fill + b, __popc(peers));
+    return __shfl_sync(peers, old, leader) + __popc(peers & ((1u << lane) - 1u));
+}
+
+// One thread per charge, in cell-list order when there is one (slot i holds
+// charge sorted_idx[i]; neighbouring threads then touch mostly the same
+// buckets and share their atomics): the interpolation window of the charge
+// (irec[i]), its spreading sources (the charge and its images, Eq. (ims)) as
+// records srcs_tmp[3i + s], and the bucket counts of every (tile, slab)
+// block each source touches.
 __global__ void k_sources_f(KP kp) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= kp.n) return;
-    const double4_32a p = kp.part[k];
+    const double4_32a p = kp.near_on ? kp.sorted[k] : kp.part[k];
     SrcF r;
     int sx, sy;
     axis_window(p.x, kp.HE, kp.hx, r.xlo, sx, r.d0x);
@@ -571,7 +589,7 @@ __global__ void k_sources_f(KP kp) {
                        (1u << 31);
                 for (int sl = j0 / kSlabM; sl <= j1 / kSlabM; ++sl)
                     for (int a = 0; a < nty; ++a)
-                        for (int c = 0; c < ntx; ++c) atomicAdd(&kp.tile_count[sl * kp.ntiles + ty[a] * kp.ntx + tx[c]], 1);
+                        for (int c = 0; c < ntx; ++c) agg_count(kp.tile_count, sl * kp.ntiles + ty[a] * kp.ntx + tx[c]);
             }
         }
         r.pack = pack;
@@ -604,7 +622,7 @@ __global__ void k_scatter_sources_f(KP kp) {
                         at[u] = -1;
                         if (a < nty && c < ntx) {
                             const int b = sl * kp.ntiles + ty[a] * kp.ntx + tx[c];
-                            at[u] = kp.tile_start[b] + atomicAdd(&kp.tile_fill[b], 1);
+                            at[u] = kp.tile_start[b] + agg_claim(kp.tile_fill, b);
                         }
                     }
 #pragma unroll
@@ -2783,7 +2801,7 @@ __global__ void __launch_bounds__(32 * kMaxInterpWarps) k_interp_f32(KP kp) {
     const int slot = blockIdx.x * (blockDim.x >> 5) + w;
     if (slot >= kp.n) return;
     const int k = kp.near_on ? kp.sorted_idx[slot] : slot;
-    const IRec r = kp.irec[k];
+    const IRec r = kp.irec[slot];
     const int sx = r.sx, sy = r.sy, j0 = r.j0, sz = r.j1 - r.j0 + 1;
     const float ig2 = kp.f.ig2, s1 = kp.f.s1norm;
     for (int i = lane; i < sx; i += 32) {
