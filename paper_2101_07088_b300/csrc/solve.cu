@@ -2556,6 +2556,13 @@ __global__ void __launch_bounds__(256) k_o_coeffs(KP kp) {
     }
 }
 
+// 2^x by the PTX base-2 exponential (ex2.approx.ftz.f32)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
     float* base = static_cast<float*>(kp.spec);
     const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
@@ -2572,6 +2579,8 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
     auto epi = [&](int plane, int row, int c0, float* v, int w) {
         const float z = kp.zn32[row];
         const bool zin = z >= -HE && z <= H + HE;
+        // the exponents' row factors in base 2: e^{-kz} = 2^{k lz}
+        const float lz = -z * 1.44269504088896341f, lhz = -(H - z) * 1.44269504088896341f;
 #pragma unroll
         for (int i = 0; i < 32; i += 2) {
             if (i >= w) break;
@@ -2579,16 +2588,18 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
             float re = v[i], im = v[i + 1];
             if (plane == 1) { re *= sz; im *= sz; }
             const ColP cp = s_cp[col - s_c0 / 2];
-            // without branches (the lanes are rows, which would diverge): the
-            // exponents are clamped at 88, where both terms are below 1e-38
-            // of the correction's amplitude, and modes without a correction
-            // or nodes outside [-H_E, H + H_E] are masked to exactly zero
-            {
-                const float m = (cp.corr && zin) ? cp.iden : 0.f;
-                // the fast exponential: its error grows as |x| 2^-24 of the
-                // result, and amplitude x e^{-x} <= 0.37 amplitude, so each
-                // term is within 2e-8 of its amplitude (below FP32 rounding)
-                const float e1 = __expf(-fminf(cp.k * z, 88.f)), e3 = __expf(-fminf(cp.k * (H - z), 88.f));
+            // a warp's lanes are rows of one column, so the test of the mode
+            // is uniform over the warp (modes without a correction add
+            // nothing); within a mode no branches (rows would diverge): the
+            // exponents are clamped at -127 (e^{-88}), where both terms are
+            // below 1e-38 of the correction's amplitude, and nodes outside
+            // [-H_E, H + H_E] are masked to exactly zero
+            if (cp.corr) {
+                const float m = zin ? cp.iden : 0.f;
+                // the hardware base-2 exponential: its error grows as |x| 2^-24
+                // of the result, and amplitude x e^{-x} <= 0.37 amplitude, so
+                // each term is within 2e-8 of its amplitude (below FP32 rounding)
+                const float e1 = ex2_approx(fmaxf(cp.k * lz, -127.f)), e3 = ex2_approx(fmaxf(cp.k * lhz, -127.f));
                 const float e2 = e3 * cp.ekH, e4 = e1 * cp.ekH;
                 const float f = plane == 0 ? m : cp.k * m;
                 const float a = plane == 0 ? -(e1 - Gt * e2) * f : (e1 + Gt * e2) * f;
