@@ -2568,12 +2568,24 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
     const size_t ld = 2 * size_t(kp.ny) * kp.nxh, pstride = size_t(kp.nz) * ld;
     const float Gb = kp.f.Gb, Gt = kp.f.Gt, H = kp.f.H, HE = kp.f.HE, sz = kp.f.sz;
     const float Ai = float(kp.scal[1]);
-    // the tile's 64 modes' correction parameters, staged once per tile
-    __shared__ ColP s_cp[kZN / 2];
+    // the tile's 64 modes' correction, staged once per tile and plane as the
+    // factors of e1 = e^{-kz} and e3 = e^{k(z-H)}: with f = iden (plane 0) or
+    // k iden (plane 1), the correction is e1 A + e3 B, A = -/+ f (P + Gb ekH Q)
+    // and B = f (Gt ekH P + Q) (the two terms of each of P and Q gathered);
+    // s_kc: k, and whether the mode has a correction
+    __shared__ float4 s_ab[kZN / 2];        // (A.re, A.im, B.re, B.im)
+    __shared__ float2 s_kc[kZN / 2];
     int s_c0 = 0;
-    auto prep = [&](int, int c0) {
+    auto prep = [&](int plane, int c0) {
         const int i = threadIdx.x, col = c0 / 2 + i;
-        if (i < kZN / 2 && col < kp.ny * kp.nxh) s_cp[i] = kp.colp[col];
+        if (i < kZN / 2 && col < kp.ny * kp.nxh) {
+            const ColP cp = kp.colp[col];
+            const float f = plane == 0 ? cp.iden : cp.k * cp.iden, sa = plane == 0 ? -f : f;
+            const float2 A = make_float2(sa * (cp.P.x + Gb * cp.ekH * cp.Q.x), sa * (cp.P.y + Gb * cp.ekH * cp.Q.y));
+            const float2 B = make_float2(f * (Gt * cp.ekH * cp.P.x + cp.Q.x), f * (Gt * cp.ekH * cp.P.y + cp.Q.y));
+            s_ab[i] = make_float4(A.x, A.y, B.x, B.y);
+            s_kc[i] = make_float2(cp.k, cp.corr ? 1.f : 0.f);
+        }
         s_c0 = c0;
     };
     auto epi = [&](int plane, int row, int c0, float* v, int w) {
@@ -2584,28 +2596,25 @@ __global__ void __launch_bounds__(kZThreads, 1) k_zgemm_inv(KP kp) {
 #pragma unroll
         for (int i = 0; i < 32; i += 2) {
             if (i >= w) break;
-            const int col = (c0 + i) >> 1;
+            const int col = (c0 + i) >> 1, m = col - s_c0 / 2;
             float re = v[i], im = v[i + 1];
             if (plane == 1) { re *= sz; im *= sz; }
-            const ColP cp = s_cp[col - s_c0 / 2];
+            const float2 kc = s_kc[m];
             // a warp's lanes are rows of one column, so the test of the mode
             // is uniform over the warp (modes without a correction add
             // nothing); within a mode no branches (rows would diverge): the
             // exponents are clamped at -127 (e^{-88}), where both terms are
             // below 1e-38 of the correction's amplitude, and nodes outside
             // [-H_E, H + H_E] are masked to exactly zero
-            if (cp.corr) {
-                const float m = zin ? cp.iden : 0.f;
+            if (kc.y != 0.f) {
                 // the hardware base-2 exponential: its error grows as |x| 2^-24
                 // of the result, and amplitude x e^{-x} <= 0.37 amplitude, so
                 // each term is within 2e-8 of its amplitude (below FP32 rounding)
-                const float e1 = ex2_approx(fmaxf(cp.k * lz, -127.f)), e3 = ex2_approx(fmaxf(cp.k * lhz, -127.f));
-                const float e2 = e3 * cp.ekH, e4 = e1 * cp.ekH;
-                const float f = plane == 0 ? m : cp.k * m;
-                const float a = plane == 0 ? -(e1 - Gt * e2) * f : (e1 + Gt * e2) * f;
-                const float b = plane == 0 ? (e3 - Gb * e4) * f : (e3 + Gb * e4) * f;
-                re += cp.P.x * a + cp.Q.x * b;
-                im += cp.P.y * a + cp.Q.y * b;
+                const float e1 = zin ? ex2_approx(fmaxf(kc.x * lz, -127.f)) : 0.f;
+                const float e3 = zin ? ex2_approx(fmaxf(kc.x * lhz, -127.f)) : 0.f;
+                const float4 ab = s_ab[m];
+                re += e1 * ab.x + e3 * ab.z;
+                im += e1 * ab.y + e3 * ab.w;
             }
             if (col == 0) re += plane == 0 ? Ai * z : Ai;
             v[i] = re;
