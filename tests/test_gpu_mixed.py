@@ -82,6 +82,15 @@ def test_mixed_small_ragged_and_paper_rule():
            mixed_energy_tol(P, 40))
 
 
+def test_mixed_without_split():
+    # xi = inf: no near field, so no cell list; the sources and the
+    # interpolation windows then follow the charges' own order
+    P = oracle_params(16.0, 16.0, 16.0, 1.0, 1e-4, 32, 32, nz=48, eps_b=1 / 80, eps_t=1 / 20, xi=math.inf)
+    pos, q = synth.electrolyte(40, 16.0, 16.0, 1.0, 15.0, seed=7)
+    _check(osolver.solve(pos, q, P), gpu_solve(plan_for(P, 40, precision=dpslab.MIXED), pos, q), "no-split",
+           mixed_energy_tol(P, 40))
+
+
 @pytest.mark.parametrize("case", ["ragged", "c2"])
 def test_interpolation_stage_against_oracle_quadrature(case):
     """The interpolation stage of the mixed form on its own (Sec. 5.2.2
