@@ -1045,27 +1045,22 @@ __global__ void k_fftx_inv_p2(KP kp, int P, int) {
         const int kk = hi ? n - k : k;
         const bool edge = kk == 0 || kk == n / 2;
         const size_t g = size_t(row) * nxh + kk;
-        if (w == 0) {
-            C a = spec[g];
-            if (edge) a.y = R(0);
-            const R kxd = edge ? R(0) : (sizeof(R) == sizeof(double) ? R(kTwoPi * kk / kp.Lx) : kxs * R(kk));
-            C r;
-            r.x = kxd * a.y;                     // -i k_x psi
-            r.y = -kxd * a.x;
-            if (hi) { a = cconj(a); r = cconj(r); }
-            z.x = a.x - r.y;                     // phi + i E_x
-            z.y = a.y + r.x;
-        } else {
-            C b = specB[g];
-            C c = spec[S + g];
-            if (edge) { b.y = R(0); c.y = R(0); }
-            C mc;
-            mc.x = -c.x;                         // E_z = -dpsi/dz
-            mc.y = -c.y;
-            if (hi) { b = cconj(b); mc = cconj(mc); }
-            z.x = b.x - mc.y;                    // E_y + i E_z
-            z.y = b.y + mc.x;
-        }
+        // the two lanes of a row pair take the same steps (no divergence):
+        // w = 0: a = psi, s = -i k_x psi, z = phi + i E_x;
+        // w = 1: a = -i k_y psi, s = -dpsi/dz, z = E_y + i E_z
+        C a = (w ? specB : spec)[g];
+        C c;
+        c.x = R(0);
+        c.y = R(0);
+        if (w) c = spec[S + g];
+        if (edge) { a.y = R(0); c.y = R(0); }
+        const R kxd = edge ? R(0) : (sizeof(R) == sizeof(double) ? R(kTwoPi * kk / kp.Lx) : kxs * R(kk));
+        C sv;
+        sv.x = w ? -c.x : kxd * a.y;
+        sv.y = w ? -c.y : -kxd * a.x;
+        if (hi) { a = cconj(a); sv = cconj(sv); }
+        z.x = a.x - sv.y;
+        z.y = a.y + sv.x;
         return z;
     };
     // the two sequences of a row sit on neighbouring lanes (w = lane parity)
