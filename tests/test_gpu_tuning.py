@@ -94,3 +94,29 @@ def test_kernel_knobs_keep_results(prec):
     plan.set_tuning(k0[:4])
     assert plan.tuning() == k0
     plan.close()
+
+
+@pytest.mark.parametrize("prec", [dpslab.FP64, dpslab.MIXED], ids=["fp64", "mixed"])
+def test_fft_knobs_on_ragged_rows_keep_results(prec):
+    """Knobs 0-3 (rows or columns per block of the four power-of-two xy
+    transforms) at 1, 2 and 4 on a 64 x 45 x 37 grid: 1665 rows, so the last
+    block of 2 or 4 rows is partial (the inverse x transform pairs each
+    row's two sequences on neighbouring lanes), and 33 columns along y; the
+    solve is unchanged."""
+    pos, q = synth.electrolyte(300, 32.0, 22.5, 1.0, 19.0, seed=41)
+    p = dict(Lx=32.0, Ly=22.5, H=20.0, gw=1.0, tol=1e-4, nx=64, ny=45, nz=37, eps_b=1 / 80, eps_t=0.5, r_cut=4.0)
+    plan = dpslab.Plan(dpslab.make_params(precision=prec, **p), len(q))
+    pt = torch.tensor(pos, dtype=torch.float64, device="cuda")
+    qt = torch.tensor(q, dtype=torch.float64, device="cuda")
+    k0 = plan.tuning()
+    U0, f0 = _solve(plan, pt, qt)
+    tol = 1e-12 if prec == dpslab.FP64 else 5e-6
+    for which in range(4):
+        for v in (1, 2, 4):
+            k = list(k0)
+            k[which] = v
+            plan.set_tuning(k)
+            U1, f1 = _solve(plan, pt, qt)
+            assert abs(U1 - U0) <= tol * abs(U0) and rel_l2(f1, f0) <= tol, (which, v)
+    plan.set_tuning(k0)
+    plan.close()
