@@ -1700,7 +1700,7 @@ constexpr int kTcTables = 15;   // j2l j2d j2u u1 u2 v1 v2 t0 tH wg hinv jt0 jjt
 __host__ __device__ inline int tc_stride(int N) { return N | 1; }   // odd: rows of modes fall in distinct banks
 
 template <int W, int R>
-__device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
+__device__ __forceinline__ void column_tc_body(const KP& kp, const int bid, const bool load_tables = true) {
     constexpr int MB = 8 * W;                 // modes per block
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = kp.nz, NP = tc_stride(N);
@@ -1735,9 +1735,10 @@ __device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
         s_corr[c] = t.z != 0.0;
         s_gauge[c] = 0.0;
     }
-    {
-        // the tables into shared memory: every load of a batch of 8 is issued
-        // before the first store (one round trip per batch)
+    if (load_tables) {
+        // the tables into shared memory (once per block: a persistent block
+        // keeps them for all its blocks of modes); every load of a batch of 8
+        // is issued before the first store (one round trip per batch)
         const float* src[kTcTables] = {kp.j2l32, kp.j2d32, kp.j2u32, kp.u132, kp.u232, kp.v132, kp.v232, kp.t032,
                                        kp.tH32, kp.wg32, kp.hinv32, kp.jt0_32, kp.jjt0_32, kp.jtH_32, kp.jjtH_32};
         for (int t0b = tid; t0b < kTcTables * N; t0b += 8 * bs) {
@@ -2041,7 +2042,14 @@ __device__ __forceinline__ void column_tc_body(const KP& kp, const int bid) {
 }
 
 template <int W, int R>
-__global__ void __launch_bounds__(64 * W, 2) k_column_tc(KP kp) { column_tc_body<W, R>(kp, blockIdx.x); }
+// persistent: as many blocks as fit on the device, each taking blocks of
+// modes bid, bid + gridDim.x, ... and loading the tables once
+__global__ void __launch_bounds__(64 * W, 2) k_column_tc(KP kp) {
+    for (int bid = blockIdx.x; bid < kp.n_col_blocks; bid += gridDim.x) {
+        column_tc_body<W, R>(kp, bid, bid == int(blockIdx.x));
+        __syncthreads();
+    }
+}
 template <int W, int R>
 __global__ void __launch_bounds__(64 * W, 2) k_column_tc_batch(const __grid_constant__ ColBatch b) {
     const int s = batch_system(b.starts, b.nsys, blockIdx.x);
@@ -3376,6 +3384,7 @@ struct dpslab_plan {
     int p2x = 0, p2y = 0, lognx = 0, logny = 0;        // power-of-two FFT kernels in x, y
     bool ztensor = false;                              // z transforms as tensor-core GEMMs
     int zgrid = 0;                                     // persistent CTAs of the z GEMMs
+    int col_grid = 0;                                  // persistent blocks of the tensor-core form's column kernel
     int thr_x_fwd = 256, thr_x_inv = 256, thr_y_fwd = 256, thr_y_inv = 256;
     size_t sm_fftx_fwd = 0, sm_ffty_fwd = 0, sm_ffty_inv = 0, sm_fftx_inv = 0, sm_col = 0, sm_interp = 0, sm_spread = 0;
     KP kp{};
@@ -3471,6 +3480,21 @@ ColKernel column_mixed_kernel(int cb) { return cb == 4 ? k_column_mixed<4> : k_c
 ColKernel column_tc_kernel(int W, int R) {
     if (R == 4) return W == 1 ? k_column_tc<1, 4> : W == 2 ? k_column_tc<2, 4> : k_column_tc<4, 4>;
     return W == 1 ? k_column_tc<1, 8> : W == 2 ? k_column_tc<2, 8> : k_column_tc<4, 8>;
+}
+// the persistent grid of the tensor-core form's column kernel: its blocks
+// resident on all SMs at once (at most one per block of modes); 0 (one block
+// per block of modes) for the other forms or when the query fails
+void col_grid_update(dpslab_plan* pl) {
+    pl->col_grid = 0;
+    if (!pl->ztensor) return;
+    int nsm = 0, per = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per, reinterpret_cast<const void*>(column_tc_kernel(pl->col_cb / 8, pl->tc_r)), 8 * pl->col_cb,
+            pl->sm_col) != cudaSuccess ||
+        per < 1 || nsm < 1)
+        return;
+    pl->col_grid = std::min(pl->kp.n_col_blocks, per * nsm);
 }
 using ColBatchKernel = void (*)(ColBatch);
 ColBatchKernel column_tc_batch_kernel(int W, int R) {
@@ -4058,6 +4082,7 @@ int plan_create_impl(const dpslab_params* p, int64_t max_n, int mode, dpslab_pla
             for (int cb = kMinColBlock; cb <= kColBlockM; cb *= 2)
                 raise_smem(reinterpret_cast<const void*>(column_mixed_kernel(cb)), col_smem(pl, cb));
         }
+        col_grid_update(pl);
         raise_smem(reinterpret_cast<const void*>(k_interp_f32),
                    size_t(kMaxInterpWarps) * (2 * kMaxSupport + kMaxNz) * sizeof(float));
     } else {
@@ -4555,6 +4580,7 @@ bool apply_kernel_knob(dpslab_plan* pl, int which, int v) {
         pl->col_cb = v;
         pl->sm_col = sm;
         pl->kp.n_col_blocks = (M + v - 1) / v;
+        col_grid_update(pl);
         return true;
     }
     if (v != 1 && !(mixed && (v == 2 || v == 4))) return false;
@@ -4818,7 +4844,7 @@ int enqueue(dpslab_plan* pl, int64_t n64, const double* pos, const double* q, do
         }
         if (column) {
         if (pl->ztensor)
-            LAUNCH(column_tc_kernel(pl->col_cb / 8, pl->tc_r)<<<kp.n_col_blocks, 8 * pl->col_cb, pl->sm_col, st>>>(kp));
+            LAUNCH(column_tc_kernel(pl->col_cb / 8, pl->tc_r)<<<pl->col_grid > 0 ? pl->col_grid : kp.n_col_blocks, 8 * pl->col_cb, pl->sm_col, st>>>(kp));
         else
             LAUNCH(column_mixed_kernel(pl->col_cb)<<<kp.n_col_blocks, 32 * pl->col_cb, pl->sm_col, st>>>(kp));
         }
