@@ -1700,7 +1700,8 @@ constexpr int kTcTables = 15;   // j2l j2d j2u u1 u2 v1 v2 t0 tH wg hinv jt0 jjt
 __host__ __device__ inline int tc_stride(int N) { return N | 1; }   // odd: rows of modes fall in distinct banks
 
 template <int W, int R>
-__device__ __forceinline__ void column_tc_body(const KP& kp, const int bid, const bool load_tables = true) {
+__device__ __forceinline__ void column_tc_body(const KP& kp, const int bid, const bool load_tables = true,
+                                               const int next_bid = -1) {
     constexpr int MB = 8 * W;                 // modes per block
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = kp.nz, NP = tc_stride(N);
@@ -1774,6 +1775,16 @@ __device__ __forceinline__ void column_tc_body(const KP& kp, const int bid, cons
         for (int u = 0; u < kLd; ++u) {
             const int t = t0 + u * bs, n = t / MB, c = t - n * MB;
             if (t < N * MB) F[c * NP + n] = make_float4(vi[u].x * scale, vi[u].y * scale, vo[u].x * scale, vo[u].y * scale);
+        }
+    }
+    // the next block of modes of a persistent block: its coefficient rows
+    // (both spectra, 128-byte lines) into L2 while this block computes
+    if (next_bid >= 0) {
+        constexpr int kLines = (MB * 8 + 127) / 128;
+        const int ncol0 = next_bid * MB;
+        for (int i = tid; i < 2 * N * kLines; i += bs) {
+            const int row = i / kLines, c = ncol0 + (i - row * kLines) * 16;
+            if (c < M) asm volatile("prefetch.global.L2 [%0];" ::"l"(sp + size_t(row) * M + c));
         }
     }
     // 1b. rho_o's coefficients from its node values at the pairs (a, m - a)
@@ -2046,7 +2057,8 @@ template <int W, int R>
 // modes bid, bid + gridDim.x, ... and loading the tables once
 __global__ void __launch_bounds__(64 * W, 2) k_column_tc(KP kp) {
     for (int bid = blockIdx.x; bid < kp.n_col_blocks; bid += gridDim.x) {
-        column_tc_body<W, R>(kp, bid, bid == int(blockIdx.x));
+        const int next = bid + int(gridDim.x);
+        column_tc_body<W, R>(kp, bid, bid == int(blockIdx.x), next < kp.n_col_blocks ? next : -1);
         __syncthreads();
     }
 }
